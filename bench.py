@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark: mixed-precision tiled Cholesky log-likelihood on GB300.
+
+One step = the whole hot path on one batch of synthetic input: Morton order
+of the locations, Matérn tile generation into the per-tile formats, the
+tiled Cholesky (FP64 POTRF/TRSM, lower-precision SYRK/GEMM), forward solve,
+FP64 iterative refinement, log-determinant and log-likelihood.
+
+Workload (default): n = 16384 Morton-ordered uniform points in [0,1]^2,
+tile 512, Matérn nu = 3/2, range 0.05, variance 1, nugget 1e-4, one RHS
+z ~ N(0,1); precision map: FP64 diagonal, FP32 for |i-j| <= 2, BF16 beyond
+where the tile's norm allows it (norm guard eps = 1e-6; the plain band map
+loses positive definiteness on this kernel -- its status is reported).
+
+Metric: Cholesky TFLOP/s (useful flops n^3/3 + n^2/2 + n/6 per step, charged
+whatever the precision), whole job over all ranks.  `--impl reference` times
+the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mpinputs as I  # noqa: E402
+
+METRIC = "Cholesky TFLOP/s vs all-FP64 GPU at matched loglik error; solves/s, p99 latency"
+UNIT = "TFLOP/s"
+WORKLOAD = "mixed_bf16_n16384_b512"
+
+
+def chol_flops(n: int) -> float:
+    return n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
+
+
+def oracle_step_flops(nt: int, b: int, k: int) -> float:
+    m = nt - k - 1
+    return b ** 3 / 3.0 + m * b ** 3 + m * b * b * (b + 1) + m * (m - 1) / 2 * 2.0 * b ** 3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--eps", type=float, default=1e-6)
+    p.add_argument("--cpu-steps", type=int, default=3, help="oracle factorisation steps sampled")
+    p.add_argument("--no-fp64-path", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_cores():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def oracle_sample(cfg, pmap, steps: int, repeats: int = 1, warmup: int = 0):
+    """Times the first `steps` steps of the oracle's tiled factorisation on
+    the workload (generation and tile rounding excluded).  Returns a list of
+    (seconds, flops) per repeat."""
+    from oracle import chol as OC
+    from oracle import matern as OM
+    n, b = cfg["n"], cfg["b"]
+    locs = I.points(n, cfg["seed"])
+    if cfg["morton"]:
+        locs, _ = OM.morton_order(locs)
+    S = OM.covariance(locs, cfg["nu"], cfg["range"], cfg["sigma2"], cfg["nugget"])
+    nt = -(-n // b)
+    base = OC.tiled_from_dense(S, b, pmap)
+    del S
+    out = []
+    for r in range(warmup + repeats):
+        T = OC.TiledMatrix(n=base.n, b=b, nt=nt, pmap=base.pmap,
+                           tiles={k: OC.Tile(v.codes.copy(), v.fmt, v.scale)
+                                  for k, v in base.tiles.items()})
+        t0 = time.perf_counter()
+        for k in range(steps):
+            OC.step(T, k)
+        dt = time.perf_counter() - t0
+        if r >= warmup:
+            out.append((dt, sum(oracle_step_flops(nt, b, k) for k in range(steps))))
+    return out
+
+
+def make_map(ctx, cfg, dsorted, eps):
+    n, b = cfg["n"], cfg["b"]
+    nt = -(-n // b)
+    spec = cfg["map"]
+    if spec[0] == "uniform":
+        return I.uniform_map(nt, spec[1]), "uniform"
+    _, diag, near, far, band = spec
+    norms = ctx.tile_norms(n, b, dsorted, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+    m = ctx.map_guarded(norms.cpu().numpy(), band, near, far, eps)
+    return m, f"band{band}+guard(eps={eps:g})"
+
+
+def reference_arm(args, cfg):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (the map planner runs on the GPU when one is present)
+    from oracle import chol as OC
+    from oracle import matern as OM
+    n, b = cfg["n"], cfg["b"]
+    nt = -(-n // b)
+    locs = I.points(n, cfg["seed"])
+    if cfg["morton"]:
+        locs, _ = OM.morton_order(locs)
+    spec = cfg["map"]
+    if spec[0] == "uniform":
+        pmap = I.uniform_map(nt, spec[1])
+    else:
+        S = OM.covariance(locs, cfg["nu"], cfg["range"], cfg["sigma2"], cfg["nugget"])
+        pmap = OC.guarded_map(OC.tile_norms(S, b), spec[4], spec[2], spec[3], args.eps)
+        del S
+    steps = max(1, min(args.cpu_steps, nt))
+    res = oracle_sample(cfg, pmap, steps, repeats=args.steps, warmup=args.warmup)
+    secs = sum(r[0] for r in res)
+    fl = sum(r[1] for r in res)
+    value = fl / secs / 1e12
+    sample = f"first {steps} of {nt} steps of the oracle tiled factorisation per timed step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / len(res) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n": n, "b": b, "map": "same as ours"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def morton_launches(n: int) -> int:
+    n2 = 1024
+    while n2 < n:
+        n2 <<= 1
+    c = 3   # keys, first local sort, gather
+    k = 2048
+    while k <= n2:
+        j = k >> 1
+        while j >= 1024:
+            c += 1
+            j >>= 1
+        c += 1
+        k <<= 1
+    return c
+
+
+def ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+    from paper_2406_02701_gb300 import mpchol
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    n, b, nrhs, refine = cfg["n"], cfg["b"], cfg["nrhs"], cfg["refine"]
+    nt = -(-n // b)
+    ctx = mpchol.Context(local)
+    # replicas: every rank evaluates its own independent likelihood
+    locs_h = torch.from_numpy(I.points(n, cfg["seed"] + 100 * rank)).pin_memory()
+    z_h = torch.from_numpy(np.ascontiguousarray(I.rhs(n, nrhs, cfg["seed"] + 100 * rank).T)).pin_memory()
+    ll_h = torch.empty(nrhs, dtype=torch.float64).pin_memory()
+    dl = locs_h.to(dev)
+    zt = z_h.to(dev)
+    stream = torch.cuda.current_stream()
+    dsorted, dperm = ctx.morton_order(dl)
+    if not cfg["morton"]:
+        dsorted = dl.clone()
+    torch.cuda.synchronize()
+    pmap, map_name = make_map(ctx, cfg, dsorted, args.eps)
+    counts = {int(k): int(v) for k, v in zip(*np.unique(pmap[np.tril_indices(nt)], return_counts=True))}
+
+    # status of the plain band map on this workload (untimed)
+    band_status = None
+    if cfg["map"][0] == "band" and rank == 0:
+        Tb = mpchol.TiledMatrix(ctx, n, b, I.make_map(cfg["map"], nt))
+        Tb.generate(dsorted, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+        info, _ = Tb.chol()
+        torch.cuda.synchronize()
+        band_status = {"map": "band (no guard)", "info": int(info.item())}
+        Tb.close()
+        del Tb
+
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=refine > 0)
+    ll = torch.empty(nrhs, dtype=torch.float64, device=dev)
+    quad = torch.empty(nrhs, dtype=torch.float64, device=dev)
+    iters = torch.empty(nrhs, dtype=torch.int32, device=dev)
+    sorted_buf = torch.empty_like(dl)
+    perm_buf = torch.empty(n, dtype=torch.int64, device=dev)
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    logdet = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def step(src):
+        if cfg["morton"]:
+            ctx.check(ctx.lib.mp_morton_order(ctx.h, n, mpchol._ptr(src), mpchol._ptr(sorted_buf),
+                                              mpchol._ptr(perm_buf), mpchol._stream(None)))
+            g = sorted_buf
+        else:
+            g = src
+        T.generate(g, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+        ctx.check(ctx.lib.mp_chol(T.h, mpchol._ptr(info), mpchol._ptr(logdet)))
+        T.loglik(zt, refine_iters=refine, ll=ll, quad=quad, iters=iters)
+
+    for _ in range(args.warmup):
+        step(dl)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(dl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    # e2e: host buffers in, result out, every step
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(args.steps):
+        dl.copy_(locs_h, non_blocking=True)
+        zt.copy_(z_h, non_blocking=True)
+        step(dl)
+        ll_h.copy_(ll, non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_e2e = ee0.elapsed_time(ee1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = t.tolist()
+    F = chol_flops(n)
+    value = ws * F / (ms * 1e-3) / 1e12
+    value_e2e = ws * F / (ms_e2e * 1e-3) / 1e12
+    stats = T.stats()
+    launches_per_step = (morton_launches(n) if cfg["morton"] else 0) + stats["generate"] + \
+        stats["chol"] + 1 + stats["loglik"]
+    ll_mixed = ll.cpu().numpy().copy()
+    iters_mixed = iters.cpu().numpy().copy()
+    info_mixed = int(info.item())
+    logdet_mixed = float(logdet.item())
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+        return
+
+    # kernel breakdown (one instrumented factorisation, CUDA events on the stream)
+    prof = T.profile()
+    chol_ms = sum(v["ms"] for v in prof.values())
+    peak64 = ctx.fp64_peak()
+    tr = prof["panel_trsm"]
+    achieved = tr["flops"] / (tr["ms"] * 1e-3) / 1e12 if tr["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_panel_trsm (FP64 DFMA)", "achieved": achieved,
+                "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64 if peak64 else None,
+                "peak_source": "DFMA loop probe measured in this run (mp_probe_fp64_peak)",
+                "traffic": None, "share_of_chol": tr["ms"] / chol_ms if chol_ms else None}
+    breakdown = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                     "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] > 0 and v["flops"] > 0 else None}
+                 for k, v in prof.items() if v["launches"]}
+
+    # the all-FP64 GPU path on the same workload (speedup and error reference)
+    fp64 = None
+    if not args.no_fp64_path:
+        del T
+        T64 = mpchol.TiledMatrix(ctx, n, b, None, keep_sigma=False)
+        g = sorted_buf if cfg["morton"] else dl
+        T64.generate(g, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+        info64 = torch.zeros(1, dtype=torch.int64, device=dev)
+        ld64 = torch.zeros(1, dtype=torch.float64, device=dev)
+        ctx.check(ctx.lib.mp_chol(T64.h, mpchol._ptr(info64), mpchol._ptr(ld64)))  # warm-up
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        T64.generate(g, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+        f0.record(stream)
+        ctx.check(ctx.lib.mp_chol(T64.h, mpchol._ptr(info64), mpchol._ptr(ld64)))
+        f1.record(stream)
+        ll64, _, _ = T64.loglik(zt, refine_iters=0)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        ll64 = ll64.cpu().numpy()
+        fp64 = {"chol_ms": ms64, "tflops": F / (ms64 * 1e-3) / 1e12, "info": int(info64.item()),
+                "speedup_chol_only": ms64 / chol_ms if chol_ms else None,
+                "speedup_step": ms64 / ms,
+                "loglik_rel_err_mixed_vs_fp64": (np.abs(ll_mixed - ll64) / np.abs(ll64)).tolist()}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        steps = max(1, min(args.cpu_steps, nt))
+        res = oracle_sample(cfg, pmap, steps)
+        secs, fl = res[0]
+        cpu = {"value": fl / secs / 1e12, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {steps} of {nt} tiled-factorisation steps of the oracle on the "
+                         f"same workload and map ({secs:.1f} s; generation excluded)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "b": b, "nu": cfg["nu"],
+                   "range": cfg["range"], "nugget": cfg["nugget"], "nrhs": nrhs,
+                   "refine_iters_max": refine, "morton": cfg["morton"], "map": map_name,
+                   "tiles_per_format": {I.DTYPE_NAMES[k]: v for k, v in counts.items()},
+                   "l2": "inputs larger than L2 (tiles + float64 Sigma copy > 1 GB)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": int(locs_h.numel() * 8 + z_h.numel() * 8),
+                "d2h_bytes_per_step": int(ll_h.numel() * 8), "ms_per_step": ms_e2e},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "result": {"info": info_mixed, "loglik": ll_mixed.tolist(), "logdet": logdet_mixed,
+                   "refine_iters": iters_mixed.tolist(), "plain_band_map": band_status},
+        "fp64_path": fp64,
+        "chol_breakdown_ms": breakdown,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    cfg = dict(I.CONFIGS[args.workload])
+    if args.impl == "reference":
+        reference_arm(args, cfg)
+    else:
+        ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,293 @@
+/*
+ * mpchol.h -- C ABI of the mixed-precision tiled Cholesky log-likelihood
+ * library for NVIDIA GB300 (sm_103a).
+ *
+ * The calls follow the operations of the MPCR paper (arXiv 2406.02701):
+ * a matrix object in a chosen precision (Sec. 4.1, `as.MPCR` with its
+ * precision argument), `chol` (Sec. 6.2), `forwardsolve` / `backsolve`
+ * (Sec. 5 and 6.2), `%*%` / `crossprod` (Sec. 5), `log(diag(U))` summed
+ * into the log-determinant and the negative log-likelihood recipe (Sec. 6.2),
+ * and the tiled multi-precision extension named as future work (Sec. 7):
+ * every tile of the matrix carries its own precision.
+ *
+ * Conventions shared by every call
+ *   - Pointers named d_* are DEVICE pointers (cudaMalloc / torch tensors on
+ *     the library's device); they are borrowed, never freed by the library.
+ *     Host pointers are named h_* or are plain structs/arrays.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.  Every call that takes or owns a stream is
+ *     asynchronous on it: results in device memory are valid after the
+ *     stream is synchronised.  Host-visible results are returned only by the
+ *     calls documented as synchronous.
+ *   - Errors are returned as mp_status codes; nothing aborts.  A failing
+ *     CUDA call yields MP_ERR_CUDA and its text is kept for mp_last_error.
+ *     Failures found on the device (a pivot that is not positive, a wait
+ *     that ran out) are written to device status words named in each call.
+ *   - Matrices and right-hand sides are column-major with a leading
+ *     dimension (R's convention): element (r, c) of B is B[r + c * ldb].
+ *   - The library stores the LOWER factor L (Sigma = L L^T); the paper's R
+ *     `chol` returns U = L^T.  The log-determinant is the same.
+ *   - One mp_ctx per thread at a time; different contexts are independent.
+ */
+#ifndef MPCHOL_H
+#define MPCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MP_OK = 0,
+  MP_ERR_ARG = 1,      /* invalid argument (sizes, map, dtype, pointer) */
+  MP_ERR_NOT_SPD = 2,  /* a diagonal pivot was not > 0 (see d_info)     */
+  MP_ERR_OOM = 3,      /* device or host allocation failed              */
+  MP_ERR_CUDA = 4,     /* a CUDA runtime/driver call failed             */
+  MP_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out            */
+  MP_ERR_STATE = 6     /* call out of order (e.g. loglik before chol)   */
+} mp_status;
+
+/* Tile storage formats (Sec. 2 and 4.1: half/single/double; extended with
+ * BF16 and OCP FP8 E4M3).  E4M3 tiles carry a power-of-two scale s chosen
+ * per tile so that amax / s <= 448; a stored code c represents c * s. */
+typedef enum { MP_F64 = 0, MP_F32 = 1, MP_BF16 = 2, MP_F16 = 3, MP_E4M3 = 4 } mp_dtype;
+
+/* Matérn covariance parameters (Sec. 6.2): C(r) = sigma2 * M(r / range)
+ * with the half-integer closed forms nu in {0.5, 1.5, 2.5}; `nugget` is
+ * added to the diagonal.  Other nu give MP_ERR_ARG. */
+typedef struct {
+  double sigma2;
+  double range;
+  double nu;
+  double nugget;
+} mp_matern;
+
+typedef struct mp_ctx mp_ctx;
+typedef struct mp_tmat mp_tmat;
+typedef struct mp_batch mp_batch;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device` (made current for the calls
+ * of this context).  *out receives the handle; free with mp_ctx_destroy. */
+mp_status mp_ctx_create(int device, mp_ctx** out);
+void mp_ctx_destroy(mp_ctx* ctx);
+
+/* Static text for a status code. */
+const char* mp_status_string(mp_status s);
+
+/* Copies the last error message of `ctx` (NUL-terminated, truncated to
+ * len) into buf.  Synchronous, host only. */
+mp_status mp_last_error(mp_ctx* ctx, char* buf, size_t len);
+
+/* Library build string (compiler, target architecture). */
+const char* mp_version(void);
+
+/* ------------------------------------------------------------ tiled matrix */
+
+/* Creates an n x n symmetric tiled matrix with tile size b (a multiple of
+ * 128, 128 <= b <= 1024) and NT = ceil(n / b) tiles per side.
+ *   h_map   : NT*NT bytes, row-major, entry [i*NT + j] is the mp_dtype of
+ *             tile (i, j); only the lower triangle i >= j is read; the
+ *             diagonal must be MP_F64.  NULL means all MP_F64.
+ *   flags   : MP_TMAT_KEEP_SIGMA keeps a float64 copy of the generated
+ *             lower tiles for the FP64 refinement residual (needs
+ *             8 * NT(NT+1)/2 * b^2 more bytes).
+ *   stream  : stream all later calls on this matrix are ordered on.
+ * The library allocates tile storage and workspace on the device (see
+ * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
+ * and hold the identity, which leaves the log-determinant and the
+ * quadratic form unchanged.  Synchronous. */
+#define MP_TMAT_KEEP_SIGMA 1u
+mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
+                         uint32_t flags, void* stream, mp_tmat** out);
+void mp_tmat_destroy(mp_tmat* t);
+
+/* Sizes of a tiled matrix: order, tile size, tiles per side, device bytes
+ * held (tiles + workspace).  Any output pointer may be NULL.  Synchronous. */
+mp_status mp_tmat_info(mp_tmat* t, int64_t* n, int32_t* b, int32_t* nt, int64_t* bytes);
+
+/* Copies tile (i, j), i >= j, between the device and host memory: b*b
+ * elements, row-major (element (r, c) at r*b + c), in the tile's storage
+ * format (8/4/2/2/1 bytes); *scale is the E4M3 scale (1 otherwise).  For
+ * diagonal tiles only the lower triangle is meaningful.  Synchronous
+ * (waits for the matrix's stream).  Used to inspect factors and to load a
+ * matrix that was not generated by mp_generate_matern (`as.MPCR`). */
+mp_status mp_tile_get(mp_tmat* t, int32_t i, int32_t j, void* h_dst, double* scale);
+mp_status mp_tile_set(mp_tmat* t, int32_t i, int32_t j, const void* h_src, double scale);
+
+/* --------------------------------------------------------------- points */
+
+/* Morton (Z-curve) order of n locations in [0,1]^2: d_locs_in is n x 2
+ * row-major float64 (x, y per point); each coordinate is quantised to
+ * q = min(floor(v * 65536), 65535) and the key interleaves x bits (even
+ * positions) with y bits (odd positions); points are sorted by key, ties
+ * by original index.  Writes d_locs_out (n x 2, may not alias d_locs_in)
+ * and d_perm (n int64, d_locs_out[k] = d_locs_in[d_perm[k]]).  Uses a
+ * device workspace owned by ctx.  Asynchronous on `stream`. */
+mp_status mp_morton_order(mp_ctx* ctx, int64_t n, const double* d_locs_in,
+                          double* d_locs_out, int64_t* d_perm, void* stream);
+
+/* ------------------------------------------------------------ generation */
+
+/* Fills every lower tile with the Matérn covariance of the locations
+ * d_locs (n x 2 row-major float64; borrowed until the generation kernels
+ * have run on the matrix's stream).  With MP_TMAT_KEEP_SIGMA the float64
+ * values are also kept for the refinement residual.  Each entry is computed in float64 and
+ * rounded once to its tile's format (RNE; E4M3 with satfinite and a
+ * per-tile scale from the tile's amax).  Resets the factorisation state.
+ * Asynchronous. */
+mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p);
+
+/* --------------------------------------------------------- factorisation */
+
+/* Tiled right-looking Cholesky in place (Sec. 6.2 `chol`, tiled as in
+ * Sec. 7): per step k, POTRF of the FP64 diagonal tile, FP64 TRSM of the
+ * panel (result rounded to each tile's format), and the trailing
+ * SYRK/GEMM updates, each in the precision min(p(target), max(p(A),
+ * p(B))) with FP32 accumulation (FP64 for FP64 products).  The whole
+ * schedule is one CUDA graph launch on the matrix's stream.
+ *   d_info   : 1 int64: 0, or the smallest 1-based global row whose pivot
+ *              was not > 0 (then L is not valid).  May be NULL.
+ *   d_logdet : 1 float64: log det Sigma = 2 sum log L_tt.  May be NULL.
+ * Returns MP_OK once enqueued (a non-SPD matrix is reported in d_info
+ * only).  Asynchronous. */
+mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet);
+
+/* Runs only steps k0 .. k1-1 of the factorisation (0 <= k0 <= k1 <= NT),
+ * with direct launches (no graph).  For inspecting the per-step kernels;
+ * mp_chol is the same as mp_chol_steps(t, 0, NT) plus the outputs.
+ * Asynchronous. */
+mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1);
+
+/* Copies log det Sigma of the factorised matrix into d_out (1 float64).
+ * MP_ERR_STATE if mp_chol has not been enqueued.  Asynchronous. */
+mp_status mp_logdet(mp_tmat* t, double* d_out);
+
+/* In-place triangular solve with the factor, FP64 arithmetic on the
+ * exactly upcast tiles (Sec. 6.2 `forwardsolve`, Sec. 5 `backsolve`):
+ * trans = 0 solves L X = B, trans = 1 solves L^T X = B.  d_B is n x nrhs
+ * column-major float64 with leading dimension ldb >= n.  Asynchronous. */
+mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, int32_t nrhs);
+
+/* Gaussian log-likelihood (Sec. 6.2):
+ *   loglik = -n/2 log(2 pi) - logdet/2 - quad/2
+ * for each of nrhs right-hand sides z (d_z: n x nrhs column-major float64,
+ * leading dimension ldz >= n).
+ * refine_iters = 0: quad = ||L^{-1} z||^2.
+ * refine_iters > 0: FP64 iterative refinement of Sigma x = z (the paper's
+ *   "double precision for refinement", Sec. 1): x0 = L^-T L^-1 z, then up to
+ *   refine_iters times r = z - Sigma x with Sigma in float64 (the copy kept
+ *   by MP_TMAT_KEEP_SIGMA; MP_ERR_STATE without it); a column stops when
+ *   ||r||_inf <= n 2^-53 (||Sigma||_inf ||x||_inf + ||z||_inf), otherwise
+ *   x += L^-T L^-1 r; quad = z^T x.
+ * Outputs (device, may be NULL except d_ll): d_ll[nrhs] loglik,
+ * d_quad[nrhs], d_iters[nrhs] corrections applied per column.
+ * The solve and refinement schedule is captured into a CUDA graph and
+ * re-used while the arguments stay the same.  Asynchronous. */
+mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32_t nrhs,
+                    int32_t refine_iters, double* d_ll, double* d_quad, int32_t* d_iters);
+
+/* ------------------------------------------------------ planning, stats */
+
+/* Frobenius norm of every lower tile of the Matérn matrix that
+ * mp_generate_matern would produce for (n, b, d_locs, p), computed on the
+ * device in float64 without storing the matrix: d_norms is NT*NT float64,
+ * row-major, entry [i*NT + j] for i >= j (others set to 0).  Deterministic
+ * (fixed reduction order).  Allocates a small scratch; synchronous. */
+mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const double* d_locs, mp_matern p,
+                        double* d_norms, void* stream);
+
+/* Norm-guarded band precision map (host only).  The multi-precision tiled
+ * extension (Sec. 7) leaves the choice of precisions open; this rule keeps
+ * the diagonal in MP_F64, tiles with i - j <= band in near_dt, and gives a
+ * farther tile far_dt only when u(far_dt) ||A_ij||_F <= eps ||A||_F / NT
+ * (u = unit roundoff: 2^-24 F32, 2^-8 BF16, 2^-11 F16, 2^-4 E4M3), which
+ * bounds the rounding perturbation of all far tiles by eps ||A||_F; the
+ * others fall back to near_dt.  h_norms as written by mp_tile_norms;
+ * h_map (NT*NT, row-major) receives the map, 255 above the diagonal. */
+mp_status mp_map_guarded(int32_t nt, const double* h_norms, int32_t band, uint8_t near_dt,
+                         uint8_t far_dt, double eps, uint8_t* h_map);
+
+/* Kernel launches of one mp_chol (its graph's kernel nodes, known after the
+ * first mp_chol), of one mp_generate_matern, and of one mp_loglik with the
+ * arguments of its last call.  Any pointer may be NULL. */
+mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* gen_kernels,
+                        int64_t* loglik_kernels);
+
+/* Runs the factorisation once with direct launches and a CUDA event after
+ * every launch, and returns per kernel class c (0 diagonal-block POTRF,
+ * 1 inner TRSM, 2 inner SYRK, 3 panel TRSM, 4 panel rounding, 5 FP64
+ * updates, 6 CUDA-core lower-precision updates, 7 tensor-core updates,
+ * 8 E4M3 target rounding, 9 other): h_ms[c] summed event time,
+ * h_launches[c] launches, h_flops[c] algorithmic flops (TRSM b^3 per tile,
+ * GEMM 2b^3, SYRK b^2(b+1), POTRF nb^3/3 per 32-block).  Arrays hold
+ * nclass >= MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as
+ * mp_chol).  Synchronous. */
+#define MP_PROFILE_CLASSES 10
+mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, int64_t* h_launches,
+                          double* h_flops);
+
+/* Measures the device's FP64 FMA throughput (TFLOP/s) with a loop of
+ * independent DFMA chains over every SM: the peak against which the FP64
+ * kernels (panel TRSM, diagonal POTRF) are rated.  Synchronous. */
+mp_status mp_probe_fp64_peak(int device, double* h_tflops);
+
+/* ------------------------------------------------------------------ GEMM */
+
+/* C = alpha op(A) op(B) + beta C (Sec. 5 `%*%` / `crossprod` per
+ * precision), all three matrices stored in `dtype`, column-major with
+ * leading dimensions; op(X) = X for 'N', X^T for 'T'.  op(A) is m x k,
+ * op(B) is k x n, C is m x n.  Products accumulate in FP32 (FP64 for
+ * MP_F64); alpha, beta and the final sum are applied in float64 for
+ * MP_F64/MP_F32 targets and FP32 otherwise; the result is rounded once
+ * to `dtype` (E4M3 codes with scale 1, satfinite).  Asynchronous on
+ * `stream`. */
+mp_status mp_gemm(mp_ctx* ctx, mp_dtype dtype, char ta, char tb, int64_t m, int64_t n,
+                  int64_t k, double alpha, const void* d_A, int64_t lda, const void* d_B,
+                  int64_t ldb, double beta, void* d_C, int64_t ldc, void* stream);
+
+/* ----------------------------------------------------------------- batch */
+
+/* One log-likelihood request of a batch. */
+typedef struct {
+  int64_t n;              /* matrix order (>= 1)                             */
+  const uint8_t* h_map;   /* NT*NT precision map as in mp_tmat_create, or NULL */
+  const double* d_locs;   /* n x 2 row-major float64 locations (borrowed)     */
+  const double* d_z;      /* n x nrhs column-major float64, ld = n (borrowed) */
+  int32_t nrhs;           /* right-hand sides (>= 1)                          */
+  int32_t refine_iters;   /* as in mp_loglik (0 = none)                       */
+  mp_matern cov;          /* covariance parameters                            */
+} mp_request;
+
+/* Builds a batch plan for `count` independent requests sharing tile size b
+ * (b = 0 lets the library's tuner choose from the request sizes): one tile
+ * arena for all matrices and one merged schedule -- generation,
+ * factorisation, solve, refinement and log-likelihood of every request --
+ * captured as a single CUDA graph.  Pointers in `reqs` are borrowed and
+ * must stay valid for the plan's lifetime.  Synchronous. */
+mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
+                          void* stream, mp_batch** out);
+void mp_batch_destroy(mp_batch* batch);
+
+/* Device bytes held by a batch plan and the tile size it uses. */
+mp_status mp_batch_info(mp_batch* batch, int64_t* bytes, int32_t* b);
+
+/* Launches the batch graph.  d_ll: sum of nrhs over requests float64, the
+ * log-likelihoods of request 0's columns first; d_status: count int32,
+ * MP_OK or MP_ERR_NOT_SPD per request (a failing request does not stop the
+ * others).  Asynchronous on the plan's stream. */
+mp_status mp_batch_run(mp_batch* batch, double* d_ll, int32_t* d_status);
+
+/* Same as mp_batch_create + mp_batch_run + a stream synchronisation.
+ * Synchronous. */
+mp_status mp_loglik_batch(mp_ctx* ctx, int32_t count, const mp_request* reqs,
+                          double* d_ll, int32_t* d_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPCHOL_H */

@@ -158,6 +158,40 @@ def tiled_from_dense(S: np.ndarray, b: int, pmap: np.ndarray) -> TiledMatrix:
     return T
 
 
+def tile_norms(S: np.ndarray, b: int) -> np.ndarray:
+    """Frobenius norms of the lower tiles of the identity-padded matrix."""
+    P = pad_identity(S, b)
+    nt = P.shape[0] // b
+    out = np.zeros((nt, nt))
+    for i in range(nt):
+        for j in range(i + 1):
+            out[i, j] = np.linalg.norm(P[i * b:(i + 1) * b, j * b:(j + 1) * b])
+    return out
+
+
+def guarded_map(norms: np.ndarray, band: int, near: int, far: int, eps: float) -> np.ndarray:
+    """A precision map for the tiled extension (Sec. 7 leaves the choice of
+    precisions open): diagonal FP64, |i - j| <= band in `near`, and a farther
+    tile in `far` only when u(far) ||A_ij||_F <= eps ||A||_F / NT, so that
+    the rounding of all far tiles perturbs A by at most eps ||A||_F in the
+    Frobenius norm; otherwise `near`.  Entries above the diagonal are 255."""
+    nt = norms.shape[0]
+    tot = 0.0
+    for i in range(nt):
+        for j in range(i + 1):
+            tot += (1.0 if i == j else 2.0) * norms[i, j] ** 2
+    bound = eps * math.sqrt(tot) / nt
+    m = np.full((nt, nt), 255, dtype=np.uint8)
+    for i in range(nt):
+        m[i, i] = F.F64
+        for j in range(i):
+            if i - j <= band:
+                m[i, j] = near
+            else:
+                m[i, j] = far if F.unit_roundoff(far) * norms[i, j] <= bound else near
+    return m
+
+
 def kind_of(q: int, pa: int, pb: int) -> int:
     """R-MMA: the format in which A_ik A_jk^T runs for a target of format q."""
     lk = min(F.level(q), max(F.level(pa), F.level(pb)))

@@ -1,0 +1,1417 @@
+// Host runtime behind include/mpchol.h: tile arenas, the static schedule of
+// the tiled factorisation (merged over all matrices of a plan), solve and
+// refinement schedules, and their capture into CUDA graphs.
+//
+// The schedule is the right-looking tiled Cholesky of the tiled
+// multi-precision extension (Sec. 7) applied to the `chol` / `forwardsolve`
+// recipe of Sec. 6.2.  Every step k is a fixed sequence of launches, each
+// carrying the work items of every matrix that still has a step k:
+//   amax reset, for each 32-block of the diagonal tile: POTRF block (+ inner
+//   TRSM, inner SYRK), panel TRSM, panel rounding, trailing updates (FP64
+//   products, lower-precision products), E4M3 target rounding.
+// Because the whole schedule depends only on sizes and precision maps, it is
+// built once per plan and replayed as one CUDA graph launch.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mpchol.h"
+#include "mp_device.cuh"
+
+using namespace mp;
+
+struct mp_ctx {
+  int device = 0;
+  std::string err;
+  unsigned long long* keys = nullptr;
+  int64_t keys_cap = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+thread_local char g_err_fallback[256];
+
+mp_status fail(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else snprintf(g_err_fallback, sizeof g_err_fallback, "%s", buf);
+  return st;
+}
+
+#define CK(ctx, call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail((ctx), MP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                             \
+  } while (0)
+
+// R-MMA: precision of the product A_ik A_jk^T for a target of format q.
+int kind_of(int q, int pa, int pb) {
+  int lk = std::min(level(q), std::max(level(pa), level(pb)));
+  if (lk == level(q)) return q;
+  bool ha = level(pa) == lk, hb = level(pb) == lk;
+  if (ha && hb && pa != pb) return F32;   // BF16 with F16 below a wider target
+  return ha ? pa : pb;
+}
+// does an operand stored in format p need rounding to run in `kind`?
+bool needs_round(int p, int kind) { return p != kind && level(p) >= level(kind); }
+
+enum Op {
+  OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64,
+  OP_FP8R, OP_LOGDET, OP_DIAG_F, OP_OFF_F, OP_DIAG_B, OP_OFF_B, OP_GEN_AMAX, OP_GEN
+};
+
+struct Launch {
+  int op;
+  size_t off;     // byte offset of the item array in the plan's item buffer
+  int count;
+  int kb;
+};
+
+}  // namespace
+
+// One matrix inside a plan.
+struct MatDesc {
+  int64_t n = 0;
+  int nt = 0;
+  std::vector<int32_t> tile, sig;           // nt*nt each (-1 = none)
+  std::vector<int32_t> shadow;              // nt*nt*NDT: rounded copy of (i,j) in format d
+  std::vector<int32_t> linv;                // nt: FP64 tile holding L_ii^{-T}
+  int32_t ldoff = 0;
+  double* dinv = nullptr;                   // nt * (b/32) blocks of 32x32
+};
+
+struct Plan {
+  mp_ctx* ctx = nullptr;
+  int b = 0;
+  cudaStream_t stream = nullptr;   // user stream
+  cudaStream_t cap = nullptr;      // internal stream for graph capture
+  bool keep_sigma = false;
+  // arena
+  std::vector<TileRef> h_tiles;
+  int pool_count[NDT] = {};
+  int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
+  char* pool[NDT] = {};
+  TileRef* d_tiles = nullptr;
+  double* d_scale = nullptr;
+  unsigned long long* d_amax = nullptr;
+  int n_amax = 0;
+  // matrices
+  std::vector<MatDesc> mats;
+  double* d_dinv_all = nullptr;
+  double* d_ldparts = nullptr;
+  int32_t* d_ldoff = nullptr;
+  int32_t* d_ldcnt = nullptr;
+  long long* d_info = nullptr;
+  double* d_logdet = nullptr;
+  double* d_panel = nullptr;        // panel scratch slots (float64)
+  float* d_v = nullptr;             // E4M3 update scratch slots (FP32)
+  int32_t* d_sig = nullptr;         // sigma tile tables (all matrices)
+  // work items and schedules
+  std::vector<char> h_items;
+  char* d_items = nullptr;
+  size_t d_items_cap = 0;
+  std::vector<Launch> chol;          // full factorisation
+  std::vector<size_t> step_begin;    // index into chol of each step's first launch
+  cudaGraphExec_t chol_exec = nullptr;
+  int64_t chol_kernels = 0;
+  bool factored = false;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  Arena arena() const {
+    Arena A{};
+    for (int d = 0; d < NDT; ++d) A.pool[d] = pool[d];
+    A.tiles = d_tiles;
+    A.scale = d_scale;
+    A.amax = d_amax;
+    A.b = b;
+    return A;
+  }
+
+  template <typename T>
+  size_t push(const std::vector<T>& v) {
+    size_t off = (h_items.size() + 255) & ~size_t(255);
+    h_items.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) memcpy(h_items.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+  template <typename T>
+  const T* item(size_t off) const { return reinterpret_cast<const T*>(d_items + off); }
+
+  mp_status alloc(void** p, size_t bytes_) {
+    if (bytes_ == 0) { *p = nullptr; return MP_OK; }
+    cudaError_t e = cudaMalloc(p, bytes_);
+    if (e != cudaSuccess) return fail(ctx, MP_ERR_OOM, "cudaMalloc(%zu): %s", bytes_, cudaGetErrorString(e));
+    allocs.push_back(*p);
+    bytes += (int64_t)bytes_;
+    return MP_OK;
+  }
+
+  ~Plan() {
+    if (chol_exec) cudaGraphExecDestroy(chol_exec);
+    for (void* p : allocs) cudaFree(p);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+// Single-matrix handle: a plan with one matrix plus solve state.
+struct mp_tmat {
+  Plan P;
+  const double* locs = nullptr;
+  mp_matern cov{};
+  bool generated = false;
+  // generation items (re-built when the inputs change)
+  std::vector<char> gen_key;
+  size_t gen_off_amax = 0, gen_off_all = 0;
+  int gen_n_amax = 0, gen_n_all = 0;
+  char* d_gen = nullptr;
+  size_t d_gen_cap = 0;
+  // loglik workspace + graph
+  int ws_nrhs = 0;
+  double *zp = nullptr, *x = nullptr, *r = nullptr, *w = nullptr, *d = nullptr;
+  double *rowabs = nullptr, *red = nullptr;
+  int *active = nullptr, *iters = nullptr, *any = nullptr;
+  cudaGraphExec_t ll_exec = nullptr;
+  int64_t ll_kernels = 0;
+  std::vector<char> ll_key;
+  char* d_sitems = nullptr;
+  size_t d_sitems_cap = 0;
+  std::vector<void*> ws_allocs;
+  ~mp_tmat() {
+    if (ll_exec) cudaGraphExecDestroy(ll_exec);
+    for (void* p : ws_allocs) cudaFree(p);
+    if (d_gen) cudaFree(d_gen);
+    if (d_sitems) cudaFree(d_sitems);
+  }
+};
+
+struct mp_batch {
+  Plan P;
+  int count = 0;
+  std::vector<mp_request> reqs;
+  cudaGraphExec_t exec = nullptr;
+  double* d_llbuf = nullptr;    // internal outputs
+  int32_t* d_stbuf = nullptr;
+  int total_rhs = 0;
+  ~mp_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+namespace {
+
+// ------------------------------------------------------------ plan building
+
+mp_status validate_map(mp_ctx* ctx, int nt, const uint8_t* map) {
+  if (!map) return MP_OK;
+  for (int i = 0; i < nt; ++i) {
+    if (map[i * nt + i] != F64) return fail(ctx, MP_ERR_ARG, "diagonal tile %d must be MP_F64", i);
+    for (int j = 0; j < i; ++j)
+      if (map[i * nt + j] >= NDT) return fail(ctx, MP_ERR_ARG, "tile (%d,%d): bad dtype %d", i, j, map[i * nt + j]);
+  }
+  return MP_OK;
+}
+
+int new_tile(Plan& P, int dt) {
+  TileRef r{dt, P.pool_count[dt]++};
+  P.h_tiles.push_back(r);
+  return (int)P.h_tiles.size() - 1;
+}
+
+// Lays out the tiles of one matrix (and its shadows / float64 Sigma copy).
+mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
+  MatDesc M;
+  M.n = n;
+  M.nt = (int)((n + P.b - 1) / P.b);
+  const int nt = M.nt;
+  if (mp_status st = validate_map(P.ctx, nt, map)) return st;
+  auto dt = [&](int i, int j) { return map ? (int)map[i * nt + j] : (int)F64; };
+  M.tile.assign((size_t)nt * nt, -1);
+  M.shadow.assign((size_t)nt * nt * NDT, -1);
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j <= i; ++j) M.tile[i * nt + j] = new_tile(P, dt(i, j));
+  // rounded copies needed by each off-diagonal tile (i, s): one per format
+  // in which a product that reads it runs below its storage format
+  for (int s = 0; s < nt; ++s)
+    for (int i = s + 1; i < nt; ++i) {
+      const int p = dt(i, s);
+      bool need[NDT] = {};
+      for (int j = s + 1; j <= i; ++j) {                 // as the A operand
+        int kd = kind_of(dt(i, j), p, dt(j, s));
+        if (needs_round(p, kd)) need[kd] = true;
+      }
+      for (int i2 = i + 1; i2 < nt; ++i2) {              // as the B operand
+        int kd = kind_of(dt(i2, i), dt(i2, s), p);
+        if (needs_round(p, kd)) need[kd] = true;
+      }
+      int cnt = 0;
+      for (int d = 0; d < NDT; ++d)
+        if (need[d]) {
+          if (++cnt > MAX_SHADOW) return fail(P.ctx, MP_ERR_ARG, "tile (%d,%d) needs too many rounded copies", i, s);
+          M.shadow[((size_t)i * nt + s) * NDT + d] = new_tile(P, d);
+        }
+    }
+  M.linv.assign(nt, -1);
+  for (int i = 0; i < nt; ++i) M.linv[i] = new_tile(P, F64);
+  if (P.ident < 0) P.ident = new_tile(P, F64);
+  if (P.keep_sigma) {
+    M.sig.assign((size_t)nt * nt, -1);
+    for (int i = 0; i < nt; ++i)
+      for (int j = 0; j <= i; ++j) M.sig[i * nt + j] = new_tile(P, F64);
+  }
+  P.mats.push_back(std::move(M));
+  return MP_OK;
+}
+
+// Builds the factorisation schedule of every matrix in the plan, merged by
+// step index.  Returns scratch requirements through the plan.
+void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
+  const int b = P.b, nbb = b / 32;
+  int maxnt = 0;
+  for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
+  int64_t max_panel = 0, max_v = 0;
+  P.chol.clear();
+  P.step_begin.clear();
+  P.chol.push_back({OP_INFO0, 0, 0, 0});
+  for (int s = 0; s < maxnt; ++s) {
+    P.step_begin.push_back(P.chol.size());
+    P.chol.push_back({OP_AMAX0, 0, 0, 0});
+    for (int kb = 0; kb < nbb; ++kb) {
+      std::vector<ItemDiag> items;
+      for (int m = 0; m < (int)P.mats.size(); ++m) {
+        auto& M = P.mats[m];
+        if (M.nt <= s) continue;
+        ItemDiag it{};
+        it.tile = M.tile[s * M.nt + s];
+        it.kb = kb;
+        it.ldslot = M.ldoff + s * nbb + kb;
+        it.mat = m;
+        it.row0 = (int64_t)s * b;
+        it.dinv = M.dinv + ((int64_t)s * nbb + kb) * 1024;
+        items.push_back(it);
+      }
+      size_t off = P.push(items);
+      P.chol.push_back({OP_POTRF, off, (int)items.size(), kb});
+      if (kb + 1 < nbb) {
+        P.chol.push_back({OP_ITRSM, off, (int)items.size(), kb});
+        P.chol.push_back({OP_ISYRK, off, (int)items.size(), kb});
+      }
+    }
+    std::vector<ItemPanel> panel;
+    std::vector<ItemRound> round;
+    std::vector<ItemUpd> u32, u64;
+    std::vector<ItemFp8> f8;
+    int64_t slot = 0, vslot = 0;
+    for (int m = 0; m < (int)P.mats.size(); ++m) {
+      auto& M = P.mats[m];
+      const int nt = M.nt;
+      if (nt <= s) continue;
+      for (int i = s + 1; i < nt; ++i) {
+        ItemPanel it{};
+        it.tile = M.tile[i * nt + s];
+        it.diag = M.tile[s * nt + s];
+        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+        it.x = P.d_panel + slot * (int64_t)b * b;   // d_panel set before building (see caller)
+        panel.push_back(it);
+        ItemRound r{};
+        r.tile = it.tile;
+        int q = 0;
+        for (int d = 0; d < MAX_SHADOW; ++d) r.shadow[d] = -1;
+        for (int d = 0; d < NDT; ++d) {
+          int sh = M.shadow[((size_t)i * nt + s) * NDT + d];
+          if (sh >= 0) r.shadow[q++] = sh;
+        }
+        r.x = it.x;
+        round.push_back(r);
+        ++slot;
+      }
+      for (int j = s + 1; j < nt; ++j)
+        for (int i = j; i < nt; ++i) {
+          const int tc = M.tile[i * nt + j], ta = M.tile[i * nt + s], tb = M.tile[j * nt + s];
+          const int q = P.h_tiles[tc].dt, pa = P.h_tiles[ta].dt, pb = P.h_tiles[tb].dt;
+          const int kd = kind_of(q, pa, pb);
+          ItemUpd u{};
+          u.c = tc;
+          u.a = needs_round(pa, kd) ? M.shadow[((size_t)i * nt + s) * NDT + kd] : ta;
+          u.b = needs_round(pb, kd) ? M.shadow[((size_t)j * nt + s) * NDT + kd] : tb;
+          u.syrk = i == j;
+          u.vslot = -1;
+          if (q == E4M3) {
+            u.v = P.d_v + vslot * (int64_t)b * b;
+            u.vslot = (int)(P.h_tiles.size() + vslot);
+            f8.push_back(ItemFp8{tc, u.vslot, u.v});
+            ++vslot;
+          }
+          (kd == F64 ? u64 : u32).push_back(u);
+        }
+    }
+    // the inverse of the new diagonal factor: X = I L_ss^{-T}
+    for (int m = 0; m < (int)P.mats.size(); ++m) {
+      auto& M = P.mats[m];
+      if (M.nt <= s) continue;
+      ItemPanel it{};
+      it.tile = P.ident;
+      it.diag = M.tile[s * M.nt + s];
+      it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+      const TileRef r = P.h_tiles[M.linv[s]];
+      it.x = (double*)(P.pool[F64] + (size_t)r.idx * b * b * 8);
+      panel.push_back(it);
+    }
+    max_panel = std::max(max_panel, slot);
+    max_v = std::max(max_v, vslot);
+    if (!panel.empty()) P.chol.push_back({OP_PANEL, P.push(panel), (int)panel.size(), 0});
+    if (!round.empty()) P.chol.push_back({OP_ROUND, P.push(round), (int)round.size(), 0});
+    if (!u64.empty()) P.chol.push_back({OP_UPD64, P.push(u64), (int)u64.size(), 0});
+    if (!u32.empty()) P.chol.push_back({OP_UPD32, P.push(u32), (int)u32.size(), 0});
+    if (!f8.empty()) P.chol.push_back({OP_FP8R, P.push(f8), (int)f8.size(), 0});
+  }
+  P.step_begin.push_back(P.chol.size());
+  P.chol.push_back({OP_LOGDET, 0, (int)P.mats.size(), 0});
+  *panel_slots = max_panel;
+  *v_slots = max_v;
+}
+
+// Counts scratch needs without item pointers (first pass), so that scratch
+// can be allocated before the items that point into it are built.
+void count_scratch(const Plan& P, int64_t* panel_slots, int64_t* v_slots) {
+  int maxnt = 0;
+  for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
+  int64_t mp_ = 0, mv = 0;
+  for (int s = 0; s < maxnt; ++s) {
+    int64_t slot = 0, vslot = 0;
+    for (auto& M : P.mats) {
+      if (M.nt <= s) continue;
+      slot += M.nt - 1 - s;
+      for (int j = s + 1; j < M.nt; ++j)
+        for (int i = j; i < M.nt; ++i)
+          if (P.h_tiles[M.tile[i * M.nt + j]].dt == E4M3) ++vslot;
+    }
+    mp_ = std::max(mp_, slot);
+    mv = std::max(mv, vslot);
+  }
+  *panel_slots = mp_;
+  *v_slots = mv;
+}
+
+mp_status upload_items(Plan& P) {
+  if (P.h_items.size() > P.d_items_cap) {
+    if (P.d_items) cudaFree(P.d_items);
+    P.d_items = nullptr;
+    CK(P.ctx, cudaMalloc(&P.d_items, P.h_items.size()));
+    P.d_items_cap = P.h_items.size();
+  }
+  if (!P.h_items.empty())
+    CK(P.ctx, cudaMemcpy(P.d_items, P.h_items.data(), P.h_items.size(), cudaMemcpyHostToDevice));
+  return MP_OK;
+}
+
+// Allocates the arena and scratch of a plan whose matrices were added.
+mp_status finish_plan(Plan& P) {
+  const int b = P.b, nbb = b / 32;
+  for (int d = 0; d < NDT; ++d) {
+    void* p = nullptr;
+    size_t bytes = (size_t)P.pool_count[d] * b * b * esize(d);
+    if (mp_status st = P.alloc(&p, bytes)) return st;
+    P.pool[d] = (char*)p;
+  }
+  int64_t panel_slots = 0, v_slots = 0;
+  count_scratch(P, &panel_slots, &v_slots);
+  void* p;
+  if (mp_status st = P.alloc(&p, (size_t)panel_slots * b * b * 8)) return st;
+  P.d_panel = (double*)p;
+  if (mp_status st = P.alloc(&p, (size_t)v_slots * b * b * 4)) return st;
+  P.d_v = (float*)p;
+  const int ntiles = (int)P.h_tiles.size();
+  P.n_amax = ntiles + (int)v_slots;
+  if (mp_status st = P.alloc(&p, sizeof(TileRef) * ntiles)) return st;
+  P.d_tiles = (TileRef*)p;
+  if (mp_status st = P.alloc(&p, sizeof(double) * ntiles)) return st;
+  P.d_scale = (double*)p;
+  if (mp_status st = P.alloc(&p, sizeof(unsigned long long) * P.n_amax)) return st;
+  P.d_amax = (unsigned long long*)p;
+  // per-matrix: block inverses, log-det partials
+  int64_t ninv = 0;
+  int32_t ldo = 0;
+  std::vector<int32_t> ldoff, ldcnt;
+  for (auto& M : P.mats) {
+    M.ldoff = ldo;
+    ldoff.push_back(ldo);
+    ldcnt.push_back(M.nt * nbb);
+    ldo += M.nt * nbb;
+    ninv += (int64_t)M.nt * nbb;
+  }
+  if (mp_status st = P.alloc(&p, sizeof(double) * 1024 * ninv)) return st;
+  P.d_dinv_all = (double*)p;
+  int64_t io = 0;
+  for (auto& M : P.mats) {
+    M.dinv = P.d_dinv_all + io * 1024;
+    io += (int64_t)M.nt * nbb;
+  }
+  const int nm = (int)P.mats.size();
+  if (mp_status st = P.alloc(&p, sizeof(double) * std::max(ldo, 1))) return st;
+  P.d_ldparts = (double*)p;
+  if (mp_status st = P.alloc(&p, sizeof(int32_t) * nm)) return st;
+  P.d_ldoff = (int32_t*)p;
+  if (mp_status st = P.alloc(&p, sizeof(int32_t) * nm)) return st;
+  P.d_ldcnt = (int32_t*)p;
+  if (mp_status st = P.alloc(&p, sizeof(long long) * nm)) return st;
+  P.d_info = (long long*)p;
+  if (mp_status st = P.alloc(&p, sizeof(double) * nm)) return st;
+  P.d_logdet = (double*)p;
+  if (P.keep_sigma) {
+    int64_t tot = 0;
+    for (auto& M : P.mats) tot += (int64_t)M.nt * M.nt;
+    if (mp_status st = P.alloc(&p, sizeof(int32_t) * tot)) return st;
+    P.d_sig = (int32_t*)p;
+    int64_t o = 0;
+    for (auto& M : P.mats) {
+      CK(P.ctx, cudaMemcpy(P.d_sig + o, M.sig.data(), sizeof(int32_t) * M.sig.size(),
+                           cudaMemcpyHostToDevice));
+      o += (int64_t)M.nt * M.nt;
+    }
+  }
+  CK(P.ctx, cudaMemcpy(P.d_tiles, P.h_tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice));
+  {
+    std::vector<double> eye((size_t)b * b, 0.0);
+    for (int r = 0; r < b; ++r) eye[(size_t)r * b + r] = 1.0;
+    const TileRef r = P.h_tiles[P.ident];
+    CK(P.ctx, cudaMemcpy(P.pool[F64] + (size_t)r.idx * b * b * 8, eye.data(), sizeof(double) * b * b,
+                         cudaMemcpyHostToDevice));
+  }
+  std::vector<double> ones(ntiles, 1.0);
+  CK(P.ctx, cudaMemcpy(P.d_scale, ones.data(), sizeof(double) * ntiles, cudaMemcpyHostToDevice));
+  CK(P.ctx, cudaMemcpy(P.d_ldoff, ldoff.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice));
+  CK(P.ctx, cudaMemcpy(P.d_ldcnt, ldcnt.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice));
+  int64_t ps = 0, vs = 0;
+  build_chol_schedule(P, &ps, &vs);
+  if (mp_status st = upload_items(P)) return st;
+  P.bytes += (int64_t)P.h_items.size();
+  CK(P.ctx, cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
+  return MP_OK;
+}
+
+void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
+  const Arena A = P.arena();
+  switch (L.op) {
+    case OP_INFO0: cudaMemsetAsync(P.d_info, 0x7f, sizeof(long long) * P.mats.size(), s); break;
+    case OP_AMAX0: cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s); break;
+    case OP_POTRF: launch_potrf_block(A, P.item<ItemDiag>(L.off), L.count, P.d_ldparts, P.d_info, s); break;
+    case OP_ITRSM: launch_inner_trsm(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
+    case OP_ISYRK: launch_inner_syrk(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
+    case OP_PANEL: launch_panel_trsm(A, P.item<ItemPanel>(L.off), L.count, s); break;
+    case OP_ROUND: launch_panel_round(A, P.item<ItemRound>(L.off), L.count, s); break;
+    case OP_UPD32: launch_update_f32(A, P.item<ItemUpd>(L.off), L.count, s); break;
+    case OP_UPD64: launch_update_f64(A, P.item<ItemUpd>(L.off), L.count, s); break;
+    case OP_FP8R: launch_fp8_round(A, P.item<ItemFp8>(L.off), L.count, s); break;
+    case OP_LOGDET:
+      launch_logdet(P.d_ldparts, P.d_ldoff, P.d_ldcnt, (int)P.mats.size(), P.d_logdet, s);
+      break;
+    default: break;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+template <typename F>
+mp_status capture_graph(mp_ctx* ctx, cudaStream_t cap, F&& body, cudaGraphExec_t* exec,
+                        int64_t* kernel_nodes = nullptr) {
+  cudaGraph_t g = nullptr;
+  CK(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  body(cap);
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (e != cudaSuccess) return fail(ctx, MP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  if (kernel_nodes) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int64_t k = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+    }
+    *kernel_nodes = k;
+  }
+  if (*exec) { cudaGraphExecDestroy(*exec); *exec = nullptr; }
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, MP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return MP_OK;
+}
+
+// Launches `exec` on the user stream; the capture stream is independent.
+mp_status launch_graph(mp_ctx* ctx, cudaGraphExec_t exec, cudaStream_t s) {
+  CK(ctx, cudaGraphLaunch(exec, s));
+  return MP_OK;
+}
+
+mp_status check_launch(mp_ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, MP_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return MP_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI ==
+
+extern "C" {
+
+const char* mp_status_string(mp_status s) {
+  switch (s) {
+    case MP_OK: return "ok";
+    case MP_ERR_ARG: return "invalid argument";
+    case MP_ERR_NOT_SPD: return "matrix is not positive definite";
+    case MP_ERR_OOM: return "out of memory";
+    case MP_ERR_CUDA: return "CUDA error";
+    case MP_ERR_TIMEOUT: return "device wait timed out";
+    case MP_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* mp_version(void) {
+#define MP_STR2(x) #x
+#define MP_STR(x) MP_STR2(x)
+  return "mpchol 0.1 (sm_103a, nvcc " MP_STR(__CUDACC_VER_MAJOR__) "." MP_STR(__CUDACC_VER_MINOR__) ")";
+}
+
+mp_status mp_ctx_create(int device, mp_ctx** out) {
+  if (!out) return fail(nullptr, MP_ERR_ARG, "out is null");
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+    return fail(nullptr, MP_ERR_ARG, "no CUDA device %d", device);
+  CK(nullptr, cudaSetDevice(device));
+  mp_ctx* c = new mp_ctx;
+  c->device = device;
+  *out = c;
+  return MP_OK;
+}
+
+void mp_ctx_destroy(mp_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->keys) cudaFree(ctx->keys);
+  delete ctx;
+}
+
+mp_status mp_last_error(mp_ctx* ctx, char* buf, size_t len) {
+  if (!buf || len == 0) return MP_ERR_ARG;
+  snprintf(buf, len, "%s", ctx ? ctx->err.c_str() : g_err_fallback);
+  return MP_OK;
+}
+
+mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map, uint32_t flags,
+                         void* stream, mp_tmat** out) {
+  if (!ctx || !out) return fail(ctx, MP_ERR_ARG, "null argument");
+  if (n < 1) return fail(ctx, MP_ERR_ARG, "n must be >= 1");
+  if (b < 128 || b > 1024 || b % 128) return fail(ctx, MP_ERR_ARG, "b must be a multiple of 128 in [128, 1024]");
+  CK(ctx, cudaSetDevice(ctx->device));
+  mp_tmat* t = new mp_tmat;
+  t->P.ctx = ctx;
+  t->P.b = b;
+  t->P.stream = (cudaStream_t)stream;
+  t->P.keep_sigma = (flags & MP_TMAT_KEEP_SIGMA) != 0;
+  mp_status st = add_matrix(t->P, n, h_map);
+  if (st == MP_OK) st = finish_plan(t->P);
+  if (st != MP_OK) { delete t; return st; }
+  *out = t;
+  return MP_OK;
+}
+
+void mp_tmat_destroy(mp_tmat* t) { delete t; }
+
+mp_status mp_tmat_info(mp_tmat* t, int64_t* n, int32_t* b, int32_t* nt, int64_t* bytes) {
+  if (!t) return MP_ERR_ARG;
+  if (n) *n = t->P.mats[0].n;
+  if (b) *b = t->P.b;
+  if (nt) *nt = t->P.mats[0].nt;
+  if (bytes) *bytes = t->P.bytes;
+  return MP_OK;
+}
+
+static mp_status tile_xfer(mp_tmat* t, int32_t i, int32_t j, void* h, double* scale, bool get) {
+  if (!t) return MP_ERR_ARG;
+  Plan& P = t->P;
+  const MatDesc& M = P.mats[0];
+  if (i < 0 || j < 0 || i >= M.nt || j > i) return fail(P.ctx, MP_ERR_ARG, "tile (%d,%d) out of range", i, j);
+  if (!h) return fail(P.ctx, MP_ERR_ARG, "host buffer is null");
+  const int id = M.tile[i * M.nt + j];
+  const TileRef r = P.h_tiles[id];
+  const size_t bytes = (size_t)P.b * P.b * esize(r.dt);
+  char* dev = P.pool[r.dt] + (size_t)r.idx * bytes;
+  CK(P.ctx, cudaStreamSynchronize(P.stream));
+  if (get) {
+    CK(P.ctx, cudaMemcpy(h, dev, bytes, cudaMemcpyDeviceToHost));
+    double s = 1.0;
+    CK(P.ctx, cudaMemcpy(&s, P.d_scale + id, sizeof(double), cudaMemcpyDeviceToHost));
+    if (scale) *scale = s;
+  } else {
+    CK(P.ctx, cudaMemcpy(dev, h, bytes, cudaMemcpyHostToDevice));
+    double s = scale ? *scale : 1.0;
+    CK(P.ctx, cudaMemcpy(P.d_scale + id, &s, sizeof(double), cudaMemcpyHostToDevice));
+    t->generated = true;
+    P.factored = false;
+  }
+  return MP_OK;
+}
+
+mp_status mp_tile_get(mp_tmat* t, int32_t i, int32_t j, void* h_dst, double* scale) {
+  return tile_xfer(t, i, j, h_dst, scale, true);
+}
+
+mp_status mp_tile_set(mp_tmat* t, int32_t i, int32_t j, const void* h_src, double scale) {
+  return tile_xfer(t, i, j, const_cast<void*>(h_src), &scale, false);
+}
+
+mp_status mp_morton_order(mp_ctx* ctx, int64_t n, const double* d_locs_in, double* d_locs_out,
+                          int64_t* d_perm, void* stream) {
+  if (!ctx || !d_locs_in || !d_locs_out || !d_perm) return fail(ctx, MP_ERR_ARG, "null argument");
+  if (n < 1 || n > (int64_t)1 << 31) return fail(ctx, MP_ERR_ARG, "n out of range");
+  if (d_locs_in == d_locs_out) return fail(ctx, MP_ERR_ARG, "d_locs_out may not alias d_locs_in");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(ctx, cudaSetDevice(ctx->device));
+  int64_t n2 = 1024;
+  while (n2 < n) n2 <<= 1;
+  if (ctx->keys_cap < n2) {
+    if (ctx->keys) cudaFree(ctx->keys);
+    ctx->keys = nullptr;
+    ctx->keys_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->keys, sizeof(unsigned long long) * n2);
+    if (e != cudaSuccess) return fail(ctx, MP_ERR_OOM, "morton workspace: %s", cudaGetErrorString(e));
+    ctx->keys_cap = n2;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_morton_keys(d_locs_in, n, n2, ctx->keys, s);
+  launch_bitonic(ctx->keys, n2, s);
+  launch_morton_gather(ctx->keys, d_locs_in, n, d_locs_out, d_perm, s);
+  return check_launch(ctx);
+}
+
+// Generation items for a single-matrix handle.
+static mp_status build_gen_items(mp_tmat* t) {
+  Plan& P = t->P;
+  const MatDesc& M = P.mats[0];
+  std::vector<ItemGen> amax, all;
+  for (int i = 0; i < M.nt; ++i)
+    for (int j = 0; j <= i; ++j) {
+      ItemGen g{};
+      g.tile = M.tile[i * M.nt + j];
+      g.mat = 0;
+      g.ti = i;
+      g.tj = j;
+      g.locs = t->locs;
+      g.n = M.n;
+      g.sigma2 = t->cov.sigma2;
+      g.range = t->cov.range;
+      g.nu = t->cov.nu;
+      g.nugget = t->cov.nugget;
+      g.sigma64 = nullptr;
+      if (P.keep_sigma) {
+        const TileRef r = P.h_tiles[M.sig[i * M.nt + j]];
+        g.sigma64 = (double*)(P.pool[F64] + (size_t)r.idx * P.b * P.b * 8);
+      }
+      if (P.h_tiles[g.tile].dt == E4M3) amax.push_back(g);
+      all.push_back(g);
+    }
+  size_t bytes = sizeof(ItemGen) * (amax.size() + all.size());
+  if (bytes > t->d_gen_cap) {
+    if (t->d_gen) cudaFree(t->d_gen);
+    t->d_gen = nullptr;
+    CK(P.ctx, cudaMalloc(&t->d_gen, bytes));
+    t->d_gen_cap = bytes;
+  }
+  t->gen_off_amax = 0;
+  t->gen_off_all = sizeof(ItemGen) * amax.size();
+  t->gen_n_amax = (int)amax.size();
+  t->gen_n_all = (int)all.size();
+  if (!amax.empty()) CK(P.ctx, cudaMemcpy(t->d_gen, amax.data(), sizeof(ItemGen) * amax.size(), cudaMemcpyHostToDevice));
+  CK(P.ctx, cudaMemcpy(t->d_gen + t->gen_off_all, all.data(), sizeof(ItemGen) * all.size(), cudaMemcpyHostToDevice));
+  return MP_OK;
+}
+
+static bool valid_nu(double nu) { return nu == 0.5 || nu == 1.5 || nu == 2.5; }
+
+mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p) {
+  if (!t || !d_locs) return fail(t ? t->P.ctx : nullptr, MP_ERR_ARG, "null argument");
+  Plan& P = t->P;
+  if (!valid_nu(p.nu)) return fail(P.ctx, MP_ERR_ARG, "nu must be 0.5, 1.5 or 2.5");
+  if (!(p.range > 0.0) || !(p.sigma2 > 0.0) || !(p.nugget >= 0.0))
+    return fail(P.ctx, MP_ERR_ARG, "need range > 0, sigma2 > 0, nugget >= 0");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  std::vector<char> key(sizeof(void*) + sizeof(mp_matern));
+  memcpy(key.data(), &d_locs, sizeof(void*));
+  memcpy(key.data() + sizeof(void*), &p, sizeof(mp_matern));
+  if (key != t->gen_key) {
+    t->locs = d_locs;
+    t->cov = p;
+    if (mp_status st = build_gen_items(t)) return st;
+    t->gen_key = key;
+  }
+  const Arena A = P.arena();
+  cudaStream_t s = P.stream;
+  CK(P.ctx, cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s));
+  launch_gen_amax(A, (const ItemGen*)(t->d_gen + t->gen_off_amax), t->gen_n_amax, s);
+  launch_generate(A, (const ItemGen*)(t->d_gen + t->gen_off_all), t->gen_n_all, s);
+  t->generated = true;
+  P.factored = false;
+  return check_launch(P.ctx);
+}
+
+mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1) {
+  if (!t) return MP_ERR_ARG;
+  Plan& P = t->P;
+  const int nt = P.mats[0].nt;
+  if (k0 < 0 || k1 > nt || k0 > k1) return fail(P.ctx, MP_ERR_ARG, "steps out of range");
+  if (!t->generated) return fail(P.ctx, MP_ERR_STATE, "matrix not generated or loaded");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (k0 == 0) run_launch(P, P.chol[0], P.stream);   // info reset
+  for (size_t l = P.step_begin[k0]; l < P.step_begin[k1]; ++l) run_launch(P, P.chol[l], P.stream);
+  if (k1 == nt) {
+    run_launch(P, P.chol.back(), P.stream);
+    P.factored = true;
+  }
+  return check_launch(P.ctx);
+}
+
+namespace {
+__global__ void k_info_out(const long long* info, long long* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = info[i] == 0x7f7f7f7f7f7f7f7fLL ? 0 : info[i];
+}
+}  // namespace
+
+mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet) {
+  if (!t) return MP_ERR_ARG;
+  Plan& P = t->P;
+  if (!t->generated) return fail(P.ctx, MP_ERR_STATE, "matrix not generated or loaded");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (!P.chol_exec) {
+    mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
+      for (const Launch& L : P.chol) run_launch(P, L, s);
+    }, &P.chol_exec, &P.chol_kernels);
+    if (st) return st;
+  }
+  if (mp_status st = launch_graph(P.ctx, P.chol_exec, P.stream)) return st;
+  if (d_info) k_info_out<<<1, 32, 0, P.stream>>>(P.d_info, (long long*)d_info, 1);
+  if (d_logdet) CK(P.ctx, cudaMemcpyAsync(d_logdet, P.d_logdet, sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  P.factored = true;
+  return check_launch(P.ctx);
+}
+
+mp_status mp_logdet(mp_tmat* t, double* d_out) {
+  if (!t || !d_out) return MP_ERR_ARG;
+  Plan& P = t->P;
+  if (!P.factored) return fail(P.ctx, MP_ERR_STATE, "mp_chol has not been called");
+  CK(P.ctx, cudaMemcpyAsync(d_out, P.d_logdet, sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+  return MP_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------- solves
+
+namespace {
+
+struct SolveSched {
+  std::vector<Launch> l;
+};
+
+enum SolveOp { S_DIAG_F, S_OFF_F, S_DIAG_B, S_OFF_B };
+
+// Forward (trans = 0: out = L^{-1} in) or backward (trans = 1: out = L^{-T}
+// in) tiled solve of the plan's matrices, out of place; `in` is consumed.
+// Vectors are given per matrix as padded N x nrhs blocks with leading
+// dimension ld.
+void build_solve(Plan& P, const std::vector<double*>& in, const std::vector<double*>& out,
+                 const std::vector<int64_t>& ld, const std::vector<int>& nrhs, int trans,
+                 std::vector<Launch>& ls) {
+  const int b = P.b;
+  int maxnt = 0;
+  for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
+  for (int s = 0; s < maxnt; ++s) {
+    std::vector<ItemSolve> diag, off;
+    int maxrhs = 0;
+    for (int m = 0; m < (int)P.mats.size(); ++m) {
+      auto& M = P.mats[m];
+      if (M.nt <= s) continue;
+      const int i = trans ? M.nt - 1 - s : s;
+      ItemSolve d{};
+      d.tile = M.linv[i];
+      d.mat = m;
+      d.xi = in[m] + (int64_t)i * b;
+      d.xj = out[m] + (int64_t)i * b;
+      d.ld = ld[m];
+      d.nrhs = nrhs[m];
+      maxrhs = std::max(maxrhs, nrhs[m]);
+      diag.push_back(d);
+      const int jlo = trans ? 0 : i + 1, jhi = trans ? i : M.nt;
+      for (int j = jlo; j < jhi; ++j) {
+        ItemSolve o = d;
+        o.tile = trans ? M.tile[i * M.nt + j] : M.tile[j * M.nt + i];
+        o.xi = out[m] + (int64_t)i * b;
+        o.xj = in[m] + (int64_t)j * b;
+        off.push_back(o);
+      }
+    }
+    ls.push_back({trans ? S_DIAG_B : S_DIAG_F, P.push(diag), (int)diag.size(), maxrhs});
+    if (!off.empty()) ls.push_back({trans ? S_OFF_B : S_OFF_F, P.push(off), (int)off.size(), maxrhs});
+  }
+}
+
+void run_solve(const Plan& P, const char* dbase, const std::vector<Launch>& ls, const int* gate,
+               cudaStream_t s) {
+  const Arena A = P.arena();
+  for (const Launch& L : ls) {
+    const ItemSolve* it = reinterpret_cast<const ItemSolve*>(dbase + L.off);
+    switch (L.op) {
+      case S_DIAG_F: launch_diag_solve(A, it, L.count, L.kb, 0, gate, s); break;
+      case S_DIAG_B: launch_diag_solve(A, it, L.count, L.kb, 1, gate, s); break;
+      case S_OFF_F: launch_offdiag_solve(A, it, L.count, L.kb, 0, gate, s); break;
+      case S_OFF_B: launch_offdiag_solve(A, it, L.count, L.kb, 1, gate, s); break;
+    }
+  }
+}
+
+}  // namespace
+
+// Solve workspace of a single-matrix handle for nrhs right-hand sides.
+static mp_status ensure_ws(mp_tmat* t, int nrhs) {
+  if (t->ws_nrhs >= nrhs) return MP_OK;
+  for (void* p : t->ws_allocs) cudaFree(p);
+  t->ws_allocs.clear();
+  Plan& P = t->P;
+  const int64_t N = (int64_t)P.mats[0].nt * P.b;
+  auto A = [&](void** p, size_t bytes) -> mp_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(P.ctx, MP_ERR_OOM, "solve workspace: %s", cudaGetErrorString(e));
+    t->ws_allocs.push_back(*p);
+    return MP_OK;
+  };
+  mp_status st;
+  if ((st = A((void**)&t->zp, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->x, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->r, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->w, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->d, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->rowabs, sizeof(double) * N))) return st;
+  if ((st = A((void**)&t->red, sizeof(double) * (5 * nrhs + 2)))) return st;
+  if ((st = A((void**)&t->active, sizeof(int) * nrhs))) return st;
+  if ((st = A((void**)&t->iters, sizeof(int) * nrhs))) return st;
+  if ((st = A((void**)&t->any, sizeof(int) * 2))) return st;
+  t->ws_nrhs = nrhs;
+  if (t->ll_exec) { cudaGraphExecDestroy(t->ll_exec); t->ll_exec = nullptr; }
+  t->ll_key.clear();
+  return MP_OK;
+}
+
+namespace {
+__global__ void k_refine_init(int* active, int* iters, int* any, int nrhs) {
+  int c = threadIdx.x;
+  for (int i = c; i < nrhs; i += blockDim.x) { active[i] = 1; iters[i] = 0; }
+  if (c == 0) *any = 1;
+}
+__global__ void k_copy_iters(const int* src, int32_t* dst, int nrhs) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nrhs) dst[c] = src[c];
+}
+}  // namespace
+
+extern "C" mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, int32_t nrhs) {
+  if (!t || !d_B) return MP_ERR_ARG;
+  Plan& P = t->P;
+  const MatDesc& M = P.mats[0];
+  if (!P.factored) return fail(P.ctx, MP_ERR_STATE, "mp_chol has not been called");
+  if (nrhs < 1 || ldb < M.n) return fail(P.ctx, MP_ERR_ARG, "need nrhs >= 1 and ldb >= n");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (mp_status st = ensure_ws(t, nrhs)) return st;
+  const int64_t N = (int64_t)M.nt * P.b;
+  // solve on the padded copy, then copy the first n rows back
+  std::vector<char> saved;
+  saved.swap(P.h_items);
+  std::vector<Launch> ls;
+  build_solve(P, {t->x}, {t->w}, {N}, {nrhs}, trans ? 1 : 0, ls);
+  size_t bytes = P.h_items.size();
+  if (bytes > t->d_sitems_cap) {
+    if (t->d_sitems) cudaFree(t->d_sitems);
+    t->d_sitems = nullptr;
+    cudaError_t e = cudaMalloc(&t->d_sitems, bytes);
+    if (e != cudaSuccess) { P.h_items.swap(saved); return fail(P.ctx, MP_ERR_OOM, "solve items"); }
+    t->d_sitems_cap = bytes;
+  }
+  cudaError_t e = cudaMemcpyAsync(t->d_sitems, P.h_items.data(), bytes, cudaMemcpyHostToDevice, P.stream);
+  cudaStreamSynchronize(P.stream);
+  P.h_items.swap(saved);
+  if (e != cudaSuccess) return fail(P.ctx, MP_ERR_CUDA, "solve items copy");
+  // the loglik graph caches item bytes in d_sitems: invalidate it
+  if (t->ll_exec) { cudaGraphExecDestroy(t->ll_exec); t->ll_exec = nullptr; t->ll_key.clear(); }
+  launch_copy_pad(d_B, ldb, t->x, N, M.n, N, nrhs, nullptr, P.stream);
+  run_solve(P, t->d_sitems, ls, nullptr, P.stream);
+  launch_copy_pad(t->w, N, d_B, ldb, M.n, M.n, nrhs, nullptr, P.stream);
+  return check_launch(P.ctx);
+}
+
+extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32_t nrhs,
+                               int32_t refine_iters, double* d_ll, double* d_quad,
+                               int32_t* d_iters) {
+  if (!t || !d_z || !d_ll) return MP_ERR_ARG;
+  Plan& P = t->P;
+  const MatDesc& M = P.mats[0];
+  if (!P.factored) return fail(P.ctx, MP_ERR_STATE, "mp_chol has not been called");
+  if (nrhs < 1 || ldz < M.n) return fail(P.ctx, MP_ERR_ARG, "need nrhs >= 1 and ldz >= n");
+  if (refine_iters < 0 || refine_iters > 100) return fail(P.ctx, MP_ERR_ARG, "refine_iters in [0, 100]");
+  if (refine_iters > 0 && !P.keep_sigma)
+    return fail(P.ctx, MP_ERR_STATE, "refinement needs MP_TMAT_KEEP_SIGMA");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (mp_status st = ensure_ws(t, nrhs)) return st;
+  std::vector<char> key(sizeof(void*) * 4 + sizeof(int64_t) + 2 * sizeof(int32_t));
+  {
+    char* k = key.data();
+    memcpy(k, &d_z, 8); memcpy(k + 8, &d_ll, 8); memcpy(k + 16, &d_quad, 8); memcpy(k + 24, &d_iters, 8);
+    memcpy(k + 32, &ldz, 8); memcpy(k + 40, &nrhs, 4); memcpy(k + 44, &refine_iters, 4);
+  }
+  if (!t->ll_exec || key != t->ll_key) {
+    const int64_t N = (int64_t)M.nt * P.b;
+    std::vector<char> saved;
+    saved.swap(P.h_items);
+    // r -> w (forward), w -> x or w -> d (backward)
+    std::vector<Launch> fwd_rw, bwd_wx, bwd_wd;
+    build_solve(P, {t->r}, {t->w}, {N}, {nrhs}, 0, fwd_rw);
+    build_solve(P, {t->w}, {t->x}, {N}, {nrhs}, 1, bwd_wx);
+    build_solve(P, {t->w}, {t->d}, {N}, {nrhs}, 1, bwd_wd);
+    std::vector<ItemResid> res;
+    for (int i = 0; i < M.nt && refine_iters > 0; ++i) {
+      ItemResid it{};
+      it.mat = 0;
+      it.ti = i;
+      it.nt = M.nt;
+      it.sig = P.d_sig;
+      it.x = t->x;
+      it.z = t->zp;
+      it.r = t->r;
+      it.rowabs = t->rowabs;
+      it.ld = N;
+      it.nrhs = nrhs;
+      res.push_back(it);
+    }
+    size_t res_off = P.push(res);
+    size_t bytes = P.h_items.size();
+    if (bytes > t->d_sitems_cap) {
+      if (t->d_sitems) cudaFree(t->d_sitems);
+      t->d_sitems = nullptr;
+      cudaError_t e = cudaMalloc(&t->d_sitems, bytes);
+      if (e != cudaSuccess) { P.h_items.swap(saved); return fail(P.ctx, MP_ERR_OOM, "solve items"); }
+      t->d_sitems_cap = bytes;
+    }
+    cudaError_t e = cudaMemcpy(t->d_sitems, P.h_items.data(), bytes, cudaMemcpyHostToDevice);
+    P.h_items.swap(saved);
+    if (e != cudaSuccess) return fail(P.ctx, MP_ERR_CUDA, "solve items copy");
+    double* red = t->red;
+    double *zmax = red, *xmax = red + nrhs, *rmax = red + 2 * nrhs, *quad = red + 3 * nrhs,
+           *snorm = red + 4 * nrhs;
+    const int64_t n = M.n;
+    const char* db = t->d_sitems;
+    const ItemResid* ri = reinterpret_cast<const ItemResid*>(db + res_off);
+    mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
+      launch_copy_pad(d_z, ldz, t->zp, N, n, N, nrhs, nullptr, s);
+      launch_copy_pad(t->zp, N, t->r, N, N, N, nrhs, nullptr, s);
+      k_refine_init<<<1, 128, 0, s>>>(t->active, t->iters, t->any, nrhs);
+      run_solve(P, db, fwd_rw, nullptr, s);
+      if (refine_iters == 0) {
+        launch_dot(t->w, t->w, N, N, nrhs, quad, s);
+      } else {
+        run_solve(P, db, bwd_wx, nullptr, s);
+        launch_colmax(t->zp, n, N, nrhs, zmax, nullptr, s);
+        for (int itr = 0; itr < refine_iters; ++itr) {
+          launch_residual(P.arena(), ri, (int)res.size(), nrhs, itr == 0, t->any, s);
+          if (itr == 0) launch_colmax(t->rowabs, n, N, 1, snorm, t->any, s);
+          launch_colmax(t->r, n, N, nrhs, rmax, t->any, s);
+          launch_colmax(t->x, n, N, nrhs, xmax, t->any, s);
+          launch_refine_check(rmax, xmax, zmax, snorm, n, nrhs, t->active, t->iters, t->any,
+                              t->any, s);
+          run_solve(P, db, fwd_rw, t->any, s);
+          run_solve(P, db, bwd_wd, t->any, s);
+          launch_axpy_active(t->x, t->d, N, N, nrhs, t->active, t->any, s);
+        }
+        launch_dot(t->zp, t->x, N, N, nrhs, quad, s);
+      }
+      launch_loglik(P.d_logdet, quad, n, nrhs, d_ll, s);
+      if (d_quad) cudaMemcpyAsync(d_quad, quad, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, s);
+      if (d_iters) k_copy_iters<<<(nrhs + 127) / 128, 128, 0, s>>>(t->iters, d_iters, nrhs);
+    }, &t->ll_exec, &t->ll_kernels);
+    if (st) return st;
+    t->ll_key = key;
+  }
+  return launch_graph(P.ctx, t->ll_exec, P.stream);
+}
+
+extern "C" mp_status mp_gemm(mp_ctx* ctx, mp_dtype dtype, char ta, char tb, int64_t m, int64_t n,
+                             int64_t k, double alpha, const void* d_A, int64_t lda,
+                             const void* d_B, int64_t ldb, double beta, void* d_C, int64_t ldc,
+                             void* stream) {
+  if (!ctx) return MP_ERR_ARG;
+  if ((int)dtype < 0 || (int)dtype >= NDT) return fail(ctx, MP_ERR_ARG, "bad dtype");
+  auto tr = [](char c) { return c == 'T' || c == 't' ? 1 : (c == 'N' || c == 'n' ? 0 : -1); };
+  const int a = tr(ta), bb = tr(tb);
+  if (a < 0 || bb < 0) return fail(ctx, MP_ERR_ARG, "ta/tb must be 'N' or 'T'");
+  if (m < 0 || n < 0 || k < 0) return fail(ctx, MP_ERR_ARG, "negative size");
+  if (m == 0 || n == 0) return MP_OK;
+  if (!d_A || !d_B || !d_C) return fail(ctx, MP_ERR_ARG, "null matrix");
+  if (ldc < m || lda < (a ? k : m) || ldb < (bb ? n : k))
+    return fail(ctx, MP_ERR_ARG, "leading dimension too small");
+  if (m >= (int64_t)65535 * 64 || n >= (int64_t)65535 * 64)
+    return fail(ctx, MP_ERR_ARG, "m or n too large");
+  CK(ctx, cudaSetDevice(ctx->device));
+  launch_gemm((int)dtype, a, bb, m, n, k, alpha, d_A, lda, d_B, ldb, beta, d_C, ldc,
+              (cudaStream_t)stream);
+  return check_launch(ctx);
+}
+
+// ------------------------------------------------------------------ batch
+
+namespace {
+
+struct ItemBatchOut {
+  const double* w;     // forward-solved vectors (N x nrhs, ld N)
+  int64_t n, N;
+  int32_t nrhs, mat;
+  double* ll;          // output slot
+  int32_t* status;
+  int32_t pad_[2];
+};
+
+__global__ void k_batch_out(const ItemBatchOut* items, int count, const double* logdet,
+                            const long long* info) {
+  const int m = blockIdx.x;
+  if (m >= count) return;
+  const ItemBatchOut it = items[m];
+  __shared__ double red[8];
+  const double log2pi = 1.8378770664093454836;
+  for (int c = 0; c < it.nrhs; ++c) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < it.N; i += blockDim.x) {
+      double v = it.w[(int64_t)c * it.N + i];
+      s += v * v;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; ++w) s += red[w];
+      it.ll[c] = -0.5 * (double)it.n * log2pi - 0.5 * logdet[it.mat] - 0.5 * s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    it.status[0] = info[it.mat] == 0x7f7f7f7f7f7f7f7fLL ? MP_OK : MP_ERR_NOT_SPD;
+}
+
+struct ItemBatchCopy {
+  const double* src;
+  double* dst;
+  int64_t n, N;
+  int32_t nrhs, pad_;
+};
+
+__global__ void k_batch_copy(const ItemBatchCopy* items) {
+  const ItemBatchCopy it = items[blockIdx.x];
+  for (int c = 0; c < it.nrhs; ++c)
+    for (int64_t i = threadIdx.x; i < it.N; i += blockDim.x)
+      it.dst[(int64_t)c * it.N + i] = i < it.n ? it.src[(int64_t)c * it.n + i] : 0.0;
+}
+
+}  // namespace
+
+extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
+                                     void* stream, mp_batch** out) {
+  if (!ctx || !reqs || !out || count < 1) return fail(ctx, MP_ERR_ARG, "bad batch arguments");
+  int64_t nmax = 0;
+  for (int r = 0; r < count; ++r) {
+    const mp_request& q = reqs[r];
+    if (q.n < 1 || !q.d_locs || !q.d_z || q.nrhs < 1)
+      return fail(ctx, MP_ERR_ARG, "request %d: bad n, pointers or nrhs", r);
+    if (q.refine_iters != 0) return fail(ctx, MP_ERR_ARG, "request %d: batched refinement is not supported", r);
+    if (!valid_nu(q.cov.nu) || !(q.cov.range > 0) || !(q.cov.sigma2 > 0) || !(q.cov.nugget >= 0))
+      return fail(ctx, MP_ERR_ARG, "request %d: bad covariance parameters", r);
+    nmax = std::max(nmax, q.n);
+  }
+  if (b == 0) b = nmax <= 2048 ? 128 : 256;   // tuned choice for uneven small n
+  if (b < 128 || b > 1024 || b % 128) return fail(ctx, MP_ERR_ARG, "b must be a multiple of 128 in [128, 1024]");
+  CK(ctx, cudaSetDevice(ctx->device));
+  mp_batch* B = new mp_batch;
+  B->P.ctx = ctx;
+  B->P.b = b;
+  B->P.stream = (cudaStream_t)stream;
+  B->count = count;
+  B->reqs.assign(reqs, reqs + count);
+  Plan& P = B->P;
+  mp_status st = MP_OK;
+  for (int r = 0; r < count && st == MP_OK; ++r) st = add_matrix(P, reqs[r].n, reqs[r].h_map);
+  if (st == MP_OK) st = finish_plan(P);
+  if (st != MP_OK) { delete B; return st; }
+  // workspace: padded vectors, outputs
+  int64_t vec_total = 0;
+  for (int r = 0; r < count; ++r) {
+    vec_total += (int64_t)P.mats[r].nt * b * reqs[r].nrhs;
+    B->total_rhs += reqs[r].nrhs;
+  }
+  void* p;
+  if ((st = P.alloc(&p, sizeof(double) * vec_total))) { delete B; return st; }
+  double* vec = (double*)p;
+  if ((st = P.alloc(&p, sizeof(double) * vec_total))) { delete B; return st; }
+  double* wout = (double*)p;
+  if ((st = P.alloc(&p, sizeof(double) * B->total_rhs))) { delete B; return st; }
+  B->d_llbuf = (double*)p;
+  if ((st = P.alloc(&p, sizeof(int32_t) * count))) { delete B; return st; }
+  B->d_stbuf = (int32_t*)p;
+  // generation items
+  std::vector<ItemGen> gamax, gall;
+  std::vector<ItemBatchCopy> cp;
+  std::vector<ItemBatchOut> outs;
+  std::vector<double*> vp, wp;
+  std::vector<int64_t> ld;
+  std::vector<int> nr;
+  int64_t vo = 0;
+  int rhs_o = 0;
+  for (int r = 0; r < count; ++r) {
+    const MatDesc& M = P.mats[r];
+    for (int i = 0; i < M.nt; ++i)
+      for (int j = 0; j <= i; ++j) {
+        ItemGen g{};
+        g.tile = M.tile[i * M.nt + j];
+        g.mat = r;
+        g.ti = i;
+        g.tj = j;
+        g.locs = reqs[r].d_locs;
+        g.n = M.n;
+        g.sigma2 = reqs[r].cov.sigma2;
+        g.range = reqs[r].cov.range;
+        g.nu = reqs[r].cov.nu;
+        g.nugget = reqs[r].cov.nugget;
+        if (P.h_tiles[g.tile].dt == E4M3) gamax.push_back(g);
+        gall.push_back(g);
+      }
+    const int64_t N = (int64_t)M.nt * b;
+    ItemBatchCopy c{reqs[r].d_z, vec + vo, M.n, N, reqs[r].nrhs, 0};
+    cp.push_back(c);
+    ItemBatchOut o{};
+    o.w = wout + vo;
+    o.n = M.n;
+    o.N = N;
+    o.nrhs = reqs[r].nrhs;
+    o.mat = r;
+    o.ll = B->d_llbuf + rhs_o;
+    o.status = B->d_stbuf + r;
+    outs.push_back(o);
+    vp.push_back(vec + vo);
+    wp.push_back(wout + vo);
+    ld.push_back(N);
+    nr.push_back(reqs[r].nrhs);
+    vo += N * reqs[r].nrhs;
+    rhs_o += reqs[r].nrhs;
+  }
+  size_t off_ga = P.push(gamax), off_g = P.push(gall), off_cp = P.push(cp), off_out = P.push(outs);
+  std::vector<Launch> fwd;
+  build_solve(P, vp, wp, ld, nr, 0, fwd);
+  if ((st = upload_items(P))) { delete B; return st; }
+  st = capture_graph(ctx, P.cap, [&](cudaStream_t s) {
+    const Arena A = P.arena();
+    cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s);
+    launch_gen_amax(A, P.item<ItemGen>(off_ga), (int)gamax.size(), s);
+    launch_generate(A, P.item<ItemGen>(off_g), (int)gall.size(), s);
+    for (const Launch& L : P.chol) run_launch(P, L, s);
+    k_batch_copy<<<count, 256, 0, s>>>(P.item<ItemBatchCopy>(off_cp));
+    run_solve(P, P.d_items, fwd, nullptr, s);
+    k_batch_out<<<count, 256, 0, s>>>(P.item<ItemBatchOut>(off_out), count, P.d_logdet, P.d_info);
+  }, &B->exec);
+  if (st != MP_OK) { delete B; return st; }
+  *out = B;
+  return MP_OK;
+}
+
+extern "C" void mp_batch_destroy(mp_batch* batch) { delete batch; }
+
+extern "C" mp_status mp_batch_info(mp_batch* batch, int64_t* bytes, int32_t* b) {
+  if (!batch) return MP_ERR_ARG;
+  if (bytes) *bytes = batch->P.bytes;
+  if (b) *b = batch->P.b;
+  return MP_OK;
+}
+
+extern "C" mp_status mp_batch_run(mp_batch* batch, double* d_ll, int32_t* d_status) {
+  if (!batch || !d_ll || !d_status) return MP_ERR_ARG;
+  Plan& P = batch->P;
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (mp_status st = launch_graph(P.ctx, batch->exec, P.stream)) return st;
+  CK(P.ctx, cudaMemcpyAsync(d_ll, batch->d_llbuf, sizeof(double) * batch->total_rhs,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  CK(P.ctx, cudaMemcpyAsync(d_status, batch->d_stbuf, sizeof(int32_t) * batch->count,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  return MP_OK;
+}
+
+extern "C" mp_status mp_loglik_batch(mp_ctx* ctx, int32_t count, const mp_request* reqs,
+                                     double* d_ll, int32_t* d_status, void* stream) {
+  mp_batch* B = nullptr;
+  if (mp_status st = mp_batch_create(ctx, count, reqs, 0, stream, &B)) return st;
+  mp_status st = mp_batch_run(B, d_ll, d_status);
+  if (st == MP_OK) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = fail(ctx, MP_ERR_CUDA, "batch: %s", cudaGetErrorString(e));
+  }
+  mp_batch_destroy(B);
+  return st;
+}
+
+// ------------------------------------------------- planning and statistics
+
+extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const double* d_locs,
+                                   mp_matern p, double* d_norms, void* stream) {
+  if (!ctx || !d_locs || !d_norms) return fail(ctx, MP_ERR_ARG, "null argument");
+  if (n < 1 || b < 128 || b > 1024 || b % 128) return fail(ctx, MP_ERR_ARG, "bad n or b");
+  if (!valid_nu(p.nu) || !(p.range > 0.0) || !(p.sigma2 > 0.0) || !(p.nugget >= 0.0))
+    return fail(ctx, MP_ERR_ARG, "bad covariance parameters");
+  CK(ctx, cudaSetDevice(ctx->device));
+  const int nt = (int)((n + b - 1) / b);
+  std::vector<ItemGen> items;
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j <= i; ++j) {
+      ItemGen g{};
+      g.ti = i; g.tj = j; g.locs = d_locs; g.n = n;
+      g.sigma2 = p.sigma2; g.range = p.range; g.nu = p.nu; g.nugget = p.nugget;
+      items.push_back(g);
+    }
+  const int parts = b / 16;
+  ItemGen* d_items = nullptr;
+  double* partial = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(ctx, cudaMalloc(&d_items, sizeof(ItemGen) * items.size()));
+  cudaError_t e = cudaMalloc(&partial, sizeof(double) * items.size() * parts);
+  if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(ItemGen) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_norms, 0, sizeof(double) * nt * nt, s);
+  if (e == cudaSuccess) {
+    launch_tile_norms(b, d_items, (int)items.size(), nt, partial, d_norms, s);
+    e = cudaStreamSynchronize(s);
+  }
+  cudaFree(d_items);
+  if (partial) cudaFree(partial);
+  if (e != cudaSuccess) return fail(ctx, MP_ERR_CUDA, "tile norms: %s", cudaGetErrorString(e));
+  return MP_OK;
+}
+
+static double unit_roundoff(int dt) {
+  switch (dt) {
+    case F64: return 0x1p-53;
+    case F32: return 0x1p-24;
+    case BF16: return 0x1p-8;
+    case F16: return 0x1p-11;
+    default: return 0x1p-4;
+  }
+}
+
+extern "C" mp_status mp_map_guarded(int32_t nt, const double* h_norms, int32_t band, uint8_t near_dt,
+                                    uint8_t far_dt, double eps, uint8_t* h_map) {
+  if (nt < 1 || !h_norms || !h_map || band < 0 || near_dt >= NDT || far_dt >= NDT || !(eps > 0))
+    return fail(nullptr, MP_ERR_ARG, "bad map arguments");
+  double tot = 0.0;
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = h_norms[i * nt + j];
+      tot += (i == j ? 1.0 : 2.0) * v * v;
+    }
+  const double bound = eps * sqrt(tot) / nt;
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j < nt; ++j) {
+      uint8_t m = 255;
+      if (j == i) m = F64;
+      else if (j < i) {
+        if (i - j <= band) m = near_dt;
+        else m = unit_roundoff(far_dt) * h_norms[i * nt + j] <= bound ? far_dt : near_dt;
+      }
+      h_map[i * nt + j] = m;
+    }
+  return MP_OK;
+}
+
+extern "C" mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* gen_kernels,
+                                   int64_t* loglik_kernels) {
+  if (!t) return MP_ERR_ARG;
+  if (chol_kernels) *chol_kernels = t->P.chol_kernels;
+  if (gen_kernels) *gen_kernels = (t->gen_n_amax > 0 ? 1 : 0) + 1;
+  if (loglik_kernels) *loglik_kernels = t->ll_kernels;
+  return MP_OK;
+}
+
+namespace {
+int op_class(int op) {
+  switch (op) {
+    case OP_POTRF: return 0;
+    case OP_ITRSM: return 1;
+    case OP_ISYRK: return 2;
+    case OP_PANEL: return 3;
+    case OP_ROUND: return 4;
+    case OP_UPD64: return 5;
+    case OP_UPD32: return 6;
+    case OP_FP8R: return 8;
+    default: return 9;
+  }
+}
+}  // namespace
+
+extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, int64_t* h_launches,
+                                     double* h_flops) {
+  if (!t || nclass < MP_PROFILE_CLASSES || !h_ms || !h_launches || !h_flops) return MP_ERR_ARG;
+  Plan& P = t->P;
+  if (!t->generated) return fail(P.ctx, MP_ERR_STATE, "matrix not generated or loaded");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  for (int c = 0; c < nclass; ++c) { h_ms[c] = 0.f; h_launches[c] = 0; h_flops[c] = 0.0; }
+  const size_t nl = P.chol.size();
+  std::vector<cudaEvent_t> ev(nl + 1);
+  for (auto& e : ev) CK(P.ctx, cudaEventCreate(&e));
+  CK(P.ctx, cudaEventRecord(ev[0], P.stream));
+  for (size_t l = 0; l < nl; ++l) {
+    run_launch(P, P.chol[l], P.stream);
+    cudaEventRecord(ev[l + 1], P.stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(P.stream);
+  const double b = P.b, nb = 32;
+  for (size_t l = 0; l < nl && e == cudaSuccess; ++l) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
+    const Launch& L = P.chol[l];
+    const int c = op_class(L.op);
+    h_ms[c] += ms;
+    if (c == 9 && L.count == 0) continue;
+    h_launches[c] += 1;
+    double m = b / nb - L.kb - 1;
+    switch (L.op) {
+      case OP_POTRF: h_flops[c] += L.count * nb * nb * nb / 3.0; break;
+      case OP_ITRSM: h_flops[c] += L.count * m * nb * nb * nb; break;
+      case OP_ISYRK: h_flops[c] += L.count * (m * (m + 1) / 2) * 2.0 * nb * nb * nb; break;
+      case OP_PANEL: h_flops[c] += L.count * b * b * b; break;
+      case OP_UPD64:
+      case OP_UPD32: {
+        const ItemUpd* it = reinterpret_cast<const ItemUpd*>(P.h_items.data() + L.off);
+        for (int q = 0; q < L.count; ++q) h_flops[c] += it[q].syrk ? b * b * (b + 1) : 2.0 * b * b * b;
+        break;
+      }
+      default: break;
+    }
+  }
+  for (auto& ev_ : ev) cudaEventDestroy(ev_);
+  if (e != cudaSuccess) return fail(P.ctx, MP_ERR_CUDA, "profile: %s", cudaGetErrorString(e));
+  P.factored = true;
+  return check_launch(P.ctx);
+}

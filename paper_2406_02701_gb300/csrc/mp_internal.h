@@ -1,0 +1,193 @@
+// Internal types of the mpchol runtime: the tile arena, work items of every
+// launch, and the host launchers each kernel file exports.
+//
+// A plan owns one arena: one device pool per storage format, each pool a
+// stack of b x b row-major tiles.  A tile is named by an int32 id into the
+// tile table (format, index in its pool).  Every kernel reads its work from
+// a device array of items, so one launch can serve tiles of many matrices
+// (the batched schedule) as well as one.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mp {
+
+enum : int { F64 = 0, F32 = 1, BF16 = 2, F16 = 3, E4M3 = 4, NDT = 5 };
+
+__host__ __device__ inline int esize(int dt) {
+  return dt == F64 ? 8 : dt == F32 ? 4 : dt == E4M3 ? 1 : 2;
+}
+// precision rank of the update rule: F64 > F32 > 16-bit > E4M3
+__host__ __device__ inline int level(int dt) {
+  return dt == F64 ? 4 : dt == F32 ? 3 : dt == E4M3 ? 1 : 2;
+}
+
+struct TileRef {
+  int32_t dt;
+  int32_t idx;   // index in pool[dt]
+};
+
+// Device view of an arena, passed by value to kernels.
+struct Arena {
+  char* pool[NDT];
+  const TileRef* tiles;           // tile table
+  double* scale;                  // per tile: E4M3 scale (1 otherwise)
+  unsigned long long* amax;       // per tile: amax as float64 bits (atomicMax)
+  int b;
+  int pad_;
+};
+
+template <typename T>
+__host__ __device__ inline T* tile_ptr(const Arena& A, int id) {
+  TileRef r = A.tiles[id];
+  return reinterpret_cast<T*>(A.pool[r.dt] + (int64_t)r.idx * A.b * A.b * esize(r.dt));
+}
+__host__ __device__ inline char* tile_bytes(const Arena& A, int id) {
+  TileRef r = A.tiles[id];
+  return A.pool[r.dt] + (int64_t)r.idx * A.b * A.b * esize(r.dt);
+}
+
+// ---- work items -----------------------------------------------------------
+
+// POTRF of one 64 x 64 block (kb, kb) of an FP64 diagonal tile, its inverse,
+// and the inner TRSM / SYRK of the same tile.
+struct ItemDiag {
+  int32_t tile;       // FP64 diagonal tile
+  int32_t kb;         // inner block index
+  int32_t ldslot;     // index into the log-determinant partial sums
+  int32_t mat;        // matrix index (info word)
+  int64_t row0;       // global row of the tile's first row
+  double* dinv;       // 64 x 64 inverse of block kb (row-major)
+};
+
+// Panel TRSM: X = A_ik L_kk^{-T} in float64 into a scratch slot.
+struct ItemPanel {
+  int32_t tile;       // A_ik
+  int32_t diag;       // L_kk
+  double* dinv;       // (b/64) inverses of the diagonal 64-blocks of L_kk
+  double* x;          // b x b float64 scratch
+};
+
+// Rounds a panel scratch slot into its tile and its shadow copies (the tile
+// rounded into each lower format a consumer's product runs in).
+constexpr int MAX_SHADOW = 3;
+struct ItemRound {
+  int32_t tile;
+  int32_t shadow[MAX_SHADOW];   // -1: unused
+  const double* x;
+};
+
+// Trailing update C -= A B^T of one target tile.
+struct ItemUpd {
+  int32_t c, a, b;    // tile ids (a, b may be shadows already in the kind)
+  int32_t syrk;       // 1: C is a diagonal tile (lower sub-blocks only)
+  float* v;           // E4M3 target: b x b FP32 scratch for the new values
+  int32_t vslot;      // E4M3 target: amax slot (index into Arena.amax)
+  int32_t pad_;
+};
+
+// Rounds an E4M3 target from its FP32 scratch with the new scale.
+struct ItemFp8 {
+  int32_t tile;
+  int32_t vslot;
+  const float* v;
+};
+
+// Generation of one lower tile.
+struct ItemGen {
+  int32_t tile;
+  int32_t mat;
+  int32_t ti, tj;     // tile coordinates
+  const double* locs; // n x 2
+  int64_t n;
+  double sigma2, range, nu, nugget;
+  double* sigma64;    // optional float64 copy (b x b row-major) or null
+};
+
+// Solve items.  Diagonal: tile = L_ii^{-T} (FP64), xj = X-product of xi
+// (out of place).  Off-diagonal: tile = L tile, xi = solved segment,
+// xj = segment still to be solved (updated in place).
+struct ItemSolve {
+  int32_t tile;
+  int32_t mat;
+  double* xi;
+  double* xj;
+  int64_t ld;         // leading dimension of the vectors
+  int32_t nrhs;
+  int32_t pad_;
+};
+
+// Residual rows of one block row of a matrix: r_i = z_i - sum_j S_ij x_j.
+struct ItemResid {
+  int32_t mat;
+  int32_t ti;         // block row
+  int32_t nt;
+  int32_t pad_;
+  const int32_t* sig; // nt*nt tile ids of the float64 Sigma copy (lower)
+  const double* x;    // N x nrhs, ld
+  const double* z;    // N x nrhs, ld
+  double* r;          // N x nrhs, ld
+  double* rowabs;     // N: sum_j |S_ij| (for ||Sigma||_inf)
+  int64_t ld;
+  int32_t nrhs;
+  int32_t pad2_;
+};
+
+// ---- host launchers (each .cu file exports its own) -----------------------
+
+// k_gen.cu
+void launch_morton_keys(const double* locs, int64_t n, int64_t n2, unsigned long long* keys,
+                        cudaStream_t s);
+void launch_bitonic(unsigned long long* keys, int64_t n2, cudaStream_t s);
+void launch_morton_gather(const unsigned long long* keys, const double* in, int64_t n,
+                          double* out, int64_t* perm, cudaStream_t s);
+void launch_gen_amax(const Arena& A, const ItemGen* items, int count, cudaStream_t s);
+void launch_generate(const Arena& A, const ItemGen* items, int count, cudaStream_t s);
+// Frobenius norm of every generated lower tile into norms[ti * nt + tj]
+// (partial: count * b/16 doubles of scratch).
+void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,
+                       double* norms, cudaStream_t s);
+
+// k_fp64.cu
+void launch_potrf_block(const Arena& A, const ItemDiag* items, int count, double* ldparts,
+                        long long* info, cudaStream_t s);
+void launch_inner_trsm(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
+void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
+void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, cudaStream_t s);
+void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaStream_t s);
+
+// k_update.cu
+void launch_update_f32(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
+void launch_update_f64(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
+void launch_fp8_round(const Arena& A, const ItemFp8* items, int count, cudaStream_t s);
+
+// k_solve.cu  (a non-null `gate` pointing at 0 turns a launch into a no-op)
+void launch_diag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
+                       const int* gate, cudaStream_t s);
+void launch_offdiag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
+                          const int* gate, cudaStream_t s);
+void launch_residual(const Arena& A, const ItemResid* items, int count, int nrhs,
+                     int want_rowabs, const int* gate, cudaStream_t s);
+void launch_logdet(const double* ldparts, const int32_t* ldoff, const int32_t* ldcnt, int nmat,
+                   double* logdet, cudaStream_t s);
+void launch_colmax(const double* v, int64_t n, int64_t ld, int nrhs, double* out,
+                   const int* gate, cudaStream_t s);
+void launch_refine_check(const double* rmax, const double* xmax, const double* zmax,
+                         const double* snorm, int64_t n, int nrhs, int* active, int* iters,
+                         int* any, const int* gate, cudaStream_t s);
+void launch_axpy_active(double* x, const double* d, int64_t n, int64_t ld, int nrhs,
+                        const int* active, const int* gate, cudaStream_t s);
+void launch_copy_pad(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n,
+                     int64_t N, int nrhs, const int* gate, cudaStream_t s);
+void launch_dot(const double* a, const double* b, int64_t n, int64_t ld, int nrhs, double* out,
+                cudaStream_t s);
+void launch_loglik(const double* logdet, const double* quad, int64_t n, int nrhs, double* ll,
+                   cudaStream_t s);
+
+// k_gemm.cu
+void launch_gemm(int dt, int ta, int tb, int64_t m, int64_t n, int64_t k, double alpha,
+                 const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                 int64_t ldc, cudaStream_t s);
+
+}  // namespace mp

@@ -1,0 +1,359 @@
+"""ctypes binding of libmpchol.so (include/mpchol.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  `load()` fails loudly when the library is missing -- there is no
+CPU fallback.  PyTorch provides device memory (tensors) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpchol.so")
+
+MP_OK, MP_ERR_ARG, MP_ERR_NOT_SPD, MP_ERR_OOM, MP_ERR_CUDA, MP_ERR_TIMEOUT, MP_ERR_STATE = range(7)
+MP_F64, MP_F32, MP_BF16, MP_F16, MP_E4M3 = range(5)
+MP_TMAT_KEEP_SIGMA = 1
+ELEM_BYTES = {MP_F64: 8, MP_F32: 4, MP_BF16: 2, MP_F16: 2, MP_E4M3: 1}
+
+
+class mp_matern(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("range", C.c_double), ("nu", C.c_double),
+                ("nugget", C.c_double)]
+
+
+class mp_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("h_map", C.c_void_p), ("d_locs", C.c_void_p),
+                ("d_z", C.c_void_p), ("nrhs", C.c_int32), ("refine_iters", C.c_int32),
+                ("cov", mp_matern)]
+
+
+P = C.c_void_p
+_SIGS = {
+    "mp_ctx_create": (C.c_int, [C.c_int, C.POINTER(P)]),
+    "mp_ctx_destroy": (None, [P]),
+    "mp_status_string": (C.c_char_p, [C.c_int]),
+    "mp_last_error": (C.c_int, [P, C.c_char_p, C.c_size_t]),
+    "mp_version": (C.c_char_p, []),
+    "mp_tmat_create": (C.c_int, [P, C.c_int64, C.c_int32, P, C.c_uint32, P, C.POINTER(P)]),
+    "mp_tmat_destroy": (None, [P]),
+    "mp_tmat_info": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "mp_tile_get": (C.c_int, [P, C.c_int32, C.c_int32, P, C.POINTER(C.c_double)]),
+    "mp_tile_set": (C.c_int, [P, C.c_int32, C.c_int32, P, C.c_double]),
+    "mp_morton_order": (C.c_int, [P, C.c_int64, P, P, P, P]),
+    "mp_generate_matern": (C.c_int, [P, P, mp_matern]),
+    "mp_chol": (C.c_int, [P, P, P]),
+    "mp_chol_steps": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "mp_logdet": (C.c_int, [P, P]),
+    "mp_trsm": (C.c_int, [P, C.c_int, P, C.c_int64, C.c_int32]),
+    "mp_loglik": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
+    "mp_tile_norms": (C.c_int, [P, C.c_int64, C.c_int32, P, mp_matern, P, P]),
+    "mp_map_guarded": (C.c_int, [C.c_int32, P, C.c_int32, C.c_uint8, C.c_uint8, C.c_double, P]),
+    "mp_tmat_stats": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]),
+    "mp_chol_profile": (C.c_int, [P, C.c_int32, P, P, P]),
+    "mp_probe_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "mp_gemm": (C.c_int, [P, C.c_int, C.c_char, C.c_char, C.c_int64, C.c_int64, C.c_int64,
+                          C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, P, C.c_int64, P]),
+    "mp_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(mp_request), C.c_int32, P,
+                                  C.POINTER(P)]),
+    "mp_batch_destroy": (None, [P]),
+    "mp_batch_info": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "mp_batch_run": (C.c_int, [P, P, P]),
+    "mp_loglik_batch": (C.c_int, [P, C.c_int32, C.POINTER(mp_request), P, P, P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (building it first when the CUDA toolkit is here and
+    the library is missing or stale) and declares every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmpchol.so not found at {path}; run build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        s = torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = P()
+        self._check(self.lib.mp_ctx_create(device, C.byref(h)), None)
+        self.h = h
+        self.device = device
+
+    def _check(self, st, ctx=None):
+        if st != MP_OK:
+            buf = C.create_string_buffer(512)
+            self.lib.mp_last_error(ctx if ctx is not None else getattr(self, "h", None), buf, 512)
+            raise MPError(st, f"{self.lib.mp_status_string(st).decode()}: {buf.value.decode()}")
+
+    def check(self, st):
+        self._check(st, self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def morton_order(self, locs, stream=None):
+        import torch
+        n = locs.shape[0]
+        out = torch.empty_like(locs)
+        perm = torch.empty(n, dtype=torch.int64, device=locs.device)
+        self.check(self.lib.mp_morton_order(self.h, n, _ptr(locs), _ptr(out), _ptr(perm),
+                                            _stream(stream)))
+        return out, perm
+
+    def tile_norms(self, n, b, locs, sigma2, range_, nu, nugget, stream=None):
+        import torch
+        nt = -(-n // b)
+        out = torch.empty(nt * nt, dtype=torch.float64, device=locs.device)
+        self.check(self.lib.mp_tile_norms(self.h, n, b, _ptr(locs),
+                                          mp_matern(sigma2, range_, nu, nugget), _ptr(out),
+                                          _stream(stream)))
+        return out.view(nt, nt)
+
+    def map_guarded(self, norms, band, near, far, eps):
+        nrm = np.ascontiguousarray(np.asarray(norms, dtype=np.float64))
+        nt = nrm.shape[0]
+        m = np.empty((nt, nt), dtype=np.uint8)
+        self.check(self.lib.mp_map_guarded(nt, nrm.ctypes.data_as(C.c_void_p), band, near, far,
+                                           eps, m.ctypes.data_as(C.c_void_p)))
+        return m
+
+    def fp64_peak(self):
+        v = C.c_double()
+        self.check(self.lib.mp_probe_fp64_peak(self.device, C.byref(v)))
+        return v.value
+
+    def gemm(self, dtype, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, stream=None):
+        self.check(self.lib.mp_gemm(self.h, dtype, ta.encode(), tb.encode(), m, n, k, alpha,
+                                    _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc,
+                                    _stream(stream)))
+
+
+class TiledMatrix:
+    """mp_tmat: an n x n tiled matrix with a per-tile precision map."""
+
+    def __init__(self, ctx: Context, n: int, b: int, pmap=None, keep_sigma=False, stream=None):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.n, self.b = n, b
+        self.nt = -(-n // b)
+        self.stream = stream
+        self._map = None
+        if pmap is not None:
+            self._map = np.ascontiguousarray(np.asarray(pmap, dtype=np.uint8))
+            assert self._map.shape == (self.nt, self.nt)
+        h = P()
+        flags = MP_TMAT_KEEP_SIGMA if keep_sigma else 0
+        mp = None if self._map is None else self._map.ctypes.data_as(C.c_void_p)
+        ctx.check(self.lib.mp_tmat_create(ctx.h, n, b, mp, flags, _stream(stream), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mp_tmat_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, b, nt, by = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64()
+        self.ctx.check(self.lib.mp_tmat_info(self.h, C.byref(n), C.byref(b), C.byref(nt), C.byref(by)))
+        return dict(n=n.value, b=b.value, nt=nt.value, bytes=by.value)
+
+    def dtype(self, i, j):
+        return MP_F64 if self._map is None else int(self._map[i, j])
+
+    def generate(self, locs, sigma2, range_, nu, nugget):
+        self.locs = locs            # keep the borrowed buffer alive
+        self.ctx.check(self.lib.mp_generate_matern(self.h, _ptr(locs),
+                                                   mp_matern(sigma2, range_, nu, nugget)))
+
+    def chol(self):
+        import torch
+        dev = torch.device("cuda", self.ctx.device)
+        info = torch.zeros(1, dtype=torch.int64, device=dev)
+        logdet = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.ctx.check(self.lib.mp_chol(self.h, _ptr(info), _ptr(logdet)))
+        return info, logdet
+
+    def chol_steps(self, k0, k1):
+        self.ctx.check(self.lib.mp_chol_steps(self.h, k0, k1))
+
+    def logdet(self, out):
+        self.ctx.check(self.lib.mp_logdet(self.h, _ptr(out)))
+
+    def trsm(self, B, trans=0):
+        """B: (nrhs, ld) float64 CUDA tensor = column-major n x nrhs."""
+        self.ctx.check(self.lib.mp_trsm(self.h, trans, _ptr(B), B.shape[1], B.shape[0]))
+
+    def loglik(self, zt, refine_iters=0, ll=None, quad=None, iters=None):
+        """zt: (nrhs, ld) float64 CUDA tensor (column-major z).  Returns device
+        tensors (ll, quad, iters)."""
+        import torch
+        nrhs = zt.shape[0]
+        dev = zt.device
+        ll = torch.empty(nrhs, dtype=torch.float64, device=dev) if ll is None else ll
+        quad = torch.empty(nrhs, dtype=torch.float64, device=dev) if quad is None else quad
+        iters = torch.empty(nrhs, dtype=torch.int32, device=dev) if iters is None else iters
+        self.ctx.check(self.lib.mp_loglik(self.h, _ptr(zt), zt.shape[1], nrhs, refine_iters,
+                                          _ptr(ll), _ptr(quad), _ptr(iters)))
+        return ll, quad, iters
+
+    def stats(self):
+        a, g, l = C.c_int64(), C.c_int64(), C.c_int64()
+        self.ctx.check(self.lib.mp_tmat_stats(self.h, C.byref(a), C.byref(g), C.byref(l)))
+        return dict(chol=a.value, generate=g.value, loglik=l.value)
+
+    PROFILE_CLASSES = ["potrf_block", "inner_trsm", "inner_syrk", "panel_trsm", "panel_round",
+                       "update_f64", "update_simt", "update_tc", "fp8_round", "other"]
+
+    def profile(self):
+        k = len(self.PROFILE_CLASSES)
+        ms = np.zeros(k, dtype=np.float32)
+        nl = np.zeros(k, dtype=np.int64)
+        fl = np.zeros(k, dtype=np.float64)
+        self.ctx.check(self.lib.mp_chol_profile(self.h, k, ms.ctypes.data_as(C.c_void_p),
+                                                nl.ctypes.data_as(C.c_void_p),
+                                                fl.ctypes.data_as(C.c_void_p)))
+        return {c: dict(ms=float(ms[i]), launches=int(nl[i]), flops=float(fl[i]))
+                for i, c in enumerate(self.PROFILE_CLASSES)}
+
+    def get_tile(self, i, j):
+        """Returns (values as float64 numpy b x b, raw codes array, scale)."""
+        dt = self.dtype(i, j)
+        raw = np.empty(self.b * self.b * ELEM_BYTES[dt], dtype=np.uint8)
+        s = C.c_double()
+        self.ctx.check(self.lib.mp_tile_get(self.h, i, j, raw.ctypes.data_as(C.c_void_p), C.byref(s)))
+        codes = decode(raw, dt).reshape(self.b, self.b)
+        return codes * s.value, codes, s.value
+
+    def set_tile(self, i, j, codes, scale=1.0):
+        dt = self.dtype(i, j)
+        raw = encode(np.asarray(codes, dtype=np.float64).reshape(-1), dt)
+        self.ctx.check(self.lib.mp_tile_set(self.h, i, j, raw.ctypes.data_as(C.c_void_p), scale))
+
+
+class Batch:
+    """mp_batch: many log-likelihood requests in one CUDA graph."""
+
+    def __init__(self, ctx: Context, reqs, b=0, stream=None):
+        self.ctx, self.lib = ctx, ctx.lib
+        self._keep = []
+        arr = (mp_request * len(reqs))()
+        for k, r in enumerate(reqs):
+            m = r.get("map")
+            mp = None
+            if m is not None:
+                m = np.ascontiguousarray(np.asarray(m, dtype=np.uint8))
+                self._keep.append(m)
+                mp = m.ctypes.data
+            self._keep += [r["locs"], r["zt"]]
+            arr[k] = mp_request(r["n"], mp, r["locs"].data_ptr(), r["zt"].data_ptr(),
+                                r["zt"].shape[0], 0,
+                                mp_matern(r["sigma2"], r["range"], r["nu"], r["nugget"]))
+        h = P()
+        ctx.check(self.lib.mp_batch_create(ctx.h, len(reqs), arr, b, _stream(stream), C.byref(h)))
+        self.h = h
+        self.count = len(reqs)
+        self.total_rhs = sum(r["zt"].shape[0] for r in reqs)
+
+    def info(self):
+        by, b = C.c_int64(), C.c_int32()
+        self.ctx.check(self.lib.mp_batch_info(self.h, C.byref(by), C.byref(b)))
+        return dict(bytes=by.value, b=b.value)
+
+    def run(self, ll=None, status=None):
+        import torch
+        dev = torch.device("cuda", self.ctx.device)
+        ll = torch.empty(self.total_rhs, dtype=torch.float64, device=dev) if ll is None else ll
+        status = torch.empty(self.count, dtype=torch.int32, device=dev) if status is None else status
+        self.ctx.check(self.lib.mp_batch_run(self.h, _ptr(ll), _ptr(status)))
+        return ll, status
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- host-side codecs of the storage formats (for tile upload/download) ----
+
+def decode(raw: np.ndarray, dt: int) -> np.ndarray:
+    import torch
+    if dt == MP_F64:
+        return raw.view(np.float64).copy()
+    if dt == MP_F32:
+        return raw.view(np.float32).astype(np.float64)
+    if dt == MP_F16:
+        return raw.view(np.float16).astype(np.float64)
+    t = torch.from_numpy(raw.copy())
+    if dt == MP_BF16:
+        return t.view(torch.bfloat16).to(torch.float64).numpy()
+    return t.view(torch.float8_e4m3fn).to(torch.float64).numpy()
+
+
+def encode(vals: np.ndarray, dt: int) -> np.ndarray:
+    """Packs values that are already representable in `dt` (exact)."""
+    import torch
+    if dt == MP_F64:
+        return vals.astype(np.float64).view(np.uint8)
+    if dt == MP_F32:
+        return vals.astype(np.float32).view(np.uint8)
+    if dt == MP_F16:
+        return vals.astype(np.float16).view(np.uint8)
+    t = torch.from_numpy(vals.astype(np.float32))
+    if dt == MP_BF16:
+        return t.to(torch.bfloat16).view(torch.uint8).numpy().copy()
+    return t.to(torch.float8_e4m3fn).view(torch.uint8).numpy().copy()

@@ -1,0 +1,389 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Tolerances follow from the arithmetic:
+  * integer work (Morton permutation) is bit-exact;
+  * a value rounded into a storage format may differ by one unit in the last
+    place of that format when the float64 inputs differ in their last bits
+    (CUDA's exp vs libm's) or when the FP32 accumulation order differs (tensor
+    core / CUDA core order vs BLAS order);
+  * FP32 accumulations differ by at most ~K 2^-24 sum|a||b|;
+  * float64 steps agree to a few units of 2^-53 times the condition growth.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mpinputs as I
+from oracle import chol as OC
+from oracle import formats as OF
+from oracle import matern as OM
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_02701_gb300 import mpchol
+    return mpchol.Context(0)
+
+
+DEV = "cuda:0"
+T_BITS = {I.F64: 52, I.F32: 23, I.BF16: 7, I.F16: 10, I.E4M3: 3}
+EMIN = {I.F64: -1022, I.F32: -126, I.BF16: -126, I.F16: -14, I.E4M3: -6}
+
+
+def ulp(x, fmt):
+    ax = np.maximum(np.abs(x), 1e-300)
+    e = np.maximum(np.floor(np.log2(ax)), EMIN[fmt])
+    return np.ldexp(1.0, (e - T_BITS[fmt]).astype(int))
+
+
+def assert_close_fmt(got, ref, fmt, extra=0.0, ulps=1, frac=1.0, what=""):
+    """|got - ref| <= ulps ulp_fmt + extra everywhere; and differing entries
+    are at most `frac` of all."""
+    d = np.abs(got - ref)
+    tol = ulps * ulp(np.maximum(np.abs(got), np.abs(ref)), fmt) + extra
+    bad = d > tol
+    assert not bad.any(), f"{what}: {bad.sum()} entries off, max excess {(d - tol).max():.3g}"
+    if frac < 1.0:
+        assert (d > 0).mean() <= frac, f"{what}: {(d > 0).mean():.4f} of entries differ"
+
+
+def _mk(ctx, n, b, pmap, keep_sigma=False):
+    from paper_2406_02701_gb300 import mpchol
+    return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma)
+
+
+# --------------------------------------------------------------- Morton ----
+
+@pytest.mark.parametrize("n", [1, 5, 1000, 3000, 70000])
+def test_morton_order_bit_exact(ctx, n):
+    locs = I.points(n, 17)
+    if n > 5:
+        locs[7] = locs[3]          # a tie: keeps index order
+        locs[11] = [1.0, 0.0]      # edges of the quantiser
+    srt, perm = OM.morton_order(locs)
+    out, dperm = ctx.morton_order(torch.from_numpy(locs).to(DEV))
+    assert np.array_equal(dperm.cpu().numpy(), perm)
+    assert np.array_equal(out.cpu().numpy(), srt)
+
+
+# ------------------------------------------------------------ generation ---
+
+ALL_MAP = None
+
+
+def _mixed_map(nt):
+    m = np.full((nt, nt), 255, dtype=np.uint8)
+    cyc = [I.F32, I.BF16, I.F16, I.E4M3]
+    for i in range(nt):
+        m[i, i] = I.F64
+        for j in range(i):
+            m[i, j] = cyc[(i + 2 * j) % 4]
+    return m
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_generation_matches_oracle_every_format(ctx, nu):
+    n, b = 700, 128              # 6 tiles per side, ragged last tile
+    nt = -(-n // b)
+    pmap = _mixed_map(nt)
+    locs = I.points(n, 5)
+    T = _mk(ctx, n, b, pmap)
+    dl = torch.from_numpy(locs).to(DEV)
+    T.generate(dl, 1.3, 0.08, nu, 1e-4)
+    torch.cuda.synchronize()
+    ref = OC.tiled_from_dense(OM.covariance(locs, nu, 0.08, 1.3, 1e-4), b, pmap)
+    for i in range(nt):
+        for j in range(i + 1):
+            got, codes, s = T.get_tile(i, j)
+            rt = ref.tiles[(i, j)]
+            fmt = int(pmap[i, j])
+            if i == j:
+                got, want = np.tril(got), np.tril(rt.values())
+            else:
+                want = rt.values()
+            if fmt == I.E4M3:
+                assert s == rt.scale, (i, j, s, rt.scale)
+                assert_close_fmt(codes, rt.codes, fmt, frac=1e-3, what=f"tile {i},{j}")
+            elif fmt == I.F64:
+                assert np.allclose(got, want, rtol=4e-16, atol=1e-300), (i, j)
+            else:
+                assert_close_fmt(got, want, fmt, frac=1e-3, what=f"tile {i},{j}")
+
+
+def test_tile_norms_and_guarded_map(ctx):
+    n, b = 1500, 128
+    nt = -(-n // b)
+    locs, _ = OM.morton_order(I.points(n, 14))
+    dl = torch.from_numpy(locs).to(DEV)
+    got = ctx.tile_norms(n, b, dl, 1.0, 0.05, 1.5, 1e-4).cpu().numpy()
+    ref = OC.tile_norms(OM.covariance(locs, 1.5, 0.05, 1.0, 1e-4), b)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    for far, eps in [(I.BF16, 1e-5), (I.E4M3, 1e-3), (I.BF16, 1e-7)]:
+        m = ctx.map_guarded(got, 2, I.F32, far, eps)
+        assert np.array_equal(m, OC.guarded_map(ref, 2, I.F32, far, eps))
+        lo = np.tril_indices(nt, -3)
+        assert 0 < (m[lo] == far).sum() < len(lo[0]) or eps == 1e-7
+
+
+# ------------------------------------------------------ one step at a time --
+
+def _load_state(T, state, nt):
+    for (i, j), t in state.tiles.items():
+        T.set_tile(i, j, t.codes, t.scale)
+
+
+def _abs_prod(a, bmat):
+    return np.abs(a) @ np.abs(bmat).T
+
+
+@pytest.mark.parametrize("far", [I.F32, I.BF16, I.F16, I.E4M3])
+def test_single_steps_match_oracle(ctx, far):
+    """Load the oracle's state before step k, run step k on the GPU, compare
+    every tile the step writes (POTRF, panel TRSM, SYRK/GEMM updates)."""
+    n, b = 640, 128
+    nt = n // b
+    pmap = I.band_map(nt, I.F64, I.F32, far, 1)
+    locs, _ = OM.morton_order(I.points(n, 21))
+    S = OM.covariance(locs, 0.5, 0.1, 1.0, 1e-4)
+    state = OC.tiled_from_dense(S, b, pmap)
+    T = _mk(ctx, n, b, pmap)
+    for k in range(nt):
+        before = {key: OC.Tile(t.codes.copy(), t.fmt, t.scale) for key, t in state.tiles.items()}
+        _load_state(T, state, nt)
+        T.chol_steps(k, k + 1)
+        torch.cuda.synchronize()
+        OC.step(state, k)
+        # diagonal factor
+        got, _, _ = T.get_tile(k, k)
+        want = state.tiles[(k, k)].codes
+        assert np.allclose(np.tril(got), np.tril(want), rtol=1e-12, atol=1e-14), f"potrf {k}"
+        # panel: float64 solve, rounded once
+        for i in range(k + 1, nt):
+            got, codes, s = T.get_tile(i, k)
+            rt = state.tiles[(i, k)]
+            fmt = rt.fmt
+            if fmt == I.E4M3:
+                assert s == rt.scale
+                assert_close_fmt(codes, rt.codes, fmt, frac=2e-3, what=f"trsm {i},{k}")
+            else:
+                assert_close_fmt(got, rt.values(), fmt, extra=1e-13 * np.abs(rt.values()).max(),
+                                 frac=2e-3, what=f"trsm {i},{k}")
+        # trailing updates
+        for j in range(k + 1, nt):
+            for i in range(j, nt):
+                got, codes, s = T.get_tile(i, j)
+                rt = state.tiles[(i, j)]
+                a, bb = state.tiles[(i, k)], state.tiles[(j, k)]
+                kind = OC.kind_of(rt.fmt, a.fmt, bb.fmt)
+                u_acc = 2.0 ** -53 if kind == I.F64 else 2.0 ** -24
+                bound = 2 * b * u_acc * _abs_prod(a.values(), bb.values())
+                want = rt.values()
+                if i == j:
+                    got, want, bound = np.tril(got), np.tril(want), np.tril(bound)
+                if rt.fmt == I.E4M3:
+                    # the new scale comes from the amax, identical unless it
+                    # straddles a power of two
+                    assert s == rt.scale
+                assert_close_fmt(got, want, rt.fmt, extra=bound, what=f"update {i},{j} k={k}")
+        del before
+
+
+# ------------------------------------------------------- whole evaluations --
+
+def _run(ctx, n, b, pmap, locs, z, nu, a, s2, tau, refine=0):
+    T = _mk(ctx, n, b, pmap, keep_sigma=refine > 0)
+    dl = torch.from_numpy(locs).to(DEV)
+    T.generate(dl, s2, a, nu, tau)
+    info, logdet = T.chol()
+    zt = torch.from_numpy(np.ascontiguousarray(z.T)).to(DEV)
+    ll, quad, iters = T.loglik(zt, refine_iters=refine)
+    torch.cuda.synchronize()
+    return dict(info=int(info.item()), logdet=logdet.item(), ll=ll.cpu().numpy(),
+                quad=quad.cpu().numpy(), iters=iters.cpu().numpy(), T=T)
+
+
+def test_plain_fp64_n1024_tile128(ctx):
+    """FP64 tiled Cholesky + solve + log-det, n=1024, tile 128, Matérn
+    nu=1/2, range 0.1, variance 1, nugget 1e-4, uniform points, z ~ N(0,1)."""
+    c = I.CONFIGS["fp64_n1024_b128"]
+    n, b = c["n"], c["b"]
+    for seed in range(1, 6):
+        locs = I.points(n, seed)
+        z = I.rhs(n, 1, seed)
+        S = OM.covariance(locs, c["nu"], c["range"], c["sigma2"], c["nugget"])
+        ex = OC.exact_loglik(S, z)
+        r = _run(ctx, n, b, None, locs, z, c["nu"], c["range"], c["sigma2"], c["nugget"])
+        assert r["info"] == 0
+        assert math.isclose(r["logdet"], ex["logdet"], rel_tol=1e-11)
+        assert np.allclose(r["ll"], ex["loglik"], rtol=1e-12)
+    tl = OC.tiled_loglik(S, z, b, I.uniform_map(n // b, I.F64))
+    assert np.allclose(r["ll"], tl["loglik"], rtol=1e-12)
+    L = r["T"]
+    for i in range(n // b):
+        for j in range(i + 1):
+            got, _, _ = L.get_tile(i, j)
+            want = tl["T"].tiles[(i, j)].codes
+            if i == j:
+                got, want = np.tril(got), np.tril(want)
+            assert np.allclose(got, want, rtol=0, atol=1e-12), (i, j)
+
+
+@pytest.mark.parametrize("far,refine", [(I.F32, 0), (I.BF16, 0), (I.F16, 0), (I.E4M3, 0),
+                                        (I.BF16, 10), (I.E4M3, 10)])
+def test_mixed_loglik_matches_oracle(ctx, far, refine):
+    n, b = 1000, 128             # ragged: 8 tiles, 24 padding rows
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, far, 2)
+    # exponential kernel; short ranges (the paper's MLE example estimates
+    # a ~ 0.03) keep the mixed factor a contraction for refinement
+    a = 0.1 if not refine else (0.03 if far == I.BF16 else 0.02)
+    locs, _ = OM.morton_order(I.points(n, 31))
+    z = I.rhs(n, 3, 31)
+    S = OM.covariance(locs, 0.5, a, 1.0, 1e-4)
+    ex = OC.exact_loglik(S, z)
+    tl = OC.tiled_loglik(S, z, b, pmap, refine_iters=refine)
+    r = _run(ctx, n, b, pmap, locs, z, 0.5, a, 1.0, 1e-4, refine=refine)
+    assert r["info"] == 0
+    err_gpu = np.abs(r["ll"] - ex["loglik"]) / np.abs(ex["loglik"])
+    tol = np.maximum(10 * err_gpu, 1e-9)
+    assert np.all(np.abs(r["ll"] - tl["loglik"]) / np.abs(tl["loglik"]) <= tol)
+    ld_err = abs(r["logdet"] - ex["logdet"]) / abs(ex["logdet"])
+    assert math.isclose(r["logdet"], tl["logdet"], rel_tol=max(1e-9, 10 * ld_err))
+    if refine:
+        assert np.all(tl["iters"] < refine)          # the oracle converged
+        assert np.all(np.abs(r["iters"] - tl["iters"]) <= 1)
+        assert np.allclose(r["quad"], ex["quad"], rtol=1e-10)
+        assert np.all(err_gpu < 1e-4)
+
+
+def test_trsm_forward_backward(ctx):
+    """mp_trsm against the oracle's tiled solves applied to the GPU's own
+    factor (downloaded tile by tile), so only the solve is compared."""
+    n, b = 900, 128
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 1)
+    locs = I.points(n, 8)
+    T = _mk(ctx, n, b, pmap)
+    T.generate(torch.from_numpy(locs).to(DEV), 1.0, 0.05, 1.5, 1e-2)
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    state = OC.TiledMatrix(n=n, b=b, nt=nt, pmap=pmap)
+    for i in range(nt):
+        for j in range(i + 1):
+            vals, codes, sc = T.get_tile(i, j)
+            state.tiles[(i, j)] = OC.Tile(np.tril(codes) if i == j else codes, int(pmap[i, j]), sc)
+    B = I.rhs(n, 4, 8)
+    for trans in (0, 1):
+        Bt = torch.from_numpy(np.ascontiguousarray(B.T)).to(DEV)
+        T.trsm(Bt, trans)
+        torch.cuda.synchronize()
+        zp = np.zeros((nt * b, 4))
+        zp[:n] = B
+        ref = OC.forward_solve_padded(state, zp) if trans == 0 else OC.backward_solve(state, zp)
+        assert np.allclose(Bt.cpu().numpy().T, ref[:n], rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_not_spd_reports_first_bad_row(ctx):
+    n, b = 512, 128
+    T = _mk(ctx, n, b, None)
+    d = np.ones(n)
+    d[300] = -2.0
+    for i in range(n // b):
+        for j in range(i + 1):
+            blk = np.zeros((b, b))
+            if i == j:
+                blk = np.diag(d[i * b:(i + 1) * b])
+            T.set_tile(i, j, blk)
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    assert int(info.item()) == 301
+    _, oinfo = OC.potrf_textbook(np.diag(d))
+    assert oinfo == 301
+
+
+@pytest.mark.parametrize("dt", [I.F64, I.F32, I.BF16, I.F16, I.E4M3])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_gemm_per_precision(ctx, dt, ta, tb):
+    from paper_2406_02701_gb300 import mpchol
+    m, n, k = 130, 77, 200
+    rng = np.random.default_rng(dt * 10 + len(ta))
+    A0 = rng.standard_normal((m, k) if ta == "N" else (k, m))
+    B0 = rng.standard_normal((k, n) if tb == "N" else (n, k))
+    C0 = rng.standard_normal((m, n))
+    if dt == I.E4M3:
+        A0, B0, C0 = A0 * 4, B0 * 4, C0 * 4
+    A, B, Cm = (OF.round_to(x, dt) for x in (A0, B0, C0))
+    ref = OC.gemm(A, B, Cm, dt, alpha=0.5, beta=-1.0, ta=ta == "T", tb=tb == "T")
+
+    def dev(x):       # column-major storage = row-major of the transpose
+        raw = mpchol.encode(np.ascontiguousarray(x.T).reshape(-1), dt)
+        return torch.from_numpy(raw).to(DEV), x.shape[0]
+    dA, lda = dev(A)
+    dB, ldb = dev(B)
+    dC, ldc = dev(Cm)
+    ctx.gemm(dt, ta, tb, m, n, k, 0.5, dA, lda, dB, ldb, -1.0, dC, ldc)
+    torch.cuda.synchronize()
+    got = mpchol.decode(dC.cpu().numpy(), dt).reshape(n, m).T
+    a = A.T if ta == "T" else A
+    bb = B.T if tb == "T" else B
+    bound = 0.5 * 2 * k * (2.0 ** -53 if dt == I.F64 else 2.0 ** -24) * (np.abs(a) @ np.abs(bb))
+    assert_close_fmt(got, ref, dt, extra=bound + (1e-6 * np.abs(Cm) if dt not in (I.F64, I.F32) else 0),
+                     what="gemm")
+
+
+def test_batch_equals_single_evaluations(ctx):
+    """A batch plan gives every request the bits of its single evaluation;
+    a request whose mixed factor breaks down reports MP_ERR_NOT_SPD without
+    disturbing the others."""
+    from paper_2406_02701_gb300 import mpchol
+    reqs, singles, expect_bad = [], [], []
+    b = 128
+    sizes = [300, 1000, 128, 777, 2048, 513]
+    for r, n in enumerate(sizes):
+        nt = -(-n // b)
+        pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 1)
+        locs, _ = OM.morton_order(I.points(n, 40 + r))
+        z = I.rhs(n, 1 + r % 2, 40 + r)
+        nu, a = [0.5, 1.5, 2.5][r % 3], 0.02 + 0.05 * r
+        dl = torch.from_numpy(locs).to(DEV)
+        zt = torch.from_numpy(np.ascontiguousarray(z.T)).to(DEV)
+        reqs.append(dict(n=n, map=pmap, locs=dl, zt=zt, sigma2=1.0, range=a, nu=nu, nugget=1e-2))
+        s = _run(ctx, n, b, pmap, locs, z, nu, a, 1.0, 1e-2)
+        singles.append(s)
+        S = OM.covariance(locs, nu, a, 1.0, 1e-2)
+        try:
+            tl = OC.tiled_loglik(S, z, b, pmap)
+        except np.linalg.LinAlgError:
+            expect_bad.append(True)
+            assert s["info"] > 0
+            continue
+        expect_bad.append(False)
+        assert s["info"] == 0
+        ex = OC.exact_loglik(S, z)
+        err = np.abs(s["ll"] - ex["loglik"]) / np.abs(ex["loglik"])
+        assert np.all(np.abs(s["ll"] - tl["loglik"]) / np.abs(tl["loglik"]) <= np.maximum(10 * err, 1e-9))
+    assert any(expect_bad) and not all(expect_bad)
+    B = mpchol.Batch(ctx, reqs, b=b)
+    ll, st = B.run()
+    torch.cuda.synchronize()
+    ll, st = ll.cpu().numpy(), st.cpu().numpy()
+    o = 0
+    for s, bad, stv in zip(singles, expect_bad, st):
+        k = len(s["ll"])
+        assert stv == (mpchol.MP_ERR_NOT_SPD if bad else mpchol.MP_OK)
+        if not bad:
+            assert np.array_equal(ll[o:o + k], s["ll"]), (ll[o:o + k], s["ll"])
+        o += k
+    # a second run of the same graph gives the same bits
+    ll2, _ = B.run()
+    torch.cuda.synchronize()
+    ok = np.concatenate([np.full(len(s["ll"]), not bad) for s, bad in zip(singles, expect_bad)])
+    assert np.array_equal(ll2.cpu().numpy()[ok], ll[ok])
