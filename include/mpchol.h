@@ -130,6 +130,29 @@ mp_status mp_tile_set(mp_tmat* t, int32_t i, int32_t j, const void* h_src, doubl
 mp_status mp_morton_order(mp_ctx* ctx, int64_t n, const double* d_locs_in,
                           double* d_locs_out, int64_t* d_perm, void* stream);
 
+/* Allocation-free Morton ordering (no counterpart in the paper; it is a
+ * service of this library).  Same result as mp_morton_order, but the sort
+ * keys live in a fixed buffer inside the library's device image instead of
+ * a cudaMalloc'd workspace, for callers that must not allocate device
+ * memory: work enqueued during CUDA graph capture, latency-critical loops
+ * that cannot absorb the allocator's implicit synchronisation, and
+ * programs whose device memory belongs to another allocator or budget.
+ *   - Runs on the calling thread's current device and on `stream`.
+ *   - n must be in [1, MP_NOALLOC_MAX_POINTS]; larger n returns MP_ERR_ARG
+ *     (use mp_morton_order).  The buffer (8 bytes per point of the limit,
+ *     1 MiB) is held by every device that loads the library until exit.
+ *   - The first call on a device looks the buffer's device address up
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture that includes this entry point.
+ *   - All calls share the one buffer: two calls whose work overlaps on the
+ *     GPU (different streams, or different threads without ordering) race
+ *     and corrupt each other's result; order them on one stream.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * d_locs_in, d_locs_out, d_perm are as in mp_morton_order. */
+#define MP_NOALLOC_MAX_POINTS 131072
+mp_status mp_morton_order_noalloc(int64_t n, const double* d_locs_in, double* d_locs_out,
+                                  int64_t* d_perm, void* stream);
+
 /* ------------------------------------------------------------ generation */
 
 /* Fills every lower tile with the Matérn covariance of the locations

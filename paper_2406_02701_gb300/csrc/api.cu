@@ -47,6 +47,15 @@ mp_status fail(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
   return st;
 }
 
+}  // namespace
+
+// Error text for calls that have no context (read by mp_last_error(NULL)).
+namespace mp {
+void set_error_text(const char* msg) { snprintf(g_err_fallback, sizeof g_err_fallback, "%s", msg); }
+}  // namespace mp
+
+namespace {
+
 #define CK(ctx, call)                                                              \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \
