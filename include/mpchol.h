@@ -94,13 +94,17 @@ const char* mp_version(void);
  *             diagonal must be MP_F64.  NULL means all MP_F64.
  *   flags   : MP_TMAT_KEEP_SIGMA keeps a float64 copy of the generated
  *             lower tiles for the FP64 refinement residual (needs
- *             8 * NT(NT+1)/2 * b^2 more bytes).
+ *             8 * NT(NT+1)/2 * b^2 more bytes).  MP_TMAT_SIMT_UPDATES runs
+ *             the lower-precision trailing updates on CUDA cores (FP32
+ *             FMA) instead of the tcgen05 tensor cores (BF16/FP16/E4M3
+ *             MMAs; FP32 products as three TF32 MMAs of hi/lo splits).
  *   stream  : stream all later calls on this matrix are ordered on.
  * The library allocates tile storage and workspace on the device (see
  * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
  * and hold the identity, which leaves the log-determinant and the
  * quadratic form unchanged.  Synchronous. */
 #define MP_TMAT_KEEP_SIGMA 1u
+#define MP_TMAT_SIMT_UPDATES 2u  /* trailing updates on CUDA cores instead of tcgen05 */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);
@@ -173,7 +177,9 @@ mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p);
  * p(B))) with FP32 accumulation (FP64 for FP64 products).  The whole
  * schedule is one CUDA graph launch on the matrix's stream.
  *   d_info   : 1 int64: 0, or the smallest 1-based global row whose pivot
- *              was not > 0 (then L is not valid).  May be NULL.
+ *              was not > 0 (then L is not valid), or -MP_ERR_TIMEOUT when a
+ *              bounded device-side wait of a tensor-core kernel ran out
+ *              (the kernel returned without hanging).  May be NULL.
  *   d_logdet : 1 float64: log det Sigma = 2 sum log L_tt.  May be NULL.
  * Returns MP_OK once enqueued (a non-SPD matrix is reported in d_info
  * only).  Asynchronous. */

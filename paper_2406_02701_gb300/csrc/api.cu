@@ -19,6 +19,9 @@
 #include <string>
 #include <vector>
 
+#include <array>
+#include <cuda.h>
+
 #include "../../include/mpchol.h"
 #include "mp_device.cuh"
 
@@ -76,7 +79,7 @@ int kind_of(int q, int pa, int pb) {
 bool needs_round(int p, int kind) { return p != kind && level(p) >= level(kind); }
 
 enum Op {
-  OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64,
+  OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64, OP_TC,
   OP_FP8R, OP_LOGDET, OP_DIAG_F, OP_OFF_F, OP_DIAG_B, OP_OFF_B, OP_GEN_AMAX, OP_GEN
 };
 
@@ -94,7 +97,9 @@ struct MatDesc {
   int64_t n = 0;
   int nt = 0;
   std::vector<int32_t> tile, sig;           // nt*nt each (-1 = none)
-  std::vector<int32_t> shadow;              // nt*nt*NDT: rounded copy of (i,j) in format d
+  std::vector<uint8_t> need;                // nt*nt: operand forms tile (i,j) must provide
+                                            // (bit d: rounded copy in format d; bit 5:
+                                            // TF32 hi/lo split)
   std::vector<int32_t> linv;                // nt: FP64 tile holding L_ii^{-T}
   int32_t ldoff = 0;
   double* dinv = nullptr;                   // nt * (b/32) blocks of 32x32
@@ -110,6 +115,13 @@ struct Plan {
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
   int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
+  bool use_tc = true;              // tensor-core updates (else CUDA cores)
+  // operand forms of the panel tiles, per panel slot of a step
+  std::vector<std::array<int32_t, NDT>> slot_shadow;
+  std::vector<int32_t> slot_hi, slot_lo;
+  CUtensorMap tmap[NDT];
+  bool have_tmap[NDT] = {};
+  int* d_err = nullptr;
   char* pool[NDT] = {};
   TileRef* d_tiles = nullptr;
   double* d_scale = nullptr;
@@ -144,6 +156,7 @@ struct Plan {
     A.tiles = d_tiles;
     A.scale = d_scale;
     A.amax = d_amax;
+    A.err = d_err;
     A.b = b;
     return A;
   }
@@ -247,29 +260,26 @@ mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
   if (mp_status st = validate_map(P.ctx, nt, map)) return st;
   auto dt = [&](int i, int j) { return map ? (int)map[i * nt + j] : (int)F64; };
   M.tile.assign((size_t)nt * nt, -1);
-  M.shadow.assign((size_t)nt * nt * NDT, -1);
+  M.need.assign((size_t)nt * nt, 0);
   for (int i = 0; i < nt; ++i)
     for (int j = 0; j <= i; ++j) M.tile[i * nt + j] = new_tile(P, dt(i, j));
-  // rounded copies needed by each off-diagonal tile (i, s): one per format
-  // in which a product that reads it runs below its storage format
+  // operand forms needed by each off-diagonal tile (i, s): a rounded copy
+  // per format in which a product that reads it runs below its storage
+  // format, and the TF32 split when a tensor-core FP32 product reads it
   for (int s = 0; s < nt; ++s)
     for (int i = s + 1; i < nt; ++i) {
       const int p = dt(i, s);
-      bool need[NDT] = {};
-      for (int j = s + 1; j <= i; ++j) {                 // as the A operand
-        int kd = kind_of(dt(i, j), p, dt(j, s));
-        if (needs_round(p, kd)) need[kd] = true;
-      }
-      for (int i2 = i + 1; i2 < nt; ++i2) {              // as the B operand
-        int kd = kind_of(dt(i2, i), dt(i2, s), p);
-        if (needs_round(p, kd)) need[kd] = true;
-      }
+      uint8_t need = 0;
+      auto use = [&](int kd) {
+        if (needs_round(p, kd)) need |= (uint8_t)(1u << kd);
+        if (P.use_tc && kd == F32) need |= 1u << 5;
+      };
+      for (int j = s + 1; j <= i; ++j) use(kind_of(dt(i, j), p, dt(j, s)));     // as A
+      for (int i2 = i + 1; i2 < nt; ++i2) use(kind_of(dt(i2, i), dt(i2, s), p)); // as B
       int cnt = 0;
-      for (int d = 0; d < NDT; ++d)
-        if (need[d]) {
-          if (++cnt > MAX_SHADOW) return fail(P.ctx, MP_ERR_ARG, "tile (%d,%d) needs too many rounded copies", i, s);
-          M.shadow[((size_t)i * nt + s) * NDT + d] = new_tile(P, d);
-        }
+      for (int d = 0; d < NDT; ++d) cnt += (need >> d) & 1;
+      if (cnt > MAX_SHADOW) return fail(P.ctx, MP_ERR_ARG, "tile (%d,%d) needs too many rounded copies", i, s);
+      M.need[(size_t)i * nt + s] = need;
     }
   M.linv.assign(nt, -1);
   for (int i = 0; i < nt; ++i) M.linv[i] = new_tile(P, F64);
@@ -320,49 +330,83 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
     std::vector<ItemPanel> panel;
     std::vector<ItemRound> round;
     std::vector<ItemUpd> u32, u64;
+    std::vector<ItemTC> tc[NDT];
     std::vector<ItemFp8> f8;
     int64_t slot = 0, vslot = 0;
     for (int m = 0; m < (int)P.mats.size(); ++m) {
       auto& M = P.mats[m];
       const int nt = M.nt;
       if (nt <= s) continue;
+      const int64_t base = slot;                       // slot of tile (s+1, s)
+      auto slot_of = [&](int i) { return base + (i - s - 1); };
+      auto form = [&](int i, int d) {                  // tile (i, s) in format d
+        return P.slot_shadow[slot_of(i)][d];
+      };
       for (int i = s + 1; i < nt; ++i) {
         ItemPanel it{};
         it.tile = M.tile[i * nt + s];
         it.diag = M.tile[s * nt + s];
         it.dinv = M.dinv + (int64_t)s * nbb * 1024;
-        it.x = P.d_panel + slot * (int64_t)b * b;   // d_panel set before building (see caller)
+        it.x = P.d_panel + slot * (int64_t)b * b;
         panel.push_back(it);
         ItemRound r{};
         r.tile = it.tile;
-        int q = 0;
         for (int d = 0; d < MAX_SHADOW; ++d) r.shadow[d] = -1;
-        for (int d = 0; d < NDT; ++d) {
-          int sh = M.shadow[((size_t)i * nt + s) * NDT + d];
-          if (sh >= 0) r.shadow[q++] = sh;
-        }
+        const uint8_t need = M.need[(size_t)i * nt + s];
+        int q = 0;
+        for (int d = 0; d < NDT; ++d)
+          if ((need >> d) & 1) r.shadow[q++] = form(i, d);
+        r.hi = (need & (1u << 5)) ? P.slot_hi[slot] : -1;
+        r.lo = (need & (1u << 5)) ? P.slot_lo[slot] : -1;
         r.x = it.x;
         round.push_back(r);
         ++slot;
       }
       for (int j = s + 1; j < nt; ++j)
         for (int i = j; i < nt; ++i) {
-          const int tc = M.tile[i * nt + j], ta = M.tile[i * nt + s], tb = M.tile[j * nt + s];
-          const int q = P.h_tiles[tc].dt, pa = P.h_tiles[ta].dt, pb = P.h_tiles[tb].dt;
+          const int tc_ = M.tile[i * nt + j], ta = M.tile[i * nt + s], tb = M.tile[j * nt + s];
+          const int q = P.h_tiles[tc_].dt, pa = P.h_tiles[ta].dt, pb = P.h_tiles[tb].dt;
           const int kd = kind_of(q, pa, pb);
-          ItemUpd u{};
-          u.c = tc;
-          u.a = needs_round(pa, kd) ? M.shadow[((size_t)i * nt + s) * NDT + kd] : ta;
-          u.b = needs_round(pb, kd) ? M.shadow[((size_t)j * nt + s) * NDT + kd] : tb;
-          u.syrk = i == j;
-          u.vslot = -1;
+          float* v = nullptr;
+          int vs = -1;
           if (q == E4M3) {
-            u.v = P.d_v + vslot * (int64_t)b * b;
-            u.vslot = (int)(P.h_tiles.size() + vslot);
-            f8.push_back(ItemFp8{tc, u.vslot, u.v});
+            v = P.d_v + vslot * (int64_t)b * b;
+            vs = (int)(P.h_tiles.size() + vslot);
+            f8.push_back(ItemFp8{tc_, vs, v});
             ++vslot;
           }
-          (kd == F64 ? u64 : u32).push_back(u);
+          if (kd == F64) {
+            ItemUpd u{tc_, ta, tb, i == j, v, vs, 0};
+            u64.push_back(u);
+          } else if (P.use_tc && kd == F32) {
+            ItemTC u{};
+            u.c = tc_;
+            u.a = P.slot_hi[slot_of(i)];
+            u.a2 = P.slot_lo[slot_of(i)];
+            u.b = P.slot_hi[slot_of(j)];
+            u.b2 = P.slot_lo[slot_of(j)];
+            u.syrk = i == j;
+            u.vslot = vs;
+            u.v = v;
+            tc[F32].push_back(u);
+          } else {
+            const int a = needs_round(pa, kd) ? form(i, kd) : ta;
+            const int bb = needs_round(pb, kd) ? form(j, kd) : tb;
+            if (P.use_tc) {
+              ItemTC u{};
+              u.c = tc_;
+              u.a = a;
+              u.b = bb;
+              u.a2 = u.b2 = -1;
+              u.syrk = i == j;
+              u.vslot = vs;
+              u.v = v;
+              tc[kd].push_back(u);
+            } else {
+              ItemUpd u{tc_, a, bb, i == j, v, vs, 0};
+              u32.push_back(u);
+            }
+          }
         }
     }
     // the inverse of the new diagonal factor: X = I L_ss^{-T}
@@ -383,6 +427,8 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
     if (!round.empty()) P.chol.push_back({OP_ROUND, P.push(round), (int)round.size(), 0});
     if (!u64.empty()) P.chol.push_back({OP_UPD64, P.push(u64), (int)u64.size(), 0});
     if (!u32.empty()) P.chol.push_back({OP_UPD32, P.push(u32), (int)u32.size(), 0});
+    for (int d : {F32, BF16, F16, E4M3})
+      if (!tc[d].empty()) P.chol.push_back({OP_TC, P.push(tc[d]), (int)tc[d].size(), d});
     if (!f8.empty()) P.chol.push_back({OP_FP8R, P.push(f8), (int)f8.size(), 0});
   }
   P.step_begin.push_back(P.chol.size());
@@ -425,9 +471,65 @@ mp_status upload_items(Plan& P) {
   return MP_OK;
 }
 
+// One 2-D tensor map per format pool that tensor-core products read: the
+// pool seen as a (tiles * b) x b row-major matrix, box 128 bytes x 128 rows,
+// 128-byte swizzle (the K-major operand layout of the MMA descriptors).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+mp_status make_tensor_maps(Plan& P) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(P.ctx, MP_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    encode = (EncodeTiledFn)fn;
+  }
+  const int b = P.b;
+  for (int d : {F32, BF16, F16, E4M3}) {
+    if (P.pool_count[d] == 0) continue;
+    CUtensorMapDataType ty = d == F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : d == BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                           : d == F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const int es = esize(d);
+    cuuint64_t dims[2] = {(cuuint64_t)b, (cuuint64_t)P.pool_count[d] * b};
+    cuuint64_t strides[1] = {(cuuint64_t)b * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&P.tmap[d], ty, 2, P.pool[d], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(P.ctx, MP_ERR_CUDA, "tensor map of pool %d: error %d", d, (int)r);
+    P.have_tmap[d] = true;
+  }
+  return MP_OK;
+}
+
 // Allocates the arena and scratch of a plan whose matrices were added.
 mp_status finish_plan(Plan& P) {
   const int b = P.b, nbb = b / 32;
+  {
+    int64_t panel_slots = 0, v_slots = 0;
+    count_scratch(P, &panel_slots, &v_slots);
+    uint8_t all = 0;
+    for (auto& M : P.mats)
+      for (uint8_t v : M.need) all |= v;
+    P.slot_shadow.assign(panel_slots, {});
+    P.slot_hi.assign(panel_slots, -1);
+    P.slot_lo.assign(panel_slots, -1);
+    for (int64_t q = 0; q < panel_slots; ++q) {
+      for (int d = 0; d < NDT; ++d) P.slot_shadow[q][d] = (all >> d) & 1 ? new_tile(P, d) : -1;
+      if (all & (1u << 5)) {
+        P.slot_hi[q] = new_tile(P, F32);
+        P.slot_lo[q] = new_tile(P, F32);
+      }
+    }
+  }
   for (int d = 0; d < NDT; ++d) {
     void* p = nullptr;
     size_t bytes = (size_t)P.pool_count[d] * b * b * esize(d);
@@ -478,6 +580,12 @@ mp_status finish_plan(Plan& P) {
   P.d_info = (long long*)p;
   if (mp_status st = P.alloc(&p, sizeof(double) * nm)) return st;
   P.d_logdet = (double*)p;
+  if (mp_status st = P.alloc(&p, sizeof(int))) return st;
+  P.d_err = (int*)p;
+  CK(P.ctx, cudaMemset(P.d_err, 0, sizeof(int)));
+  if (P.use_tc) {
+    if (mp_status st = make_tensor_maps(P)) return st;
+  }
   if (P.keep_sigma) {
     int64_t tot = 0;
     for (auto& M : P.mats) tot += (int64_t)M.nt * M.nt;
@@ -513,7 +621,10 @@ mp_status finish_plan(Plan& P) {
 void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
   const Arena A = P.arena();
   switch (L.op) {
-    case OP_INFO0: cudaMemsetAsync(P.d_info, 0x7f, sizeof(long long) * P.mats.size(), s); break;
+    case OP_INFO0:
+      cudaMemsetAsync(P.d_info, 0x7f, sizeof(long long) * P.mats.size(), s);
+      cudaMemsetAsync(P.d_err, 0, sizeof(int), s);
+      break;
     case OP_AMAX0: cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s); break;
     case OP_POTRF: launch_potrf_block(A, P.item<ItemDiag>(L.off), L.count, P.d_ldparts, P.d_info, s); break;
     case OP_ITRSM: launch_inner_trsm(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
@@ -522,6 +633,12 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
     case OP_ROUND: launch_panel_round(A, P.item<ItemRound>(L.off), L.count, s); break;
     case OP_UPD32: launch_update_f32(A, P.item<ItemUpd>(L.off), L.count, s); break;
     case OP_UPD64: launch_update_f64(A, P.item<ItemUpd>(L.off), L.count, s); break;
+    case OP_TC: {
+      // FP32 products read the TF32 splits from the FP32 pool; the others
+      // read their own format's pool
+      launch_update_tc(A, L.kb, P.item<ItemTC>(L.off), L.count, P.tmap[L.kb], s);
+      break;
+    }
     case OP_FP8R: launch_fp8_round(A, P.item<ItemFp8>(L.off), L.count, s); break;
     case OP_LOGDET:
       launch_logdet(P.d_ldparts, P.d_ldoff, P.d_ldcnt, (int)P.mats.size(), P.d_logdet, s);
@@ -633,6 +750,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.b = b;
   t->P.stream = (cudaStream_t)stream;
   t->P.keep_sigma = (flags & MP_TMAT_KEEP_SIGMA) != 0;
+  t->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
@@ -796,9 +914,9 @@ mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1) {
 }
 
 namespace {
-__global__ void k_info_out(const long long* info, long long* out, int n) {
+__global__ void k_info_out(const long long* info, const int* err, long long* out, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = info[i] == 0x7f7f7f7f7f7f7f7fLL ? 0 : info[i];
+  if (i < n) out[i] = *err ? -(long long)MP_ERR_TIMEOUT : info[i] == 0x7f7f7f7f7f7f7f7fLL ? 0 : info[i];
 }
 }  // namespace
 
@@ -814,7 +932,7 @@ mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet) {
     if (st) return st;
   }
   if (mp_status st = launch_graph(P.ctx, P.chol_exec, P.stream)) return st;
-  if (d_info) k_info_out<<<1, 32, 0, P.stream>>>(P.d_info, (long long*)d_info, 1);
+  if (d_info) k_info_out<<<1, 32, 0, P.stream>>>(P.d_info, P.d_err, (long long*)d_info, 1);
   if (d_logdet) CK(P.ctx, cudaMemcpyAsync(d_logdet, P.d_logdet, sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
   P.factored = true;
   return check_launch(P.ctx);
@@ -1102,7 +1220,7 @@ struct ItemBatchOut {
 };
 
 __global__ void k_batch_out(const ItemBatchOut* items, int count, const double* logdet,
-                            const long long* info) {
+                            const long long* info, const int* err) {
   const int m = blockIdx.x;
   if (m >= count) return;
   const ItemBatchOut it = items[m];
@@ -1124,7 +1242,8 @@ __global__ void k_batch_out(const ItemBatchOut* items, int count, const double* 
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    it.status[0] = info[it.mat] == 0x7f7f7f7f7f7f7f7fLL ? MP_OK : MP_ERR_NOT_SPD;
+    it.status[0] = *err ? MP_ERR_TIMEOUT
+                        : info[it.mat] == 0x7f7f7f7f7f7f7f7fLL ? MP_OK : MP_ERR_NOT_SPD;
 }
 
 struct ItemBatchCopy {
@@ -1243,7 +1362,8 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
     for (const Launch& L : P.chol) run_launch(P, L, s);
     k_batch_copy<<<count, 256, 0, s>>>(P.item<ItemBatchCopy>(off_cp));
     run_solve(P, P.d_items, fwd, nullptr, s);
-    k_batch_out<<<count, 256, 0, s>>>(P.item<ItemBatchOut>(off_out), count, P.d_logdet, P.d_info);
+    k_batch_out<<<count, 256, 0, s>>>(P.item<ItemBatchOut>(off_out), count, P.d_logdet, P.d_info,
+                                      P.d_err);
   }, &B->exec);
   if (st != MP_OK) { delete B; return st; }
   *out = B;
@@ -1373,6 +1493,7 @@ int op_class(int op) {
     case OP_ROUND: return 4;
     case OP_UPD64: return 5;
     case OP_UPD32: return 6;
+    case OP_TC: return 7;
     case OP_FP8R: return 8;
     default: return 9;
   }
@@ -1413,6 +1534,11 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
       case OP_UPD64:
       case OP_UPD32: {
         const ItemUpd* it = reinterpret_cast<const ItemUpd*>(P.h_items.data() + L.off);
+        for (int q = 0; q < L.count; ++q) h_flops[c] += it[q].syrk ? b * b * (b + 1) : 2.0 * b * b * b;
+        break;
+      }
+      case OP_TC: {
+        const ItemTC* it = reinterpret_cast<const ItemTC*>(P.h_items.data() + L.off);
         for (int q = 0; q < L.count; ++q) h_flops[c] += it[q].syrk ? b * b * (b + 1) : 2.0 * b * b * b;
         break;
       }

@@ -227,15 +227,25 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
     sdst[q] = it.shadow[q] >= 0 ? tile_bytes(A, it.shadow[q]) : nullptr;
     ss[q] = sdt[q] == E4M3 ? e4m3_scale(stored_amax) : 1.0;
   }
+  float* hi = it.hi >= 0 ? tile_ptr<float>(A, it.hi) : nullptr;
+  float* lo = it.lo >= 0 ? tile_ptr<float>(A, it.lo) : nullptr;
   const int64_t r0 = (int64_t)blockIdx.y * 16 * b;
   for (int e = threadIdx.x; e < 16 * b; e += blockDim.x) {
     double v = it.x[r0 + e];
     store_round(dst, dt, r0 + e, dt == E4M3 ? v / s : v);
-    if (sdst[0]) {
+    if (sdst[0] || hi) {
       double stored = load_f64(dst, dt, r0 + e) * s;
 #pragma unroll
       for (int q = 0; q < MAX_SHADOW; ++q)
         if (sdst[q]) store_round(sdst[q], sdt[q], r0 + e, sdt[q] == E4M3 ? stored / ss[q] : stored);
+      if (hi) {
+        // the stored value is exact in FP32 (formats up to FP32)
+        const float f = (float)stored;
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+        hi[r0 + e] = __uint_as_float(h);
+        lo[r0 + e] = f - __uint_as_float(h);
+      }
     }
   }
   if (blockIdx.y == 0 && threadIdx.x == 0) {
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
 #pragma unroll
     for (int q = 0; q < MAX_SHADOW; ++q)
       if (it.shadow[q] >= 0) A.scale[it.shadow[q]] = ss[q];
+    if (it.hi >= 0) { A.scale[it.hi] = 1.0; A.scale[it.lo] = 1.0; }
   }
 }
 

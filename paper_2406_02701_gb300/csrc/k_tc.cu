@@ -1,0 +1,333 @@
+// Trailing updates on the 5th-generation tensor cores (tcgen05), for the
+// products whose precision (min(p(target), max(p(A), p(B))), Sec. 4.3's
+// promotion rule capped by the target tile) is below FP64:
+//   BF16 / FP16  kind::f16     A, B in the 16-bit format, FP32 accumulate
+//   E4M3         kind::f8f6f4  scaled codes; FP32 sum times s_a s_b
+//   FP32         kind::tf32    three products of hi/lo splits,
+//                              A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
+//                              where hi = A rounded to TF32 and lo = A - hi
+// One CTA computes a 128 x 128 sub-tile of the target with the full
+// contraction K = b.  Warp 0 (one lane) streams 128-byte-wide K slices of
+// the operand tiles into shared memory with TMA (128-byte swizzle, one
+// tensor map per format pool; no multicast), warp 1 (one lane) issues the
+// MMAs into a 128-column FP32 accumulator in tensor memory, and all four
+// warps read the accumulator back (each its 32 lanes) and apply the update
+// to the target tile in global memory:
+//   FP64 target (SYRK into the diagonal)  C -= acc            (float64)
+//   FP32 target                           C = f32(C - acc)    (float64 sub)
+//   16-bit target                         C = round(C - acc)  (FP32 sub)
+//   E4M3 target                           FP32 scratch + amax (rounded by
+//                                         k_fp8_round with the new scale)
+// Every mbarrier wait is bounded: when it runs out the CTA records the
+// failure in the arena's error word, lets the MMAs it issued complete, frees
+// its tensor memory and returns.
+#include <cuda.h>
+
+#include "mp_device.cuh"
+
+namespace mp {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128;
+constexpr int TC_BUF = 128 * 128;          // one 128-row x 128-byte operand slice
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; on time-out records the failure and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand slice, 128-byte swizzle,
+// rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused: 16 B)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = FP32, A/B format code `fmt`, both K-major,
+// M = 128, N = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+         ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  constexpr uint32_t idesc = instr_desc(KIND == 0 ? 1u : KIND == 1 ? 0u : KIND == 2 ? 0u : 2u);
+  if constexpr (KIND == 0 || KIND == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else if constexpr (KIND == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// KIND: 0 BF16, 1 FP16, 2 E4M3, 3 FP32 as three TF32 products.
+template <int KIND, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+    k_update_tc(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int NA = KIND == 3 ? 2 : 1;              // operand slices per side
+  constexpr int STAGE_BYTES = 2 * NA * TC_BUF;
+  constexpr int KCH = KIND == 2 ? 128 : KIND == 3 ? 32 : 64;   // elements per slice
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+
+  const ItemTC it = items[blockIdx.x];
+  const int b = A.b, nsub = b / TC_BM;
+  const int rb = blockIdx.y / nsub, cb = blockIdx.y % nsub;
+  if (it.syrk && cb > rb) return;                  // strictly above the diagonal
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int KT = b / KCH;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA of the K slices
+    const int ya0 = A.tiles[it.a].idx * b + rb * TC_BM;
+    const int yb0 = A.tiles[it.b].idx * b + cb * TC_BN;
+    const int ya1 = NA == 2 ? A.tiles[it.a2].idx * b + rb * TC_BM : 0;
+    const int yb1 = NA == 2 ? A.tiles[it.b2].idx * b + cb * TC_BN : 0;
+    int issued = 0;
+    bool ok = true;
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES;
+      if (kt >= STAGES && !(ok = mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1, A.err))) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(st, &tmap, kt * KCH, ya0, &full[s]);
+      if (NA == 2) tma_load_2d(st + TC_BUF, &tmap, kt * KCH, ya1, &full[s]);
+      tma_load_2d(st + NA * TC_BUF, &tmap, kt * KCH, yb0, &full[s]);
+      if (NA == 2) tma_load_2d(st + (NA + 1) * TC_BUF, &tmap, kt * KCH, yb1, &full[s]);
+      ++issued;
+    }
+    if (!ok) {
+      // let the copies already in flight land before the CTA's memory goes away
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+        mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1, nullptr);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kt = 0; kt < KT; ++kt) {
+      const int s = kt % STAGES;
+      if (!mbar_wait(&full[s], (kt / STAGES) & 1, A.err)) break;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t a1 = a0 + TC_BUF;
+      const uint32_t b0 = a0 + NA * TC_BUF;
+      const uint32_t b1 = b0 + TC_BUF;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {                 // 32 bytes of K per MMA
+        const uint32_t off = kk * 32;
+        const uint32_t acc = (kt | kk) != 0;
+        mma<KIND>(tmem, smem_desc(a0 + off), smem_desc(b0 + off), acc);
+        if (KIND == 3) {
+          mma<KIND>(tmem, smem_desc(a0 + off), smem_desc(b1 + off), 1);
+          mma<KIND>(tmem, smem_desc(a1 + off), smem_desc(b0 + off), 1);
+        }
+      }
+      mma_commit(&empty[s]);                           // frees the stage when done
+    }
+    mma_commit(accf);                                  // all issued MMAs complete
+  }
+  __syncwarp();
+
+  // epilogue: every warp reads its 32 accumulator lanes
+  const bool have = mbar_wait(accf, 0, A.err);
+  tc_fence_after();
+  const TileRef rc = A.tiles[it.c];
+  char* pc = tile_bytes(A, it.c);
+  const float sab = (float)(A.scale[it.a] * A.scale[it.b]);
+  const double sc = A.scale[it.c];
+  const int row = rb * TC_BM + warp * 32 + lane;
+  float mx = 0.f;
+#pragma unroll 1
+  for (int ch = 0; ch < TC_BN / 32; ++ch) {
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
+    if (!have) continue;
+    const int64_t o0 = (int64_t)row * b + cb * TC_BN + ch * 32;
+    if (it.syrk && cb * TC_BN + ch * 32 > row) continue;   // above the diagonal
+    if (rc.dt == F64) {
+      double* c = reinterpret_cast<double*>(pc) + o0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c[j] -= (double)(v[j] * sab);
+    } else if (rc.dt == F32) {
+      float* c = reinterpret_cast<float*>(pc) + o0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) c[j] = __double2float_rn((double)c[j] - (double)(v[j] * sab));
+    } else if (rc.dt == E4M3) {
+      const float fs = (float)sc;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float w = load_f32(pc, E4M3, o0 + j) * fs - v[j] * sab;
+        it.v[o0 + j] = w;
+        mx = fmaxf(mx, fabsf(w));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        store_round_f32(pc, rc.dt, o0 + j, load_f32(pc, rc.dt, o0 + j) - v[j] * sab);
+    }
+  }
+  if (rc.dt == E4M3) {
+    __shared__ float red[4];
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 4; ++w) mx = fmaxf(mx, red[w]);
+      atomic_max_pos(&A.amax[it.vslot], (double)mx);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+                 : "memory");
+  }
+}
+
+template <int KIND, int STAGES>
+constexpr size_t tc_smem() {
+  return (size_t)STAGES * 2 * (KIND == 3 ? 2 : 1) * TC_BUF + 8 * (2 * STAGES + 1) + 16 + 1024;
+}
+
+template <int KIND, int STAGES>
+void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap& map,
+               cudaStream_t s) {
+  static bool attr = false;
+  constexpr size_t smem = tc_smem<KIND, STAGES>();
+  if (!attr) {
+    cudaFuncSetAttribute(k_update_tc<KIND, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  const int nsub = A.b / TC_BM;
+  k_update_tc<KIND, STAGES><<<dim3(count, nsub * nsub), 128, smem, s>>>(A, items, map);
+}
+
+}  // namespace
+
+// kind: BF16, F16, E4M3 or F32 (three TF32 products); map: the tensor map of
+// the operand pool (box 128 bytes x 128 rows, 128-byte swizzle).
+void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
+                      const CUtensorMap& map, cudaStream_t s) {
+  if (count <= 0) return;
+  switch (kind) {
+    case BF16: launch_tc<0, 3>(A, items, count, map, s); break;
+    case F16: launch_tc<1, 3>(A, items, count, map, s); break;
+    case E4M3: launch_tc<2, 3>(A, items, count, map, s); break;
+    default: launch_tc<3, 3>(A, items, count, map, s); break;
+  }
+}
+
+}  // namespace mp

@@ -34,6 +34,7 @@ struct Arena {
   const TileRef* tiles;           // tile table
   double* scale;                  // per tile: E4M3 scale (1 otherwise)
   unsigned long long* amax;       // per tile: amax as float64 bits (atomicMax)
+  int* err;                       // set to 1 when a bounded device wait ran out
   int b;
   int pad_;
 };
@@ -75,6 +76,7 @@ constexpr int MAX_SHADOW = 3;
 struct ItemRound {
   int32_t tile;
   int32_t shadow[MAX_SHADOW];   // -1: unused
+  int32_t hi, lo;               // FP32 tiles: value split as TF32 hi + remainder (-1: none)
   const double* x;
 };
 
@@ -85,6 +87,16 @@ struct ItemUpd {
   float* v;           // E4M3 target: b x b FP32 scratch for the new values
   int32_t vslot;      // E4M3 target: amax slot (index into Arena.amax)
   int32_t pad_;
+};
+
+// Tensor-core update of one target tile; for three-TF32 products a/a2 and
+// b/b2 are the hi/lo splits of the operands.
+struct ItemTC {
+  int32_t c, a, b, a2, b2;
+  int32_t syrk;
+  int32_t vslot;
+  int32_t pad_;
+  float* v;
 };
 
 // Rounds an E4M3 target from its FP32 scratch with the new scale.
@@ -161,6 +173,11 @@ void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaS
 void launch_update_f32(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
 void launch_update_f64(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
 void launch_fp8_round(const Arena& A, const ItemFp8* items, int count, cudaStream_t s);
+
+// k_tc.cu (kind: BF16, F16, E4M3, or F32 as three TF32 products; the map
+// is a const CUtensorMap& of the operands' pool)
+void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
+                      const struct CUtensorMap_st& map, cudaStream_t s);
 
 // k_solve.cu  (a non-null `gate` pointing at 0 turns a launch into a no-op)
 void launch_diag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,

@@ -54,9 +54,9 @@ def assert_close_fmt(got, ref, fmt, extra=0.0, ulps=1, frac=1.0, what=""):
         assert (d > 0).mean() <= frac, f"{what}: {(d > 0).mean():.4f} of entries differ"
 
 
-def _mk(ctx, n, b, pmap, keep_sigma=False):
+def _mk(ctx, n, b, pmap, keep_sigma=False, simt=False):
     from paper_2406_02701_gb300 import mpchol
-    return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma)
+    return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma, simt_updates=simt)
 
 
 # --------------------------------------------------------------- Morton ----
@@ -143,17 +143,23 @@ def _abs_prod(a, bmat):
     return np.abs(a) @ np.abs(bmat).T
 
 
+@pytest.mark.parametrize("simt", [False, True], ids=["tcgen05", "cudacore"])
 @pytest.mark.parametrize("far", [I.F32, I.BF16, I.F16, I.E4M3])
-def test_single_steps_match_oracle(ctx, far):
+def test_single_steps_match_oracle(ctx, far, simt):
     """Load the oracle's state before step k, run step k on the GPU, compare
-    every tile the step writes (POTRF, panel TRSM, SYRK/GEMM updates)."""
+    every tile the step writes (POTRF, panel TRSM, SYRK/GEMM updates), with
+    the trailing updates on the tensor cores or on the CUDA cores.  FP32
+    products on the tensor cores are three TF32 products of hi/lo splits;
+    each product then carries at most 3 * 2^-22 |a||b| error (the dropped
+    lo*lo term and the truncation of the lo parts), within the same
+    2 K 2^-24 sum|a||b| bound as FP32 accumulation for K >= 12."""
     n, b = 640, 128
     nt = n // b
     pmap = I.band_map(nt, I.F64, I.F32, far, 1)
     locs, _ = OM.morton_order(I.points(n, 21))
     S = OM.covariance(locs, 0.5, 0.1, 1.0, 1e-4)
     state = OC.tiled_from_dense(S, b, pmap)
-    T = _mk(ctx, n, b, pmap)
+    T = _mk(ctx, n, b, pmap, simt=simt)
     for k in range(nt):
         before = {key: OC.Tile(t.codes.copy(), t.fmt, t.scale) for key, t in state.tiles.items()}
         _load_state(T, state, nt)
