@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle factorisation steps sampled")
     p.add_argument("--no-fp64-path", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=36)
+    p.add_argument("--serve-rate", type=float, default=6.0, help="Poisson arrivals per second")
     return p.parse_args()
 
 
@@ -203,6 +206,34 @@ def reference_arm(args, cfg):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def serving_run(ctx, args):
+    """Continuous batching of a Poisson stream of likelihood requests:
+    n in {2048, 8192, 32768} at 8:3:1, Matérn parameters drawn as in an MLE
+    search, 1 RHS, 3 refinement sweeps at most, far tiles BF16 where the
+    norm bound allows (eps 1e-6)."""
+    from paper_2406_02701_gb300 import mpchol, serving
+    reqs = serving.make_requests(args.serve_requests, args.serve_rate, seed=31)
+    srv = mpchol.Server(ctx, hbm_budget=200 << 30, max_slots=8, eps=1e-6, far=mpchol.MP_BF16)
+    warm = serving.make_requests(3, 1e6, seed=7, sizes=(2048,), weights=(1,))
+    for r in warm:
+        r["arrival"] = 0.0
+    serving.run(srv, warm, refine_iters=3)
+    res, wall = serving.run(srv, reqs, refine_iters=3)
+    srv.close()
+    lat = serving.latency_stats(res)
+    by_n = {}
+    for i, r in res.items():
+        by_n.setdefault(reqs[i]["n"], []).append((r["t_done"] - r["t_submit"]) * 1e3)
+    ok = sum(1 for r in res.values() if r["status"] == 0)
+    low = sum(r["low_tiles"] for r in res.values())
+    tiles = sum(r["offdiag_tiles"] for r in res.values())
+    return {"requests": len(reqs), "ok": ok, "rate_hz": args.serve_rate, "wall_s": wall,
+            "solves_per_s": len(reqs) / wall, **lat,
+            "p50_ms_by_n": {str(k): float(np.percentile(v, 50)) for k, v in sorted(by_n.items())},
+            "bf16_offdiag_tile_share": low / tiles if tiles else 0.0,
+            "slots": 8, "mix": "n 2048/8192/32768 at 8:3:1, Poisson arrivals"}
 
 
 def morton_launches(n: int) -> int:
@@ -371,6 +402,10 @@ def ours(args, cfg):
                 "speedup_step": ms64 / ms,
                 "loglik_rel_err_mixed_vs_fp64": (np.abs(ll_mixed - ll64) / np.abs(ll64)).tolist()}
 
+    serve = None
+    if not args.no_serving:
+        serve = serving_run(ctx, args)
+
     cpu = None
     if not args.no_cpu_baseline:
         steps = max(1, min(args.cpu_steps, nt))
@@ -399,6 +434,7 @@ def ours(args, cfg):
         "result": {"info": info_mixed, "loglik": ll_mixed.tolist(), "logdet": logdet_mixed,
                    "refine_iters": iters_mixed.tolist(), "plain_band_map": band_status},
         "fp64_path": fp64,
+        "serving": serve,
         "chol_breakdown_ms": breakdown,
     }
     print(json.dumps(line), flush=True)

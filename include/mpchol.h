@@ -98,6 +98,10 @@ const char* mp_version(void);
  *             the lower-precision trailing updates on CUDA cores (FP32
  *             FMA) instead of the tcgen05 tensor cores (BF16/FP16/E4M3
  *             MMAs; FP32 products as three TF32 MMAs of hi/lo splits).
+ *             MP_TMAT_STREAM_ALLOC allocates and frees the matrix's device
+ *             memory with cudaMallocAsync / cudaFreeAsync on `stream` (and
+ *             uploads with cudaMemcpyAsync), so that creating or destroying
+ *             a matrix never waits for other streams' work.
  *   stream  : stream all later calls on this matrix are ordered on.
  * The library allocates tile storage and workspace on the device (see
  * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
@@ -105,6 +109,7 @@ const char* mp_version(void);
  * quadratic form unchanged.  Synchronous. */
 #define MP_TMAT_KEEP_SIGMA 1u
 #define MP_TMAT_SIMT_UPDATES 2u  /* trailing updates on CUDA cores instead of tcgen05 */
+#define MP_TMAT_STREAM_ALLOC 4u  /* stream-ordered allocation on `stream` (no device sync) */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);
@@ -314,6 +319,82 @@ mp_status mp_batch_run(mp_batch* batch, double* d_ll, int32_t* d_status);
  * Synchronous. */
 mp_status mp_loglik_batch(mp_ctx* ctx, int32_t count, const mp_request* reqs,
                           double* d_ll, int32_t* d_status, void* stream);
+
+/* --------------------------------------------------------------- serving */
+
+/* Continuous-batching server of log-likelihood requests (an MLE search is
+ * a stream of likelihood evaluations, Sec. 6.2).  Requests arrive with HOST
+ * buffers and queue; mp_server_poll retires finished requests and admits
+ * queued ones -- in arrival order, later ones backfilling when an earlier
+ * one does not fit -- while one of `max_slots` streams is free and the
+ * request's device footprint fits `hbm_budget` bytes.  Admitted requests
+ * run concurrently, each on its own stream: locations are Morton-ordered
+ * on the host, the precision map comes from mp_map_bound (diagonal FP64,
+ * |i-j| <= 2 FP32, far tiles in `far_dt` where the norm bound allows it
+ * with `eps`), and generation, factorisation and log-likelihood run on
+ * the device; tile size 128 (n <= 2048), 256 (n <= 8192) or 512.  A
+ * finished request keeps its factor on the device until released; when
+ * a request needs the memory, the least recently finished unreleased
+ * factors are evicted.  One thread drives a server. */
+typedef struct mp_server mp_server;
+
+typedef struct {
+  int64_t id;
+  int32_t status;       /* MP_OK, MP_ERR_NOT_SPD, MP_ERR_TIMEOUT, ...           */
+  int32_t nrhs;
+  int64_t n;
+  int32_t b;
+  int32_t low_tiles;    /* off-diagonal tiles stored in far_dt                 */
+  int32_t offdiag_tiles;
+  int32_t pad_;
+  double t_submit, t_admit, t_done;   /* host clock (seconds)                 */
+  double logdet;
+  double loglik0;       /* log-likelihood of the first right-hand side         */
+} mp_serve_result;
+
+/* Creates a server (max_slots in [1, 64] streams).  Synchronous. */
+mp_status mp_server_create(mp_ctx* ctx, int64_t hbm_budget, int32_t max_slots, double eps,
+                           uint8_t far_dt, mp_server** out);
+/* Waits for all work, frees everything. */
+void mp_server_destroy(mp_server* s);
+
+/* Queues a request: h_locs n x 2 row-major, h_z n x nrhs column-major (ld
+ * n), both copied at the call; refine_iters as in mp_loglik.  *id is the
+ * request's id (1, 2, ...).  Host only. */
+mp_status mp_server_submit(mp_server* s, int64_t n, const double* h_locs, const double* h_z,
+                           int32_t nrhs, int32_t refine_iters, mp_matern cov, int64_t* id);
+
+/* Progress without blocking: writes up to max_out results of requests that
+ * finished since the last poll (completion time = the poll that saw them)
+ * and admits queued requests.  Call it in a loop. */
+mp_status mp_server_poll(mp_server* s, mp_serve_result* out, int32_t max_out, int32_t* n_out);
+
+/* Host copies of a finished request's log-likelihoods and quadratic forms
+ * (nrhs each; either pointer may be NULL).  Returns the request's status
+ * (MP_ERR_STATE while it has not finished). */
+mp_status mp_server_result(mp_server* s, int64_t id, double* h_ll, double* h_quad);
+
+/* The device factor a finished, not yet evicted request keeps (valid until
+ * mp_server_release or eviction). */
+mp_status mp_server_factor(mp_server* s, int64_t id, mp_tmat** t);
+
+/* Frees a finished request's device memory. */
+mp_status mp_server_release(mp_server* s, int64_t id);
+
+/* Queue length, requests on the GPU, kept factors, device bytes in use. */
+mp_status mp_server_stats(mp_server* s, int64_t* queued, int64_t* running, int64_t* kept,
+                          int64_t* bytes_used);
+
+/* Precision map from closed-form norm bounds (host only; the server's map).
+ * h_sorted_locs: n x 2, already in the order the matrix will use.  As
+ * mp_map_guarded, with ||A_ij||_F replaced by the upper bound
+ * sqrt(rows_i cols_j) C(d_ij) (d_ij: distance between the bounding boxes
+ * of the two tiles' points; C decreases with distance) and ||A||_F by the
+ * lower bound sqrt(n) (sigma2 + nugget); both make the map more
+ * conservative than the exact-norm rule.  h_map: NT*NT, 255 above the
+ * diagonal. */
+mp_status mp_map_bound(int64_t n, int32_t b, const double* h_sorted_locs, mp_matern c,
+                       int32_t band, uint8_t near_dt, uint8_t far_dt, double eps, uint8_t* h_map);
 
 #ifdef __cplusplus
 }

@@ -192,6 +192,37 @@ def guarded_map(norms: np.ndarray, band: int, near: int, far: int, eps: float) -
     return m
 
 
+def bound_map(sorted_locs: np.ndarray, b: int, nu: float, a: float, sigma2: float,
+              nugget: float, band: int, near: int, far: int, eps: float) -> np.ndarray:
+    """The guarded map with ||A_ij||_F replaced by the upper bound
+    sqrt(rows_i cols_j) C(d_ij), d_ij the distance between the bounding
+    boxes of the two tiles' points (the Matérn covariance decreases with
+    distance), and ||A||_F by its lower bound sqrt(n) (sigma2 + nugget)
+    (the diagonal alone): a more conservative choice than guarded_map."""
+    from .matern import matern_closed
+    n = sorted_locs.shape[0]
+    nt = -(-n // b)
+    boxes = []
+    for t in range(nt):
+        p = sorted_locs[t * b:min(n, (t + 1) * b)]
+        boxes.append((p[:, 0].min(), p[:, 0].max(), p[:, 1].min(), p[:, 1].max(), p.shape[0]))
+    bound = eps * math.sqrt(n) * (sigma2 + nugget) / nt
+    m = np.full((nt, nt), 255, dtype=np.uint8)
+    for i in range(nt):
+        m[i, i] = F.F64
+        for j in range(i):
+            if i - j <= band:
+                m[i, j] = near
+                continue
+            xi0, xi1, yi0, yi1, ci = boxes[i]
+            xj0, xj1, yj0, yj1, cj = boxes[j]
+            dx = max(0.0, max(xi0 - xj1, xj0 - xi1))
+            dy = max(0.0, max(yi0 - yj1, yj0 - yi1))
+            B = math.sqrt(float(ci) * float(cj)) * float(matern_closed(math.sqrt(dx * dx + dy * dy), nu, a, sigma2))
+            m[i, j] = far if F.unit_roundoff(far) * B <= bound else near
+    return m
+
+
 def kind_of(q: int, pa: int, pb: int) -> int:
     """R-MMA: the format in which A_ik A_jk^T runs for a target of format q."""
     lk = min(F.level(q), max(F.level(pa), F.level(pb)))

@@ -149,6 +149,7 @@ struct Plan {
   bool factored = false;
   int64_t bytes = 0;
   std::vector<void*> allocs;
+  bool stream_alloc = false;       // cudaMallocAsync / cudaFreeAsync on `stream`
 
   Arena arena() const {
     Arena A{};
@@ -171,9 +172,21 @@ struct Plan {
   template <typename T>
   const T* item(size_t off) const { return reinterpret_cast<const T*>(d_items + off); }
 
+  cudaError_t raw_alloc(void** p, size_t bytes_) {
+    return stream_alloc ? cudaMallocAsync(p, bytes_, stream) : cudaMalloc(p, bytes_);
+  }
+  void raw_free(void* p) {
+    if (!p) return;
+    if (stream_alloc) cudaFreeAsync(p, stream);
+    else cudaFree(p);
+  }
+  cudaError_t upload(void* dst, const void* src, size_t bytes_) {
+    return stream_alloc ? cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, stream)
+                        : cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice);
+  }
   mp_status alloc(void** p, size_t bytes_) {
     if (bytes_ == 0) { *p = nullptr; return MP_OK; }
-    cudaError_t e = cudaMalloc(p, bytes_);
+    cudaError_t e = raw_alloc(p, bytes_);
     if (e != cudaSuccess) return fail(ctx, MP_ERR_OOM, "cudaMalloc(%zu): %s", bytes_, cudaGetErrorString(e));
     allocs.push_back(*p);
     bytes += (int64_t)bytes_;
@@ -182,7 +195,8 @@ struct Plan {
 
   ~Plan() {
     if (chol_exec) cudaGraphExecDestroy(chol_exec);
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) raw_free(p);
+    if (d_items) raw_free(d_items);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -212,9 +226,9 @@ struct mp_tmat {
   std::vector<void*> ws_allocs;
   ~mp_tmat() {
     if (ll_exec) cudaGraphExecDestroy(ll_exec);
-    for (void* p : ws_allocs) cudaFree(p);
-    if (d_gen) cudaFree(d_gen);
-    if (d_sitems) cudaFree(d_sitems);
+    for (void* p : ws_allocs) P.raw_free(p);
+    P.raw_free(d_gen);
+    P.raw_free(d_sitems);
   }
 };
 
@@ -461,13 +475,12 @@ void count_scratch(const Plan& P, int64_t* panel_slots, int64_t* v_slots) {
 
 mp_status upload_items(Plan& P) {
   if (P.h_items.size() > P.d_items_cap) {
-    if (P.d_items) cudaFree(P.d_items);
+    P.raw_free(P.d_items);
     P.d_items = nullptr;
-    CK(P.ctx, cudaMalloc(&P.d_items, P.h_items.size()));
+    CK(P.ctx, P.raw_alloc((void**)&P.d_items, P.h_items.size()));
     P.d_items_cap = P.h_items.size();
   }
-  if (!P.h_items.empty())
-    CK(P.ctx, cudaMemcpy(P.d_items, P.h_items.data(), P.h_items.size(), cudaMemcpyHostToDevice));
+  if (!P.h_items.empty()) CK(P.ctx, P.upload(P.d_items, P.h_items.data(), P.h_items.size()));
   return MP_OK;
 }
 
@@ -582,7 +595,8 @@ mp_status finish_plan(Plan& P) {
   P.d_logdet = (double*)p;
   if (mp_status st = P.alloc(&p, sizeof(int))) return st;
   P.d_err = (int*)p;
-  CK(P.ctx, cudaMemset(P.d_err, 0, sizeof(int)));
+  CK(P.ctx, P.stream_alloc ? cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream)
+                           : cudaMemset(P.d_err, 0, sizeof(int)));
   if (P.use_tc) {
     if (mp_status st = make_tensor_maps(P)) return st;
   }
@@ -593,23 +607,21 @@ mp_status finish_plan(Plan& P) {
     P.d_sig = (int32_t*)p;
     int64_t o = 0;
     for (auto& M : P.mats) {
-      CK(P.ctx, cudaMemcpy(P.d_sig + o, M.sig.data(), sizeof(int32_t) * M.sig.size(),
-                           cudaMemcpyHostToDevice));
+      CK(P.ctx, P.upload(P.d_sig + o, M.sig.data(), sizeof(int32_t) * M.sig.size()));
       o += (int64_t)M.nt * M.nt;
     }
   }
-  CK(P.ctx, cudaMemcpy(P.d_tiles, P.h_tiles.data(), sizeof(TileRef) * ntiles, cudaMemcpyHostToDevice));
+  CK(P.ctx, P.upload(P.d_tiles, P.h_tiles.data(), sizeof(TileRef) * ntiles));
   {
     std::vector<double> eye((size_t)b * b, 0.0);
     for (int r = 0; r < b; ++r) eye[(size_t)r * b + r] = 1.0;
     const TileRef r = P.h_tiles[P.ident];
-    CK(P.ctx, cudaMemcpy(P.pool[F64] + (size_t)r.idx * b * b * 8, eye.data(), sizeof(double) * b * b,
-                         cudaMemcpyHostToDevice));
+    CK(P.ctx, P.upload(P.pool[F64] + (size_t)r.idx * b * b * 8, eye.data(), sizeof(double) * b * b));
   }
   std::vector<double> ones(ntiles, 1.0);
-  CK(P.ctx, cudaMemcpy(P.d_scale, ones.data(), sizeof(double) * ntiles, cudaMemcpyHostToDevice));
-  CK(P.ctx, cudaMemcpy(P.d_ldoff, ldoff.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice));
-  CK(P.ctx, cudaMemcpy(P.d_ldcnt, ldcnt.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice));
+  CK(P.ctx, P.upload(P.d_scale, ones.data(), sizeof(double) * ntiles));
+  CK(P.ctx, P.upload(P.d_ldoff, ldoff.data(), sizeof(int32_t) * nm));
+  CK(P.ctx, P.upload(P.d_ldcnt, ldcnt.data(), sizeof(int32_t) * nm));
   int64_t ps = 0, vs = 0;
   build_chol_schedule(P, &ps, &vs);
   if (mp_status st = upload_items(P)) return st;
@@ -751,6 +763,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.stream = (cudaStream_t)stream;
   t->P.keep_sigma = (flags & MP_TMAT_KEEP_SIGMA) != 0;
   t->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
+  t->P.stream_alloc = (flags & MP_TMAT_STREAM_ALLOC) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
@@ -855,17 +868,17 @@ static mp_status build_gen_items(mp_tmat* t) {
     }
   size_t bytes = sizeof(ItemGen) * (amax.size() + all.size());
   if (bytes > t->d_gen_cap) {
-    if (t->d_gen) cudaFree(t->d_gen);
+    P.raw_free(t->d_gen);
     t->d_gen = nullptr;
-    CK(P.ctx, cudaMalloc(&t->d_gen, bytes));
+    CK(P.ctx, P.raw_alloc((void**)&t->d_gen, bytes));
     t->d_gen_cap = bytes;
   }
   t->gen_off_amax = 0;
   t->gen_off_all = sizeof(ItemGen) * amax.size();
   t->gen_n_amax = (int)amax.size();
   t->gen_n_all = (int)all.size();
-  if (!amax.empty()) CK(P.ctx, cudaMemcpy(t->d_gen, amax.data(), sizeof(ItemGen) * amax.size(), cudaMemcpyHostToDevice));
-  CK(P.ctx, cudaMemcpy(t->d_gen + t->gen_off_all, all.data(), sizeof(ItemGen) * all.size(), cudaMemcpyHostToDevice));
+  if (!amax.empty()) CK(P.ctx, P.upload(t->d_gen, amax.data(), sizeof(ItemGen) * amax.size()));
+  CK(P.ctx, P.upload(t->d_gen + t->gen_off_all, all.data(), sizeof(ItemGen) * all.size()));
   return MP_OK;
 }
 
@@ -1017,12 +1030,12 @@ void run_solve(const Plan& P, const char* dbase, const std::vector<Launch>& ls, 
 // Solve workspace of a single-matrix handle for nrhs right-hand sides.
 static mp_status ensure_ws(mp_tmat* t, int nrhs) {
   if (t->ws_nrhs >= nrhs) return MP_OK;
-  for (void* p : t->ws_allocs) cudaFree(p);
-  t->ws_allocs.clear();
   Plan& P = t->P;
+  for (void* p : t->ws_allocs) P.raw_free(p);
+  t->ws_allocs.clear();
   const int64_t N = (int64_t)P.mats[0].nt * P.b;
   auto A = [&](void** p, size_t bytes) -> mp_status {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = P.raw_alloc(p, bytes);
     if (e != cudaSuccess) return fail(P.ctx, MP_ERR_OOM, "solve workspace: %s", cudaGetErrorString(e));
     t->ws_allocs.push_back(*p);
     return MP_OK;
@@ -1072,9 +1085,9 @@ extern "C" mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, in
   build_solve(P, {t->x}, {t->w}, {N}, {nrhs}, trans ? 1 : 0, ls);
   size_t bytes = P.h_items.size();
   if (bytes > t->d_sitems_cap) {
-    if (t->d_sitems) cudaFree(t->d_sitems);
+    P.raw_free(t->d_sitems);
     t->d_sitems = nullptr;
-    cudaError_t e = cudaMalloc(&t->d_sitems, bytes);
+    cudaError_t e = P.raw_alloc((void**)&t->d_sitems, bytes);
     if (e != cudaSuccess) { P.h_items.swap(saved); return fail(P.ctx, MP_ERR_OOM, "solve items"); }
     t->d_sitems_cap = bytes;
   }
@@ -1136,13 +1149,13 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
     size_t res_off = P.push(res);
     size_t bytes = P.h_items.size();
     if (bytes > t->d_sitems_cap) {
-      if (t->d_sitems) cudaFree(t->d_sitems);
+      P.raw_free(t->d_sitems);
       t->d_sitems = nullptr;
-      cudaError_t e = cudaMalloc(&t->d_sitems, bytes);
+      cudaError_t e = P.raw_alloc((void**)&t->d_sitems, bytes);
       if (e != cudaSuccess) { P.h_items.swap(saved); return fail(P.ctx, MP_ERR_OOM, "solve items"); }
       t->d_sitems_cap = bytes;
     }
-    cudaError_t e = cudaMemcpy(t->d_sitems, P.h_items.data(), bytes, cudaMemcpyHostToDevice);
+    cudaError_t e = P.upload(t->d_sitems, P.h_items.data(), bytes);
     P.h_items.swap(saved);
     if (e != cudaSuccess) return fail(P.ctx, MP_ERR_CUDA, "solve items copy");
     double* red = t->red;

@@ -26,6 +26,13 @@ class mp_matern(C.Structure):
                 ("nugget", C.c_double)]
 
 
+class mp_serve_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("nrhs", C.c_int32), ("n", C.c_int64),
+                ("b", C.c_int32), ("low_tiles", C.c_int32), ("offdiag_tiles", C.c_int32),
+                ("pad_", C.c_int32), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("logdet", C.c_double), ("loglik0", C.c_double)]
+
+
 class mp_request(C.Structure):
     _fields_ = [("n", C.c_int64), ("h_map", C.c_void_p), ("d_locs", C.c_void_p),
                 ("d_z", C.c_void_p), ("nrhs", C.c_int32), ("refine_iters", C.c_int32),
@@ -60,6 +67,18 @@ _SIGS = {
     "mp_probe_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "mp_gemm": (C.c_int, [P, C.c_int, C.c_char, C.c_char, C.c_int64, C.c_int64, C.c_int64,
                           C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, P, C.c_int64, P]),
+    "mp_server_create": (C.c_int, [P, C.c_int64, C.c_int32, C.c_double, C.c_uint8, C.POINTER(P)]),
+    "mp_server_destroy": (None, [P]),
+    "mp_server_submit": (C.c_int, [P, C.c_int64, P, P, C.c_int32, C.c_int32, mp_matern,
+                                   C.POINTER(C.c_int64)]),
+    "mp_server_poll": (C.c_int, [P, P, C.c_int32, C.POINTER(C.c_int32)]),
+    "mp_server_result": (C.c_int, [P, C.c_int64, P, P]),
+    "mp_server_factor": (C.c_int, [P, C.c_int64, C.POINTER(P)]),
+    "mp_server_release": (C.c_int, [P, C.c_int64]),
+    "mp_server_stats": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mp_map_bound": (C.c_int, [C.c_int64, C.c_int32, P, mp_matern, C.c_int32, C.c_uint8, C.c_uint8,
+                               C.c_double, P]),
     "mp_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(mp_request), C.c_int32, P,
                                   C.POINTER(P)]),
     "mp_batch_destroy": (None, [P]),
@@ -328,6 +347,75 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """mp_server: continuous batching of log-likelihood requests."""
+
+    def __init__(self, ctx: Context, hbm_budget: int, max_slots: int = 8, eps: float = 1e-6,
+                 far=MP_BF16):
+        self.ctx, self.lib = ctx, ctx.lib
+        h = P()
+        ctx.check(self.lib.mp_server_create(ctx.h, int(hbm_budget), max_slots, eps, far, C.byref(h)))
+        self.h = h
+        self._buf = (mp_serve_result * 64)()
+
+    def submit(self, locs: np.ndarray, z: np.ndarray, cov, refine_iters=0) -> int:
+        """locs (n, 2) float64; z (n, nrhs) float64 (copied); cov = (sigma2, range, nu, nugget)."""
+        locs = np.ascontiguousarray(locs, dtype=np.float64)
+        zt = np.ascontiguousarray(np.asarray(z, dtype=np.float64).reshape(locs.shape[0], -1).T)
+        rid = C.c_int64()
+        self.ctx.check(self.lib.mp_server_submit(self.h, locs.shape[0], locs.ctypes.data_as(C.c_void_p),
+                                                 zt.ctypes.data_as(C.c_void_p), zt.shape[0],
+                                                 refine_iters, mp_matern(*cov), C.byref(rid)))
+        return rid.value
+
+    def poll(self):
+        n = C.c_int32()
+        self.ctx.check(self.lib.mp_server_poll(self.h, self._buf, len(self._buf), C.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = self._buf[i]
+            out.append({k: getattr(r, k) for k, _ in mp_serve_result._fields_ if k != "pad_"})
+        return out
+
+    def result(self, rid: int, nrhs: int):
+        ll = np.empty(nrhs)
+        quad = np.empty(nrhs)
+        st = self.lib.mp_server_result(self.h, rid, ll.ctypes.data_as(C.c_void_p),
+                                       quad.ctypes.data_as(C.c_void_p))
+        return st, ll, quad
+
+    def release(self, rid: int):
+        self.ctx.check(self.lib.mp_server_release(self.h, rid))
+
+    def stats(self):
+        q, r, k, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self.ctx.check(self.lib.mp_server_stats(self.h, C.byref(q), C.byref(r), C.byref(k), C.byref(b)))
+        return dict(queued=q.value, running=r.value, kept=k.value, bytes=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def map_bound(n, b, sorted_locs, cov, band, near, far, eps):
+    lib = load()
+    nt = -(-n // b)
+    m = np.empty((nt, nt), dtype=np.uint8)
+    locs = np.ascontiguousarray(sorted_locs, dtype=np.float64)
+    st = lib.mp_map_bound(n, b, locs.ctypes.data_as(C.c_void_p), mp_matern(*cov), band, near, far,
+                          eps, m.ctypes.data_as(C.c_void_p))
+    if st != MP_OK:
+        raise MPError(st, "mp_map_bound")
+    return m
 
 
 # ---- host-side codecs of the storage formats (for tile upload/download) ----
