@@ -18,6 +18,8 @@
 //
 // GB300 has little FP64 throughput (about 1.2 TFLOP/s of DFMA), so these
 // kernels are bound by the FP64 pipe, not by memory.
+#include <algorithm>
+
 #include "mp_device.cuh"
 
 namespace mp {
@@ -54,26 +56,44 @@ __global__ void __launch_bounds__(256) k_potrf_block(Arena A, const ItemDiag* __
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    double s = 0.0;
-    for (int c = 0; c < NB; ++c) s += log(S[c][c]);
-    ldparts[it.ldslot] = 2.0 * s;
+  // 2 sum log L_tt: one log per lane of warp 0, fixed-order butterfly sum
+  if (tid < 32) {
+    double lg = log(S[tid][tid]);
+    for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
+    if (tid == 0) ldparts[it.ldslot] = 2.0 * lg;
   }
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int r = e / NB, c = e % NB;
     if (c <= r) T[(int64_t)r * b + c] = S[r][c];
   }
-  // inverse of the lower triangular block: row sweep, Di[r][t] for t <= r
+  // inverse of the lower triangular block by recursive doubling: with
+  // L = [A 0; C D], L^{-1} = [A^{-1} 0; -D^{-1} C A^{-1}  D^{-1}]; blocks of
+  // size 1, 2, 4, 8, 16 are combined pairwise (dependency depth 2 * 31)
   __shared__ double Di[NB][NB + 1];
-  __shared__ double rdiag[NB];
-  for (int e = tid; e < NB * NB; e += blockDim.x) Di[e / NB][e % NB] = 0.0;
-  if (tid < NB) rdiag[tid] = 1.0 / S[tid][tid];
+  __shared__ double Tm[NB][NB + 1];
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int r = e / NB, c = e % NB;
+    Di[r][c] = r == c ? 1.0 / S[r][r] : 0.0;
+  }
   __syncthreads();
-  for (int r = 0; r < NB; ++r) {
-    for (int t = tid; t <= r; t += blockDim.x) {
-      double acc = (t == r) ? 1.0 : 0.0;
-      for (int s = t; s < r; ++s) acc -= S[r][s] * Di[s][t];
-      Di[r][t] = acc * rdiag[r];
+  for (int sz = 1; sz < NB; sz <<= 1) {
+    const int per = sz * sz, pairs = NB / (2 * sz);
+    // T = C A^{-1}: C = S[d0 + r][a0 + t], A^{-1} = Di[a0 + t][a0 + c]
+    for (int e = tid; e < pairs * per; e += blockDim.x) {
+      const int pr = e / per, r = (e % per) / sz, c = e % sz;
+      const int a0 = pr * 2 * sz, d0 = a0 + sz;
+      double acc = 0.0;
+      for (int t = c; t < sz; ++t) acc += S[d0 + r][a0 + t] * Di[a0 + t][a0 + c];
+      Tm[d0 + r][a0 + c] = acc;
+    }
+    __syncthreads();
+    // W = -D^{-1} T: D^{-1} = Di[d0 + r][d0 + t] (t <= r)
+    for (int e = tid; e < pairs * per; e += blockDim.x) {
+      const int pr = e / per, r = (e % per) / sz, c = e % sz;
+      const int a0 = pr * 2 * sz, d0 = a0 + sz;
+      double acc = 0.0;
+      for (int t = 0; t <= r; ++t) acc += Di[d0 + r][d0 + t] * Tm[d0 + t][a0 + c];
+      Di[d0 + r][a0 + c] = -acc;
     }
     __syncthreads();
   }
@@ -99,9 +119,14 @@ __global__ void __launch_bounds__(256) k_inner_trsm(Arena A, const ItemDiag* __r
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int c = tx + 8 * j;
-    double acc = 0.0;
-    for (int t = 0; t <= c; ++t) acc += X[ty][t] * D[c][t];
-    out[j] = acc;
+    double a0 = 0.0, a1 = 0.0;
+    int t = 0;
+    for (; t + 1 <= c; t += 2) {
+      a0 += X[ty][t] * D[c][t];
+      a1 += X[ty][t + 1] * D[c][t + 1];
+    }
+    if (t <= c) a0 += X[ty][t] * D[c][t];
+    out[j] = a0 + a1;
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) T[(int64_t)(r0 + ty) * b + kb * NB + tx + 8 * j] = out[j];
@@ -126,83 +151,130 @@ __global__ void __launch_bounds__(256) k_inner_syrk(Arena A, const ItemDiag* __r
   }
   __syncthreads();
   const int ty = tid / 8, tx = tid % 8;
-  double acc[4] = {};
-  for (int t = 0; t < NB; ++t) {
-    double a = Xr[ty][t];
+  double acc[4] = {}, acc2[4] = {};
+  for (int t = 0; t < NB; t += 2) {
+    double a = Xr[ty][t], a2 = Xr[ty][t + 1];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] += a * Xc[tx + 8 * j][t];
+    for (int j = 0; j < 4; ++j) {
+      acc[j] += a * Xc[tx + 8 * j][t];
+      acc2[j] += a2 * Xc[tx + 8 * j][t + 1];
+    }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int64_t o = (int64_t)(R0 + ty) * b + C0 + tx + 8 * j;
-    T[o] -= acc[j];
+    T[o] -= acc[j] + acc2[j];
   }
 }
 
-constexpr int PR = 16;     // panel rows per CTA
+constexpr int PR = 16;     // panel rows per work unit
 constexpr int PK = 32;     // K chunk of L staged in shared memory
 
-__global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __restrict__ items) {
+// Persistent over work units (panel tile, 16-row block): CTA u processes
+// units u, u + gridDim.x, ...  The chunks of L_kk are double-buffered: the
+// next chunk is fetched into registers while the current one is used.
+__global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __restrict__ items,
+                                                    int units) {
   extern __shared__ double sm[];
-  const ItemPanel it = items[blockIdx.x];
   const int b = A.b, tid = threadIdx.x;
-  const int r0 = blockIdx.y * PR;
   double* X = sm;                                  // [PR][b]
-  double* Ls = X + PR * b;                         // [NB][PK+1]
-  double* Dv = Ls + NB * (PK + 1);                 // [NB][NB+1]
+  double* Ls = X + PR * b;                         // 2 x [NB][PK+1]
+  double* Dv = Ls + 2 * NB * (PK + 1);             // [NB][NB+1]
   double* Ac = Dv + NB * (NB + 1);                 // [PR][NB+1]
-  const TileRef ref = A.tiles[it.tile];
-  const char* src = tile_bytes(A, it.tile);
-  const double s_in = A.scale[it.tile];
-  for (int e = tid; e < PR * b; e += blockDim.x)
-    X[e] = load_f64(src, ref.dt, (int64_t)r0 * b + e) * s_in;
-  const double* L = tile_ptr<double>(A, it.diag);
   const int r = tid / 8, cx = tid % 8;
-  __syncthreads();
-  for (int cb = 0; cb < b / NB; ++cb) {
-    for (int e = tid; e < NB * NB; e += blockDim.x) Dv[(e / NB) * (NB + 1) + e % NB] = it.dinv[(int64_t)cb * NB * NB + e];
-    double acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = X[r * b + cb * NB + cx + 8 * q];
-    for (int t0 = 0; t0 < cb * NB; t0 += PK) {
-      __syncthreads();
-      for (int e = tid; e < NB * PK; e += blockDim.x) {
-        int rr = e / PK, tt = e % PK;
-        Ls[rr * (PK + 1) + tt] = L[(int64_t)(cb * NB + rr) * b + t0 + tt];
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int tt = 0; tt < PK; ++tt) {
-        double xv = X[r * b + t0 + tt];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] -= xv * Ls[(cx + 8 * q) * (PK + 1) + tt];
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Ac[r * (NB + 1) + cx + 8 * q] = acc[q];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int c = cx + 8 * q;
-      double v = 0.0;
-      for (int t = 0; t <= c; ++t) v += Ac[r * (NB + 1) + t] * Dv[c * (NB + 1) + t];
-      X[r * b + cb * NB + c] = v;
-    }
-    __syncthreads();
-  }
-  double mx = 0.0;
-  for (int e = tid; e < PR * b; e += blockDim.x) {
-    double v = X[e];
-    it.x[(int64_t)r0 * b + e] = v;
-    mx = fmax(mx, fabs(v));
-  }
+  const int per_tile = b / PR;
   __shared__ double red[4];
-  mx = warp_max(mx);
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
-  __syncthreads();
-  if (tid == 0) {
-    for (int w = 1; w < 4; ++w) mx = fmax(mx, red[w]);
-    atomic_max_pos(&A.amax[it.tile], mx);
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const ItemPanel it = items[u / per_tile];
+    const int r0 = (u % per_tile) * PR;
+    const TileRef ref = A.tiles[it.tile];
+    const char* src = tile_bytes(A, it.tile);
+    const double s_in = A.scale[it.tile];
+    const double* L = tile_ptr<double>(A, it.diag);
+    __syncthreads();                               // previous unit done with X
+    for (int e = tid; e < PR * b; e += blockDim.x)
+      X[e] = load_f64(src, ref.dt, (int64_t)r0 * b + e) * s_in;
+    for (int cb = 0; cb < b / NB; ++cb) {
+      for (int e = tid; e < NB * NB; e += blockDim.x)
+        Dv[(e / NB) * (NB + 1) + e % NB] = it.dinv[(int64_t)cb * NB * NB + e];
+      __syncthreads();
+      double acc[4], acc2[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { acc[q] = X[r * b + cb * NB + cx + 8 * q]; acc2[q] = 0.0; }
+      const int nch = cb * NB / PK;
+      double pre[NB * PK / 128];
+      if (nch > 0) {
+#pragma unroll
+        for (int k = 0; k < NB * PK / 128; ++k) {
+          const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
+          pre[k] = L[(int64_t)(cb * NB + rr) * b + tt];
+        }
+#pragma unroll
+        for (int k = 0; k < NB * PK / 128; ++k) {
+          const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
+          Ls[rr * (PK + 1) + tt] = pre[k];
+        }
+        __syncthreads();
+      }
+      for (int ch = 0; ch < nch; ++ch) {
+        const double* Lc = Ls + (ch & 1) * NB * (PK + 1);
+        if (ch + 1 < nch) {
+#pragma unroll
+          for (int k = 0; k < NB * PK / 128; ++k) {
+            const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
+            pre[k] = L[(int64_t)(cb * NB + rr) * b + (ch + 1) * PK + tt];
+          }
+        }
+        const double* Xr = X + r * b + ch * PK;
+#pragma unroll 8
+        for (int tt = 0; tt < PK; tt += 2) {
+          const double x0 = Xr[tt], x1 = Xr[tt + 1];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[q] -= x0 * Lc[(cx + 8 * q) * (PK + 1) + tt];
+            acc2[q] -= x1 * Lc[(cx + 8 * q) * (PK + 1) + tt + 1];
+          }
+        }
+        if (ch + 1 < nch) {
+          double* Ln = Ls + ((ch + 1) & 1) * NB * (PK + 1);
+#pragma unroll
+          for (int k = 0; k < NB * PK / 128; ++k) {
+            const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
+            Ln[rr * (PK + 1) + tt] = pre[k];
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Ac[r * (NB + 1) + cx + 8 * q] = acc[q] + acc2[q];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = cx + 8 * q;
+        double v0 = 0.0, v1 = 0.0;
+        int t = 0;
+        for (; t + 1 <= c; t += 2) {
+          v0 += Ac[r * (NB + 1) + t] * Dv[c * (NB + 1) + t];
+          v1 += Ac[r * (NB + 1) + t + 1] * Dv[c * (NB + 1) + t + 1];
+        }
+        if (t <= c) v0 += Ac[r * (NB + 1) + t] * Dv[c * (NB + 1) + t];
+        X[r * b + cb * NB + c] = v0 + v1;
+      }
+      __syncthreads();
+    }
+    double mx = 0.0;
+    for (int e = tid; e < PR * b; e += blockDim.x) {
+      const double v = X[e];
+      it.x[(int64_t)r0 * b + e] = v;
+      mx = fmax(mx, fabs(v));
+    }
+    mx = warp_max(mx);
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < 4; ++w) mx = fmax(mx, red[w]);
+      atomic_max_pos(&A.amax[it.tile], mx);
+    }
   }
 }
 
@@ -279,13 +351,21 @@ void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb,
 
 void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, cudaStream_t s) {
   if (count <= 0) return;
-  size_t smem = sizeof(double) * ((size_t)PR * A.b + NB * (PK + 1) + NB * (NB + 1) + PR * (NB + 1));
-  static bool attr = false;
-  if (!attr) {
+  const size_t smem =
+      sizeof(double) * ((size_t)PR * A.b + 2 * NB * (PK + 1) + NB * (NB + 1) + PR * (NB + 1));
+  static int slots = 0;
+  if (!slots) {
     cudaFuncSetAttribute(k_panel_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    slots = sms;
   }
-  k_panel_trsm<<<dim3(count, A.b / PR), 128, smem, s>>>(A, items);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_trsm, 128, smem);
+  const int units = count * (A.b / PR);
+  const int grid = std::min(units, slots * std::max(per_sm, 1));
+  k_panel_trsm<<<grid, 128, smem, s>>>(A, items, units);
 }
 
 void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaStream_t s) {
