@@ -80,14 +80,16 @@ bool needs_round(int p, int kind) { return p != kind && level(p) >= level(kind);
 
 enum Op {
   OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64, OP_TC,
+  OP_REC, OP_WAIT, OP_AMAXR,
   OP_FP8R, OP_LOGDET, OP_DIAG_F, OP_OFF_F, OP_DIAG_B, OP_OFF_B, OP_GEN_AMAX, OP_GEN
 };
 
 struct Launch {
   int op;
-  size_t off;     // byte offset of the item array in the plan's item buffer
-  int count;
+  size_t off;     // byte offset of the item array (OP_AMAXR: first amax slot)
+  int count;      // items (OP_AMAXR: slots; OP_REC/OP_WAIT: event index)
   int kb;
+  int stream = 0; // 0: the critical chain, 1: the bulk (lookahead)
 };
 
 }  // namespace
@@ -109,7 +111,11 @@ struct Plan {
   mp_ctx* ctx = nullptr;
   int b = 0;
   cudaStream_t stream = nullptr;   // user stream
-  cudaStream_t cap = nullptr;      // internal stream for graph capture
+  cudaStream_t cap = nullptr;      // internal stream for graph capture (chain)
+  cudaStream_t cap2 = nullptr;     // second capture stream (bulk work)
+  std::vector<cudaEvent_t> events; // dependencies between the two streams
+  int64_t pslots = 0;              // panel slots per step parity
+  int64_t amax_panel0 = 0, amax_v0 = 0, amax_dummy = 0;
   bool keep_sigma = false;
   // arena
   std::vector<TileRef> h_tiles;
@@ -195,6 +201,8 @@ struct Plan {
 
   ~Plan() {
     if (chol_exec) cudaGraphExecDestroy(chol_exec);
+    for (auto e : events) cudaEventDestroy(e);
+    if (cap2) cudaStreamDestroy(cap2);
     for (void* p : allocs) raw_free(p);
     if (d_items) raw_free(d_items);
     if (cap) cudaStreamDestroy(cap);
@@ -308,18 +316,40 @@ mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
 }
 
 // Builds the factorisation schedule of every matrix in the plan, merged by
-// step index.  Returns scratch requirements through the plan.
+// step index, as two streams with lookahead:
+//   chain (stream 0): POTRF(k); the panel solve of the first tile (k+1, k)
+//     and its rounding; the SYRK of (k+1, k+1);
+//   bulk (stream 1):  the rest of panel k (and L_kk^{-T}) and its rounding;
+//     the updates of column k+1 below the diagonal; all other updates.
+// Events order them: POTRF(k) after the bulk of step k-2; the first panel
+// tile after the column-(k) updates of step k-1; the SYRK of (k+1, k+1)
+// after the bulk of step k-1; the bulk of step k after POTRF(k) and, for
+// its column updates, after the first tile.  Panel scratch, operand copies
+// and panel amax slots alternate between two sets by step parity, so the
+// chain of step k+1 never touches what the bulk of step k reads.
 void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
   const int b = P.b, nbb = b / 32;
   int maxnt = 0;
   for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
-  int64_t max_panel = 0, max_v = 0;
+  int64_t max_v = 0;
   P.chol.clear();
   P.step_begin.clear();
-  P.chol.push_back({OP_INFO0, 0, 0, 0});
+  P.chol.push_back({OP_INFO0, 0, 0, 0, 0});
+  auto ev = [](int s, int which) { return 4 * s + which; };   // 0 potrf 1 first 2 col 3 rest
+  auto add = [&](int op, size_t off, int count, int kb, int stream) {
+    P.chol.push_back({op, off, count, kb, stream});
+  };
+  auto rec = [&](int e, int st) { add(OP_REC, 0, e, 0, st); };
+  auto wait = [&](int e, int st) { add(OP_WAIT, 0, e, 0, st); };
+  auto amax_reset = [&](int64_t first, int64_t n, int st) {
+    if (n > 0) add(OP_AMAXR, (size_t)first, (int)n, 0, st);
+  };
   for (int s = 0; s < maxnt; ++s) {
     P.step_begin.push_back(P.chol.size());
-    P.chol.push_back({OP_AMAX0, 0, 0, 0});
+    const int par = s & 1;
+    const int64_t slot0 = par * P.pslots;
+    // ---------------- chain: POTRF(s)
+    if (s >= 2) wait(ev(s - 2, 3), 0);
     for (int kb = 0; kb < nbb; ++kb) {
       std::vector<ItemDiag> items;
       for (int m = 0; m < (int)P.mats.size(); ++m) {
@@ -335,119 +365,170 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         items.push_back(it);
       }
       size_t off = P.push(items);
-      P.chol.push_back({OP_POTRF, off, (int)items.size(), kb});
+      add(OP_POTRF, off, (int)items.size(), kb, 0);
       if (kb + 1 < nbb) {
-        P.chol.push_back({OP_ITRSM, off, (int)items.size(), kb});
-        P.chol.push_back({OP_ISYRK, off, (int)items.size(), kb});
+        add(OP_ITRSM, off, (int)items.size(), kb, 0);
+        add(OP_ISYRK, off, (int)items.size(), kb, 0);
       }
     }
-    std::vector<ItemPanel> panel;
-    std::vector<ItemRound> round;
-    std::vector<ItemUpd> u32, u64;
-    std::vector<ItemTC> tc[NDT];
-    std::vector<ItemFp8> f8;
-    int64_t slot = 0, vslot = 0;
+    rec(ev(s, 0), 0);
+    // slot of panel tile (i, s) of matrix m: first tiles first, then the rest
+    std::vector<int64_t> first_slot(P.mats.size(), -1), rest_base(P.mats.size(), 0);
+    int64_t nfirst = 0, nrest = 0;
     for (int m = 0; m < (int)P.mats.size(); ++m) {
+      if (P.mats[m].nt > s + 1) first_slot[m] = nfirst++;
+    }
+    for (int m = 0; m < (int)P.mats.size(); ++m) {
+      rest_base[m] = nfirst + nrest;
+      if (P.mats[m].nt > s + 2) nrest += P.mats[m].nt - s - 2;
+    }
+    auto slot_of = [&](int m, int i) {
+      return slot0 + (i == s + 1 ? first_slot[m] : rest_base[m] + (i - s - 2));
+    };
+    auto form = [&](int m, int i, int d) { return P.slot_shadow[slot_of(m, i)][d]; };
+    auto panel_items = [&](int m, int i, std::vector<ItemPanel>& panel, std::vector<ItemRound>& round) {
       auto& M = P.mats[m];
       const int nt = M.nt;
-      if (nt <= s) continue;
-      const int64_t base = slot;                       // slot of tile (s+1, s)
-      auto slot_of = [&](int i) { return base + (i - s - 1); };
-      auto form = [&](int i, int d) {                  // tile (i, s) in format d
-        return P.slot_shadow[slot_of(i)][d];
-      };
-      for (int i = s + 1; i < nt; ++i) {
-        ItemPanel it{};
-        it.tile = M.tile[i * nt + s];
-        it.diag = M.tile[s * nt + s];
-        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
-        it.x = P.d_panel + slot * (int64_t)b * b;
-        panel.push_back(it);
-        ItemRound r{};
-        r.tile = it.tile;
-        for (int d = 0; d < MAX_SHADOW; ++d) r.shadow[d] = -1;
-        const uint8_t need = M.need[(size_t)i * nt + s];
-        int q = 0;
-        for (int d = 0; d < NDT; ++d)
-          if ((need >> d) & 1) r.shadow[q++] = form(i, d);
-        r.hi = (need & (1u << 5)) ? P.slot_hi[slot] : -1;
-        r.lo = (need & (1u << 5)) ? P.slot_lo[slot] : -1;
-        r.x = it.x;
-        round.push_back(r);
-        ++slot;
-      }
-      for (int j = s + 1; j < nt; ++j)
-        for (int i = j; i < nt; ++i) {
-          const int tc_ = M.tile[i * nt + j], ta = M.tile[i * nt + s], tb = M.tile[j * nt + s];
-          const int q = P.h_tiles[tc_].dt, pa = P.h_tiles[ta].dt, pb = P.h_tiles[tb].dt;
-          const int kd = kind_of(q, pa, pb);
-          float* v = nullptr;
-          int vs = -1;
-          if (q == E4M3) {
-            v = P.d_v + vslot * (int64_t)b * b;
-            vs = (int)(P.h_tiles.size() + vslot);
-            f8.push_back(ItemFp8{tc_, vs, v});
-            ++vslot;
-          }
-          if (kd == F64) {
-            ItemUpd u{tc_, ta, tb, i == j, v, vs, 0};
-            u64.push_back(u);
-          } else if (P.use_tc && kd == F32) {
-            ItemTC u{};
-            u.c = tc_;
-            u.a = P.slot_hi[slot_of(i)];
-            u.a2 = P.slot_lo[slot_of(i)];
-            u.b = P.slot_hi[slot_of(j)];
-            u.b2 = P.slot_lo[slot_of(j)];
-            u.syrk = i == j;
-            u.vslot = vs;
-            u.v = v;
-            tc[F32].push_back(u);
-          } else {
-            const int a = needs_round(pa, kd) ? form(i, kd) : ta;
-            const int bb = needs_round(pb, kd) ? form(j, kd) : tb;
-            if (P.use_tc) {
-              ItemTC u{};
-              u.c = tc_;
-              u.a = a;
-              u.b = bb;
-              u.a2 = u.b2 = -1;
-              u.syrk = i == j;
-              u.vslot = vs;
-              u.v = v;
-              tc[kd].push_back(u);
-            } else {
-              ItemUpd u{tc_, a, bb, i == j, v, vs, 0};
-              u32.push_back(u);
-            }
-          }
-        }
-    }
-    // the inverse of the new diagonal factor: X = I L_ss^{-T}
-    for (int m = 0; m < (int)P.mats.size(); ++m) {
-      auto& M = P.mats[m];
-      if (M.nt <= s) continue;
+      const int64_t q = slot_of(m, i);
       ItemPanel it{};
-      it.tile = P.ident;
-      it.diag = M.tile[s * M.nt + s];
+      it.tile = M.tile[i * nt + s];
+      it.diag = M.tile[s * nt + s];
+      it.amax = (int)(P.amax_panel0 + q);
       it.dinv = M.dinv + (int64_t)s * nbb * 1024;
-      const TileRef r = P.h_tiles[M.linv[s]];
-      it.x = (double*)(P.pool[F64] + (size_t)r.idx * b * b * 8);
+      it.x = P.d_panel + q * (int64_t)b * b;
       panel.push_back(it);
+      ItemRound r{};
+      r.tile = it.tile;
+      for (int d = 0; d < MAX_SHADOW; ++d) r.shadow[d] = -1;
+      const uint8_t need = M.need[(size_t)i * nt + s];
+      int c = 0;
+      for (int d = 0; d < NDT; ++d)
+        if ((need >> d) & 1) r.shadow[c++] = form(m, i, d);
+      r.hi = (need & (1u << 5)) ? P.slot_hi[q] : -1;
+      r.lo = (need & (1u << 5)) ? P.slot_lo[q] : -1;
+      r.amax = it.amax;
+      r.x = it.x;
+      round.push_back(r);
+    };
+    // update items of targets (i, j) with operands from column s
+    int64_t vslot = 0;
+    struct Group {
+      std::vector<ItemUpd> u32, u64;
+      std::vector<ItemTC> tc[NDT];
+      std::vector<ItemFp8> f8;
+    };
+    auto add_update = [&](Group& g, int m, int i, int j) {
+      auto& M = P.mats[m];
+      const int nt = M.nt;
+      const int tc_ = M.tile[i * nt + j], ta = M.tile[i * nt + s], tb = M.tile[j * nt + s];
+      const int q = P.h_tiles[tc_].dt, pa = P.h_tiles[ta].dt, pb = P.h_tiles[tb].dt;
+      const int kd = kind_of(q, pa, pb);
+      float* v = nullptr;
+      int vs = -1;
+      if (q == E4M3) {
+        v = P.d_v + vslot * (int64_t)b * b;
+        vs = (int)(P.amax_v0 + vslot);
+        g.f8.push_back(ItemFp8{tc_, vs, v});
+        ++vslot;
+      }
+      if (kd == F64) {
+        g.u64.push_back(ItemUpd{tc_, ta, tb, i == j, v, vs, 0});
+      } else if (P.use_tc && kd == F32) {
+        ItemTC u{};
+        u.c = tc_;
+        u.a = P.slot_hi[slot_of(m, i)];
+        u.a2 = P.slot_lo[slot_of(m, i)];
+        u.b = P.slot_hi[slot_of(m, j)];
+        u.b2 = P.slot_lo[slot_of(m, j)];
+        u.syrk = i == j;
+        u.vslot = vs;
+        u.v = v;
+        g.tc[F32].push_back(u);
+      } else {
+        const int a = needs_round(pa, kd) ? form(m, i, kd) : ta;
+        const int bb = needs_round(pb, kd) ? form(m, j, kd) : tb;
+        if (P.use_tc) {
+          ItemTC u{};
+          u.c = tc_;
+          u.a = a;
+          u.b = bb;
+          u.a2 = u.b2 = -1;
+          u.syrk = i == j;
+          u.vslot = vs;
+          u.v = v;
+          g.tc[kd].push_back(u);
+        } else {
+          g.u32.push_back(ItemUpd{tc_, a, bb, i == j, v, vs, 0});
+        }
+      }
+    };
+    auto emit = [&](Group& g, int st) {
+      if (!g.u64.empty()) add(OP_UPD64, P.push(g.u64), (int)g.u64.size(), 0, st);
+      if (!g.u32.empty()) add(OP_UPD32, P.push(g.u32), (int)g.u32.size(), 0, st);
+      for (int d : {F32, BF16, F16, E4M3})
+        if (!g.tc[d].empty()) add(OP_TC, P.push(g.tc[d]), (int)g.tc[d].size(), d, st);
+      if (!g.f8.empty()) add(OP_FP8R, P.push(g.f8), (int)g.f8.size(), 0, st);
+    };
+    // ---------------- chain: first panel tile, its rounding, SYRK (s+1, s+1)
+    {
+      std::vector<ItemPanel> panel;
+      std::vector<ItemRound> round;
+      Group syrk;
+      for (int m = 0; m < (int)P.mats.size(); ++m)
+        if (P.mats[m].nt > s + 1) panel_items(m, s + 1, panel, round);
+      if (s >= 1) wait(ev(s - 1, 2), 0);
+      amax_reset(P.amax_panel0 + slot0, nfirst, 0);
+      if (!panel.empty()) {
+        add(OP_PANEL, P.push(panel), (int)panel.size(), 0, 0);
+        add(OP_ROUND, P.push(round), (int)round.size(), 0, 0);
+      }
+      rec(ev(s, 1), 0);
+      for (int m = 0; m < (int)P.mats.size(); ++m)
+        if (P.mats[m].nt > s + 1) add_update(syrk, m, s + 1, s + 1);
+      if (s >= 1) wait(ev(s - 1, 3), 0);
+      emit(syrk, 0);
     }
-    max_panel = std::max(max_panel, slot);
+    // ---------------- bulk: rest of the panel (+ L_ss^{-T}), column s+1, rest
+    {
+      std::vector<ItemPanel> panel;
+      std::vector<ItemRound> round;
+      for (int m = 0; m < (int)P.mats.size(); ++m)
+        for (int i = s + 2; i < P.mats[m].nt; ++i) panel_items(m, i, panel, round);
+      for (int m = 0; m < (int)P.mats.size(); ++m) {
+        auto& M = P.mats[m];
+        if (M.nt <= s) continue;
+        ItemPanel it{};
+        it.tile = P.ident;
+        it.diag = M.tile[s * M.nt + s];
+        it.amax = (int)P.amax_dummy;
+        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+        const TileRef r = P.h_tiles[M.linv[s]];
+        it.x = (double*)(P.pool[F64] + (size_t)r.idx * b * b * 8);
+        panel.push_back(it);
+      }
+      wait(ev(s, 0), 1);
+      amax_reset(P.amax_panel0 + slot0 + nfirst, nrest, 1);
+      add(OP_PANEL, P.push(panel), (int)panel.size(), 0, 1);
+      if (!round.empty()) add(OP_ROUND, P.push(round), (int)round.size(), 0, 1);
+      Group col, rest;
+      for (int m = 0; m < (int)P.mats.size(); ++m)
+        for (int i = s + 2; i < P.mats[m].nt; ++i) add_update(col, m, i, s + 1);
+      for (int m = 0; m < (int)P.mats.size(); ++m)
+        for (int j = s + 2; j < P.mats[m].nt; ++j)
+          for (int i = j; i < P.mats[m].nt; ++i) add_update(rest, m, i, j);
+      wait(ev(s, 1), 1);
+      amax_reset(P.amax_v0, vslot, 1);
+      emit(col, 1);
+      rec(ev(s, 2), 1);
+      emit(rest, 1);
+      rec(ev(s, 3), 1);
+    }
     max_v = std::max(max_v, vslot);
-    if (!panel.empty()) P.chol.push_back({OP_PANEL, P.push(panel), (int)panel.size(), 0});
-    if (!round.empty()) P.chol.push_back({OP_ROUND, P.push(round), (int)round.size(), 0});
-    if (!u64.empty()) P.chol.push_back({OP_UPD64, P.push(u64), (int)u64.size(), 0});
-    if (!u32.empty()) P.chol.push_back({OP_UPD32, P.push(u32), (int)u32.size(), 0});
-    for (int d : {F32, BF16, F16, E4M3})
-      if (!tc[d].empty()) P.chol.push_back({OP_TC, P.push(tc[d]), (int)tc[d].size(), d});
-    if (!f8.empty()) P.chol.push_back({OP_FP8R, P.push(f8), (int)f8.size(), 0});
   }
   P.step_begin.push_back(P.chol.size());
-  P.chol.push_back({OP_LOGDET, 0, (int)P.mats.size(), 0});
-  *panel_slots = max_panel;
+  wait(ev(maxnt - 1, 3), 0);
+  add(OP_LOGDET, 0, (int)P.mats.size(), 0, 0);
+  *panel_slots = P.pslots;
   *v_slots = max_v;
 }
 
@@ -529,13 +610,15 @@ mp_status finish_plan(Plan& P) {
   {
     int64_t panel_slots = 0, v_slots = 0;
     count_scratch(P, &panel_slots, &v_slots);
+    P.pslots = panel_slots;
     uint8_t all = 0;
     for (auto& M : P.mats)
       for (uint8_t v : M.need) all |= v;
-    P.slot_shadow.assign(panel_slots, {});
-    P.slot_hi.assign(panel_slots, -1);
-    P.slot_lo.assign(panel_slots, -1);
-    for (int64_t q = 0; q < panel_slots; ++q) {
+    const int64_t nslot = 2 * panel_slots;            // two sets: step parity
+    P.slot_shadow.assign(nslot, {});
+    P.slot_hi.assign(nslot, -1);
+    P.slot_lo.assign(nslot, -1);
+    for (int64_t q = 0; q < nslot; ++q) {
       for (int d = 0; d < NDT; ++d) P.slot_shadow[q][d] = (all >> d) & 1 ? new_tile(P, d) : -1;
       if (all & (1u << 5)) {
         P.slot_hi[q] = new_tile(P, F32);
@@ -552,12 +635,15 @@ mp_status finish_plan(Plan& P) {
   int64_t panel_slots = 0, v_slots = 0;
   count_scratch(P, &panel_slots, &v_slots);
   void* p;
-  if (mp_status st = P.alloc(&p, (size_t)panel_slots * b * b * 8)) return st;
+  if (mp_status st = P.alloc(&p, (size_t)2 * panel_slots * b * b * 8)) return st;
   P.d_panel = (double*)p;
   if (mp_status st = P.alloc(&p, (size_t)v_slots * b * b * 4)) return st;
   P.d_v = (float*)p;
   const int ntiles = (int)P.h_tiles.size();
-  P.n_amax = ntiles + (int)v_slots;
+  P.amax_panel0 = ntiles;
+  P.amax_v0 = ntiles + 2 * panel_slots;
+  P.amax_dummy = P.amax_v0 + v_slots;
+  P.n_amax = (int)(P.amax_dummy + 1);
   if (mp_status st = P.alloc(&p, sizeof(TileRef) * ntiles)) return st;
   P.d_tiles = (TileRef*)p;
   if (mp_status st = P.alloc(&p, sizeof(double) * ntiles)) return st;
@@ -626,13 +712,30 @@ mp_status finish_plan(Plan& P) {
   build_chol_schedule(P, &ps, &vs);
   if (mp_status st = upload_items(P)) return st;
   P.bytes += (int64_t)P.h_items.size();
-  CK(P.ctx, cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
+  // the critical chain gets the highest stream priority, the bulk the lowest
+  int lo_pri = 0, hi_pri = 0;
+  CK(P.ctx, cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+  CK(P.ctx, cudaStreamCreateWithPriority(&P.cap, cudaStreamNonBlocking, hi_pri));
+  CK(P.ctx, cudaStreamCreateWithPriority(&P.cap2, cudaStreamNonBlocking, lo_pri));
+  int maxnt = 0;
+  for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
+  P.events.resize(4 * maxnt + 2);
+  for (auto& e : P.events) CK(P.ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   return MP_OK;
 }
 
-void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
+
+// Runs one entry of a schedule.  With s2 == nullptr everything goes to s in
+// list order (a valid sequential order) and event entries are skipped.
+void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2 = nullptr) {
   const Arena A = P.arena();
+  cudaStream_t s = (s2 && L.stream == 1) ? s2 : s0;
   switch (L.op) {
+    case OP_REC: if (s2) cudaEventRecord(P.events[L.count], s); break;
+    case OP_WAIT: if (s2) cudaStreamWaitEvent(s, P.events[L.count], 0); break;
+    case OP_AMAXR:
+      cudaMemsetAsync(P.d_amax + L.off, 0, sizeof(unsigned long long) * L.count, s);
+      break;
     case OP_INFO0:
       cudaMemsetAsync(P.d_info, 0x7f, sizeof(long long) * P.mats.size(), s);
       cudaMemsetAsync(P.d_err, 0, sizeof(int), s);
@@ -641,7 +744,10 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
     case OP_POTRF: launch_potrf_block(A, P.item<ItemDiag>(L.off), L.count, P.d_ldparts, P.d_info, s); break;
     case OP_ITRSM: launch_inner_trsm(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
     case OP_ISYRK: launch_inner_syrk(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
-    case OP_PANEL: launch_panel_trsm(A, P.item<ItemPanel>(L.off), L.count, s); break;
+    case OP_PANEL:
+      // the bulk panel leaves SMs free for the chain running beside it
+      launch_panel_trsm(A, P.item<ItemPanel>(L.off), L.count, (s2 && L.stream == 1) ? 16 : 0, s);
+      break;
     case OP_ROUND: launch_panel_round(A, P.item<ItemRound>(L.off), L.count, s); break;
     case OP_UPD32: launch_update_f32(A, P.item<ItemUpd>(L.off), L.count, s); break;
     case OP_UPD64: launch_update_f64(A, P.item<ItemUpd>(L.off), L.count, s); break;
@@ -657,6 +763,17 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s) {
       break;
     default: break;
   }
+}
+
+// Enqueues the factorisation schedule on `s` with the bulk work forked to
+// the plan's second stream (inside a graph capture: two graph branches).
+void run_chol_forked(const Plan& P, cudaStream_t s) {
+  cudaEvent_t fork = P.events[P.events.size() - 2], join = P.events.back();
+  cudaEventRecord(fork, s);
+  cudaStreamWaitEvent(P.cap2, fork, 0);
+  for (const Launch& L : P.chol) run_launch(P, L, s, P.cap2);
+  cudaEventRecord(join, P.cap2);
+  cudaStreamWaitEvent(s, join, 0);
 }
 
 }  // namespace
@@ -940,7 +1057,7 @@ mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet) {
   CK(P.ctx, cudaSetDevice(P.ctx->device));
   if (!P.chol_exec) {
     mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
-      for (const Launch& L : P.chol) run_launch(P, L, s);
+      run_chol_forked(P, s);
     }, &P.chol_exec, &P.chol_kernels);
     if (st) return st;
   }
@@ -1372,7 +1489,7 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
     cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s);
     launch_gen_amax(A, P.item<ItemGen>(off_ga), (int)gamax.size(), s);
     launch_generate(A, P.item<ItemGen>(off_g), (int)gall.size(), s);
-    for (const Launch& L : P.chol) run_launch(P, L, s);
+    run_chol_forked(P, s);
     k_batch_copy<<<count, 256, 0, s>>>(P.item<ItemBatchCopy>(off_cp));
     run_solve(P, P.d_items, fwd, nullptr, s);
     k_batch_out<<<count, 256, 0, s>>>(P.item<ItemBatchOut>(off_out), count, P.d_logdet, P.d_info,

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
     __syncthreads();
     if (tid == 0) {
       for (int w = 1; w < 4; ++w) mx = fmax(mx, red[w]);
-      atomic_max_pos(&A.amax[it.tile], mx);
+      atomic_max_pos(&A.amax[it.amax], mx);
     }
   }
 }
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
   const ItemRound it = items[blockIdx.x];
   const int b = A.b;
   const int dt = A.tiles[it.tile].dt;
-  const double amax = amax_value(&A.amax[it.tile]);
+  const double amax = amax_value(&A.amax[it.amax]);
   const double s = dt == E4M3 ? e4m3_scale(amax) : 1.0;
   char* dst = tile_bytes(A, it.tile);
   // amax of the stored (rounded) tile = the rounded amax (rounding is monotone)
@@ -349,7 +349,8 @@ void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb,
   k_inner_syrk<<<dim3(count, m * (m + 1) / 2), 256, 0, s>>>(A, items, kb);
 }
 
-void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, cudaStream_t s) {
+void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
+                       cudaStream_t s) {
   if (count <= 0) return;
   const size_t smem =
       sizeof(double) * ((size_t)PR * A.b + 2 * NB * (PK + 1) + NB * (NB + 1) + PR * (NB + 1));
@@ -364,7 +365,7 @@ void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, cudaSt
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_trsm, 128, smem);
   const int units = count * (A.b / PR);
-  const int grid = std::min(units, slots * std::max(per_sm, 1));
+  const int grid = std::min(units, std::max(1, slots - reserve_sms) * std::max(per_sm, 1));
   k_panel_trsm<<<grid, 128, smem, s>>>(A, items, units);
 }
 

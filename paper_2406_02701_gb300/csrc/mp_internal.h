@@ -66,7 +66,9 @@ struct ItemDiag {
 struct ItemPanel {
   int32_t tile;       // A_ik
   int32_t diag;       // L_kk
-  double* dinv;       // (b/64) inverses of the diagonal 64-blocks of L_kk
+  int32_t amax;       // amax slot of the result
+  int32_t pad_;
+  double* dinv;       // (b/32) inverses of the diagonal 32-blocks of L_kk
   double* x;          // b x b float64 scratch
 };
 
@@ -77,6 +79,8 @@ struct ItemRound {
   int32_t tile;
   int32_t shadow[MAX_SHADOW];   // -1: unused
   int32_t hi, lo;               // FP32 tiles: value split as TF32 hi + remainder (-1: none)
+  int32_t amax;                 // amax slot written by the panel solve
+  int32_t pad_;
   const double* x;
 };
 
@@ -166,7 +170,9 @@ void launch_potrf_block(const Arena& A, const ItemDiag* items, int count, double
                         long long* info, cudaStream_t s);
 void launch_inner_trsm(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
 void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
-void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, cudaStream_t s);
+// reserve_sms: SMs left free by the persistent grid (for concurrent work)
+void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
+                       cudaStream_t s);
 void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaStream_t s);
 
 // k_update.cu
