@@ -255,12 +255,13 @@ mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* gen_kernels,
  * every launch, and returns per kernel class c (0 diagonal-block POTRF,
  * 1 inner TRSM, 2 inner SYRK, 3 panel TRSM, 4 panel rounding, 5 FP64
  * updates, 6 CUDA-core lower-precision updates, 7 tensor-core updates,
- * 8 E4M3 target rounding, 9 other): h_ms[c] summed event time,
+ * 8 E4M3 target rounding, 9 other, 10 panel TRSM of the first tile of each
+ * step (the lookahead chain's part)): h_ms[c] summed event time,
  * h_launches[c] launches, h_flops[c] algorithmic flops (TRSM b^3 per tile,
  * GEMM 2b^3, SYRK b^2(b+1), POTRF nb^3/3 per 32-block).  Arrays hold
  * nclass >= MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as
  * mp_chol).  Synchronous. */
-#define MP_PROFILE_CLASSES 10
+#define MP_PROFILE_CLASSES 11
 mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, int64_t* h_launches,
                           double* h_flops);
 

@@ -1614,7 +1614,9 @@ extern "C" mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* g
 }
 
 namespace {
-int op_class(int op) {
+int op_class(const Launch& L) {
+  const int op = L.op;
+  if (op == OP_PANEL && L.stream == 0) return 10;
   switch (op) {
     case OP_POTRF: return 0;
     case OP_ITRSM: return 1;
@@ -1651,7 +1653,7 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
     const Launch& L = P.chol[l];
-    const int c = op_class(L.op);
+    const int c = op_class(L);
     h_ms[c] += ms;
     if (c == 9 && L.count == 0) continue;
     h_launches[c] += 1;
@@ -1660,7 +1662,7 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
       case OP_POTRF: h_flops[c] += L.count * nb * nb * nb / 3.0; break;
       case OP_ITRSM: h_flops[c] += L.count * m * nb * nb * nb; break;
       case OP_ISYRK: h_flops[c] += L.count * (m * (m + 1) / 2) * 2.0 * nb * nb * nb; break;
-      case OP_PANEL: h_flops[c] += L.count * b * b * b; break;
+      case OP_PANEL: h_flops[c] += L.count * b * b * b; break;  // incl. L_kk^{-T} rows
       case OP_UPD64:
       case OP_UPD32: {
         const ItemUpd* it = reinterpret_cast<const ItemUpd*>(P.h_items.data() + L.off);

@@ -130,20 +130,22 @@ __global__ void __launch_bounds__(256) k_offdiag_fwd(Arena A, const ItemSolve* _
   }
 }
 
-// Backward: in_j -= L_ij^T out_i (tile columns).  One CTA: 128 columns, two
-// halves of the rows.
+// Backward: in_j -= L_ij^T out_i (tile columns).  One CTA: 32 columns (one
+// per lane, so a warp reads 256 contiguous bytes of a row), eight warps
+// splitting the rows with two accumulator chains each, partial sums added
+// in a fixed order.
 template <int RCT>
 __global__ void __launch_bounds__(256) k_offdiag_bwd(Arena A, const ItemSolve* __restrict__ items,
                                                      const int* gate) {
   if (gated(gate)) return;
   extern __shared__ double xs[];         // [b][RCT]
-  __shared__ double part[128][RCT + 1];
+  __shared__ double part[8][32][RCT];
   const ItemSolve it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x;
+  const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const TileRef ref = A.tiles[it.tile];
   const char* L = tile_bytes(A, it.tile);
   const double sc = A.scale[it.tile];
-  const int col = blockIdx.y * 128 + (tid & 127), half = tid >> 7;
+  const int col = blockIdx.y * 32 + lane;
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
     const int nc = min(RCT, it.nrhs - c0);
     __syncthreads();
@@ -152,77 +154,89 @@ __global__ void __launch_bounds__(256) k_offdiag_bwd(Arena A, const ItemSolve* _
       xs[e] = c < nc ? it.xi[(int64_t)(c0 + c) * it.ld + t] : 0.0;
     }
     __syncthreads();
-    double acc[RCT];
+    double a0[RCT], a1[RCT];
 #pragma unroll
-    for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
-    for (int r = half; r < b; r += 2) {
-      double l = load_f64(L, ref.dt, (int64_t)r * b + col) * sc;
+    for (int c = 0; c < RCT; ++c) { a0[c] = 0.0; a1[c] = 0.0; }
+    for (int r = warp; r < b; r += 16) {
+      const double l0 = load_f64(L, ref.dt, (int64_t)r * b + col) * sc;
+      const double l1 = load_f64(L, ref.dt, (int64_t)(r + 8) * b + col) * sc;
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) acc[c] += l * xs[r * RCT + c];
+      for (int c = 0; c < RCT; ++c) {
+        a0[c] += l0 * xs[r * RCT + c];
+        a1[c] += l1 * xs[(r + 8) * RCT + c];
+      }
     }
-    if (half == 1) {
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) part[tid & 127][c] = acc[c];
-    }
+    for (int c = 0; c < RCT; ++c) part[warp][lane][c] = a0[c] + a1[c];
     __syncthreads();
-    if (half == 0) {
+    if (warp == 0) {
 #pragma unroll
-      for (int c = 0; c < RCT; ++c)
-        if (c < nc) it.xj[(int64_t)(c0 + c) * it.ld + col] -= acc[c] + part[tid][c];
+      for (int c = 0; c < RCT; ++c) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += part[w][lane][c];
+        if (c < nc) it.xj[(int64_t)(c0 + c) * it.ld + col] -= v;
+      }
     }
   }
 }
 
-// r_i = z_i - sum_j Sigma_ij x_j for 32 rows of block row ti.
+// r_i = z_i - sum_j Sigma_ij x_j for 32 rows of block row ti, in chunks of
+// 32 rows x 128 columns of Sigma staged through shared memory.
+constexpr int RW = 128;
 template <int RC>
 __global__ void __launch_bounds__(256) k_residual(Arena A, const ItemResid* __restrict__ items,
                                                   int want_rowabs, const int* gate) {
   if (gated(gate)) return;
-  __shared__ double blk[32][33];
-  __shared__ double xs[32][RC];
+  __shared__ double blk[32][RW + 1];
+  __shared__ double xs[RW][RC];
   const ItemResid it = items[blockIdx.x];
   const int b = A.b, tid = threadIdx.x;
   const int lr0 = blockIdx.y * 32;                // local row offset in block row ti
   const int64_t g0 = (int64_t)it.ti * b + lr0;    // global row
-  const int row = tid / 8, part = tid % 8;
+  const int row = tid / 8, part = tid % 8;        // 8 threads per row, 16 columns each
   for (int c0 = 0; c0 < it.nrhs; c0 += RC) {
     const int nc = min(RC, it.nrhs - c0);
-    double acc[RC];
+    double acc[RC], acc2[RC];
 #pragma unroll
-    for (int c = 0; c < RC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < RC; ++c) { acc[c] = 0.0; acc2[c] = 0.0; }
     double rabs = 0.0;
     for (int tj = 0; tj < it.nt; ++tj) {
       const bool lower = tj <= it.ti;
       const int tile = lower ? it.sig[it.ti * it.nt + tj] : it.sig[tj * it.nt + it.ti];
       const double* S = tile_ptr<double>(A, tile);
-      for (int cc0 = 0; cc0 < b; cc0 += 32) {
+      for (int cc0 = 0; cc0 < b; cc0 += RW) {
         __syncthreads();
-        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        for (int e = tid; e < 32 * RW; e += blockDim.x) {
           if (tj > it.ti) {
             // upper part: Sigma_ij = Sigma_ji^T; consecutive threads read a row of S
             int cc = e / 32, rr = e % 32;
             blk[rr][cc] = S[(int64_t)(cc0 + cc) * b + lr0 + rr];
           } else {
-            int rr = e / 32, cc = e % 32;
+            int rr = e / RW, cc = e % RW;
             int gr = lr0 + rr, gc = cc0 + cc;
             blk[rr][cc] = (tj < it.ti || gc <= gr) ? S[(int64_t)gr * b + gc] : S[(int64_t)gc * b + gr];
           }
         }
-        for (int e = tid; e < 32 * RC; e += blockDim.x) {
-          int t = e % 32, c = e / 32;
+        for (int e = tid; e < RW * RC; e += blockDim.x) {
+          int t = e / RC, c = e % RC;
           xs[t][c] = c < nc ? it.x[(int64_t)(c0 + c) * it.ld + (int64_t)tj * b + cc0 + t] : 0.0;
         }
         __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < RW / 8; q += 2) {
+          const int cc = part + 8 * q, cc2 = cc + 8;
+          const double v = blk[row][cc], v2 = blk[row][cc2];
+          if (want_rowabs && c0 == 0) rabs += fabs(v) + fabs(v2);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int cc = part * 4 + q;
-          const double v = blk[row][cc];
-          if (want_rowabs && c0 == 0) rabs += fabs(v);
-#pragma unroll
-          for (int c = 0; c < RC; ++c) acc[c] += v * xs[cc][c];
+          for (int c = 0; c < RC; ++c) {
+            acc[c] += v * xs[cc][c];
+            acc2[c] += v2 * xs[cc2][c];
+          }
         }
       }
     }
+#pragma unroll
+    for (int c = 0; c < RC; ++c) acc[c] += acc2[c];
     for (int o = 4; o > 0; o >>= 1) {
 #pragma unroll
       for (int c = 0; c < RC; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
@@ -356,7 +370,7 @@ void launch_offdiag_solve(const Arena& A, const ItemSolve* items, int count, int
   const int rc = nrhs == 1 ? 1 : RCMAX;
   size_t smem = sizeof(double) * A.b * rc;
   if (trans) {
-    dim3 grid(count, A.b / 128);
+    dim3 grid(count, A.b / 32);
     if (rc == 1) k_offdiag_bwd<1><<<grid, 256, smem, s>>>(A, items, gate);
     else k_offdiag_bwd<RCMAX><<<grid, 256, smem, s>>>(A, items, gate);
   } else {

@@ -272,7 +272,8 @@ class TiledMatrix:
         return dict(chol=a.value, generate=g.value, loglik=l.value)
 
     PROFILE_CLASSES = ["potrf_block", "inner_trsm", "inner_syrk", "panel_trsm", "panel_round",
-                       "update_f64", "update_simt", "update_tc", "fp8_round", "other"]
+                       "update_f64", "update_simt", "update_tc", "fp8_round", "other",
+                       "panel_trsm_first"]
 
     def profile(self):
         k = len(self.PROFILE_CLASSES)
