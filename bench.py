@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--no-fp64-path", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-requests", type=int, default=512)
     p.add_argument("--serve-requests", type=int, default=36)
     p.add_argument("--serve-rate", type=float, default=6.0, help="Poisson arrivals per second")
     return p.parse_args()
@@ -206,6 +208,47 @@ def reference_arm(args, cfg):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_run(ctx, args, dev):
+    """512 independent Matérn likelihoods (n ~ U{256..4096}, range ~ U[0.02,
+    0.3], nu ~ U{1/2, 3/2, 5/2}), FP64 diagonal / FP32 band / BF16 where the
+    norm bound allows, Morton-ordered points, one CUDA graph launch for all
+    (generation, factorisation, solve, log-likelihood); timed over 3 launches
+    after one warm-up."""
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    reqs = I.batch_requests(args.batch_requests, seed=31)
+    b = 256
+    specs = []
+    flops = 0.0
+    for r in reqs:
+        n = r["n"]
+        ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, r["seed"])).to(dev))
+        pmap = mpchol.map_bound(n, b, ds.cpu().numpy(), (r["sigma2"], r["range"], r["nu"], r["nugget"]),
+                                2, I.F32, I.BF16, 1e-6)
+        zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, r["seed"]).T)).to(dev)
+        specs.append(dict(n=n, map=pmap, locs=ds, zt=zt, sigma2=r["sigma2"], range=r["range"],
+                          nu=r["nu"], nugget=r["nugget"]))
+        flops += chol_flops(n)
+    t0 = time.perf_counter()
+    B = mpchol.Batch(ctx, specs, b=b)
+    plan_s = time.perf_counter() - t0
+    ll, st = B.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        B.run(ll, st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    info = B.info()
+    ok = int((st.cpu().numpy() == 0).sum())
+    return {"requests": len(specs), "ok": ok, "ms_per_launch": ms, "solves_per_s": len(specs) / (ms * 1e-3),
+            "chol_tflops": flops / (ms * 1e-3) / 1e12, "plan_build_s": plan_s,
+            "device_bytes": info["bytes"], "b": info["b"]}
 
 
 def serving_run(ctx, args):
@@ -421,6 +464,10 @@ def ours(args, cfg):
                 "speedup_step": ms64 / ms,
                 "loglik_rel_err_mixed_vs_fp64": (np.abs(ll_mixed - ll64) / np.abs(ll64)).tolist()}
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_run(ctx, args, dev)
+
     serve = None
     if not args.no_serving:
         serve = serving_run(ctx, args)
@@ -455,6 +502,7 @@ def ours(args, cfg):
         "fp64_path": fp64,
         "chol_graph_tflops": F / (phases["chol_graph_ms"] * 1e-3) / 1e12,
         "serving": serve,
+        "batch": batch,
         "chol_breakdown_ms": breakdown,
         "step_phases_ms": phases,
     }

@@ -1,0 +1,166 @@
+"""Full-size checks in the configurations the benchmark runs, on outputs the
+oracle can compute one at a time (entries of L L^T against Sigma_ij,
+residual rows r_i = z_i - Sigma_i x) and on properties that hold at any size
+(refinement convergence, agreement with the all-FP64 path)."""
+import math
+
+import numpy as np
+import pytest
+
+import mpinputs as I
+from oracle import matern as OM
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_02701_gb300 import mpchol
+    return mpchol.Context(0)
+
+
+def _rows_of_L(T, rows, n, b):
+    """Full rows of the factor (lower part) for the given global rows."""
+    out = {}
+    for r in rows:
+        ti = r // b
+        row = np.zeros(n)
+        for tj in range(ti + 1):
+            vals, _, _ = T.get_tile(ti, tj)
+            seg = vals[r - ti * b]
+            lo, hi = tj * b, min(n, (tj + 1) * b)
+            if tj == ti:
+                seg = np.where(np.arange(b) <= r - ti * b, seg, 0.0)
+            row[lo:hi] = seg[:hi - lo]
+        out[r] = row
+    return out
+
+
+def _check_llt(T, locs, n, b, c, u, rng, npairs=24):
+    rows = sorted(set(rng.integers(0, n, 8).tolist()))
+    R = _rows_of_L(T, rows, n, b)
+    for _ in range(npairs):
+        i, j = rng.choice(rows, 2)
+        li, lj = R[i], R[j]
+        llt = float(np.dot(li, lj))
+        d = math.hypot(locs[i, 0] - locs[j, 0], locs[i, 1] - locs[j, 1])
+        sig = float(OM.matern_closed(d, c["nu"], c["range"], c["sigma2"])) + (c["nugget"] if i == j else 0.0)
+        tol = 8 * u * (float(np.dot(np.abs(li), np.abs(lj))) + abs(sig))
+        assert abs(llt - sig) <= tol, (i, j, llt, sig, tol)
+
+
+def _setup(ctx, cfg, pmap_eps):
+    from paper_2406_02701_gb300 import mpchol
+    n, b = cfg["n"], cfg["b"]
+    dl = torch.from_numpy(I.points(n, cfg["seed"])).cuda()
+    ds, _ = ctx.morton_order(dl)
+    _, diag, near, far, band = cfg["map"]
+    norms = ctx.tile_norms(n, b, ds, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+    pmap = ctx.map_guarded(norms.cpu().numpy(), band, near, far, pmap_eps)
+    return dl, ds, pmap
+
+
+def test_bench_workload_n16384_matches_fp64_path_and_sigma(ctx):
+    from paper_2406_02701_gb300 import mpchol
+    c = I.CONFIGS["mixed_bf16_n16384_b512"]
+    n, b = c["n"], c["b"]
+    dl, ds, pmap = _setup(ctx, c, 1e-6)
+    zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, c["seed"]).T)).cuda()
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
+    T.generate(ds, c["sigma2"], c["range"], c["nu"], c["nugget"])
+    info, logdet = T.chol()
+    ll, quad, iters = T.loglik(zt, refine_iters=10)
+    T64 = mpchol.TiledMatrix(ctx, n, b, None)
+    T64.generate(ds, c["sigma2"], c["range"], c["nu"], c["nugget"])
+    info64, logdet64 = T64.chol()
+    ll64, quad64, _ = T64.loglik(zt)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0 and int(info64.item()) == 0
+    assert int(iters.item()) < 10
+    err = abs(ll.item() - ll64.item()) / abs(ll64.item())
+    assert err <= 1e-6, err
+    # both quadratic forms carry a forward error of about kappa(Sigma) u64
+    # (kappa ~ 1e7-1e8 here: nugget 1e-4 against a smooth kernel), so they
+    # agree to that level, not to the last digits
+    assert math.isclose(quad.item(), quad64.item(), rel_tol=1e-6)
+    locs = ds.cpu().numpy()
+    _check_llt(T, locs, n, b, c, 2.0 ** -8, np.random.default_rng(3))
+    _check_llt(T64, locs, n, b, c, 2.0 ** -50, np.random.default_rng(4))
+
+
+def test_fp8_workload_n65536_16rhs_refinement(ctx):
+    from paper_2406_02701_gb300 import mpchol
+    c = I.CONFIGS["mixed_fp8_n65536_b1024"]
+    n, b = c["n"], c["b"]
+    dl, ds, pmap = _setup(ctx, c, 1e-6)
+    nrhs = c["nrhs"]
+    z = I.rhs(n, nrhs, c["seed"])
+    zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
+    T.generate(ds, c["sigma2"], c["range"], c["nu"], c["nugget"])
+    info, logdet = T.chol()
+    ll, quad, iters = T.loglik(zt, refine_iters=10)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    it = iters.cpu().numpy()
+    assert np.all(it < 10), it
+    # solution of Sigma x = z from the same refinement: x = L^-T L^-1 z
+    # recomputed here through the library's solves, then sampled residual rows
+    X = zt.clone()
+    T.trsm(X, 0)
+    T.trsm(X, 1)
+    locs = ds.cpu().numpy()
+    x = X.cpu().numpy().T
+    rng = np.random.default_rng(5)
+    for i in rng.integers(0, n, 6):
+        d = np.hypot(locs[:, 0] - locs[i, 0], locs[:, 1] - locs[i, 1])
+        srow = OM.matern_closed(d, c["nu"], c["range"], c["sigma2"])
+        srow[i] += c["nugget"]
+        r = z[i] - srow @ x
+        # one mixed-precision solve (no refinement): small relative residual
+        assert np.all(np.abs(r) <= 1e-2 * (np.abs(srow) @ np.abs(x) + np.abs(z[i]))), r
+    q = quad.cpu().numpy()
+    assert np.all(np.isfinite(q)) and np.all(q > 0)
+    _check_llt(T, locs, n, b, c, 2.0 ** -4, np.random.default_rng(6), npairs=12)
+
+
+def test_batch_512_requests(ctx):
+    """512 Matérn matrices, n ~ U{256..4096}, range ~ U[0.02, 0.3],
+    nu ~ U{1/2, 3/2, 5/2}, FP32/BF16 maps, one graph launch."""
+    from paper_2406_02701_gb300 import mpchol
+    reqs = I.batch_requests(512, seed=31)
+    b = 256
+    specs, keep = [], []
+    for r in reqs:
+        n = r["n"]
+        dl = torch.from_numpy(I.points(n, r["seed"])).cuda()
+        ds, _ = ctx.morton_order(dl)
+        srt = ds.cpu().numpy()
+        pmap = mpchol.map_bound(n, b, srt, (r["sigma2"], r["range"], r["nu"], r["nugget"]), 2,
+                                I.F32, I.BF16, 1e-6)
+        zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, r["seed"]).T)).cuda()
+        specs.append(dict(n=n, map=pmap, locs=ds, zt=zt, sigma2=r["sigma2"], range=r["range"],
+                          nu=r["nu"], nugget=r["nugget"]))
+    B = mpchol.Batch(ctx, specs, b=b)
+    ll, st = B.run()
+    torch.cuda.synchronize()
+    ll, st = ll.cpu().numpy(), st.cpu().numpy()
+    # the smoothest kernels in the range (range 0.3, nu 5/2, nugget 1e-4) can
+    # lose definiteness already in FP32 storage; those requests report it
+    assert np.mean(st == 0) >= 0.9, np.mean(st == 0)
+    assert set(np.unique(st).tolist()) <= {0, 2}
+    bad = [k for k in range(len(specs)) if st[k] != 0]
+    for k in [0, 7, 100, 333, 511] + bad[:2]:
+        s = specs[k]
+        T = mpchol.TiledMatrix(ctx, s["n"], b, s["map"])
+        T.generate(s["locs"], s["sigma2"], s["range"], s["nu"], s["nugget"])
+        info, _ = T.chol()
+        one, _, _ = T.loglik(s["zt"])
+        torch.cuda.synchronize()
+        if st[k] == 0:
+            assert int(info.item()) == 0 and one.item() == ll[k]
+        else:
+            assert int(info.item()) > 0
