@@ -47,18 +47,30 @@ __global__ void __launch_bounds__(256) k_diag_gemv(Arena A, const ItemSolve* __r
     __syncthreads();
     if (!TRANS) {
       // out[r0 + lane] = sum_{t <= r} X[t][r] v[t]; warps split t
-      double acc[RCT];
+      double acc[4][RCT];
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc[u][c] = 0.0;
       const int r = r0 + lane;
-      for (int t = warp; t < r0 + 32; t += 8) {
-        double x = X[(int64_t)t * b + r];
-        if (t > r) x = 0.0;
+      const int tend = r0 + 32;
+      int t = warp;
+      for (; t + 24 < tend; t += 32) {        // four independent chains
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[c] += x * vs[t * RCT + c];
+        for (int u = 0; u < 4; ++u) {
+          const int tu = t + 8 * u;
+          const double x = tu > r ? 0.0 : X[(int64_t)tu * b + r];
+#pragma unroll
+          for (int c = 0; c < RCT; ++c) acc[u][c] += x * vs[tu * RCT + c];
+        }
+      }
+      for (; t < tend; t += 8) {
+        const double x = t > r ? 0.0 : X[(int64_t)t * b + r];
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc[0][c] += x * vs[t * RCT + c];
       }
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) part[warp][lane][c] = acc[c];
+      for (int c = 0; c < RCT; ++c) part[warp][lane][c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
       __syncthreads();
       if (warp == 0) {
 #pragma unroll
@@ -76,11 +88,25 @@ __global__ void __launch_bounds__(256) k_diag_gemv(Arena A, const ItemSolve* __r
 #pragma unroll
         for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
         const double* Xr = X + (int64_t)r * b;
-        for (int t = (r & ~31) + lane; t < b; t += 32) {
-          double x = t >= r ? Xr[t] : 0.0;
+        double acc2[RCT];
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc2[c] = 0.0;
+        int t = (r & ~31) + lane;
+        for (; t + 32 < b; t += 64) {
+          const double x0 = t >= r ? Xr[t] : 0.0, x1 = Xr[t + 32];
+#pragma unroll
+          for (int c = 0; c < RCT; ++c) {
+            acc[c] += x0 * vs[t * RCT + c];
+            acc2[c] += x1 * vs[(t + 32) * RCT + c];
+          }
+        }
+        for (; t < b; t += 32) {
+          const double x = t >= r ? Xr[t] : 0.0;
 #pragma unroll
           for (int c = 0; c < RCT; ++c) acc[c] += x * vs[t * RCT + c];
         }
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc[c] += acc2[c];
 #pragma unroll
         for (int c = 0; c < RCT; ++c) {
           double v = warp_sum(acc[c]);
@@ -116,11 +142,21 @@ __global__ void __launch_bounds__(256) k_offdiag_fwd(Arena A, const ItemSolve* _
       double acc[RCT];
 #pragma unroll
       for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
-      for (int t = lane; t < b; t += 32) {
-        double l = load_f64(L, ref.dt, (int64_t)r * b + t) * sc;
+      double acc2[RCT];
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[c] += l * xs[t * RCT + c];
+      for (int c = 0; c < RCT; ++c) acc2[c] = 0.0;
+#pragma unroll 4
+      for (int t = lane; t < b; t += 64) {        // b is a multiple of 64
+        const double l0 = load_f64(L, ref.dt, (int64_t)r * b + t) * sc;
+        const double l1 = load_f64(L, ref.dt, (int64_t)r * b + t + 32) * sc;
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) {
+          acc[c] += l0 * xs[t * RCT + c];
+          acc2[c] += l1 * xs[(t + 32) * RCT + c];
+        }
       }
+#pragma unroll
+      for (int c = 0; c < RCT; ++c) acc[c] += acc2[c];
 #pragma unroll
       for (int c = 0; c < RCT; ++c) {
         double v = warp_sum(acc[c]);
@@ -157,6 +193,7 @@ __global__ void __launch_bounds__(256) k_offdiag_bwd(Arena A, const ItemSolve* _
     double a0[RCT], a1[RCT];
 #pragma unroll
     for (int c = 0; c < RCT; ++c) { a0[c] = 0.0; a1[c] = 0.0; }
+#pragma unroll 4
     for (int r = warp; r < b; r += 16) {
       const double l0 = load_f64(L, ref.dt, (int64_t)r * b + col) * sc;
       const double l1 = load_f64(L, ref.dt, (int64_t)(r + 8) * b + col) * sc;
