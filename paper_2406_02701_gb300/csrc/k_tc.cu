@@ -14,7 +14,8 @@
 // warps read the accumulator back (each its 32 lanes) and apply the update
 // to the target tile in global memory:
 //   FP64 target (SYRK into the diagonal)  C -= acc            (float64)
-//   FP32 target                           C = f32(C - acc)    (float64 sub)
+//   FP32 target                           C = C - acc         (one FP32 sub,
+//                                         correctly rounded)
 //   16-bit target                         C = round(C - acc)  (FP32 sub)
 //   E4M3 target                           FP32 scratch + amax (rounded by
 //                                         k_fp8_round with the new scale)
@@ -261,9 +262,10 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) c[j] -= (double)(v[j] * sab);
     } else if (rc.dt == F32) {
+      // one correctly rounded FP32 subtraction = the exact difference rounded once
       float* c = reinterpret_cast<float*>(pc) + o0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] = __double2float_rn((double)c[j] - (double)(v[j] * sab));
+      for (int j = 0; j < 32; ++j) c[j] = __fsub_rn(c[j], v[j] * sab);
     } else if (rc.dt == E4M3) {
       const float fs = (float)sc;
 #pragma unroll

@@ -11,7 +11,8 @@
 // E4M3 operands use their codes; the FP32 sum is multiplied by the two
 // power-of-two scales.  The epilogue subtracts from the target:
 //   FP64 target  in float64,
-//   FP32 target  in float64, rounded once to FP32,
+//   FP32 target  one FP32 subtraction (correctly rounded, so the exact
+//                difference of the two FP32 values rounded once),
 //   16-bit       in FP32, rounded to the target format,
 //   E4M3         in FP32 into a scratch slot plus the slot's amax; the
 //                target is rounded with its new scale by k_fp8_round.
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(256) k_update_f32(Arena A, const ItemUpd* __re
         case F64: reinterpret_cast<double*>(pc)[o] -= (double)p; break;
         case F32: {
           float* c = reinterpret_cast<float*>(pc);
-          c[o] = __double2float_rn((double)c[o] - (double)p);
+          c[o] = __fsub_rn(c[o], p);        // correctly rounded: the exact difference rounded once
           break;
         }
         case E4M3: {
