@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--eps", type=float, default=1e-6)
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle factorisation steps sampled")
+    p.add_argument("--panel", default="fp64", choices=["fp64", "ozaki"],
+                   help="panel solve of tiles stored in FP32 or below: FP64 substitution, or "
+                        "integer-digit products on the tensor cores")
     p.add_argument("--no-fp64-path", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
@@ -333,7 +336,7 @@ def ours(args, cfg):
         Tb.close()
         del Tb
 
-    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=refine > 0)
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=refine > 0, ozaki=args.panel == "ozaki")
     ll = torch.empty(nrhs, dtype=torch.float64, device=dev)
     quad = torch.empty(nrhs, dtype=torch.float64, device=dev)
     iters = torch.empty(nrhs, dtype=torch.int32, device=dev)
@@ -488,6 +491,7 @@ def ours(args, cfg):
         "config": {"workload": args.workload, "n": n, "b": b, "nu": cfg["nu"],
                    "range": cfg["range"], "nugget": cfg["nugget"], "nrhs": nrhs,
                    "refine_iters_max": refine, "morton": cfg["morton"], "map": map_name,
+                   "panel_solve": args.panel,
                    "tiles_per_format": {I.DTYPE_NAMES[k]: v for k, v in counts.items()},
                    "l2": "inputs larger than L2 (tiles + float64 Sigma copy > 1 GB)",
                    "parallelism": f"replicas x{ws}"},

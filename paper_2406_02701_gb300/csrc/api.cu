@@ -80,7 +80,7 @@ bool needs_round(int p, int kind) { return p != kind && level(p) >= level(kind);
 
 enum Op {
   OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64, OP_TC,
-  OP_REC, OP_WAIT, OP_AMAXR,
+  OP_REC, OP_WAIT, OP_AMAXR, OP_OZA, OP_OZW, OP_OZG,
   OP_FP8R, OP_LOGDET, OP_DIAG_F, OP_OFF_F, OP_DIAG_B, OP_OFF_B, OP_GEN_AMAX, OP_GEN
 };
 
@@ -122,6 +122,13 @@ struct Plan {
   int pool_count[NDT] = {};
   int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
   bool use_tc = true;              // tensor-core updates (else CUDA cores)
+  bool ozaki = false;              // panel solve on the tensor cores (integer digits)
+  int oz_s = 0;                    // digits per operand
+  std::vector<std::array<int32_t, OZ_SMAX>> slot_oz;   // digit tiles per panel slot
+  std::vector<std::array<int32_t, OZ_SMAX>> wdig;      // digit tiles of W, per parity x matrix
+  float* d_sigma = nullptr;        // row bounds per panel slot (b each)
+  float* d_tau = nullptr;          // column bounds per parity x matrix (b each)
+  CUtensorMap tmap_bf16_64;        // BF16 pool, box 128 bytes x 64 rows (digit products)
   // operand forms of the panel tiles, per panel slot of a step
   std::vector<std::array<int32_t, NDT>> slot_shadow;
   std::vector<int32_t> slot_hi, slot_lo;
@@ -393,6 +400,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
       ItemPanel it{};
       it.tile = M.tile[i * nt + s];
       it.diag = M.tile[s * nt + s];
+      it.mat = m;
       it.amax = (int)(P.amax_panel0 + q);
       it.dinv = M.dinv + (int64_t)s * nbb * 1024;
       it.x = P.d_panel + q * (int64_t)b * b;
@@ -499,6 +507,8 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         if (M.nt <= s) continue;
         ItemPanel it{};
         it.tile = P.ident;
+        it.identity = 1;
+        it.mat = m;
         it.diag = M.tile[s * M.nt + s];
         it.amax = (int)P.amax_dummy;
         it.dinv = M.dinv + (int64_t)s * nbb * 1024;
@@ -506,9 +516,50 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         it.x = (double*)(P.pool[F64] + (size_t)r.idx * b * b * 8);
         panel.push_back(it);
       }
+      // Ozaki mode: panel tiles stored in FP32 or below take X = A W on the
+      // tensor cores, W = L_ss^{-T} (the identity solve above) split once
+      std::vector<ItemOzA> oza;
+      std::vector<ItemOzW> ozw;
+      std::vector<ItemOz> ozg;
+      if (P.ozaki) {
+        std::vector<ItemPanel> native;
+        std::vector<char> uses(P.mats.size(), 0);
+        for (const ItemPanel& it : panel) {
+          if (it.tile == P.ident || P.h_tiles[it.tile].dt == F64) { native.push_back(it); continue; }
+          const int64_t q = (it.x - P.d_panel) / ((int64_t)b * b);
+          const int m = it.mat;
+          uses[m] = 1;
+          ItemOzA a{};
+          a.tile = it.tile;
+          for (int d = 0; d < OZ_SMAX; ++d) a.slices[d] = P.slot_oz[q][d];
+          a.sigma = P.d_sigma + q * b;
+          oza.push_back(a);
+          ItemOz g{};
+          for (int d = 0; d < OZ_SMAX; ++d) { g.a[d] = P.slot_oz[q][d]; g.w[d] = P.wdig[par * P.mats.size() + m][d]; }
+          g.amax = it.amax;
+          g.sigma = a.sigma;
+          g.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
+          g.x = it.x;
+          ozg.push_back(g);
+        }
+        for (int m = 0; m < (int)P.mats.size(); ++m) {
+          if (!uses[m]) continue;
+          ItemOzW w{};
+          w.wtile = P.mats[m].linv[s];
+          for (int d = 0; d < OZ_SMAX; ++d) w.slices[d] = P.wdig[par * P.mats.size() + m][d];
+          w.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
+          ozw.push_back(w);
+        }
+        panel.swap(native);
+      }
       wait(ev(s, 0), 1);
       amax_reset(P.amax_panel0 + slot0 + nfirst, nrest, 1);
+      if (!oza.empty()) add(OP_OZA, P.push(oza), (int)oza.size(), 0, 1);
       add(OP_PANEL, P.push(panel), (int)panel.size(), 0, 1);
+      if (!ozw.empty()) {
+        add(OP_OZW, P.push(ozw), (int)ozw.size(), 0, 1);
+        add(OP_OZG, P.push(ozg), (int)ozg.size(), 0, 1);
+      }
       if (!round.empty()) add(OP_ROUND, P.push(round), (int)round.size(), 0, 1);
       Group col, rest;
       for (int m = 0; m < (int)P.mats.size(); ++m)
@@ -600,6 +651,13 @@ mp_status make_tensor_maps(Plan& P) {
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(P.ctx, MP_ERR_CUDA, "tensor map of pool %d: error %d", d, (int)r);
     P.have_tmap[d] = true;
+    if (d == BF16) {
+      cuuint32_t box64[2] = {(cuuint32_t)(128 / es), 64};
+      r = encode(&P.tmap_bf16_64, ty, 2, P.pool[d], dims, strides, box64, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(P.ctx, MP_ERR_CUDA, "tensor map (64 rows): error %d", (int)r);
+    }
   }
   return MP_OK;
 }
@@ -625,6 +683,15 @@ mp_status finish_plan(Plan& P) {
         P.slot_lo[q] = new_tile(P, F32);
       }
     }
+    if (P.ozaki) {
+      P.oz_s = oz_slices(b);
+      P.slot_oz.assign(nslot, {});
+      for (int64_t q = 0; q < nslot; ++q)
+        for (int d = 0; d < OZ_SMAX; ++d) P.slot_oz[q][d] = d < P.oz_s ? new_tile(P, BF16) : -1;
+      P.wdig.assign(2 * P.mats.size(), {});
+      for (auto& w : P.wdig)
+        for (int d = 0; d < OZ_SMAX; ++d) w[d] = d < P.oz_s ? new_tile(P, BF16) : -1;
+    }
   }
   for (int d = 0; d < NDT; ++d) {
     void* p = nullptr;
@@ -637,6 +704,12 @@ mp_status finish_plan(Plan& P) {
   void* p;
   if (mp_status st = P.alloc(&p, (size_t)2 * panel_slots * b * b * 8)) return st;
   P.d_panel = (double*)p;
+  if (P.ozaki) {
+    if (mp_status st = P.alloc(&p, sizeof(float) * (size_t)2 * std::max<int64_t>(panel_slots, 1) * b)) return st;
+    P.d_sigma = (float*)p;
+    if (mp_status st = P.alloc(&p, sizeof(float) * 2 * P.mats.size() * b)) return st;
+    P.d_tau = (float*)p;
+  }
   if (mp_status st = P.alloc(&p, (size_t)v_slots * b * b * 4)) return st;
   P.d_v = (float*)p;
   const int ntiles = (int)P.h_tiles.size();
@@ -683,7 +756,7 @@ mp_status finish_plan(Plan& P) {
   P.d_err = (int*)p;
   CK(P.ctx, P.stream_alloc ? cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream)
                            : cudaMemset(P.d_err, 0, sizeof(int)));
-  if (P.use_tc) {
+  if (P.use_tc || P.ozaki) {
     if (mp_status st = make_tensor_maps(P)) return st;
   }
   if (P.keep_sigma) {
@@ -731,6 +804,11 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
   const Arena A = P.arena();
   cudaStream_t s = (s2 && L.stream == 1) ? s2 : s0;
   switch (L.op) {
+    case OP_OZA: launch_oz_split_rows(A, P.item<ItemOzA>(L.off), L.count, s); break;
+    case OP_OZW: launch_oz_split_cols(A, P.item<ItemOzW>(L.off), L.count, s); break;
+    case OP_OZG:
+      launch_oz_gemm(A, P.item<ItemOz>(L.off), L.count, P.tmap[BF16], P.tmap_bf16_64, s);
+      break;
     case OP_REC: if (s2) cudaEventRecord(P.events[L.count], s); break;
     case OP_WAIT: if (s2) cudaStreamWaitEvent(s, P.events[L.count], 0); break;
     case OP_AMAXR:
@@ -880,6 +958,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.stream = (cudaStream_t)stream;
   t->P.keep_sigma = (flags & MP_TMAT_KEEP_SIGMA) != 0;
   t->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
+  t->P.ozaki = (flags & MP_TMAT_OZAKI_TRSM) != 0;
   t->P.stream_alloc = (flags & MP_TMAT_STREAM_ALLOC) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
@@ -1618,6 +1697,9 @@ int op_class(const Launch& L) {
   const int op = L.op;
   if (op == OP_PANEL && L.stream == 0) return 10;
   switch (op) {
+    case OP_OZG: return 11;
+    case OP_OZA:
+    case OP_OZW: return 12;
     case OP_POTRF: return 0;
     case OP_ITRSM: return 1;
     case OP_ISYRK: return 2;
@@ -1663,6 +1745,7 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
       case OP_ITRSM: h_flops[c] += L.count * m * nb * nb * nb; break;
       case OP_ISYRK: h_flops[c] += L.count * (m * (m + 1) / 2) * 2.0 * nb * nb * nb; break;
       case OP_PANEL: h_flops[c] += L.count * b * b * b; break;  // incl. L_kk^{-T} rows
+      case OP_OZG: h_flops[c] += L.count * b * b * b; break;    // the solve it stands for
       case OP_UPD64:
       case OP_UPD32: {
         const ItemUpd* it = reinterpret_cast<const ItemUpd*>(P.h_items.data() + L.off);

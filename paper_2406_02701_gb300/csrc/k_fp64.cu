@@ -173,15 +173,18 @@ constexpr int PK = 32;     // K chunk of L staged in shared memory
 // Persistent over work units (panel tile, 16-row block): CTA u processes
 // units u, u + gridDim.x, ...  The chunks of L_kk are double-buffered: the
 // next chunk is fetched into registers while the current one is used.
+template <int PR>
 __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __restrict__ items,
                                                     int units) {
+  constexpr int LPR = 128 / PR;                    // threads per row
+  constexpr int NQ = NB / LPR;                     // columns of a 32-block per thread
   extern __shared__ double sm[];
   const int b = A.b, tid = threadIdx.x;
   double* X = sm;                                  // [PR][b]
   double* Ls = X + PR * b;                         // 2 x [NB][PK+1]
   double* Dv = Ls + 2 * NB * (PK + 1);             // [NB][NB+1]
   double* Ac = Dv + NB * (NB + 1);                 // [PR][NB+1]
-  const int r = tid / 8, cx = tid % 8;
+  const int r = tid / LPR, cx = tid % LPR;
   const int per_tile = b / PR;
   __shared__ double red[4];
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
@@ -194,20 +197,23 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
     __syncthreads();                               // previous unit done with X
     for (int e = tid; e < PR * b; e += blockDim.x)
       X[e] = load_f64(src, ref.dt, (int64_t)r0 * b + e) * s_in;
-    for (int cb = 0; cb < b / NB; ++cb) {
+    // rows r0.. of I L^{-T} vanish left of column r0: skip those blocks
+    const int cb0 = it.identity ? r0 / NB : 0;
+    for (int cb = cb0; cb < b / NB; ++cb) {
       for (int e = tid; e < NB * NB; e += blockDim.x)
         Dv[(e / NB) * (NB + 1) + e % NB] = it.dinv[(int64_t)cb * NB * NB + e];
       __syncthreads();
-      double acc[4], acc2[4];
+      double acc[NQ], acc2[NQ];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { acc[q] = X[r * b + cb * NB + cx + 8 * q]; acc2[q] = 0.0; }
-      const int nch = cb * NB / PK;
+      for (int q = 0; q < NQ; ++q) { acc[q] = X[r * b + cb * NB + cx + LPR * q]; acc2[q] = 0.0; }
+      const int ch0 = cb0 * NB / PK;
+      const int nch = cb * NB / PK - ch0;
       double pre[NB * PK / 128];
       if (nch > 0) {
 #pragma unroll
         for (int k = 0; k < NB * PK / 128; ++k) {
           const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
-          pre[k] = L[(int64_t)(cb * NB + rr) * b + tt];
+          pre[k] = L[(int64_t)(cb * NB + rr) * b + ch0 * PK + tt];
         }
 #pragma unroll
         for (int k = 0; k < NB * PK / 128; ++k) {
@@ -222,17 +228,17 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
 #pragma unroll
           for (int k = 0; k < NB * PK / 128; ++k) {
             const int e = tid + 128 * k, rr = e / PK, tt = e % PK;
-            pre[k] = L[(int64_t)(cb * NB + rr) * b + (ch + 1) * PK + tt];
+            pre[k] = L[(int64_t)(cb * NB + rr) * b + (ch0 + ch + 1) * PK + tt];
           }
         }
-        const double* Xr = X + r * b + ch * PK;
+        const double* Xr = X + r * b + (ch0 + ch) * PK;
 #pragma unroll 8
         for (int tt = 0; tt < PK; tt += 2) {
           const double x0 = Xr[tt], x1 = Xr[tt + 1];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            acc[q] -= x0 * Lc[(cx + 8 * q) * (PK + 1) + tt];
-            acc2[q] -= x1 * Lc[(cx + 8 * q) * (PK + 1) + tt + 1];
+          for (int q = 0; q < NQ; ++q) {
+            acc[q] -= x0 * Lc[(cx + LPR * q) * (PK + 1) + tt];
+            acc2[q] -= x1 * Lc[(cx + LPR * q) * (PK + 1) + tt + 1];
           }
         }
         if (ch + 1 < nch) {
@@ -246,11 +252,11 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
         __syncthreads();
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Ac[r * (NB + 1) + cx + 8 * q] = acc[q] + acc2[q];
+      for (int q = 0; q < NQ; ++q) Ac[r * (NB + 1) + cx + LPR * q] = acc[q] + acc2[q];
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = cx + 8 * q;
+      for (int q = 0; q < NQ; ++q) {
+        const int c = cx + LPR * q;
         double v0 = 0.0, v1 = 0.0;
         int t = 0;
         for (; t + 1 <= c; t += 2) {
@@ -349,24 +355,44 @@ void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb,
   k_inner_syrk<<<dim3(count, m * (m + 1) / 2), 256, 0, s>>>(A, items, kb);
 }
 
-void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
-                       cudaStream_t s) {
-  if (count <= 0) return;
+namespace {
+
+template <int PR>
+void panel_launch(const Arena& A, const ItemPanel* items, int count, int reserve_sms, cudaStream_t s) {
   const size_t smem =
       sizeof(double) * ((size_t)PR * A.b + 2 * NB * (PK + 1) + NB * (NB + 1) + PR * (NB + 1));
   static int slots = 0;
   if (!slots) {
-    cudaFuncSetAttribute(k_panel_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_panel_trsm<PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     slots = sms;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_trsm, 128, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_trsm<PR>, 128, smem);
   const int units = count * (A.b / PR);
   const int grid = std::min(units, std::max(1, slots - reserve_sms) * std::max(per_sm, 1));
-  k_panel_trsm<<<grid, 128, smem, s>>>(A, items, units);
+  k_panel_trsm<PR><<<grid, 128, smem, s>>>(A, items, units);
+}
+
+}  // namespace
+
+// 16 rows per work unit keep L_kk's chunks reused across rows; a launch
+// with fewer 16-row units than SMs (one panel tile on the critical chain,
+// the identity solve for L_kk^{-T}) takes 4-row units instead, so that its
+// latency, set by the slowest unit, drops about fourfold.
+void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
+                       cudaStream_t s) {
+  if (count <= 0) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if ((int64_t)count * (A.b / 16) < sms) panel_launch<4>(A, items, count, reserve_sms, s);
+  else panel_launch<16>(A, items, count, reserve_sms, s);
 }
 
 void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaStream_t s) {

@@ -1,0 +1,412 @@
+// Panel triangular solve X = A L_kk^{-T} = A W on the tensor cores, with
+// float64-class accuracy, by exact integer-slice arithmetic (the Ozaki
+// scheme: error-free splitting of both operands into short integer digits
+// whose products and sums are exact in FP32).
+//
+//   rows of A:    a = sigma_r sum_p d_p 2^(-6(p+1)),  p < S
+//   columns of W: w = tau_c   sum_q e_q 2^(-6(q+1)),  q < S
+// with sigma_r, tau_c powers of two bounding the row / column and the
+// digits taken by rounding to nearest: |d_0| <= 64, every later digit
+// <= 32, so a digit is an integer of at most 7 bits, exact in BF16.  For one
+// level l = p + q the products d_p e_q summed over K = b are integers of
+// magnitude at most K 2^12 (l = 0) or K (l + 3) 2^10 (l >= 1); for S = 8 and
+// K <= 1024 that is below 2^24, so every level accumulates exactly in an
+// FP32 tensor-memory accumulator of a kind::f16 BF16 MMA (the S = 8 levels
+// of a 128 x 64 output block fill the 512 TMEM columns).  Levels l >= S are
+// dropped:
+//   X = sigma_r tau_c sum_{l < S} 2^(-6(l+2)) sum_{p+q=l} (D_p E_q^T)
+// which, with the digits' own remainders, leaves an error of at most
+// K (1 + (S + 3) / 3) 2^(-6S) sigma_r tau_c (about 8.5e-12 sigma_r tau_c
+// for K = 512).  The levels are added from the smallest to the largest in
+// float-float (pairs of FP32 numbers: about S^2 2^-48 relative error),
+// scaled by the power of two sigma_r tau_c, and written in float64.  Both
+// bounds sit far below the FP32/BF16 rounding the panel result then
+// receives.
+//
+// Data movement of the product (one CTA = 128 rows x 64 columns of X):
+// per K chunk of 64, the S digit chunks of W^T (S x 8 KB) are loaded once
+// into a two-slot ring and the S digit chunks of A (16 KB each) stream
+// through a four-slot ring; every A chunk meets all W chunks it pairs with
+// while both are resident.
+#include <cuda.h>
+
+#include "mp_device.cuh"
+
+namespace mp {
+
+namespace {
+
+constexpr int OZ_BN = 64;                  // output columns per CTA
+constexpr uint32_t OZ_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ void mb_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t par) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(par)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t par, int* err) {
+  for (uint32_t i = 0; i < OZ_WAIT_LIMIT; ++i)
+    if (mb_try(b, par)) return true;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// kind::f16, D = FP32, A = B = BF16, K-major, M = 128, N = 64
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Smallest power of two >= x (1 for x = 0).
+__device__ __forceinline__ float pow2_above(float x) {
+  if (!(x > 0.f)) return 1.f;
+  int e;
+  float m = frexpf(x, &e);                    // x = m 2^e, m in [0.5, 1)
+  return m == 0.5f ? ldexpf(1.f, e - 1) : ldexpf(1.f, e);
+}
+__device__ __forceinline__ double pow2_above_d(double x) {
+  if (!(x > 0.0)) return 1.0;
+  int e;
+  double m = frexp(x, &e);
+  return m == 0.5 ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t c = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return a | (c << 16);
+}
+
+// Rows of A (tile in any storage format; values exact in FP32) into S BF16
+// digit tiles and the row bounds sigma.  One warp per row, four consecutive
+// entries per lane (8-byte stores of four digits).
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_split_rows(Arena A, const ItemOzA* __restrict__ items) {
+  const ItemOzA it = items[blockIdx.x];
+  const int b = A.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.y * 8 + warp;
+  const TileRef ref = A.tiles[it.tile];
+  const char* src = tile_bytes(A, it.tile);
+  const float sc = (float)A.scale[it.tile];
+  uint2* dst[S];
+#pragma unroll
+  for (int p = 0; p < S; ++p)
+    dst[p] = reinterpret_cast<uint2*>(tile_ptr<__nv_bfloat16>(A, it.slices[p]) + (int64_t)row * b);
+  const int64_t r0 = (int64_t)row * b;
+  float mx = 0.f;
+  for (int k = lane * 4; k < b; k += 128)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(load_f32(src, ref.dt, r0 + k + e) * sc));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float sig = pow2_above(mx);
+  if (lane == 0) it.sigma[row] = sig;
+  const float inv = 1.f / sig;                // exact: a power of two
+  for (int k = lane * 4; k < b; k += 128) {
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = load_f32(src, ref.dt, r0 + k + e) * sc * inv;
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      float d[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float t = v[e] * 64.f;
+        d[e] = rintf(t);
+        v[e] = t - d[e];                      // exact
+      }
+      dst[p][k / 4] = make_uint2(pack_bf16x2(d[0], d[1]), pack_bf16x2(d[2], d[3]));
+    }
+  }
+}
+
+// Columns of W (FP64 tile, row-major) into S BF16 digit tiles of W^T (the
+// MMA's K-major B operand: row n of a digit tile is column n of W) and the
+// column bounds tau.  One CTA: 32 columns x 64 rows; the column bound is
+// taken over all b rows by every CTA of the column block (same value).
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_split_cols(Arena A, const ItemOzW* __restrict__ items) {
+  __shared__ double tr[32][65];
+  __shared__ double cmax[8][32];
+  const ItemOzW it = items[blockIdx.x];
+  const int b = A.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n0 = blockIdx.y * 32, k0 = blockIdx.z * 64;
+  const double* W = tile_ptr<double>(A, it.wtile);
+  double mx = 0.0;
+  for (int k = warp; k < b; k += 8) mx = fmax(mx, fabs(W[(int64_t)k * b + n0 + lane]));
+  cmax[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, cmax[w][lane]);
+    const double t = pow2_above_d(mx);
+    if (blockIdx.z == 0) it.tau[n0 + lane] = (float)t;
+    cmax[0][lane] = 1.0 / t;                  // exact: a power of two
+  }
+  __syncthreads();
+  // tr[n][k] = W[k0 + k][n0 + n] / tau_n
+  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+    const int k = e / 32, n = e % 32;
+    tr[n][k] = W[(int64_t)(k0 + k) * b + n0 + n] * cmax[0][n];
+  }
+  __syncthreads();
+  // thread: row n = e / 16 of W^T, four consecutive k (8-byte stores)
+  for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+    const int n = e / 16, kq = (e % 16) * 4;
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = tr[n][kq + j];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      float d[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double t = v[j] * 64.0;
+        const double r = rint(t);
+        v[j] = t - r;                         // exact
+        d[j] = (float)r;
+      }
+      uint2* dst = reinterpret_cast<uint2*>(tile_ptr<__nv_bfloat16>(A, it.slices[q]) +
+                                            (int64_t)(n0 + n) * b + k0 + kq);
+      *dst = make_uint2(pack_bf16x2(d[0], d[1]), pack_bf16x2(d[2], d[3]));
+    }
+  }
+}
+
+constexpr int OZ_ACH = 128 * 128;          // A digit chunk: 128 rows x 128 bytes
+constexpr int OZ_BCH = OZ_BN * 128;        // W digit chunk: 64 rows x 128 bytes
+constexpr int OZ_ASTG = 4;                 // A ring slots
+constexpr int OZ_BSTG = 2;                 // W ring slots (S chunks each)
+
+template <int S>
+__global__ void __launch_bounds__(128, 1)
+    k_oz_gemm(Arena A, const ItemOz* __restrict__ items, const __grid_constant__ CUtensorMap mapA,
+              const __grid_constant__ CUtensorMap mapB) {
+  static_assert(S * OZ_BN <= 512, "levels exceed tensor memory");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bring = smem;                                   // OZ_BSTG x S x OZ_BCH
+  uint8_t* aring = bring + OZ_BSTG * S * OZ_BCH;           // OZ_ASTG x OZ_ACH
+  uint64_t* afull = reinterpret_cast<uint64_t*>(aring + OZ_ASTG * OZ_ACH);
+  uint64_t* aempty = afull + OZ_ASTG;
+  uint64_t* bfull = aempty + OZ_ASTG;
+  uint64_t* bempty = bfull + OZ_BSTG;
+  uint64_t* accf = bempty + OZ_BSTG;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+  const ItemOz it = items[blockIdx.x];
+  const int b = A.b;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.z * OZ_BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_ASTG; ++s) { mb_init(&afull[s], 1); mb_init(&aempty[s], 1); }
+    for (int s = 0; s < OZ_BSTG; ++s) { mb_init(&bfull[s], 1); mb_init(&bempty[s], 1); }
+    mb_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int KT = b / 64;
+  if (warp == 0 && lane == 0) {
+    // producer: per K chunk, the S chunks of W^T, then the S chunks of A
+    int32_t aidx[S], widx[S];
+#pragma unroll
+    for (int p = 0; p < S; ++p) { aidx[p] = A.tiles[it.a[p]].idx; widx[p] = A.tiles[it.w[p]].idx; }
+    bool ok = true;
+    int na = 0, nb = 0;
+    for (int kt = 0; kt < KT && ok; ++kt) {
+      const int sb = kt % OZ_BSTG;
+      if (kt >= OZ_BSTG && !(ok = mb_wait(&bempty[sb], ((kt / OZ_BSTG) - 1) & 1, A.err))) break;
+      mb_expect(&bfull[sb], S * OZ_BCH);
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        tma2d(bring + (sb * S + q) * OZ_BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
+      ++nb;
+#pragma unroll 1
+      for (int p = 0; p < S; ++p) {
+        const int i = kt * S + p, sa = i % OZ_ASTG;
+        if (i >= OZ_ASTG && !(ok = mb_wait(&aempty[sa], ((i / OZ_ASTG) - 1) & 1, A.err))) break;
+        mb_expect(&afull[sa], OZ_ACH);
+        tma2d(aring + sa * OZ_ACH, &mapA, kt * 64, aidx[p] * b + m0, &afull[sa]);
+        ++na;
+      }
+    }
+    if (!ok) {
+      // let the copies in flight land before the CTA exits
+      for (int i = (na > OZ_ASTG ? na - OZ_ASTG : 0); i < na; ++i)
+        mb_wait(&afull[i % OZ_ASTG], (i / OZ_ASTG) & 1, nullptr);
+      for (int k = (nb > OZ_BSTG ? nb - OZ_BSTG : 0); k < nb; ++k)
+        mb_wait(&bfull[k % OZ_BSTG], (k / OZ_BSTG) & 1, nullptr);
+    }
+  } else if (warp == 1 && lane == 0) {
+    bool ok = true;
+    for (int kt = 0; kt < KT && ok; ++kt) {
+      const int sb = kt % OZ_BSTG;
+      if (!(ok = mb_wait(&bfull[sb], (kt / OZ_BSTG) & 1, A.err))) break;
+      const uint32_t b0 = su32(bring + sb * S * OZ_BCH);
+#pragma unroll 1
+      for (int p = 0; p < S; ++p) {
+        const int i = kt * S + p, sa = i % OZ_ASTG;
+        if (!(ok = mb_wait(&afull[sa], (i / OZ_ASTG) & 1, A.err))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = su32(aring + sa * OZ_ACH);
+#pragma unroll 1
+        for (int q = 0; q < S - p; ++q) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
+            mma_bf16(tmem + (uint32_t)(p + q) * OZ_BN, sdesc(a0 + kk * 32),
+                     sdesc(b0 + q * OZ_BCH + kk * 32), acc);
+          }
+        }
+        commit(&aempty[sa]);
+      }
+      commit(&bempty[sb]);
+    }
+    commit(accf);
+  }
+  __syncwarp();
+  const bool have = mb_wait(accf, 0, A.err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  const float sg = it.sigma[row];
+  float mx = 0.f;
+#pragma unroll 1
+  for (int h = 0; h < OZ_BN / 32; ++h) {
+    // levels from the smallest (l = S-1) to the largest, in float-float
+    float hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+#pragma unroll 1
+    for (int l = S - 1; l >= 0; --l) {
+      float v[32];
+      ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * OZ_BN + h * 32), v);
+      const float scl = ldexpf(1.f, -6 * (l + 2));
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float x = v[j] * scl;             // exact: the level sum is an integer < 2^24
+        const float s = hi[j] + x;              // two-sum
+        const float bb = s - hi[j];
+        const float e = (hi[j] - (s - bb)) + (x - bb);
+        hi[j] = s;
+        lo[j] += e;
+      }
+    }
+    if (have) {
+      double* xr = it.x + (int64_t)row * b + n0 + h * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float st = sg * it.tau[n0 + h * 32 + j];   // power of two: scaling is exact
+        const double xv = (double)(hi[j] * st) + (double)(lo[j] * st);
+        xr[j] = xv;
+        mx = fmaxf(mx, fabsf((float)xv));
+      }
+    }
+  }
+  __shared__ float red[4];
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 4; ++w) mx = fmaxf(mx, red[w]);
+    atomic_max_pos(&A.amax[it.amax], (double)mx);
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+template <int S>
+constexpr size_t oz_smem() {
+  return (size_t)OZ_BSTG * S * OZ_BCH + (size_t)OZ_ASTG * OZ_ACH +
+         8 * (2 * OZ_ASTG + 2 * OZ_BSTG + 1) + 16 + 1024;
+}
+
+}  // namespace
+
+constexpr int OZ_S = 8;
+
+int oz_slices(int) { return OZ_S; }
+
+void launch_oz_split_rows(const Arena& A, const ItemOzA* items, int count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_oz_split_rows<OZ_S><<<dim3(count, A.b / 8), 256, 0, s>>>(A, items);
+}
+
+void launch_oz_split_cols(const Arena& A, const ItemOzW* items, int count, cudaStream_t s) {
+  if (count <= 0) return;
+  k_oz_split_cols<OZ_S><<<dim3(count, A.b / 32, A.b / 64), 256, 0, s>>>(A, items);
+}
+
+void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const CUtensorMap& mapA,
+                    const CUtensorMap& mapB, cudaStream_t s) {
+  if (count <= 0) return;
+  constexpr size_t smem = oz_smem<OZ_S>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oz_gemm<OZ_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_oz_gemm<OZ_S><<<dim3(count, A.b / 128, A.b / OZ_BN), 128, smem, s>>>(A, items, mapA, mapB);
+}
+
+}  // namespace mp

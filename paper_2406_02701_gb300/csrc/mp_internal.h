@@ -67,6 +67,8 @@ struct ItemPanel {
   int32_t tile;       // A_ik
   int32_t diag;       // L_kk
   int32_t amax;       // amax slot of the result
+  int32_t identity;   // 1: tile is the identity (rows r >= r0 of X are 0 left of r0)
+  int32_t mat;        // matrix of the plan (host bookkeeping)
   int32_t pad_;
   double* dinv;       // (b/32) inverses of the diagonal 32-blocks of L_kk
   double* x;          // b x b float64 scratch
@@ -101,6 +103,29 @@ struct ItemTC {
   int32_t vslot;
   int32_t pad_;
   float* v;
+};
+
+// Panel solve on the tensor cores (k_ozaki.cu): digit tiles of the rows of
+// A_ik and of the columns of W = L_kk^{-T}.
+constexpr int OZ_SMAX = 8;
+struct ItemOzA {            // split of one panel tile's rows
+  int32_t tile;
+  int32_t slices[OZ_SMAX];  // BF16 digit tiles
+  float* sigma;             // b row bounds
+};
+struct ItemOzW {            // split of W's columns (transposed digit tiles)
+  int32_t wtile;            // FP64 tile holding W
+  int32_t slices[OZ_SMAX];
+  float* tau;               // b column bounds
+};
+struct ItemOz {             // X = A W for one panel tile
+  int32_t a[OZ_SMAX];       // digit tiles of A
+  int32_t w[OZ_SMAX];       // digit tiles of W^T
+  int32_t amax;
+  int32_t pad_;
+  const float* sigma;
+  const float* tau;
+  double* x;                // b x b float64 result
 };
 
 // Rounds an E4M3 target from its FP32 scratch with the new scale.
@@ -179,6 +204,13 @@ void launch_panel_round(const Arena& A, const ItemRound* items, int count, cudaS
 void launch_update_f32(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
 void launch_update_f64(const Arena& A, const ItemUpd* items, int count, cudaStream_t s);
 void launch_fp8_round(const Arena& A, const ItemFp8* items, int count, cudaStream_t s);
+
+// k_ozaki.cu (8 digits per operand for every tile size up to 1024)
+int oz_slices(int b);
+void launch_oz_split_rows(const Arena& A, const ItemOzA* items, int count, cudaStream_t s);
+void launch_oz_split_cols(const Arena& A, const ItemOzW* items, int count, cudaStream_t s);
+void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const struct CUtensorMap_st& mapA,
+                    const struct CUtensorMap_st& mapB, cudaStream_t s);
 
 // k_tc.cu (kind: BF16, F16, E4M3, or F32 as three TF32 products; the map
 // is a const CUtensorMap& of the operands' pool)

@@ -63,13 +63,14 @@ def _setup(ctx, cfg, pmap_eps):
     return dl, ds, pmap
 
 
-def test_bench_workload_n16384_matches_fp64_path_and_sigma(ctx):
+@pytest.mark.parametrize("ozaki", [False, True], ids=["fp64_panel", "ozaki_panel"])
+def test_bench_workload_n16384_matches_fp64_path_and_sigma(ctx, ozaki):
     from paper_2406_02701_gb300 import mpchol
     c = I.CONFIGS["mixed_bf16_n16384_b512"]
     n, b = c["n"], c["b"]
     dl, ds, pmap = _setup(ctx, c, 1e-6)
     zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, c["seed"]).T)).cuda()
-    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True, ozaki=ozaki)
     T.generate(ds, c["sigma2"], c["range"], c["nu"], c["nugget"])
     info, logdet = T.chol()
     ll, quad, iters = T.loglik(zt, refine_iters=10)
@@ -91,7 +92,8 @@ def test_bench_workload_n16384_matches_fp64_path_and_sigma(ctx):
     _check_llt(T64, locs, n, b, c, 2.0 ** -50, np.random.default_rng(4))
 
 
-def test_fp8_workload_n65536_16rhs_refinement(ctx):
+@pytest.mark.parametrize("ozaki", [False, True], ids=["fp64_panel", "ozaki_panel"])
+def test_fp8_workload_n65536_16rhs_refinement(ctx, ozaki):
     from paper_2406_02701_gb300 import mpchol
     c = I.CONFIGS["mixed_fp8_n65536_b1024"]
     n, b = c["n"], c["b"]
@@ -99,7 +101,7 @@ def test_fp8_workload_n65536_16rhs_refinement(ctx):
     nrhs = c["nrhs"]
     z = I.rhs(n, nrhs, c["seed"])
     zt = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
-    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True, ozaki=ozaki)
     T.generate(ds, c["sigma2"], c["range"], c["nu"], c["nugget"])
     info, logdet = T.chol()
     ll, quad, iters = T.loglik(zt, refine_iters=10)

@@ -54,9 +54,29 @@ def assert_close_fmt(got, ref, fmt, extra=0.0, ulps=1, frac=1.0, what=""):
         assert (d > 0).mean() <= frac, f"{what}: {(d > 0).mean():.4f} of entries differ"
 
 
-def _mk(ctx, n, b, pmap, keep_sigma=False, simt=False):
+def _mk(ctx, n, b, pmap, keep_sigma=False, simt=False, ozaki=False):
     from paper_2406_02701_gb300 import mpchol
-    return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma, simt_updates=simt)
+    return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma, simt_updates=simt, ozaki=ozaki)
+
+
+def _pow2_above(x):
+    """Smallest power of two >= x (1 where x == 0)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(np.where(x > 0, x, 1.0))
+    return np.where(x > 0, np.ldexp(1.0, np.where(m == 0.5, e - 1, e)), 1.0)
+
+
+def _ozaki_bound(a, lkk, x, digits=8):
+    """Error bound of X = A W, W = L^{-T}, from 6-bit digit splits: digit
+    remainders and dropped levels K (1 + (S + 3) / 3) 2^(-6S) sigma_r tau_c,
+    float-float level sums S^2 2^-48 |X| (sigma_r, tau_c: powers of two
+    bounding row r of A and column c of W)."""
+    w = np.linalg.inv(np.tril(lkk)).T
+    sig = _pow2_above(np.abs(a).max(axis=1))
+    tau = _pow2_above(np.abs(w).max(axis=0))
+    k = a.shape[1]
+    return (k * (1 + (digits + 3) / 3) * 2.0 ** (-6 * digits) * np.outer(sig, tau)
+            + digits ** 2 * 2.0 ** -48 * np.abs(x))
 
 
 # --------------------------------------------------------------- Morton ----
@@ -143,23 +163,27 @@ def _abs_prod(a, bmat):
     return np.abs(a) @ np.abs(bmat).T
 
 
-@pytest.mark.parametrize("simt", [False, True], ids=["tcgen05", "cudacore"])
+@pytest.mark.parametrize("mode", ["tcgen05", "cudacore", "ozaki"])
 @pytest.mark.parametrize("far", [I.F32, I.BF16, I.F16, I.E4M3])
-def test_single_steps_match_oracle(ctx, far, simt):
+def test_single_steps_match_oracle(ctx, far, mode):
     """Load the oracle's state before step k, run step k on the GPU, compare
     every tile the step writes (POTRF, panel TRSM, SYRK/GEMM updates), with
     the trailing updates on the tensor cores or on the CUDA cores.  FP32
     products on the tensor cores are three TF32 products of hi/lo splits;
     each product then carries at most 3 * 2^-22 |a||b| error (the dropped
     lo*lo term and the truncation of the lo parts), within the same
-    2 K 2^-24 sum|a||b| bound as FP32 accumulation for K >= 12."""
+    2 K 2^-24 sum|a||b| bound as FP32 accumulation for K >= 12.  In the
+    "ozaki" mode the panel tiles below the first one are integer-digit
+    tensor-core products A L_kk^{-T}, within the bound of _ozaki_bound of
+    the float64 solve before their rounding."""
+    simt, ozaki = mode == "cudacore", mode == "ozaki"
     n, b = 640, 128
     nt = n // b
     pmap = I.band_map(nt, I.F64, I.F32, far, 1)
     locs, _ = OM.morton_order(I.points(n, 21))
     S = OM.covariance(locs, 0.5, 0.1, 1.0, 1e-4)
     state = OC.tiled_from_dense(S, b, pmap)
-    T = _mk(ctx, n, b, pmap, simt=simt)
+    T = _mk(ctx, n, b, pmap, simt=simt, ozaki=ozaki)
     for k in range(nt):
         before = {key: OC.Tile(t.codes.copy(), t.fmt, t.scale) for key, t in state.tiles.items()}
         _load_state(T, state, nt)
@@ -179,8 +203,15 @@ def test_single_steps_match_oracle(ctx, far, simt):
                 assert s == rt.scale
                 assert_close_fmt(codes, rt.codes, fmt, frac=2e-3, what=f"trsm {i},{k}")
             else:
-                assert_close_fmt(got, rt.values(), fmt, extra=1e-13 * np.abs(rt.values()).max(),
-                                 frac=2e-3, what=f"trsm {i},{k}")
+                extra = 1e-13 * np.abs(rt.values()).max()
+                frac = 2e-3
+                if ozaki and i > k + 1:
+                    ob = _ozaki_bound(before[(i, k)].values(), state.tiles[(k, k)].codes, rt.values())
+                    extra = extra + ob
+                    # a rounding flips where the exact value lies within the
+                    # error of a rounding boundary: at most 2 bound / ulp
+                    frac += 2 * np.mean(np.minimum(ob / ulp(rt.values(), fmt), 0.5))
+                assert_close_fmt(got, rt.values(), fmt, extra=extra, frac=frac, what=f"trsm {i},{k}")
         # trailing updates
         for j in range(k + 1, nt):
             for i in range(j, nt):
@@ -203,8 +234,8 @@ def test_single_steps_match_oracle(ctx, far, simt):
 
 # ------------------------------------------------------- whole evaluations --
 
-def _run(ctx, n, b, pmap, locs, z, nu, a, s2, tau, refine=0):
-    T = _mk(ctx, n, b, pmap, keep_sigma=refine > 0)
+def _run(ctx, n, b, pmap, locs, z, nu, a, s2, tau, refine=0, ozaki=False):
+    T = _mk(ctx, n, b, pmap, keep_sigma=refine > 0, ozaki=ozaki)
     dl = torch.from_numpy(locs).to(DEV)
     T.generate(dl, s2, a, nu, tau)
     info, logdet = T.chol()
@@ -241,9 +272,11 @@ def test_plain_fp64_n1024_tile128(ctx):
             assert np.allclose(got, want, rtol=0, atol=1e-12), (i, j)
 
 
-@pytest.mark.parametrize("far,refine", [(I.F32, 0), (I.BF16, 0), (I.F16, 0), (I.E4M3, 0),
-                                        (I.BF16, 10), (I.E4M3, 10)])
-def test_mixed_loglik_matches_oracle(ctx, far, refine):
+@pytest.mark.parametrize("far,refine,ozaki", [(I.F32, 0, False), (I.BF16, 0, False), (I.F16, 0, False),
+                                              (I.E4M3, 0, False), (I.BF16, 10, False),
+                                              (I.E4M3, 10, False), (I.F32, 0, True), (I.E4M3, 0, True),
+                                              (I.BF16, 10, True)])
+def test_mixed_loglik_matches_oracle(ctx, far, refine, ozaki):
     n, b = 1000, 128             # ragged: 8 tiles, 24 padding rows
     nt = -(-n // b)
     pmap = I.band_map(nt, I.F64, I.F32, far, 2)
@@ -255,7 +288,7 @@ def test_mixed_loglik_matches_oracle(ctx, far, refine):
     S = OM.covariance(locs, 0.5, a, 1.0, 1e-4)
     ex = OC.exact_loglik(S, z)
     tl = OC.tiled_loglik(S, z, b, pmap, refine_iters=refine)
-    r = _run(ctx, n, b, pmap, locs, z, 0.5, a, 1.0, 1e-4, refine=refine)
+    r = _run(ctx, n, b, pmap, locs, z, 0.5, a, 1.0, 1e-4, refine=refine, ozaki=ozaki)
     assert r["info"] == 0
     err_gpu = np.abs(r["ll"] - ex["loglik"]) / np.abs(ex["loglik"])
     tol = np.maximum(10 * err_gpu, 1e-9)
