@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--eps", type=float, default=1e-6)
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle factorisation steps sampled")
-    p.add_argument("--panel", default="fp64", choices=["fp64", "ozaki"],
+    p.add_argument("--panel", default="ozaki", choices=["fp64", "ozaki"],
                    help="panel solve of tiles stored in FP32 or below: FP64 substitution, or "
                         "integer-digit products on the tensor cores")
     p.add_argument("--no-fp64-path", action="store_true")

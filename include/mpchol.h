@@ -102,16 +102,16 @@ const char* mp_version(void);
  *             memory with cudaMallocAsync / cudaFreeAsync on `stream` (and
  *             uploads with cudaMemcpyAsync), so that creating or destroying
  *             a matrix never waits for other streams' work.
- *             MP_TMAT_OZAKI_TRSM computes the panel solve of every panel
- *             tile stored in FP32 or below as the product X = A_ik W with
- *             W = L_kk^{-T} (FP64, from the identity solve), on the tensor
- *             cores: both operands are split into 8 integer digits of
+ *             By default the panel solve of every panel tile stored in
+ *             FP32 or below is the product X = A_ik W with W = L_kk^{-T}
+ *             (FP64, from the identity solve), on the tensor cores: both operands are split into 8 integer digits of
  *             6 bits, every digit level accumulates exactly in FP32, and
  *             the levels are summed in float-float; the dropped levels
  *             bound the error by b (1 + 11/3) 2^-48 times the product of
  *             the row bound of A and the column bound of W, far below the
  *             FP32 rounding the result then receives.  FP64-stored panel
- *             tiles keep the FP64 solve.
+ *             tiles keep the FP64 solve.  MP_TMAT_FP64_PANEL solves every
+ *             panel tile by FP64 substitution instead.
  *   stream  : stream all later calls on this matrix are ordered on.
  * The library allocates tile storage and workspace on the device (see
  * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
@@ -120,7 +120,7 @@ const char* mp_version(void);
 #define MP_TMAT_KEEP_SIGMA 1u
 #define MP_TMAT_SIMT_UPDATES 2u  /* trailing updates on CUDA cores instead of tcgen05 */
 #define MP_TMAT_STREAM_ALLOC 4u  /* stream-ordered allocation on `stream` (no device sync) */
-#define MP_TMAT_OZAKI_TRSM 8u    /* panel solves of tiles <= FP32 as integer-digit tcgen05 products */
+#define MP_TMAT_FP64_PANEL 8u    /* panel solves by FP64 substitution (default: integer-digit tcgen05 products) */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);
@@ -263,17 +263,16 @@ mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* gen_kernels,
                         int64_t* loglik_kernels);
 
 /* Runs the factorisation once with direct launches and a CUDA event after
- * every launch, and returns per kernel class c (0 diagonal-block POTRF,
- * 1 inner TRSM, 2 inner SYRK, 3 panel TRSM, 4 panel rounding, 5 FP64
- * updates, 6 CUDA-core lower-precision updates, 7 tensor-core updates,
- * 8 E4M3 target rounding, 9 other, 10 panel TRSM of the first tile of each
- * step (the lookahead chain's part), 11 integer-digit panel products
- * (MP_TMAT_OZAKI_TRSM), 12 their digit splits): h_ms[c] summed event time,
- * h_launches[c] launches, h_flops[c] algorithmic flops (TRSM b^3 per tile,
- * GEMM 2b^3, SYRK b^2(b+1), POTRF nb^3/3 per 32-block).  Arrays hold
- * nclass >= MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as
- * mp_chol).  Synchronous. */
-#define MP_PROFILE_CLASSES 13
+ * every launch, and returns per kernel class c (0 diagonal-tile POTRF task
+ * graph, 1 panel TRSM, 2 panel rounding, 3 FP64 updates, 4 CUDA-core
+ * lower-precision updates, 5 tensor-core updates, 6 E4M3 target rounding,
+ * 7 other, 8 panel TRSM of the first tile of each step (the lookahead
+ * chain's part), 9 integer-digit panel products, 10 their digit splits): h_ms[c] summed event time, h_launches[c]
+ * launches, h_flops[c] algorithmic flops (POTRF b^3/3 per tile, TRSM b^3
+ * per tile, GEMM 2b^3, SYRK b^2(b+1)).  Arrays hold nclass >=
+ * MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as mp_chol).
+ * Synchronous. */
+#define MP_PROFILE_CLASSES 11
 mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, int64_t* h_launches,
                           double* h_flops);
 

@@ -79,7 +79,7 @@ int kind_of(int q, int pa, int pb) {
 bool needs_round(int p, int kind) { return p != kind && level(p) >= level(kind); }
 
 enum Op {
-  OP_AMAX0, OP_INFO0, OP_POTRF, OP_ITRSM, OP_ISYRK, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64, OP_TC,
+  OP_AMAX0, OP_INFO0, OP_POTRF_DAG, OP_PANEL, OP_ROUND, OP_UPD32, OP_UPD64, OP_TC,
   OP_REC, OP_WAIT, OP_AMAXR, OP_OZA, OP_OZW, OP_OZG,
   OP_FP8R, OP_LOGDET, OP_DIAG_F, OP_OFF_F, OP_DIAG_B, OP_OFF_B, OP_GEN_AMAX, OP_GEN
 };
@@ -121,6 +121,10 @@ struct Plan {
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
   int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
+  int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix (b/32)^2 counters
+  size_t dag_bytes = 0;
+  size_t dag_tasks_off = 0;        // task list (items buffer offset)
+  int dag_ntasks = 0;
   bool use_tc = true;              // tensor-core updates (else CUDA cores)
   bool ozaki = false;              // panel solve on the tensor cores (integer digits)
   int oz_s = 0;                    // digits per operand
@@ -341,6 +345,11 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
   int64_t max_v = 0;
   P.chol.clear();
   P.step_begin.clear();
+  {
+    const std::vector<DagTask> tasks = potrf_dag_tasks(nbb);
+    P.dag_tasks_off = P.push(tasks);
+    P.dag_ntasks = (int)tasks.size();
+  }
   P.chol.push_back({OP_INFO0, 0, 0, 0, 0});
   auto ev = [](int s, int which) { return 4 * s + which; };   // 0 potrf 1 first 2 col 3 rest
   auto add = [&](int op, size_t off, int count, int kb, int stream) {
@@ -357,26 +366,21 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
     const int64_t slot0 = par * P.pslots;
     // ---------------- chain: POTRF(s)
     if (s >= 2) wait(ev(s - 2, 3), 0);
-    for (int kb = 0; kb < nbb; ++kb) {
-      std::vector<ItemDiag> items;
+    {
+      std::vector<ItemPotrf> items;
       for (int m = 0; m < (int)P.mats.size(); ++m) {
         auto& M = P.mats[m];
         if (M.nt <= s) continue;
-        ItemDiag it{};
+        ItemPotrf it{};
         it.tile = M.tile[s * M.nt + s];
-        it.kb = kb;
-        it.ldslot = M.ldoff + s * nbb + kb;
         it.mat = m;
+        it.ldslot = M.ldoff + s * nbb;
         it.row0 = (int64_t)s * b;
-        it.dinv = M.dinv + ((int64_t)s * nbb + kb) * 1024;
+        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+        it.ver = P.d_dag + 32 + (int64_t)m * nbb * nbb;
         items.push_back(it);
       }
-      size_t off = P.push(items);
-      add(OP_POTRF, off, (int)items.size(), kb, 0);
-      if (kb + 1 < nbb) {
-        add(OP_ITRSM, off, (int)items.size(), kb, 0);
-        add(OP_ISYRK, off, (int)items.size(), kb, 0);
-      }
+      add(OP_POTRF_DAG, P.push(items), (int)items.size(), 0, 0);
     }
     rec(ev(s, 0), 0);
     // slot of panel tile (i, s) of matrix m: first tiles first, then the rest
@@ -754,6 +758,9 @@ mp_status finish_plan(Plan& P) {
   P.d_logdet = (double*)p;
   if (mp_status st = P.alloc(&p, sizeof(int))) return st;
   P.d_err = (int*)p;
+  P.dag_bytes = sizeof(int) * (32 + (size_t)nm * nbb * nbb);
+  if (mp_status st = P.alloc(&p, P.dag_bytes)) return st;
+  P.d_dag = (int*)p;
   CK(P.ctx, P.stream_alloc ? cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream)
                            : cudaMemset(P.d_err, 0, sizeof(int)));
   if (P.use_tc || P.ozaki) {
@@ -819,9 +826,11 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
       cudaMemsetAsync(P.d_err, 0, sizeof(int), s);
       break;
     case OP_AMAX0: cudaMemsetAsync(P.d_amax, 0, sizeof(unsigned long long) * P.n_amax, s); break;
-    case OP_POTRF: launch_potrf_block(A, P.item<ItemDiag>(L.off), L.count, P.d_ldparts, P.d_info, s); break;
-    case OP_ITRSM: launch_inner_trsm(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
-    case OP_ISYRK: launch_inner_syrk(A, P.item<ItemDiag>(L.off), L.count, L.kb, s); break;
+    case OP_POTRF_DAG:
+      cudaMemsetAsync(P.d_dag, 0, P.dag_bytes, s);
+      launch_potrf_dag(A, P.item<ItemPotrf>(L.off), L.count, P.item<DagTask>(P.dag_tasks_off),
+                       P.dag_ntasks, P.d_dag, P.d_ldparts, P.d_info, s);
+      break;
     case OP_PANEL:
       // the bulk panel leaves SMs free for the chain running beside it
       launch_panel_trsm(A, P.item<ItemPanel>(L.off), L.count, (s2 && L.stream == 1) ? 16 : 0, s);
@@ -958,7 +967,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.stream = (cudaStream_t)stream;
   t->P.keep_sigma = (flags & MP_TMAT_KEEP_SIGMA) != 0;
   t->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
-  t->P.ozaki = (flags & MP_TMAT_OZAKI_TRSM) != 0;
+  t->P.ozaki = (flags & MP_TMAT_FP64_PANEL) == 0;
   t->P.stream_alloc = (flags & MP_TMAT_STREAM_ALLOC) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
@@ -1695,21 +1704,19 @@ extern "C" mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* g
 namespace {
 int op_class(const Launch& L) {
   const int op = L.op;
-  if (op == OP_PANEL && L.stream == 0) return 10;
+  if (op == OP_PANEL && L.stream == 0) return 8;
   switch (op) {
-    case OP_OZG: return 11;
+    case OP_POTRF_DAG: return 0;
+    case OP_PANEL: return 1;
+    case OP_ROUND: return 2;
+    case OP_UPD64: return 3;
+    case OP_UPD32: return 4;
+    case OP_TC: return 5;
+    case OP_FP8R: return 6;
+    case OP_OZG: return 9;
     case OP_OZA:
-    case OP_OZW: return 12;
-    case OP_POTRF: return 0;
-    case OP_ITRSM: return 1;
-    case OP_ISYRK: return 2;
-    case OP_PANEL: return 3;
-    case OP_ROUND: return 4;
-    case OP_UPD64: return 5;
-    case OP_UPD32: return 6;
-    case OP_TC: return 7;
-    case OP_FP8R: return 8;
-    default: return 9;
+    case OP_OZW: return 10;
+    default: return 7;
   }
 }
 }  // namespace
@@ -1730,20 +1737,17 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
     cudaEventRecord(ev[l + 1], P.stream);
   }
   cudaError_t e = cudaStreamSynchronize(P.stream);
-  const double b = P.b, nb = 32;
+  const double b = P.b;
   for (size_t l = 0; l < nl && e == cudaSuccess; ++l) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
     const Launch& L = P.chol[l];
     const int c = op_class(L);
     h_ms[c] += ms;
-    if (c == 9 && L.count == 0) continue;
+    if (c == 7 && L.count == 0) continue;
     h_launches[c] += 1;
-    double m = b / nb - L.kb - 1;
     switch (L.op) {
-      case OP_POTRF: h_flops[c] += L.count * nb * nb * nb / 3.0; break;
-      case OP_ITRSM: h_flops[c] += L.count * m * nb * nb * nb; break;
-      case OP_ISYRK: h_flops[c] += L.count * (m * (m + 1) / 2) * 2.0 * nb * nb * nb; break;
+      case OP_POTRF_DAG: h_flops[c] += L.count * b * b * b / 3.0; break;
       case OP_PANEL: h_flops[c] += L.count * b * b * b; break;  // incl. L_kk^{-T} rows
       case OP_OZG: h_flops[c] += L.count * b * b * b; break;    // the solve it stands for
       case OP_UPD64:

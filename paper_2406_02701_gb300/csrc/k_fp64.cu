@@ -3,12 +3,13 @@
 // tile by tile, as in the tiled extension of Sec. 7).
 //
 // The FP64 diagonal tile (b x b, b a multiple of 64) is factored by a
-// blocked right-looking Cholesky over 32 x 32 blocks:
-//   potrf_block  one CTA factors block (kb, kb) in shared memory, adds
-//                2 sum log L_tt to the log-determinant partials, flags the
-//                first pivot that is not > 0, and forms the block's inverse;
-//   inner_trsm   the blocks below: X = A L_kb^{-T} = A Dinv^T;
-//   inner_syrk   the trailing blocks of the tile: A -= X X^T.
+// blocked right-looking Cholesky over 32 x 32 blocks, run as a task graph
+// by one persistent launch (k_potrf_dag): per block column k, one CTA
+// factors block (k, k) in shared memory (adding 2 sum log L_tt to the
+// log-determinant partials, flagging the first pivot that is not > 0, and
+// forming the block's inverse), the blocks below are solved as
+// X = A Dinv_k^T, and the trailing blocks are updated, A -= X X^T, each
+// task starting as soon as its input blocks are final.
 // The panel solve X = A_ik L_kk^{-T} keeps 16 rows of the panel tile in
 // shared memory in float64 and sweeps L_kk's 32-column blocks left to right:
 // acc = A[:, c] - X[:, <c] L[c, <c]^T, then X[:, c] = acc Dinv_c^T.  The
@@ -19,6 +20,7 @@
 // GB300 has little FP64 throughput (about 1.2 TFLOP/s of DFMA), so these
 // kernels are bound by the FP64 pipe, not by memory.
 #include <algorithm>
+#include <vector>
 
 #include "mp_device.cuh"
 
@@ -28,23 +30,41 @@ namespace {
 
 constexpr int NB = 32;   // inner block of the diagonal tile
 
-__global__ void __launch_bounds__(256) k_potrf_block(Arena A, const ItemDiag* __restrict__ items,
-                                                     double* __restrict__ ldparts,
-                                                     long long* __restrict__ info) {
-  __shared__ double S[NB][NB + 1];
-  const ItemDiag it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x;
-  double* T = tile_ptr<double>(A, it.tile) + (int64_t)it.kb * NB * b + it.kb * NB;
-  for (int e = tid; e < NB * NB; e += blockDim.x) S[e / NB][e % NB] = T[(int64_t)(e / NB) * b + e % NB];
-  __syncthreads();
+constexpr uint32_t DAG_WAIT_LIMIT = 1u << 21;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Waits until *ver >= need; false on timeout or when another CTA gave up.
+__device__ bool dag_wait(const int* ver, int need, const int* err) {
+  for (uint32_t i = 0; i < DAG_WAIT_LIMIT; ++i) {
+    if (ld_acquire(ver) >= need) return true;
+    if ((i & 63) == 63 && ld_acquire(err) != 0) return false;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// Block (k, k) in S: Cholesky factor in place (lower part), written back to
+// the tile; 2 sum log L_tt into the log-determinant partial; the first
+// pivot that is not > 0 into info; the block's inverse into dinv.
+__device__ void dag_factor(double (*S)[NB + 1], double (*Di)[NB + 1], double (*Tm)[NB + 1],
+                           double* Tk, int b, double* dinv, double* ldpart, long long* info,
+                           long long row0) {
+  const int tid = threadIdx.x;
   __shared__ double rpiv;
   for (int c = 0; c < NB; ++c) {
     if (tid == 0) {
       const double d = S[c][c];
-      const double piv = sqrt(d);
-      if (!(d > 0.0)) atomicMin(&info[it.mat], (long long)(it.row0 + it.kb * NB + c + 1));
-      S[c][c] = piv;
-      rpiv = 1.0 / piv;
+      if (!(d > 0.0)) atomicMin(info, row0 + c + 1);
+      const double rp = rsqrt(d);            // one rounding-level error: d rp^2 = 1 (1 + O(u))
+      S[c][c] = d * rp;
+      rpiv = rp;
     }
     __syncthreads();
     for (int r = c + 1 + tid; r < NB; r += blockDim.x) S[r][c] *= rpiv;
@@ -60,17 +80,15 @@ __global__ void __launch_bounds__(256) k_potrf_block(Arena A, const ItemDiag* __
   if (tid < 32) {
     double lg = log(S[tid][tid]);
     for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
-    if (tid == 0) ldparts[it.ldslot] = 2.0 * lg;
+    if (tid == 0) *ldpart = 2.0 * lg;
   }
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int r = e / NB, c = e % NB;
-    if (c <= r) T[(int64_t)r * b + c] = S[r][c];
+    if (c <= r) Tk[(int64_t)r * b + c] = S[r][c];
   }
   // inverse of the lower triangular block by recursive doubling: with
   // L = [A 0; C D], L^{-1} = [A^{-1} 0; -D^{-1} C A^{-1}  D^{-1}]; blocks of
   // size 1, 2, 4, 8, 16 are combined pairwise (dependency depth 2 * 31)
-  __shared__ double Di[NB][NB + 1];
-  __shared__ double Tm[NB][NB + 1];
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int r = e / NB, c = e % NB;
     Di[r][c] = r == c ? 1.0 / S[r][r] : 0.0;
@@ -97,73 +115,113 @@ __global__ void __launch_bounds__(256) k_potrf_block(Arena A, const ItemDiag* __
     }
     __syncthreads();
   }
-  for (int e = tid; e < NB * NB; e += blockDim.x) it.dinv[e] = Di[e / NB][e % NB];
+  for (int e = tid; e < NB * NB; e += blockDim.x) dinv[e] = Di[e / NB][e % NB];
 }
 
-// Rows below block kb inside the diagonal tile: X = A Dinv^T.
-__global__ void __launch_bounds__(256) k_inner_trsm(Arena A, const ItemDiag* __restrict__ items, int kb) {
-  __shared__ double X[NB][NB + 1];
-  __shared__ double D[NB][NB + 1];
-  const ItemDiag it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x;
-  const int r0 = (kb + 1 + blockIdx.y) * NB;
-  double* T = tile_ptr<double>(A, it.tile);
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    X[r][c] = T[(int64_t)(r0 + r) * b + kb * NB + c];
-    D[r][c] = it.dinv[e];
-  }
-  __syncthreads();
+// One persistent launch factors the FP64 diagonal tile of every item as a
+// task graph over its 32 x 32 blocks (nb = b / 32):
+//   F(k)       factor block (k, k): L_kk, Dinv_k = L_kk^{-1}, log-det part
+//   T(r, k)    r > k:  L_rk = A_rk Dinv_k^T
+//   U(r, c, k) k < c <= r:  A_rc -= L_rk L_ck^T
+// ver[r nb + c] counts the operations finished on block (r, c): its c
+// updates, then F or T.  CTAs take tasks by an atomic ticket in a fixed
+// topological order (every task's inputs come earlier in the order), so a
+// task only ever waits on tasks that running CTAs have already taken: the
+// schedule cannot deadlock, whatever the number of co-resident CTAs.  Blocks
+// written by other CTAs are read through L2 (ld.global.cg).
+__global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __restrict__ items,
+                                                   int count, const DagTask* __restrict__ tasks,
+                                                   int ntasks, int* ticket, double* ldparts,
+                                                   long long* info) {
+  __shared__ double S0[NB][NB + 1];
+  __shared__ double S1[NB][NB + 1];
+  __shared__ double S2[NB][NB + 1];
+  __shared__ int s_t, s_ok;
+  const int b = A.b, nb = b / NB, tid = threadIdx.x;
   const int ty = tid / 8, tx = tid % 8;
-  double out[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int c = tx + 8 * j;
-    double a0 = 0.0, a1 = 0.0;
-    int t = 0;
-    for (; t + 1 <= c; t += 2) {
-      a0 += X[ty][t] * D[c][t];
-      a1 += X[ty][t + 1] * D[c][t + 1];
+  const int total = ntasks * count;
+  for (;;) {
+    if (tid == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= total) break;
+    const ItemPotrf it = items[t % count];
+    const DagTask tk = tasks[t / count];
+    const int r = tk.r, c = tk.c, k = tk.k;
+    int* ver = it.ver;
+    if (tid == 0) {
+      bool ok;
+      if (tk.op == 0) ok = dag_wait(&ver[k * nb + k], k, A.err);
+      else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err) && dag_wait(&ver[r * nb + k], k, A.err);
+      else ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
+                dag_wait(&ver[r * nb + c], k, A.err);
+      if (!ok) atomicExch(A.err, 1);
+      s_ok = ok;
     }
-    if (t <= c) a0 += X[ty][t] * D[c][t];
-    out[j] = a0 + a1;
-  }
+    __syncthreads();
+    if (!s_ok) break;
+    double* T = tile_ptr<double>(A, it.tile);
+    if (tk.op == 0) {
+      double* Tk = T + (int64_t)k * NB * b + k * NB;
+      for (int e = tid; e < NB * NB; e += blockDim.x) S0[e / NB][e % NB] = __ldcg(Tk + (int64_t)(e / NB) * b + e % NB);
+      __syncthreads();
+      dag_factor(S0, S1, S2, Tk, b, it.dinv + (int64_t)k * NB * NB, ldparts + it.ldslot + k,
+                 info + it.mat, it.row0 + (long long)k * NB);
+    } else if (tk.op == 1) {
+      // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
+      double* Tr = T + (int64_t)r * NB * b + k * NB;
+      const double* D = it.dinv + (int64_t)k * NB * NB;
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        S0[e / NB][e % NB] = __ldcg(Tr + (int64_t)(e / NB) * b + e % NB);
+        S1[e / NB][e % NB] = __ldcg(D + e);
+      }
+      __syncthreads();
+      double out[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) T[(int64_t)(r0 + ty) * b + kb * NB + tx + 8 * j] = out[j];
-}
-
-// Trailing blocks (rb, cb), kb < cb <= rb, of the diagonal tile: A -= X_r X_c^T.
-__global__ void __launch_bounds__(256) k_inner_syrk(Arena A, const ItemDiag* __restrict__ items, int kb) {
-  __shared__ double Xr[NB][NB + 1];
-  __shared__ double Xc[NB][NB + 1];
-  const ItemDiag it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x;
-  // blockIdx.y -> (rb, cb) over the lower triangle of the m x m trailing blocks
-  int p = blockIdx.y, rb = 0;
-  while (p > rb) { p -= rb + 1; ++rb; }
-  const int cb = p;
-  const int R0 = (kb + 1 + rb) * NB, C0 = (kb + 1 + cb) * NB;
-  double* T = tile_ptr<double>(A, it.tile);
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    Xr[r][c] = T[(int64_t)(R0 + r) * b + kb * NB + c];
-    Xc[r][c] = T[(int64_t)(C0 + r) * b + kb * NB + c];
-  }
-  __syncthreads();
-  const int ty = tid / 8, tx = tid % 8;
-  double acc[4] = {}, acc2[4] = {};
-  for (int t = 0; t < NB; t += 2) {
-    double a = Xr[ty][t], a2 = Xr[ty][t + 1];
+      for (int j = 0; j < 4; ++j) {
+        const int cc = tx + 8 * j;
+        double a0 = 0.0, a1 = 0.0;
+        int q = 0;
+        for (; q + 1 <= cc; q += 2) {
+          a0 += S0[ty][q] * S1[cc][q];
+          a1 += S0[ty][q + 1] * S1[cc][q + 1];
+        }
+        if (q <= cc) a0 += S0[ty][q] * S1[cc][q];
+        out[j] = a0 + a1;
+      }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      acc[j] += a * Xc[tx + 8 * j][t];
-      acc2[j] += a2 * Xc[tx + 8 * j][t + 1];
+      for (int j = 0; j < 4; ++j) Tr[(int64_t)ty * b + tx + 8 * j] = out[j];
+    } else {
+      // A_rc -= L_rk L_ck^T
+      const double* Lr = T + (int64_t)r * NB * b + k * NB;
+      const double* Lc = T + (int64_t)c * NB * b + k * NB;
+      double* Trc = T + (int64_t)r * NB * b + c * NB;
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        S0[e / NB][e % NB] = __ldcg(Lr + (int64_t)(e / NB) * b + e % NB);
+        S1[e / NB][e % NB] = __ldcg(Lc + (int64_t)(e / NB) * b + e % NB);
+      }
+      double cur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cur[j] = __ldcg(Trc + (int64_t)ty * b + tx + 8 * j);
+      __syncthreads();
+      double acc[4] = {}, acc2[4] = {};
+      for (int q = 0; q < NB; q += 2) {
+        const double a = S0[ty][q], a2 = S0[ty][q + 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[j] += a * S1[tx + 8 * j][q];
+          acc2[j] += a2 * S1[tx + 8 * j][q + 1];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Trc[(int64_t)ty * b + tx + 8 * j] = cur[j] - (acc[j] + acc2[j]);
     }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int64_t o = (int64_t)(R0 + ty) * b + C0 + tx + 8 * j;
-    T[o] -= acc[j] + acc2[j];
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const int blk = tk.op == 0 ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
+      st_release(&ver[blk], k + 1);
+    }
   }
 }
 
@@ -337,22 +395,39 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
 
 }  // namespace
 
-void launch_potrf_block(const Arena& A, const ItemDiag* items, int count, double* ldparts,
-                        long long* info, cudaStream_t s) {
+std::vector<DagTask> potrf_dag_tasks(int nb) {
+  // F(0), T(., 0); then per k: the update of (k+1, k+1) and F(k+1) first
+  // (the critical chain), the column-(k+1) updates and T(., k+1), then the
+  // rest of step k's updates
+  std::vector<DagTask> v;
+  auto add = [&](int op, int r, int c, int k) {
+    v.push_back(DagTask{(uint8_t)op, (uint8_t)r, (uint8_t)c, (uint8_t)k});
+  };
+  add(0, 0, 0, 0);
+  for (int r = 1; r < nb; ++r) add(1, r, 0, 0);
+  for (int k = 0; k + 1 < nb; ++k) {
+    add(2, k + 1, k + 1, k);
+    add(0, k + 1, k + 1, k + 1);
+    for (int r = k + 2; r < nb; ++r) add(2, r, k + 1, k);
+    for (int r = k + 2; r < nb; ++r) add(1, r, k + 1, k + 1);
+    for (int c = k + 2; c < nb; ++c)
+      for (int r = c; r < nb; ++r) add(2, r, c, k);
+  }
+  return v;
+}
+
+void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const DagTask* tasks,
+                      int ntasks, int* ticket, double* ldparts, long long* info, cudaStream_t s) {
   if (count <= 0) return;
-  k_potrf_block<<<count, 256, 0, s>>>(A, items, ldparts, info);
-}
-
-void launch_inner_trsm(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s) {
-  int m = A.b / NB - kb - 1;
-  if (count <= 0 || m <= 0) return;
-  k_inner_trsm<<<dim3(count, m), 256, 0, s>>>(A, items, kb);
-}
-
-void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s) {
-  int m = A.b / NB - kb - 1;
-  if (count <= 0 || m <= 0) return;
-  k_inner_syrk<<<dim3(count, m * (m + 1) / 2), 256, 0, s>>>(A, items, kb);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int64_t total = (int64_t)ntasks * count;
+  const int grid = (int)std::min<int64_t>(total, std::max<int64_t>(16, std::min<int64_t>(2 * sms, total / 8)));
+  k_potrf_dag<<<grid, 256, 0, s>>>(A, items, count, tasks, ntasks, ticket, ldparts, info);
 }
 
 namespace {

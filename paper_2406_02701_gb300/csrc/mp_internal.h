@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace mp {
@@ -51,15 +52,20 @@ __host__ __device__ inline char* tile_bytes(const Arena& A, int id) {
 
 // ---- work items -----------------------------------------------------------
 
-// POTRF of one 64 x 64 block (kb, kb) of an FP64 diagonal tile, its inverse,
-// and the inner TRSM / SYRK of the same tile.
-struct ItemDiag {
+// Factorisation of one FP64 diagonal tile by the 32 x 32-block task graph
+// (k_potrf_dag); ver and the launch's ticket are zero when it starts.
+struct ItemPotrf {
   int32_t tile;       // FP64 diagonal tile
-  int32_t kb;         // inner block index
-  int32_t ldslot;     // index into the log-determinant partial sums
   int32_t mat;        // matrix index (info word)
+  int32_t ldslot;     // first of b/32 log-determinant partial slots
+  int32_t pad_;
   int64_t row0;       // global row of the tile's first row
-  double* dinv;       // 64 x 64 inverse of block kb (row-major)
+  double* dinv;       // b/32 inverses of the 32 x 32 diagonal blocks (row-major)
+  int32_t* ver;       // (b/32)^2 per-block progress counters
+};
+struct DagTask {
+  uint8_t op;         // 0 factor block (k, k), 1 solve block (r, k), 2 update block (r, c)
+  uint8_t r, c, k;
 };
 
 // Panel TRSM: X = A_ik L_kk^{-T} in float64 into a scratch slot.
@@ -191,10 +197,9 @@ void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* p
                        double* norms, cudaStream_t s);
 
 // k_fp64.cu
-void launch_potrf_block(const Arena& A, const ItemDiag* items, int count, double* ldparts,
-                        long long* info, cudaStream_t s);
-void launch_inner_trsm(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
-void launch_inner_syrk(const Arena& A, const ItemDiag* items, int count, int kb, cudaStream_t s);
+std::vector<DagTask> potrf_dag_tasks(int nb);
+void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const DagTask* tasks,
+                      int ntasks, int* ticket, double* ldparts, long long* info, cudaStream_t s);
 // reserve_sms: SMs left free by the persistent grid (for concurrent work)
 void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
                        cudaStream_t s);

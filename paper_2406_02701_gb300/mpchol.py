@@ -19,7 +19,7 @@ MP_F64, MP_F32, MP_BF16, MP_F16, MP_E4M3 = range(5)
 MP_TMAT_KEEP_SIGMA = 1
 MP_TMAT_SIMT_UPDATES = 2
 MP_TMAT_STREAM_ALLOC = 4
-MP_TMAT_OZAKI_TRSM = 8
+MP_TMAT_FP64_PANEL = 8
 ELEM_BYTES = {MP_F64: 8, MP_F32: 4, MP_BF16: 2, MP_F16: 2, MP_E4M3: 1}
 
 
@@ -198,7 +198,7 @@ class TiledMatrix:
     """mp_tmat: an n x n tiled matrix with a per-tile precision map."""
 
     def __init__(self, ctx: Context, n: int, b: int, pmap=None, keep_sigma=False, stream=None,
-                 simt_updates=False, ozaki=False):
+                 simt_updates=False, ozaki=True):
         self.ctx, self.lib = ctx, ctx.lib
         self.n, self.b = n, b
         self.nt = -(-n // b)
@@ -209,7 +209,7 @@ class TiledMatrix:
             assert self._map.shape == (self.nt, self.nt)
         h = P()
         flags = ((MP_TMAT_KEEP_SIGMA if keep_sigma else 0) | (MP_TMAT_SIMT_UPDATES if simt_updates else 0)
-                 | (MP_TMAT_OZAKI_TRSM if ozaki else 0))
+                 | (0 if ozaki else MP_TMAT_FP64_PANEL))
         mp = None if self._map is None else self._map.ctypes.data_as(C.c_void_p)
         ctx.check(self.lib.mp_tmat_create(ctx.h, n, b, mp, flags, _stream(stream), C.byref(h)))
         self.h = h
@@ -274,9 +274,9 @@ class TiledMatrix:
         self.ctx.check(self.lib.mp_tmat_stats(self.h, C.byref(a), C.byref(g), C.byref(l)))
         return dict(chol=a.value, generate=g.value, loglik=l.value)
 
-    PROFILE_CLASSES = ["potrf_block", "inner_trsm", "inner_syrk", "panel_trsm", "panel_round",
-                       "update_f64", "update_simt", "update_tc", "fp8_round", "other",
-                       "panel_trsm_first", "panel_ozaki_gemm", "ozaki_split"]
+    PROFILE_CLASSES = ["potrf_tile", "panel_trsm", "panel_round", "update_f64", "update_simt",
+                       "update_tc", "fp8_round", "other", "panel_trsm_first", "panel_ozaki_gemm",
+                       "ozaki_split"]
 
     def profile(self):
         k = len(self.PROFILE_CLASSES)

@@ -55,6 +55,7 @@ def assert_close_fmt(got, ref, fmt, extra=0.0, ulps=1, frac=1.0, what=""):
 
 
 def _mk(ctx, n, b, pmap, keep_sigma=False, simt=False, ozaki=False):
+    """Panel solves by FP64 substitution unless `ozaki` (the library default)."""
     from paper_2406_02701_gb300 import mpchol
     return mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=keep_sigma, simt_updates=simt, ozaki=ozaki)
 
