@@ -50,85 +50,120 @@ __device__ bool dag_wait(const int* ver, int need, const int* err) {
   return false;
 }
 
-// Block (k, k) in S: Cholesky factor in place (lower part), written back to
-// the tile; 2 sum log L_tt into the log-determinant partial; the first
-// pivot that is not > 0 into info; the block's inverse into dinv.
-__device__ void dag_factor(double (*S)[NB + 1], double (*Di)[NB + 1], double (*Tm)[NB + 1],
-                           double* Tk, int b, double* dinv, double* ldpart, long long* info,
-                           long long row0) {
-  const int tid = threadIdx.x;
-  __shared__ double rpiv;
-  for (int c = 0; c < NB; ++c) {
-    if (tid == 0) {
-      const double d = S[c][c];
-      if (!(d > 0.0)) atomicMin(info, row0 + c + 1);
-      const double rp = rsqrt(d);            // one rounding-level error: d rp^2 = 1 (1 + O(u))
-      S[c][c] = d * rp;
-      rpiv = rp;
-    }
-    __syncthreads();
-    for (int r = c + 1 + tid; r < NB; r += blockDim.x) S[r][c] *= rpiv;
-    __syncthreads();
-    const int m = NB - 1 - c;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      int rr = e / m, cc = e - rr * m;
-      if (cc <= rr) S[c + 1 + rr][c + 1 + cc] -= S[c + 1 + rr][c] * S[c + 1 + cc][c];
-    }
-    __syncthreads();
-  }
-  // 2 sum log L_tt: one log per lane of warp 0, fixed-order butterfly sum
+// Block (k, k) in S: Cholesky factor in place (lower part) and the block's
+// inverse Y = L^{-1} in R, in one right-looking sweep run as a two-stage
+// pipeline.  In iteration c column c of L is final; warp 0 then finishes
+// column c + 1 (its update with column c, the pivot d, 1/sqrt(d), the
+// scaling), so the sequential chain per column is one FMA and one rsqrt,
+// while warps 1-7 apply column c to the columns beyond c + 1 and advance
+// the inverse: Y[c-1, .] = R[c-1, .] / L_{c-1,c-1}, then
+// R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Writes L and the
+// inverse to global memory; info gets the first pivot that is not > 0.
+__device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk, int b,
+                           double* dinv, long long* info, long long row0) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int NO = 224;                        // threads of warps 1-7
+  __shared__ double rps[NB];                     // 1 / L_cc
+  for (int e = tid; e < NB * NB; e += blockDim.x) R[e / NB][e % NB] = (e / NB == e % NB) ? 1.0 : 0.0;
   if (tid < 32) {
-    double lg = log(S[tid][tid]);
-    for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
-    if (tid == 0) *ldpart = 2.0 * lg;
+    const double d = S[0][0];
+    if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + 1);
+    const double rp = rsqrt(d);
+    if (lane == 0) { S[0][0] = d * rp; rps[0] = rp; }
+    else S[lane][0] *= rp;
   }
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    if (c <= r) Tk[(int64_t)r * b + c] = S[r][c];
-  }
-  // inverse of the lower triangular block by recursive doubling: with
-  // L = [A 0; C D], L^{-1} = [A^{-1} 0; -D^{-1} C A^{-1}  D^{-1}]; blocks of
-  // size 1, 2, 4, 8, 16 are combined pairwise (dependency depth 2 * 31)
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    Di[r][c] = r == c ? 1.0 / S[r][r] : 0.0;
+  for (int c = 0; c < NB; ++c) {
+    __syncthreads();
+    if (tid < 32) {
+      if (c + 1 < NB) {
+        const int n = c + 1;
+        double v = 0.0;
+        if (lane >= n) v = S[lane][n] - S[lane][c] * S[n][c];
+        const double d = __shfl_sync(0xffffffffu, v, n);
+        if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + n + 1);
+        const double rp = rsqrt(d);
+        if (lane == n) S[n][n] = d * rp;           // sqrt(d) = d / sqrt(d)
+        else if (lane > n) S[lane][n] = v * rp;
+        if (lane == 0) rps[n] = rp;
+      }
+    } else {
+      const int t = tid - 32;
+      if (c >= 1 && t < c) R[c - 1][t] *= rps[c - 1];
+      asm volatile("bar.sync 1, %0;" ::"r"(NO));
+      // trailing rows c+2.. on columns c+2..r, then inverse rows c.. on columns < c
+      const int m = NB - 2 - c;
+      const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
+      const int total = ntri + (c >= 1 ? (NB - c) * c : 0);
+      for (int e = t; e < total; e += NO) {
+        if (e < ntri) {
+          int rr = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+          while (rr * (rr + 1) / 2 > e) --rr;
+          while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+          const int r = c + 2 + rr, j = c + 2 + (e - rr * (rr + 1) / 2);
+          S[r][j] -= S[r][c] * S[j][c];
+        } else {
+          const int q = e - ntri;
+          const int r = c + q / c, j = q % c;
+          R[r][j] -= S[r][c - 1] * R[c - 1][j];
+        }
+      }
+    }
   }
   __syncthreads();
-  for (int sz = 1; sz < NB; sz <<= 1) {
-    const int per = sz * sz, pairs = NB / (2 * sz);
-    // T = C A^{-1}: C = S[d0 + r][a0 + t], A^{-1} = Di[a0 + t][a0 + c]
-    for (int e = tid; e < pairs * per; e += blockDim.x) {
-      const int pr = e / per, r = (e % per) / sz, c = e % sz;
-      const int a0 = pr * 2 * sz, d0 = a0 + sz;
-      double acc = 0.0;
-      for (int t = c; t < sz; ++t) acc += S[d0 + r][a0 + t] * Di[a0 + t][a0 + c];
-      Tm[d0 + r][a0 + c] = acc;
-    }
-    __syncthreads();
-    // W = -D^{-1} T: D^{-1} = Di[d0 + r][d0 + t] (t <= r)
-    for (int e = tid; e < pairs * per; e += blockDim.x) {
-      const int pr = e / per, r = (e % per) / sz, c = e % sz;
-      const int a0 = pr * 2 * sz, d0 = a0 + sz;
-      double acc = 0.0;
-      for (int t = 0; t <= r; ++t) acc += Di[d0 + r][d0 + t] * Tm[d0 + t][a0 + c];
-      Di[d0 + r][a0 + c] = -acc;
-    }
-    __syncthreads();
+  if (tid < NB) R[NB - 1][tid] *= rps[NB - 1];
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    if (c <= r) Tk[(int64_t)r * b + c] = S[r][c];
+    dinv[e] = R[r][c];
   }
-  for (int e = tid; e < NB * NB; e += blockDim.x) dinv[e] = Di[e / NB][e % NB];
+}
+
+// 2 sum log L_tt of the block in S: one log per lane of warp 0, fixed-order
+// butterfly sum.
+__device__ void dag_logdet(double (*S)[NB + 1], double* ldpart) {
+  if (threadIdx.x < 32) {
+    double lg = log(S[threadIdx.x][threadIdx.x]);
+    for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
+    if (threadIdx.x == 0) *ldpart = 2.0 * lg;
+  }
+}
+
+// X = A Dinv^T for a 32 x 32 block (Dinv lower triangular): X[i][j] =
+// sum_{t <= j} A[i][t] Dinv[j][t].  Thread (ty, tx) returns row ty,
+// columns tx + 8 q.
+__device__ __forceinline__ void dag_solve(const double (*Ab)[NB + 1], const double (*D)[NB + 1],
+                                          double out[4]) {
+  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  double acc[4] = {};
+  // four independent accumulation chains; q beyond 8 j + 7 is inactive in
+  // the whole warp for column group j
+#pragma unroll 4
+  for (int q = 0; q < NB; ++q) {
+    const double a = Ab[ty][q];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (q <= 8 * j + 7 && q <= tx + 8 * j) acc[j] += a * D[tx + 8 * j][q];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = acc[j];
 }
 
 // One persistent launch factors the FP64 diagonal tile of every item as a
 // task graph over its 32 x 32 blocks (nb = b / 32):
-//   F(k)       factor block (k, k): L_kk, Dinv_k = L_kk^{-1}, log-det part
-//   T(r, k)    r > k:  L_rk = A_rk Dinv_k^T
-//   U(r, c, k) k < c <= r:  A_rc -= L_rk L_ck^T
+//   F(0)       factor block (0, 0): L_00, Dinv_0 = L_00^{-1}, log-det part
+//   G(k)       k >= 1, the critical chain: L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T
+//              (published at once), A_kk -= L_{k,k-1} L_{k,k-1}^T (lower
+//              part), then factor block (k, k)
+//   T(r, k)    r > k + 1:  L_rk = A_rk Dinv_k^T
+//   U(r, c, k) k < c <= r, (r, c) != (k+1, k+1):  A_rc -= L_rk L_ck^T
 // ver[r nb + c] counts the operations finished on block (r, c): its c
-// updates, then F or T.  CTAs take tasks by an atomic ticket in a fixed
-// topological order (every task's inputs come earlier in the order), so a
-// task only ever waits on tasks that running CTAs have already taken: the
-// schedule cannot deadlock, whatever the number of co-resident CTAs.  Blocks
-// written by other CTAs are read through L2 (ld.global.cg).
+// updates, then the factorisation or solve.  CTAs take tasks by an atomic
+// ticket in a fixed topological order (every task's inputs come earlier in
+// the order), so a task only ever waits on tasks that running CTAs have
+// already taken: the schedule cannot deadlock, whatever the number of
+// co-resident CTAs.  Blocks written by other CTAs are read through L2
+// (ld.global.cg); every wait is bounded and reports through the error word.
 __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __restrict__ items,
                                                    int count, const DagTask* __restrict__ tasks,
                                                    int ntasks, int* ticket, double* ldparts,
@@ -151,7 +186,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     int* ver = it.ver;
     if (tid == 0) {
       bool ok;
-      if (tk.op == 0) ok = dag_wait(&ver[k * nb + k], k, A.err);
+      if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err);
+      else if (tk.op == 3)   // G(k): F(k-1), block (k, k-1) and (k, k) updated up to k-2
+        ok = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err) && dag_wait(&ver[k * nb + k - 1], k - 1, A.err) &&
+             dag_wait(&ver[k * nb + k], k - 1, A.err);
       else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err) && dag_wait(&ver[r * nb + k], k, A.err);
       else ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
                 dag_wait(&ver[r * nb + c], k, A.err);
@@ -161,12 +199,49 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     __syncthreads();
     if (!s_ok) break;
     double* T = tile_ptr<double>(A, it.tile);
-    if (tk.op == 0) {
+    if (tk.op == 0 || tk.op == 3) {
       double* Tk = T + (int64_t)k * NB * b + k * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) S0[e / NB][e % NB] = __ldcg(Tk + (int64_t)(e / NB) * b + e % NB);
+      for (int e = tid; e < NB * NB; e += blockDim.x) S2[e / NB][e % NB] = __ldcg(Tk + (int64_t)(e / NB) * b + e % NB);
+      if (tk.op == 3) {
+        // L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T, published before the rest
+        double* Tl = T + (int64_t)k * NB * b + (k - 1) * NB;
+        const double* D = it.dinv + (int64_t)(k - 1) * NB * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+          S0[e / NB][e % NB] = __ldcg(Tl + (int64_t)(e / NB) * b + e % NB);
+          S1[e / NB][e % NB] = __ldcg(D + e);
+        }
+        __syncthreads();
+        double out[4];
+        dag_solve(S0, S1, out);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          S0[ty][tx + 8 * j] = out[j];
+          Tl[(int64_t)ty * b + tx + 8 * j] = out[j];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_release(&ver[k * nb + k - 1], k);
+        }
+        // A_kk -= X X^T on the lower triangle (528 entries)
+        for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) {
+          int rr = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+          while (rr * (rr + 1) / 2 > e) --rr;
+          while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+          const int cc = e - rr * (rr + 1) / 2;
+          double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+          for (int q = 0; q < NB; q += 2) {
+            a0 += S0[rr][q] * S0[cc][q];
+            a1 += S0[rr][q + 1] * S0[cc][q + 1];
+          }
+          S2[rr][cc] -= a0 + a1;
+        }
+      }
       __syncthreads();
-      dag_factor(S0, S1, S2, Tk, b, it.dinv + (int64_t)k * NB * NB, ldparts + it.ldslot + k,
-                 info + it.mat, it.row0 + (long long)k * NB);
+      dag_factor(S2, S1, Tk, b, it.dinv + (int64_t)k * NB * NB, info + it.mat,
+                 it.row0 + (long long)k * NB);
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * NB * b + k * NB;
@@ -177,18 +252,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       }
       __syncthreads();
       double out[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cc = tx + 8 * j;
-        double a0 = 0.0, a1 = 0.0;
-        int q = 0;
-        for (; q + 1 <= cc; q += 2) {
-          a0 += S0[ty][q] * S1[cc][q];
-          a1 += S0[ty][q + 1] * S1[cc][q + 1];
-        }
-        if (q <= cc) a0 += S0[ty][q] * S1[cc][q];
-        out[j] = a0 + a1;
-      }
+      dag_solve(S0, S1, out);
 #pragma unroll
       for (int j = 0; j < 4; ++j) Tr[(int64_t)ty * b + tx + 8 * j] = out[j];
     } else {
@@ -219,13 +283,14 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      const int blk = tk.op == 0 ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
+      const int blk = (tk.op == 0 || tk.op == 3) ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
       st_release(&ver[blk], k + 1);
     }
+    // the log-determinant part is off the critical chain: after publishing
+    if (tk.op == 0 || tk.op == 3) dag_logdet(S2, ldparts + it.ldslot + k);
   }
 }
 
-constexpr int PR = 16;     // panel rows per work unit
 constexpr int PK = 32;     // K chunk of L staged in shared memory
 
 // Persistent over work units (panel tile, 16-row block): CTA u processes
@@ -396,20 +461,19 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
 }  // namespace
 
 std::vector<DagTask> potrf_dag_tasks(int nb) {
-  // F(0), T(., 0); then per k: the update of (k+1, k+1) and F(k+1) first
-  // (the critical chain), the column-(k+1) updates and T(., k+1), then the
-  // rest of step k's updates
+  // F(0), T(r, 0) for r >= 2; then per k: G(k+1) (the critical chain), the
+  // column-(k+1) updates, T(r, k+1) for r >= k+3, then the rest of step k's
+  // updates.  Every task's inputs come earlier in this order.
   std::vector<DagTask> v;
   auto add = [&](int op, int r, int c, int k) {
     v.push_back(DagTask{(uint8_t)op, (uint8_t)r, (uint8_t)c, (uint8_t)k});
   };
   add(0, 0, 0, 0);
-  for (int r = 1; r < nb; ++r) add(1, r, 0, 0);
+  for (int r = 2; r < nb; ++r) add(1, r, 0, 0);
   for (int k = 0; k + 1 < nb; ++k) {
-    add(2, k + 1, k + 1, k);
-    add(0, k + 1, k + 1, k + 1);
+    add(3, k + 1, k + 1, k + 1);
     for (int r = k + 2; r < nb; ++r) add(2, r, k + 1, k);
-    for (int r = k + 2; r < nb; ++r) add(1, r, k + 1, k + 1);
+    for (int r = k + 3; r < nb; ++r) add(1, r, k + 1, k + 1);
     for (int c = k + 2; c < nb; ++c)
       for (int r = c; r < nb; ++r) add(2, r, c, k);
   }

@@ -64,7 +64,8 @@ struct ItemPotrf {
   int32_t* ver;       // (b/32)^2 per-block progress counters
 };
 struct DagTask {
-  uint8_t op;         // 0 factor block (k, k), 1 solve block (r, k), 2 update block (r, c)
+  uint8_t op;         // 0 factor (0, 0), 1 solve (r, k), 2 update (r, c), 3 solve (k, k-1) +
+                      //   update and factor (k, k)
   uint8_t r, c, k;
 };
 
