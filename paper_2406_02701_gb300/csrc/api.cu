@@ -122,6 +122,11 @@ struct Plan {
   int pool_count[NDT] = {};
   int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix (b/32)^2 counters
+  int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
+  std::vector<int64_t> ltab_off;
+  int* d_scnt = nullptr;           // solve task graph: ticket, then per matrix nt (b/32 + 1) counters
+  size_t scnt_bytes = 0;
+  std::vector<int64_t> scnt_off;
   size_t dag_bytes = 0;
   size_t dag_tasks_off = 0;        // task list (items buffer offset)
   int dag_ntasks = 0;
@@ -288,6 +293,7 @@ int new_tile(Plan& P, int dt) {
 mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
   MatDesc M;
   M.n = n;
+  if ((n + P.b - 1) / P.b > 4095) return fail(P.ctx, MP_ERR_ARG, "at most 4095 tiles per side");
   M.nt = (int)((n + P.b - 1) / P.b);
   const int nt = M.nt;
   if (mp_status st = validate_map(P.ctx, nt, map)) return st;
@@ -761,6 +767,23 @@ mp_status finish_plan(Plan& P) {
   P.dag_bytes = sizeof(int) * (32 + (size_t)nm * nbb * nbb);
   if (mp_status st = P.alloc(&p, P.dag_bytes)) return st;
   P.d_dag = (int*)p;
+  {
+    std::vector<int32_t> ltab;
+    size_t cnt = 32;
+    for (auto& M : P.mats) {
+      P.ltab_off.push_back((int64_t)ltab.size());
+      ltab.insert(ltab.end(), M.tile.begin(), M.tile.end());
+      ltab.insert(ltab.end(), M.linv.begin(), M.linv.end());
+      P.scnt_off.push_back((int64_t)cnt);
+      cnt += (size_t)M.nt * (nbb + 1);
+    }
+    if (mp_status st = P.alloc(&p, sizeof(int32_t) * ltab.size())) return st;
+    P.d_ltab = (int32_t*)p;
+    CK(P.ctx, P.upload(P.d_ltab, ltab.data(), sizeof(int32_t) * ltab.size()));
+    P.scnt_bytes = sizeof(int) * cnt;
+    if (mp_status st = P.alloc(&p, P.scnt_bytes)) return st;
+    P.d_scnt = (int*)p;
+  }
   CK(P.ctx, P.stream_alloc ? cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream)
                            : cudaMemset(P.d_err, 0, sizeof(int)));
   if (P.use_tc || P.ozaki) {
@@ -1170,64 +1193,49 @@ mp_status mp_logdet(mp_tmat* t, double* d_out) {
 
 namespace {
 
-struct SolveSched {
-  std::vector<Launch> l;
+// One triangular solve of the plan's matrices, run by the solve task graph.
+struct SolvePlan {
+  size_t items_off = 0, tasks_off = 0;
+  int ntasks = 0, trans = 0, nrhs_max = 1;
 };
-
-enum SolveOp { S_DIAG_F, S_OFF_F, S_DIAG_B, S_OFF_B };
 
 // Forward (trans = 0: out = L^{-1} in) or backward (trans = 1: out = L^{-T}
 // in) tiled solve of the plan's matrices, out of place; `in` is consumed.
 // Vectors are given per matrix as padded N x nrhs blocks with leading
 // dimension ld.
-void build_solve(Plan& P, const std::vector<double*>& in, const std::vector<double*>& out,
-                 const std::vector<int64_t>& ld, const std::vector<int>& nrhs, int trans,
-                 std::vector<Launch>& ls) {
-  const int b = P.b;
-  int maxnt = 0;
-  for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
-  for (int s = 0; s < maxnt; ++s) {
-    std::vector<ItemSolve> diag, off;
-    int maxrhs = 0;
-    for (int m = 0; m < (int)P.mats.size(); ++m) {
-      auto& M = P.mats[m];
-      if (M.nt <= s) continue;
-      const int i = trans ? M.nt - 1 - s : s;
-      ItemSolve d{};
-      d.tile = M.linv[i];
-      d.mat = m;
-      d.xi = in[m] + (int64_t)i * b;
-      d.xj = out[m] + (int64_t)i * b;
-      d.ld = ld[m];
-      d.nrhs = nrhs[m];
-      maxrhs = std::max(maxrhs, nrhs[m]);
-      diag.push_back(d);
-      const int jlo = trans ? 0 : i + 1, jhi = trans ? i : M.nt;
-      for (int j = jlo; j < jhi; ++j) {
-        ItemSolve o = d;
-        o.tile = trans ? M.tile[i * M.nt + j] : M.tile[j * M.nt + i];
-        o.xi = out[m] + (int64_t)i * b;
-        o.xj = in[m] + (int64_t)j * b;
-        off.push_back(o);
-      }
-    }
-    ls.push_back({trans ? S_DIAG_B : S_DIAG_F, P.push(diag), (int)diag.size(), maxrhs});
-    if (!off.empty()) ls.push_back({trans ? S_OFF_B : S_OFF_F, P.push(off), (int)off.size(), maxrhs});
+SolvePlan build_solve(Plan& P, const std::vector<double*>& in, const std::vector<double*>& out,
+                      const std::vector<int64_t>& ld, const std::vector<int>& nrhs, int trans) {
+  SolvePlan sp;
+  std::vector<ItemSolveDag> items;
+  std::vector<int> nts;
+  for (int m = 0; m < (int)P.mats.size(); ++m) {
+    const MatDesc& M = P.mats[m];
+    ItemSolveDag it{};
+    it.tiles = P.d_ltab + P.ltab_off[m];
+    it.linv = it.tiles + (int64_t)M.nt * M.nt;
+    it.in = in[m];
+    it.out = out[m];
+    it.cnt = P.d_scnt + P.scnt_off[m];
+    it.ld = ld[m];
+    it.nt = M.nt;
+    it.nrhs = nrhs[m];
+    sp.nrhs_max = std::max(sp.nrhs_max, nrhs[m]);
+    items.push_back(it);
+    nts.push_back(M.nt);
   }
+  const std::vector<SolveTask> tasks = solve_dag_tasks(nts, P.b / 32, trans);
+  sp.items_off = P.push(items);
+  sp.tasks_off = P.push(tasks);
+  sp.ntasks = (int)tasks.size();
+  sp.trans = trans;
+  return sp;
 }
 
-void run_solve(const Plan& P, const char* dbase, const std::vector<Launch>& ls, const int* gate,
-               cudaStream_t s) {
-  const Arena A = P.arena();
-  for (const Launch& L : ls) {
-    const ItemSolve* it = reinterpret_cast<const ItemSolve*>(dbase + L.off);
-    switch (L.op) {
-      case S_DIAG_F: launch_diag_solve(A, it, L.count, L.kb, 0, gate, s); break;
-      case S_DIAG_B: launch_diag_solve(A, it, L.count, L.kb, 1, gate, s); break;
-      case S_OFF_F: launch_offdiag_solve(A, it, L.count, L.kb, 0, gate, s); break;
-      case S_OFF_B: launch_offdiag_solve(A, it, L.count, L.kb, 1, gate, s); break;
-    }
-  }
+void run_solve(const Plan& P, const char* dbase, const SolvePlan& sp, const int* gate, cudaStream_t s) {
+  cudaMemsetAsync(P.d_scnt, 0, P.scnt_bytes, s);
+  launch_solve_dag(P.arena(), reinterpret_cast<const ItemSolveDag*>(dbase + sp.items_off),
+                   reinterpret_cast<const SolveTask*>(dbase + sp.tasks_off), sp.ntasks, P.d_scnt,
+                   sp.trans, sp.nrhs_max, gate, s);
 }
 
 }  // namespace
@@ -1286,8 +1294,7 @@ extern "C" mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, in
   // solve on the padded copy, then copy the first n rows back
   std::vector<char> saved;
   saved.swap(P.h_items);
-  std::vector<Launch> ls;
-  build_solve(P, {t->x}, {t->w}, {N}, {nrhs}, trans ? 1 : 0, ls);
+  const SolvePlan ls = build_solve(P, {t->x}, {t->w}, {N}, {nrhs}, trans ? 1 : 0);
   size_t bytes = P.h_items.size();
   if (bytes > t->d_sitems_cap) {
     P.raw_free(t->d_sitems);
@@ -1332,10 +1339,9 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
     std::vector<char> saved;
     saved.swap(P.h_items);
     // r -> w (forward), w -> x or w -> d (backward)
-    std::vector<Launch> fwd_rw, bwd_wx, bwd_wd;
-    build_solve(P, {t->r}, {t->w}, {N}, {nrhs}, 0, fwd_rw);
-    build_solve(P, {t->w}, {t->x}, {N}, {nrhs}, 1, bwd_wx);
-    build_solve(P, {t->w}, {t->d}, {N}, {nrhs}, 1, bwd_wd);
+    const SolvePlan fwd_rw = build_solve(P, {t->r}, {t->w}, {N}, {nrhs}, 0);
+    const SolvePlan bwd_wx = build_solve(P, {t->w}, {t->x}, {N}, {nrhs}, 1);
+    const SolvePlan bwd_wd = build_solve(P, {t->w}, {t->d}, {N}, {nrhs}, 1);
     std::vector<ItemResid> res;
     for (int i = 0; i < M.nt && refine_iters > 0; ++i) {
       ItemResid it{};
@@ -1569,8 +1575,7 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
     rhs_o += reqs[r].nrhs;
   }
   size_t off_ga = P.push(gamax), off_g = P.push(gall), off_cp = P.push(cp), off_out = P.push(outs);
-  std::vector<Launch> fwd;
-  build_solve(P, vp, wp, ld, nr, 0, fwd);
+  const SolvePlan fwd = build_solve(P, vp, wp, ld, nr, 0);
   if ((st = upload_items(P))) { delete B; return st; }
   st = capture_graph(ctx, P.cap, [&](cudaStream_t s) {
     const Arena A = P.arena();

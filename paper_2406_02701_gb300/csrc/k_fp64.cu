@@ -30,26 +30,6 @@ namespace {
 
 constexpr int NB = 32;   // inner block of the diagonal tile
 
-constexpr uint32_t DAG_WAIT_LIMIT = 1u << 21;
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-// Waits until *ver >= need; false on timeout or when another CTA gave up.
-__device__ bool dag_wait(const int* ver, int need, const int* err) {
-  for (uint32_t i = 0; i < DAG_WAIT_LIMIT; ++i) {
-    if (ld_acquire(ver) >= need) return true;
-    if ((i & 63) == 63 && ld_acquire(err) != 0) return false;
-    __nanosleep(64);
-  }
-  return false;
-}
-
 // Block (k, k) in S: Cholesky factor in place (lower part) and the block's
 // inverse Y = L^{-1} in R, in one right-looking sweep run as a two-stage
 // pipeline.  In iteration c column c of L is final; warp 0 then finishes

@@ -3,16 +3,18 @@
 // squares, the log-determinant from the factor's diagonal; Sec. 1: float64
 // refinement).
 //
-// Solves run on the identity-padded system of order N = NT b with float64
-// arithmetic on the exactly upcast tiles.  Per tile column i (forward) the
-// diagonal solve uses the 32 x 32 block inverses kept by the factorisation,
-// and every tile below it updates its own segment in one launch; the
-// backward solve mirrors this with transposed tiles.  The residual
-// r = z - Sigma x reads the float64 copy of Sigma's lower tiles, using a
-// tile transposed for the upper part.
+// Solves run on the identity-padded system of order N = NT b as one task
+// graph per solve (below): the diagonal steps use the explicit inverses
+// L_ii^{-T} kept by the factorisation (float64), the off-diagonal tiles
+// update the right-hand side block by block.  The residual r = z - Sigma x
+// reads the float64 copy of Sigma's lower tiles, using a tile transposed
+// for the upper part.
 //
 // Every kernel that a refinement iteration may skip takes a `gate`: when
 // the pointed-to flag is 0 (all columns converged) it returns at once.
+#include <algorithm>
+#include <vector>
+
 #include "mp_device.cuh"
 
 namespace mp {
@@ -24,195 +26,336 @@ constexpr int RCMAX = 8;   // right-hand sides per pass (1 when there is one)
 
 __device__ __forceinline__ bool gated(const int* gate) { return gate && *gate == 0; }
 
-// Diagonal step with the explicit inverse X = L_ii^{-T} (upper triangular,
-// row-major, computed by the factorisation): forward out_i = X^T in_i,
-// backward out_i = X in_i.  32 output rows per CTA.
-template <int TRANS, int RCT>
-__global__ void __launch_bounds__(256) k_diag_gemv(Arena A, const ItemSolve* __restrict__ items,
-                                                   const int* gate) {
-  if (gated(gate)) return;
-  extern __shared__ double vs[];          // [b][RCT]
-  __shared__ double part[8][32][RCT];
-  const ItemSolve it = items[blockIdx.x];
+// ------------------------------------------------------------ solve graph
+//
+// One persistent launch runs a whole tiled triangular solve as tasks over
+// 32-row blocks (P = b / 32 per tile row):
+//   D(i, p)     diagonal block: out_i[p] from in_i with the explicit
+//               inverse X = L_ii^{-T} (float64);
+//   O(i, j, p)  off-diagonal block: in_i[p] -= L_ij out_j (forward) or
+//               in_i[p] -= L_ji^T out_j (backward).
+// Counters (zero at launch) per tile row i: updates applied to each block
+// of in_i, and finished blocks of out_i.  D(i, p) waits until the blocks of
+// in_i it reads have all their updates; O(i, j, p) waits for the whole of
+// out_j and for the update before it on the same block (updates to one
+// block are applied in a fixed order, so the result is deterministic).
+// Tasks are taken by an atomic ticket in a topological order, so the graph
+// cannot deadlock whatever the number of co-resident CTAs.
+//
+// Off-diagonal tiles stored in FP32 or below hold values exact in FP32, so
+// their products run on the FP32 pipe in float-float arithmetic: out_j is
+// split as h + l (two floats), a tile value a gives a h exactly as p + e
+// (one product and one FMA), a l to 2^-24 of a term already 2^-24 small,
+// and the row sums accumulate as compensated pairs; the result carries
+// about 2^-46 relative error against a float64 sum.  FP64 tiles use float64.
+
+// Value i of a tile stored in format DT (exact in FP32).
+template <int DT>
+__device__ __forceinline__ float tval(const char* base, int64_t i) {
+  if (DT == F32) return reinterpret_cast<const float*>(base)[i];
+  if (DT == BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[i]);
+  if (DT == F16) return __half2float(reinterpret_cast<const __half*>(base)[i]);
+  __nv_fp8_e4m3 v;
+  v.__x = reinterpret_cast<const __nv_fp8_storage_t*>(base)[i];
+  return (float)v;
+}
+
+// (hi, lo) += a (h + l) with a exact in FP32.
+__device__ __forceinline__ void ff_madd(float& hi, float& lo, float a, float h, float l) {
+  const float p = a * h;
+  const float e = fmaf(a, h, -p);               // a h = p + e exactly
+  const float s = hi + p;                       // two-sum of hi and p
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + e + a * l;
+}
+
+constexpr int MLP = 16;   // loads a thread issues before using them
+
+// Diagonal block: out_i[p] from in_i with X = L_ii^{-T} (float64).
+template <int RCT>
+__device__ void solve_diag(const Arena& A, const ItemSolveDag& it, int i, int p, int trans,
+                           double* vs, double* part) {
   const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* X = tile_ptr<double>(A, it.tile);
-  const int r0 = blockIdx.y * 32;
+  const double* X = tile_ptr<double>(A, it.linv[i]);
+  const double* v = it.in + (int64_t)i * b;
+  double* o = it.out + (int64_t)i * b;
+  const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
     const int nc = min(RCT, it.nrhs - c0);
     __syncthreads();
-    for (int e = tid; e < b * RCT; e += blockDim.x) {
-      int t = e / RCT, c = e % RCT;
-      vs[e] = c < nc ? it.xi[(int64_t)(c0 + c) * it.ld + t] : 0.0;
+    for (int e = tid; e < (t1 - t0) * RCT; e += blockDim.x) {
+      const int t = t0 + e / RCT, c = e % RCT;
+      vs[t * RCT + c] = c < nc ? __ldcg(v + (int64_t)(c0 + c) * it.ld + t) : 0.0;
     }
     __syncthreads();
-    if (!TRANS) {
-      // out[r0 + lane] = sum_{t <= r} X[t][r] v[t]; warps split t
-      double acc[4][RCT];
+    double acc[RCT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+    for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
+    if (!trans) {
+      // out[r] = sum_{t <= r} X[t][r] v[t], r = 32 p + lane; warp w takes t = w + 8 k
+      const int r = p * 32 + lane;
+      const int nk = t1 / 8;
+      for (int k0 = 0; k0 < nk; k0 += MLP) {
+        double x[MLP];
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[u][c] = 0.0;
-      const int r = r0 + lane;
-      const int tend = r0 + 32;
-      int t = warp;
-      for (; t + 24 < tend; t += 32) {        // four independent chains
+        for (int u = 0; u < MLP; ++u) {
+          const int t = warp + 8 * (k0 + u);
+          x[u] = (k0 + u < nk && t <= r) ? X[(int64_t)t * b + r] : 0.0;
+        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int tu = t + 8 * u;
-          const double x = tu > r ? 0.0 : X[(int64_t)tu * b + r];
+        for (int u = 0; u < MLP; ++u) {
+          if (k0 + u >= nk) break;                 // uniform: nk is the same for all threads
+          const int t = warp + 8 * (k0 + u);
 #pragma unroll
-          for (int c = 0; c < RCT; ++c) acc[u][c] += x * vs[tu * RCT + c];
+          for (int c = 0; c < RCT; ++c) acc[c] += x[u] * vs[t * RCT + c];
         }
       }
-      for (; t < tend; t += 8) {
-        const double x = t > r ? 0.0 : X[(int64_t)t * b + r];
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[0][c] += x * vs[t * RCT + c];
-      }
-#pragma unroll
-      for (int c = 0; c < RCT; ++c) part[warp][lane][c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
+      for (int c = 0; c < RCT; ++c) part[(warp * 32 + lane) * RCT + c] = acc[c];
       __syncthreads();
       if (warp == 0) {
-#pragma unroll
-        for (int c = 0; c < RCT; ++c) {
-          double v = 0.0;
-          for (int w = 0; w < 8; ++w) v += part[w][lane][c];
-          if (c < nc) it.xj[(int64_t)(c0 + c) * it.ld + r] = v;
+        for (int c = 0; c < nc; ++c) {
+          double sum = 0.0;
+          for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
+          o[(int64_t)(c0 + c) * it.ld + r] = sum;
         }
       }
     } else {
-      // out[r] = sum_{t >= r} X[r][t] v[t]; a warp per 4 rows, lanes over t
-      for (int rr = 0; rr < 4; ++rr) {
-        const int r = r0 + warp * 4 + rr;
-        double acc[RCT];
+      // out[r] = sum_{t >= r} X[r][t] v[t]: thread (row r = 32 p + tid / 8,
+      // s = tid % 8) takes t = 32 p + s + 8 k
+      const int r = p * 32 + (tid >> 3), sg = tid & 7;
+      const double* Xr = X + (int64_t)r * b;
+      const int nk = (b - p * 32) / 8;
+      for (int k0 = 0; k0 < nk; k0 += MLP) {
+        double x[MLP];
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
-        const double* Xr = X + (int64_t)r * b;
-        double acc2[RCT];
-#pragma unroll
-        for (int c = 0; c < RCT; ++c) acc2[c] = 0.0;
-        int t = (r & ~31) + lane;
-        for (; t + 32 < b; t += 64) {
-          const double x0 = t >= r ? Xr[t] : 0.0, x1 = Xr[t + 32];
-#pragma unroll
-          for (int c = 0; c < RCT; ++c) {
-            acc[c] += x0 * vs[t * RCT + c];
-            acc2[c] += x1 * vs[(t + 32) * RCT + c];
-          }
-        }
-        for (; t < b; t += 32) {
-          const double x = t >= r ? Xr[t] : 0.0;
-#pragma unroll
-          for (int c = 0; c < RCT; ++c) acc[c] += x * vs[t * RCT + c];
+        for (int u = 0; u < MLP; ++u) {
+          const int t = p * 32 + sg + 8 * (k0 + u);
+          x[u] = (k0 + u < nk && t >= r) ? Xr[t] : 0.0;
         }
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) acc[c] += acc2[c];
+        for (int u = 0; u < MLP; ++u) {
+          if (k0 + u >= nk) break;
+          const int t = p * 32 + sg + 8 * (k0 + u);
 #pragma unroll
-        for (int c = 0; c < RCT; ++c) {
-          double v = warp_sum(acc[c]);
-          if (lane == 0 && c < nc) it.xj[(int64_t)(c0 + c) * it.ld + r] = v;
+          for (int c = 0; c < RCT; ++c) acc[c] += x[u] * vs[t * RCT + c];
         }
+      }
+      for (int c = 0; c < nc; ++c) {
+        double sum = acc[c];
+        for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+        if (sg == 0) o[(int64_t)(c0 + c) * it.ld + r] = sum;
       }
     }
   }
 }
 
-// Forward: in_j -= L_ji out_i (tile rows).  One CTA: 32 rows, a warp per 4 rows.
-template <int RCT>
-__global__ void __launch_bounds__(256) k_offdiag_fwd(Arena A, const ItemSolve* __restrict__ items,
-                                                     const int* gate) {
-  if (gated(gate)) return;
-  extern __shared__ double xs[];         // [b][RCT]
-  const ItemSolve it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const TileRef ref = A.tiles[it.tile];
-  const char* L = tile_bytes(A, it.tile);
-  const double sc = A.scale[it.tile];
-  const int r0 = blockIdx.y * 32;
-  for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
-    const int nc = min(RCT, it.nrhs - c0);
-    __syncthreads();
-    for (int e = tid; e < b * RCT; e += blockDim.x) {
-      int t = e / RCT, c = e % RCT;
-      xs[e] = c < nc ? it.xi[(int64_t)(c0 + c) * it.ld + t] : 0.0;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = r0 + warp * 4 + rr;
-      double acc[RCT];
+// Off-diagonal block, tiles stored in FP32 or below (DT), float-float sums.
+template <int RCT, int DT>
+__device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, int b, int p,
+                             int trans, const float2* ys, double* part, double* r, int c0, int nc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float hi[RCT], lo[RCT];
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
-      double acc2[RCT];
+  for (int c = 0; c < RCT; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+  if (!trans) {
+    // in_i[q] -= sum_t L_ij[q][t] y[t]: thread (row q = 32 p + tid / 8, s = tid % 8), t = s + 8 k
+    const int q = p * 32 + (tid >> 3), sg = tid & 7;
+    const int64_t row = (int64_t)q * b;
+    const int nk = b / 8;
+    for (int k0 = 0; k0 < nk; k0 += MLP) {
+      float a[MLP];
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) acc2[c] = 0.0;
-#pragma unroll 4
-      for (int t = lane; t < b; t += 64) {        // b is a multiple of 64
-        const double l0 = load_f64(L, ref.dt, (int64_t)r * b + t) * sc;
-        const double l1 = load_f64(L, ref.dt, (int64_t)r * b + t + 32) * sc;
+      for (int u = 0; u < MLP; ++u) a[u] = tval<DT>(L, row + sg + 8 * (k0 + u)) * scf;
+#pragma unroll
+      for (int u = 0; u < MLP; ++u) {
+        const int t = sg + 8 * (k0 + u);
 #pragma unroll
         for (int c = 0; c < RCT; ++c) {
-          acc[c] += l0 * xs[t * RCT + c];
-          acc2[c] += l1 * xs[(t + 32) * RCT + c];
+          const float2 h = ys[t * RCT + c];
+          ff_madd(hi[c], lo[c], a[u], h.x, h.y);
         }
       }
-#pragma unroll
-      for (int c = 0; c < RCT; ++c) acc[c] += acc2[c];
-#pragma unroll
-      for (int c = 0; c < RCT; ++c) {
-        double v = warp_sum(acc[c]);
-        if (lane == 0 && c < nc) it.xj[(int64_t)(c0 + c) * it.ld + r] -= v;
+    }
+    for (int c = 0; c < nc; ++c) {
+      double sum = (double)hi[c] + (double)lo[c];
+      for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+      if (sg == 0) {
+        double* rp = r + (int64_t)(c0 + c) * it.ld + q;
+        *rp = __ldcg(rp) - sum;
       }
     }
-  }
-}
-
-// Backward: in_j -= L_ij^T out_i (tile columns).  One CTA: 32 columns (one
-// per lane, so a warp reads 256 contiguous bytes of a row), eight warps
-// splitting the rows with two accumulator chains each, partial sums added
-// in a fixed order.
-template <int RCT>
-__global__ void __launch_bounds__(256) k_offdiag_bwd(Arena A, const ItemSolve* __restrict__ items,
-                                                     const int* gate) {
-  if (gated(gate)) return;
-  extern __shared__ double xs[];         // [b][RCT]
-  __shared__ double part[8][32][RCT];
-  const ItemSolve it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const TileRef ref = A.tiles[it.tile];
-  const char* L = tile_bytes(A, it.tile);
-  const double sc = A.scale[it.tile];
-  const int col = blockIdx.y * 32 + lane;
-  for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
-    const int nc = min(RCT, it.nrhs - c0);
-    __syncthreads();
-    for (int e = tid; e < b * RCT; e += blockDim.x) {
-      int t = e / RCT, c = e % RCT;
-      xs[e] = c < nc ? it.xi[(int64_t)(c0 + c) * it.ld + t] : 0.0;
-    }
-    __syncthreads();
-    double a0[RCT], a1[RCT];
+  } else {
+    // in_i[q] -= sum_t L_ji[t][q] y[t]: q = 32 p + lane, warp w takes t = w + 8 k
+    const int q = p * 32 + lane;
+    const int nk = b / 8;
+    for (int k0 = 0; k0 < nk; k0 += MLP) {
+      float a[MLP];
 #pragma unroll
-    for (int c = 0; c < RCT; ++c) { a0[c] = 0.0; a1[c] = 0.0; }
-#pragma unroll 4
-    for (int r = warp; r < b; r += 16) {
-      const double l0 = load_f64(L, ref.dt, (int64_t)r * b + col) * sc;
-      const double l1 = load_f64(L, ref.dt, (int64_t)(r + 8) * b + col) * sc;
+      for (int u = 0; u < MLP; ++u) a[u] = tval<DT>(L, (int64_t)(warp + 8 * (k0 + u)) * b + q) * scf;
 #pragma unroll
-      for (int c = 0; c < RCT; ++c) {
-        a0[c] += l0 * xs[r * RCT + c];
-        a1[c] += l1 * xs[(r + 8) * RCT + c];
+      for (int u = 0; u < MLP; ++u) {
+        const int t = warp + 8 * (k0 + u);
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) {
+          const float2 h = ys[t * RCT + c];
+          ff_madd(hi[c], lo[c], a[u], h.x, h.y);
+        }
       }
     }
 #pragma unroll
-    for (int c = 0; c < RCT; ++c) part[warp][lane][c] = a0[c] + a1[c];
+    for (int c = 0; c < RCT; ++c) part[(warp * 32 + lane) * RCT + c] = (double)hi[c] + (double)lo[c];
     __syncthreads();
     if (warp == 0) {
-#pragma unroll
-      for (int c = 0; c < RCT; ++c) {
-        double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += part[w][lane][c];
-        if (c < nc) it.xj[(int64_t)(c0 + c) * it.ld + col] -= v;
+      for (int c = 0; c < nc; ++c) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
+        double* rp = r + (int64_t)(c0 + c) * it.ld + q;
+        *rp = __ldcg(rp) - sum;
       }
+    }
+  }
+}
+
+// Off-diagonal block of an FP64 tile, float64 sums.
+template <int RCT>
+__device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, int p, int trans,
+                              const double* vs, double* part, double* r, int c0, int nc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double acc[RCT];
+#pragma unroll
+  for (int c = 0; c < RCT; ++c) acc[c] = 0.0;
+  if (!trans) {
+    const int q = p * 32 + (tid >> 3), sg = tid & 7;
+    const int64_t row = (int64_t)q * b;
+    const int nk = b / 8;
+    for (int k0 = 0; k0 < nk; k0 += MLP) {
+      double a[MLP];
+#pragma unroll
+      for (int u = 0; u < MLP; ++u) a[u] = L[row + sg + 8 * (k0 + u)];
+#pragma unroll
+      for (int u = 0; u < MLP; ++u)
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc[c] += a[u] * vs[(sg + 8 * (k0 + u)) * RCT + c];
+    }
+    for (int c = 0; c < nc; ++c) {
+      double sum = acc[c];
+      for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+      if (sg == 0) {
+        double* rp = r + (int64_t)(c0 + c) * it.ld + q;
+        *rp = __ldcg(rp) - sum;
+      }
+    }
+  } else {
+    const int q = p * 32 + lane;
+    const int nk = b / 8;
+    for (int k0 = 0; k0 < nk; k0 += MLP) {
+      double a[MLP];
+#pragma unroll
+      for (int u = 0; u < MLP; ++u) a[u] = L[(int64_t)(warp + 8 * (k0 + u)) * b + q];
+#pragma unroll
+      for (int u = 0; u < MLP; ++u)
+#pragma unroll
+        for (int c = 0; c < RCT; ++c) acc[c] += a[u] * vs[(warp + 8 * (k0 + u)) * RCT + c];
+    }
+#pragma unroll
+    for (int c = 0; c < RCT; ++c) part[(warp * 32 + lane) * RCT + c] = acc[c];
+    __syncthreads();
+    if (warp == 0) {
+      for (int c = 0; c < nc; ++c) {
+        double sum = 0.0;
+        for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
+        double* rp = r + (int64_t)(c0 + c) * it.ld + q;
+        *rp = __ldcg(rp) - sum;
+      }
+    }
+  }
+}
+
+template <int RCT>
+__device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, int p, int trans,
+                          double* vs, double* part) {
+  const int b = A.b, tid = threadIdx.x, nt = it.nt;
+  const int tile = trans ? it.tiles[j * nt + i] : it.tiles[i * nt + j];
+  const TileRef ref = A.tiles[tile];
+  const char* L = tile_bytes(A, tile);
+  const float scf = (float)A.scale[tile];       // a power of two (1 except E4M3)
+  const bool f64 = ref.dt == F64;
+  const double* y = it.out + (int64_t)j * b;
+  double* r = it.in + (int64_t)i * b;
+  float2* ys = reinterpret_cast<float2*>(vs);
+  for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
+    const int nc = min(RCT, it.nrhs - c0);
+    __syncthreads();
+    for (int e = tid; e < b * RCT; e += blockDim.x) {
+      const int t = e / RCT, c = e % RCT;
+      const double v = c < nc ? __ldcg(y + (int64_t)(c0 + c) * it.ld + t) : 0.0;
+      if (f64) {
+        vs[e] = v;
+      } else {
+        const float h = (float)v;
+        ys[e] = make_float2(h, (float)(v - (double)h));
+      }
+    }
+    __syncthreads();
+    switch (ref.dt) {
+      case F64: solve_off_f64<RCT>(reinterpret_cast<const double*>(L), it, b, p, trans, vs, part, r, c0, nc); break;
+      case F32: solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
+      case BF16: solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
+      case F16: solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
+      default: solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
+    }
+  }
+}
+
+template <int RCT>
+__global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* __restrict__ items,
+                                                   const SolveTask* __restrict__ tasks, int ntasks,
+                                                   int* ticket, int trans, const int* gate) {
+  if (gated(gate)) return;
+  extern __shared__ double sm[];
+  double* vs = sm;                               // b x RCT (doubles or float pairs)
+  double* part = sm + A.b * RCT;                 // 8 warps x 32 lanes x RCT
+  __shared__ int s_t, s_ok;
+  const int b = A.b, P = b / 32, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= ntasks) break;
+    const SolveTask tk = tasks[t];
+    const int m = (int)(tk & 0xffffff), op = (int)((tk >> 24) & 0xf);
+    const int i = (int)((tk >> 28) & 0xfff), j = (int)((tk >> 40) & 0xfff), p = (int)((tk >> 52) & 0xff);
+    const ItemSolveDag it = items[m];
+    int* cnt = it.cnt;
+    const int nt = it.nt;
+    if (warp == 0) {
+      bool ok = true;
+      if (op == 0) {
+        // the blocks of in_i this block reads: p' <= p (forward), p' >= p (backward)
+        const int need = trans ? nt - 1 - i : i;
+        if (lane < P && (trans ? lane >= p : lane <= p)) ok = dag_wait(&cnt[i * (P + 1) + lane], need, A.err);
+      } else if (lane == 0) {
+        const int need = trans ? nt - 1 - j : j;
+        ok = dag_wait(&cnt[j * (P + 1) + P], P, A.err) && dag_wait(&cnt[i * (P + 1) + p], need, A.err);
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0) {
+        if (!ok) atomicExch(A.err, 1);
+        s_ok = ok;
+      }
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    if (op == 0) solve_diag<RCT>(A, it, i, p, trans, vs, part);
+    else solve_off<RCT>(A, it, i, j, p, trans, vs, part);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      if (op == 0) atomicAdd(&cnt[i * (P + 1) + P], 1);
+      else st_release(&cnt[i * (P + 1) + p], trans ? nt - j : j + 1);
     }
   }
 }
@@ -372,49 +515,56 @@ __global__ void k_loglik(const double* logdet, const double* quad, int64_t n, in
 
 }  // namespace
 
-void launch_diag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
-                       const int* gate, cudaStream_t s) {
-  if (count <= 0) return;
-  dim3 grid(count, A.b / 32);
-  static bool attr = false;
-  if (!attr) {
-    for (auto f : {(const void*)k_diag_gemv<0, 1>, (const void*)k_diag_gemv<1, 1>,
-                   (const void*)k_diag_gemv<0, RCMAX>, (const void*)k_diag_gemv<1, RCMAX>})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
+std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int P, int trans) {
+  // per matrix: for each step the diagonal blocks, then the updates of the
+  // next tile row (the critical chain), then the other updates; matrices
+  // are interleaved round-robin, which keeps each matrix's order
+  std::vector<std::vector<SolveTask>> per(nts.size());
+  auto pack = [](int m, int op, int i, int j, int p) {
+    return (SolveTask)m | ((SolveTask)op << 24) | ((SolveTask)i << 28) | ((SolveTask)j << 40) |
+           ((SolveTask)p << 52);
+  };
+  size_t total = 0;
+  for (size_t m = 0; m < nts.size(); ++m) {
+    const int nt = nts[m];
+    auto& v = per[m];
+    for (int st = 0; st < nt; ++st) {
+      const int s = trans ? nt - 1 - st : st;
+      for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 0, s, 0, trans ? P - 1 - q : q));
+      if (!trans) {
+        for (int i = s + 1; i < nt; ++i)
+          for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 1, i, s, q));
+      } else {
+        for (int i = s - 1; i >= 0; --i)
+          for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 1, i, s, q));
+      }
+    }
+    total += v.size();
   }
-  if (nrhs == 1) {
-    size_t smem = sizeof(double) * A.b;
-    if (trans) k_diag_gemv<1, 1><<<grid, 256, smem, s>>>(A, items, gate);
-    else k_diag_gemv<0, 1><<<grid, 256, smem, s>>>(A, items, gate);
-  } else {
-    size_t smem = sizeof(double) * A.b * RCMAX;
-    if (trans) k_diag_gemv<1, RCMAX><<<grid, 256, smem, s>>>(A, items, gate);
-    else k_diag_gemv<0, RCMAX><<<grid, 256, smem, s>>>(A, items, gate);
-  }
+  std::vector<SolveTask> out;
+  out.reserve(total);
+  for (size_t k = 0; out.size() < total; ++k)
+    for (auto& v : per)
+      if (k < v.size()) out.push_back(v[k]);
+  return out;
 }
 
-void launch_offdiag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
-                          const int* gate, cudaStream_t s) {
-  if (count <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    for (auto f : {(const void*)k_offdiag_fwd<1>, (const void*)k_offdiag_fwd<RCMAX>,
-                   (const void*)k_offdiag_bwd<1>, (const void*)k_offdiag_bwd<RCMAX>})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
+void launch_solve_dag(const Arena& A, const ItemSolveDag* items, const SolveTask* tasks, int ntasks,
+                      int* ticket, int trans, int nrhs_max, const int* gate, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_solve_dag<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_solve_dag<RCMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   }
-  const int rc = nrhs == 1 ? 1 : RCMAX;
-  size_t smem = sizeof(double) * A.b * rc;
-  if (trans) {
-    dim3 grid(count, A.b / 32);
-    if (rc == 1) k_offdiag_bwd<1><<<grid, 256, smem, s>>>(A, items, gate);
-    else k_offdiag_bwd<RCMAX><<<grid, 256, smem, s>>>(A, items, gate);
-  } else {
-    dim3 grid(count, A.b / 32);
-    if (rc == 1) k_offdiag_fwd<1><<<grid, 256, smem, s>>>(A, items, gate);
-    else k_offdiag_fwd<RCMAX><<<grid, 256, smem, s>>>(A, items, gate);
-  }
+  const int rc = nrhs_max == 1 ? 1 : RCMAX;
+  const size_t smem = sizeof(double) * ((size_t)A.b * rc + 8 * 32 * rc);
+  const int grid = std::min(ntasks, 2 * sms);
+  if (rc == 1) k_solve_dag<1><<<grid, 256, smem, s>>>(A, items, tasks, ntasks, ticket, trans, gate);
+  else k_solve_dag<RCMAX><<<grid, 256, smem, s>>>(A, items, tasks, ntasks, ticket, trans, gate);
 }
 
 void launch_residual(const Arena& A, const ItemResid* items, int count, int nrhs,

@@ -93,4 +93,26 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Progress counters of the task-graph kernels: acquire loads, release
+// stores, and a bounded wait that gives up when the error word is set.
+constexpr uint32_t DAG_WAIT_LIMIT = 1u << 21;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Waits until *ver >= need; false on timeout or when another CTA gave up.
+__device__ __forceinline__ bool dag_wait(const int* ver, int need, const int* err) {
+  for (uint32_t i = 0; i < DAG_WAIT_LIMIT; ++i) {
+    if (ld_acquire(ver) >= need) return true;
+    if ((i & 63) == 63 && ld_acquire(err) != 0) return false;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 }  // namespace mp

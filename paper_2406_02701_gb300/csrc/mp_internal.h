@@ -156,15 +156,24 @@ struct ItemGen {
 // Solve items.  Diagonal: tile = L_ii^{-T} (FP64), xj = X-product of xi
 // (out of place).  Off-diagonal: tile = L tile, xi = solved segment,
 // xj = segment still to be solved (updated in place).
-struct ItemSolve {
-  int32_t tile;
-  int32_t mat;
-  double* xi;
-  double* xj;
-  int64_t ld;         // leading dimension of the vectors
-  int32_t nrhs;
-  int32_t pad_;
+// One matrix's triangular solve run by the solve task graph (k_solve_dag):
+// forward out = L^{-1} in or backward out = L^{-T} in, `in` updated in
+// place.  cnt holds nt (b/32 + 1) progress counters, zero at launch: per
+// tile row i, the updates applied to each 32-row block, then the number of
+// finished 32-row blocks of out_i.
+struct ItemSolveDag {
+  const int32_t* tiles;   // nt x nt tile ids of the factor (lower part)
+  const int32_t* linv;    // nt tile ids of L_ii^{-T} (FP64, upper triangular)
+  double* in;             // N x nrhs (column stride ld), consumed
+  double* out;            // N x nrhs (column stride ld)
+  int* cnt;
+  int64_t ld;
+  int32_t nt, nrhs;
 };
+// Task of the solve graph: matrix (bits 0-23), op (24-27: 0 diagonal block,
+// 1 off-diagonal block), target tile row i (28-39), source tile row j
+// (40-51), 32-row block p (52-59).
+typedef uint64_t SolveTask;
 
 // Residual rows of one block row of a matrix: r_i = z_i - sum_j S_ij x_j.
 struct ItemResid {
@@ -224,10 +233,9 @@ void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
                       const struct CUtensorMap_st& map, cudaStream_t s);
 
 // k_solve.cu  (a non-null `gate` pointing at 0 turns a launch into a no-op)
-void launch_diag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
-                       const int* gate, cudaStream_t s);
-void launch_offdiag_solve(const Arena& A, const ItemSolve* items, int count, int nrhs, int trans,
-                          const int* gate, cudaStream_t s);
+std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int p_blocks, int trans);
+void launch_solve_dag(const Arena& A, const ItemSolveDag* items, const SolveTask* tasks, int ntasks,
+                      int* ticket, int trans, int nrhs_max, const int* gate, cudaStream_t s);
 void launch_residual(const Arena& A, const ItemResid* items, int count, int nrhs,
                      int want_rowabs, const int* gate, cudaStream_t s);
 void launch_logdet(const double* ldparts, const int32_t* ldoff, const int32_t* ldcnt, int nmat,
