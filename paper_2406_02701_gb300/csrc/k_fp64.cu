@@ -411,22 +411,48 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
   float* hi = it.hi >= 0 ? tile_ptr<float>(A, it.hi) : nullptr;
   float* lo = it.lo >= 0 ? tile_ptr<float>(A, it.lo) : nullptr;
   const int64_t r0 = (int64_t)blockIdx.y * 16 * b;
-  for (int e = threadIdx.x; e < 16 * b; e += blockDim.x) {
-    double v = it.x[r0 + e];
-    store_round(dst, dt, r0 + e, dt == E4M3 ? v / s : v);
-    if (sdst[0] || hi) {
-      double stored = load_f64(dst, dt, r0 + e) * s;
+  // one float64 rounding per entry; the shadow copies and the TF32 split
+  // derive from the stored value, which is exact in FP32 (GB300 runs FP64
+  // conversions on its narrow FP64 pipe)
+  float sss[MAX_SHADOW];
+#pragma unroll
+  for (int q = 0; q < MAX_SHADOW; ++q) sss[q] = (float)(1.0 / ss[q]);   // powers of two
+  const float fs = (float)s;
+  if (dt == F64) {
+    // FP64 tile: every copy is rounded once from the float64 value
+    for (int e = threadIdx.x; e < 16 * b; e += blockDim.x) {
+      const double v = it.x[r0 + e];
+      reinterpret_cast<double*>(dst)[r0 + e] = v;
 #pragma unroll
       for (int q = 0; q < MAX_SHADOW; ++q)
-        if (sdst[q]) store_round(sdst[q], sdt[q], r0 + e, sdt[q] == E4M3 ? stored / ss[q] : stored);
+        if (sdst[q]) store_round(sdst[q], sdt[q], r0 + e, sdt[q] == E4M3 ? v / ss[q] : v);
       if (hi) {
-        // the stored value is exact in FP32 (formats up to FP32)
-        const float f = (float)stored;
+        const float f = (float)v;
         uint32_t h;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
         hi[r0 + e] = __uint_as_float(h);
         lo[r0 + e] = f - __uint_as_float(h);
       }
+    }
+  } else
+  for (int e = threadIdx.x; e < 16 * b; e += blockDim.x) {
+    const double v = it.x[r0 + e];
+    float stored;
+    if (dt == F32) {
+      stored = __double2float_rn(v);
+      reinterpret_cast<float*>(dst)[r0 + e] = stored;
+    } else {
+      store_round(dst, dt, r0 + e, dt == E4M3 ? v / s : v);
+      stored = load_f32(dst, dt, r0 + e) * fs;
+    }
+#pragma unroll
+    for (int q = 0; q < MAX_SHADOW; ++q)
+      if (sdst[q]) store_round_f32(sdst[q], sdt[q], r0 + e, sdt[q] == E4M3 ? stored * sss[q] : stored);
+    if (hi) {
+      uint32_t h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(stored));
+      hi[r0 + e] = __uint_as_float(h);
+      lo[r0 + e] = stored - __uint_as_float(h);
     }
   }
   if (blockIdx.y == 0 && threadIdx.x == 0) {

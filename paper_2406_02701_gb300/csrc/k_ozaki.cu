@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = m0 + warp * 32 + lane;
   const float sg = it.sigma[row];
+  double (*Sx)[33] = reinterpret_cast<double (*)[33]>(smem + warp * 32 * 33 * sizeof(double));
   float mx = 0.f;
 #pragma unroll 1
   for (int h = 0; h < OZ_BN / 32; ++h) {
@@ -352,14 +353,22 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
     if (have) {
-      double* xr = it.x + (int64_t)row * b + n0 + h * 32;
+      // stage the warp's 32 x 32 chunk in shared memory (the ring buffers are
+      // free once every MMA has completed), then write rows with lanes over
+      // columns: coalesced
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const float st = sg * it.tau[n0 + h * 32 + j];   // power of two: scaling is exact
-        const double xv = (double)(hi[j] * st) + (double)(lo[j] * st);
-        xr[j] = xv;
+        Sx[lane][j] = (double)(hi[j] * st) + (double)(lo[j] * st);
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const double xv = Sx[rr][lane];
+        it.x[(int64_t)(m0 + warp * 32 + rr) * b + n0 + h * 32 + lane] = xv;
         mx = fmaxf(mx, fabsf((float)xv));
       }
+      __syncwarp();
     }
   }
   __shared__ float red[4];

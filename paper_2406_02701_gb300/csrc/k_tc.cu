@@ -248,37 +248,62 @@ __global__ void __launch_bounds__(128, 1)
   char* pc = tile_bytes(A, it.c);
   const float sab = (float)(A.scale[it.a] * A.scale[it.b]);
   const double sc = A.scale[it.c];
-  const int row = rb * TC_BM + warp * 32 + lane;
+  // each warp stages a 32 x 32 chunk of its rows through shared memory (the
+  // pipeline buffers are free once every MMA has completed) and updates the
+  // target row by row, lanes over columns: coalesced reads and writes
+  float (*S)[33] = reinterpret_cast<float (*)[33]>(smem + warp * 32 * 33 * sizeof(float));
   float mx = 0.f;
 #pragma unroll 1
   for (int ch = 0; ch < TC_BN / 32; ++ch) {
     float v[32];
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
     if (!have) continue;
-    const int64_t o0 = (int64_t)row * b + cb * TC_BN + ch * 32;
-    if (it.syrk && cb * TC_BN + ch * 32 > row) continue;   // above the diagonal
-    if (rc.dt == F64) {
-      double* c = reinterpret_cast<double*>(pc) + o0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] -= (double)(v[j] * sab);
-    } else if (rc.dt == F32) {
-      // one correctly rounded FP32 subtraction = the exact difference rounded once
+    for (int j = 0; j < 32; ++j) S[lane][j] = v[j] * sab;
+    __syncwarp();
+    const int col = cb * TC_BN + ch * 32 + lane;
+    const int row0 = rb * TC_BM + warp * 32;
+    // rows of this chunk strictly above the diagonal of a SYRK target: none
+    // when the chunk starts at or left of the row
+    const int rlo = it.syrk ? max(0, cb * TC_BN + ch * 32 - row0) : 0;
+    const int64_t o0 = (int64_t)row0 * b + col;
+    // all 32 loads are issued before the arithmetic (one memory round trip)
+    if (rc.dt == F32) {
       float* c = reinterpret_cast<float*>(pc) + o0;
+      float cur[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) c[j] = __fsub_rn(c[j], v[j] * sab);
-    } else if (rc.dt == E4M3) {
-      const float fs = (float)sc;
+      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float w = load_f32(pc, E4M3, o0 + j) * fs - v[j] * sab;
-        it.v[o0 + j] = w;
-        mx = fmaxf(mx, fabsf(w));
-      }
+      for (int rr = 0; rr < 32; ++rr)    // one correctly rounded FP32 subtraction
+        if (rr >= rlo) c[(int64_t)rr * b] = __fsub_rn(cur[rr], S[rr][lane]);
+    } else if (rc.dt == F64) {
+      double* c = reinterpret_cast<double*>(pc) + o0;
+      double cur[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.0;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr)
+        if (rr >= rlo) c[(int64_t)rr * b] = cur[rr] - (double)S[rr][lane];
     } else {
+      float cur[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        store_round_f32(pc, rc.dt, o0 + j, load_f32(pc, rc.dt, o0 + j) - v[j] * sab);
+      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? load_f32(pc, rc.dt, o0 + (int64_t)rr * b) : 0.f;
+      if (rc.dt == E4M3) {
+        const float fs = (float)sc;
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          if (rr >= rlo) {
+            const float w = cur[rr] * fs - S[rr][lane];
+            it.v[o0 + (int64_t)rr * b] = w;
+            mx = fmaxf(mx, fabsf(w));
+          }
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          if (rr >= rlo) store_round_f32(pc, rc.dt, o0 + (int64_t)rr * b, cur[rr] - S[rr][lane]);
+      }
     }
+    __syncwarp();
   }
   if (rc.dt == E4M3) {
     __shared__ float red[4];
