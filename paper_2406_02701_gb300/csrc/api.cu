@@ -120,7 +120,6 @@ struct Plan {
   // arena
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
-  int32_t ident = -1;              // FP64 identity tile (input of the L^{-T} solves)
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix (b/32)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
   std::vector<int64_t> ltab_off;
@@ -322,7 +321,6 @@ mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
     }
   M.linv.assign(nt, -1);
   for (int i = 0; i < nt; ++i) M.linv[i] = new_tile(P, F64);
-  if (P.ident < 0) P.ident = new_tile(P, F64);
   if (P.keep_sigma) {
     M.sig.assign((size_t)nt * nt, -1);
     for (int i = 0; i < nt; ++i)
@@ -383,10 +381,28 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         it.ldslot = M.ldoff + s * nbb;
         it.row0 = (int64_t)s * b;
         it.dinv = M.dinv + (int64_t)s * nbb * 1024;
-        it.ver = P.d_dag + 32 + (int64_t)m * nbb * nbb;
+        it.w = (double*)(P.pool[F64] + (size_t)P.h_tiles[M.linv[s]].idx * b * b * 8);
+        it.ver = P.d_dag + 32 + (int64_t)m * 2 * nbb * nbb;
         items.push_back(it);
       }
       add(OP_POTRF_DAG, P.push(items), (int)items.size(), 0, 0);
+    }
+    // Ozaki mode: digits of W = L_ss^{-T} (formed by the POTRF graph), used
+    // by the first tile's product here and by the rest of the panel
+    if (P.ozaki) {
+      std::vector<ItemOzW> ozw;
+      for (int m = 0; m < (int)P.mats.size(); ++m) {
+        auto& M = P.mats[m];
+        bool any = false;
+        for (int i = s + 1; i < M.nt; ++i) any |= P.h_tiles[M.tile[i * M.nt + s]].dt != F64;
+        if (!any) continue;
+        ItemOzW w{};
+        w.wtile = M.linv[s];
+        for (int d = 0; d < OZ_SMAX; ++d) w.slices[d] = P.wdig[par * P.mats.size() + m][d];
+        w.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
+        ozw.push_back(w);
+      }
+      if (!ozw.empty()) add(OP_OZW, P.push(ozw), (int)ozw.size(), 0, 0);
     }
     rec(ev(s, 0), 0);
     // slot of panel tile (i, s) of matrix m: first tiles first, then the rest
@@ -487,6 +503,40 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         if (!g.tc[d].empty()) add(OP_TC, P.push(g.tc[d]), (int)g.tc[d].size(), d, st);
       if (!g.f8.empty()) add(OP_FP8R, P.push(g.f8), (int)g.f8.size(), 0, st);
     };
+    // panel tiles stored in FP32 or below take X = A W on the tensor cores
+    // (Ozaki mode); the others keep the FP64 solve
+    auto split_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemOzA>& oza,
+                           std::vector<ItemOz>& ozg) {
+      if (!P.ozaki) return;
+      std::vector<ItemPanel> native;
+      for (const ItemPanel& it : panel) {
+        if (P.h_tiles[it.tile].dt == F64) { native.push_back(it); continue; }
+        const int64_t q = (it.x - P.d_panel) / ((int64_t)b * b);
+        const int m = it.mat;
+        ItemOzA a{};
+        a.tile = it.tile;
+        for (int d = 0; d < OZ_SMAX; ++d) a.slices[d] = P.slot_oz[q][d];
+        a.sigma = P.d_sigma + q * b;
+        oza.push_back(a);
+        ItemOz g{};
+        for (int d = 0; d < OZ_SMAX; ++d) { g.a[d] = P.slot_oz[q][d]; g.w[d] = P.wdig[par * P.mats.size() + m][d]; }
+        g.amax = it.amax;
+        g.sigma = a.sigma;
+        g.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
+        g.x = it.x;
+        ozg.push_back(g);
+      }
+      panel.swap(native);
+    };
+    auto emit_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemRound>& round, int st) {
+      std::vector<ItemOzA> oza;
+      std::vector<ItemOz> ozg;
+      split_panel(panel, oza, ozg);
+      if (!oza.empty()) add(OP_OZA, P.push(oza), (int)oza.size(), 0, st);
+      if (!panel.empty()) add(OP_PANEL, P.push(panel), (int)panel.size(), 0, st);
+      if (!ozg.empty()) add(OP_OZG, P.push(ozg), (int)ozg.size(), 0, st);
+      if (!round.empty()) add(OP_ROUND, P.push(round), (int)round.size(), 0, st);
+    };
     // ---------------- chain: first panel tile, its rounding, SYRK (s+1, s+1)
     {
       std::vector<ItemPanel> panel;
@@ -496,81 +546,22 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         if (P.mats[m].nt > s + 1) panel_items(m, s + 1, panel, round);
       if (s >= 1) wait(ev(s - 1, 2), 0);
       amax_reset(P.amax_panel0 + slot0, nfirst, 0);
-      if (!panel.empty()) {
-        add(OP_PANEL, P.push(panel), (int)panel.size(), 0, 0);
-        add(OP_ROUND, P.push(round), (int)round.size(), 0, 0);
-      }
+      emit_panel(panel, round, 0);
       rec(ev(s, 1), 0);
       for (int m = 0; m < (int)P.mats.size(); ++m)
         if (P.mats[m].nt > s + 1) add_update(syrk, m, s + 1, s + 1);
       if (s >= 1) wait(ev(s - 1, 3), 0);
       emit(syrk, 0);
     }
-    // ---------------- bulk: rest of the panel (+ L_ss^{-T}), column s+1, rest
+    // ---------------- bulk: rest of the panel, column s+1, rest
     {
       std::vector<ItemPanel> panel;
       std::vector<ItemRound> round;
       for (int m = 0; m < (int)P.mats.size(); ++m)
         for (int i = s + 2; i < P.mats[m].nt; ++i) panel_items(m, i, panel, round);
-      for (int m = 0; m < (int)P.mats.size(); ++m) {
-        auto& M = P.mats[m];
-        if (M.nt <= s) continue;
-        ItemPanel it{};
-        it.tile = P.ident;
-        it.identity = 1;
-        it.mat = m;
-        it.diag = M.tile[s * M.nt + s];
-        it.amax = (int)P.amax_dummy;
-        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
-        const TileRef r = P.h_tiles[M.linv[s]];
-        it.x = (double*)(P.pool[F64] + (size_t)r.idx * b * b * 8);
-        panel.push_back(it);
-      }
-      // Ozaki mode: panel tiles stored in FP32 or below take X = A W on the
-      // tensor cores, W = L_ss^{-T} (the identity solve above) split once
-      std::vector<ItemOzA> oza;
-      std::vector<ItemOzW> ozw;
-      std::vector<ItemOz> ozg;
-      if (P.ozaki) {
-        std::vector<ItemPanel> native;
-        std::vector<char> uses(P.mats.size(), 0);
-        for (const ItemPanel& it : panel) {
-          if (it.tile == P.ident || P.h_tiles[it.tile].dt == F64) { native.push_back(it); continue; }
-          const int64_t q = (it.x - P.d_panel) / ((int64_t)b * b);
-          const int m = it.mat;
-          uses[m] = 1;
-          ItemOzA a{};
-          a.tile = it.tile;
-          for (int d = 0; d < OZ_SMAX; ++d) a.slices[d] = P.slot_oz[q][d];
-          a.sigma = P.d_sigma + q * b;
-          oza.push_back(a);
-          ItemOz g{};
-          for (int d = 0; d < OZ_SMAX; ++d) { g.a[d] = P.slot_oz[q][d]; g.w[d] = P.wdig[par * P.mats.size() + m][d]; }
-          g.amax = it.amax;
-          g.sigma = a.sigma;
-          g.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
-          g.x = it.x;
-          ozg.push_back(g);
-        }
-        for (int m = 0; m < (int)P.mats.size(); ++m) {
-          if (!uses[m]) continue;
-          ItemOzW w{};
-          w.wtile = P.mats[m].linv[s];
-          for (int d = 0; d < OZ_SMAX; ++d) w.slices[d] = P.wdig[par * P.mats.size() + m][d];
-          w.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
-          ozw.push_back(w);
-        }
-        panel.swap(native);
-      }
       wait(ev(s, 0), 1);
       amax_reset(P.amax_panel0 + slot0 + nfirst, nrest, 1);
-      if (!oza.empty()) add(OP_OZA, P.push(oza), (int)oza.size(), 0, 1);
-      add(OP_PANEL, P.push(panel), (int)panel.size(), 0, 1);
-      if (!ozw.empty()) {
-        add(OP_OZW, P.push(ozw), (int)ozw.size(), 0, 1);
-        add(OP_OZG, P.push(ozg), (int)ozg.size(), 0, 1);
-      }
-      if (!round.empty()) add(OP_ROUND, P.push(round), (int)round.size(), 0, 1);
+      emit_panel(panel, round, 1);
       Group col, rest;
       for (int m = 0; m < (int)P.mats.size(); ++m)
         for (int i = s + 2; i < P.mats[m].nt; ++i) add_update(col, m, i, s + 1);
@@ -764,7 +755,7 @@ mp_status finish_plan(Plan& P) {
   P.d_logdet = (double*)p;
   if (mp_status st = P.alloc(&p, sizeof(int))) return st;
   P.d_err = (int*)p;
-  P.dag_bytes = sizeof(int) * (32 + (size_t)nm * nbb * nbb);
+  P.dag_bytes = sizeof(int) * (32 + (size_t)nm * 2 * nbb * nbb);
   if (mp_status st = P.alloc(&p, P.dag_bytes)) return st;
   P.d_dag = (int*)p;
   {
@@ -801,12 +792,6 @@ mp_status finish_plan(Plan& P) {
     }
   }
   CK(P.ctx, P.upload(P.d_tiles, P.h_tiles.data(), sizeof(TileRef) * ntiles));
-  {
-    std::vector<double> eye((size_t)b * b, 0.0);
-    for (int r = 0; r < b; ++r) eye[(size_t)r * b + r] = 1.0;
-    const TileRef r = P.h_tiles[P.ident];
-    CK(P.ctx, P.upload(P.pool[F64] + (size_t)r.idx * b * b * 8, eye.data(), sizeof(double) * b * b));
-  }
   std::vector<double> ones(ntiles, 1.0);
   CK(P.ctx, P.upload(P.d_scale, ones.data(), sizeof(double) * ntiles));
   CK(P.ctx, P.upload(P.d_ldoff, ldoff.data(), sizeof(int32_t) * nm));

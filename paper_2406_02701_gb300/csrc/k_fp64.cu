@@ -130,20 +130,28 @@ __device__ __forceinline__ void dag_solve(const double (*Ab)[NB + 1], const doub
 }
 
 // One persistent launch factors the FP64 diagonal tile of every item as a
-// task graph over its 32 x 32 blocks (nb = b / 32):
+// task graph over its 32 x 32 blocks (nb = b / 32) and forms
+// W = L^{-T} (the operand of the panel products and of the solves):
 //   F(0)       factor block (0, 0): L_00, Dinv_0 = L_00^{-1}, log-det part
 //   G(k)       k >= 1, the critical chain: L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T
 //              (published at once), A_kk -= L_{k,k-1} L_{k,k-1}^T (lower
 //              part), then factor block (k, k)
 //   T(r, k)    r > k + 1:  L_rk = A_rk Dinv_k^T
 //   U(r, c, k) k < c <= r, (r, c) != (k+1, k+1):  A_rc -= L_rk L_ck^T
-// ver[r nb + c] counts the operations finished on block (r, c): its c
-// updates, then the factorisation or solve.  CTAs take tasks by an atomic
-// ticket in a fixed topological order (every task's inputs come earlier in
-// the order), so a task only ever waits on tasks that running CTAs have
-// already taken: the schedule cannot deadlock, whatever the number of
-// co-resident CTAs.  Blocks written by other CTAs are read through L2
-// (ld.global.cg); every wait is bounded and reports through the error word.
+// and for Y = L^{-1} by block rows (Y_kk = Dinv_k, Y_rj = Dinv_r R_rj with
+// R_rj = -sum_{k=j}^{r-1} L_rk Y_kj), stored transposed as W:
+//   E(r, k, j) r > k >= j:  W_jr -= W_jk L_rk^T   (R_rj -= L_rk Y_kj)
+//   V(r, j)    r > j:       W_jr = W_jr Dinv_r^T   (Y_rj = Dinv_r R_rj)
+// F and G also write W_kk = Dinv_k^T and zero the blocks of W left of it.
+// ver[r nb + c] counts the operations finished on block (r, c) of the
+// factor (its c updates, then the factorisation or solve); ver[nb^2 +
+// j nb + r] those on block (j, r) of W (its r - j updates, then the solve).
+// CTAs take tasks by an atomic ticket in a fixed topological order (every
+// task's inputs come earlier in the order), so a task only ever waits on
+// tasks that running CTAs have already taken: the schedule cannot
+// deadlock, whatever the number of co-resident CTAs.  Blocks written by
+// other CTAs are read through L2 (ld.global.cg); every wait is bounded and
+// reports through the error word.
 __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __restrict__ items,
                                                    int count, const DagTask* __restrict__ tasks,
                                                    int ntasks, int* ticket, double* ldparts,
@@ -164,6 +172,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     const DagTask tk = tasks[t / count];
     const int r = tk.r, c = tk.c, k = tk.k;
     int* ver = it.ver;
+    int* wv = ver + nb * nb;
     if (tid == 0) {
       bool ok;
       if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err);
@@ -171,8 +180,15 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         ok = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err) && dag_wait(&ver[k * nb + k - 1], k - 1, A.err) &&
              dag_wait(&ver[k * nb + k], k - 1, A.err);
       else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err) && dag_wait(&ver[r * nb + k], k, A.err);
-      else ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
-                dag_wait(&ver[r * nb + c], k, A.err);
+      else if (tk.op == 2)
+        ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
+             dag_wait(&ver[r * nb + c], k, A.err);
+      else if (tk.op == 4)   // V(r, j = c): F(r) done, W_jr has its r - j updates
+        ok = dag_wait(&ver[r * nb + r], r + 1, A.err) && dag_wait(&wv[c * nb + r], r - c, A.err);
+      else                   // E(r, k, j = c): L_rk, W_jk final; the previous update of W_jr
+        ok = dag_wait(&ver[r * nb + k], k + 1, A.err) &&
+             (k == c ? dag_wait(&ver[c * nb + c], c + 1, A.err) : dag_wait(&wv[c * nb + k], k - c + 1, A.err)) &&
+             dag_wait(&wv[c * nb + r], k - c, A.err);
       if (!ok) atomicExch(A.err, 1);
       s_ok = ok;
     }
@@ -222,6 +238,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       __syncthreads();
       dag_factor(S2, S1, Tk, b, it.dinv + (int64_t)k * NB * NB, info + it.mat,
                  it.row0 + (long long)k * NB);
+      // W_kk = Dinv_k^T; the blocks of W left of it are zero
+      double* Wk = it.w + (int64_t)k * NB * b;
+      for (int e = tid; e < NB * NB; e += blockDim.x) Wk[(int64_t)(e / NB) * b + k * NB + e % NB] = S1[e % NB][e / NB];
+      for (int e = tid; e < NB * k * NB; e += blockDim.x) Wk[(int64_t)(e / (k * NB)) * b + e % (k * NB)] = 0.0;
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * NB * b + k * NB;
@@ -235,6 +255,43 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       dag_solve(S0, S1, out);
 #pragma unroll
       for (int j = 0; j < 4; ++j) Tr[(int64_t)ty * b + tx + 8 * j] = out[j];
+    } else if (tk.op == 4) {
+      // W_jr = W_jr Dinv_r^T
+      double* Wb = it.w + (int64_t)c * NB * b + r * NB;
+      const double* D = it.dinv + (int64_t)r * NB * NB;
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        S0[e / NB][e % NB] = __ldcg(Wb + (int64_t)(e / NB) * b + e % NB);
+        S1[e / NB][e % NB] = __ldcg(D + e);
+      }
+      __syncthreads();
+      double out[4];
+      dag_solve(S0, S1, out);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Wb[(int64_t)ty * b + tx + 8 * j] = out[j];
+    } else if (tk.op == 5) {
+      // W_jr -= W_jk L_rk^T (the first update, k = j, starts from zero)
+      const double* Wj = it.w + (int64_t)c * NB * b + k * NB;
+      const double* Lr = T + (int64_t)r * NB * b + k * NB;
+      double* Wb = it.w + (int64_t)c * NB * b + r * NB;
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        S0[e / NB][e % NB] = __ldcg(Wj + (int64_t)(e / NB) * b + e % NB);
+        S1[e / NB][e % NB] = __ldcg(Lr + (int64_t)(e / NB) * b + e % NB);
+      }
+      double cur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cur[j] = k == c ? 0.0 : __ldcg(Wb + (int64_t)ty * b + tx + 8 * j);
+      __syncthreads();
+      double acc[4] = {}, acc2[4] = {};
+      for (int q = 0; q < NB; q += 2) {
+        const double a = S0[ty][q], a2 = S0[ty][q + 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[j] += a * S1[tx + 8 * j][q];
+          acc2[j] += a2 * S1[tx + 8 * j][q + 1];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Wb[(int64_t)ty * b + tx + 8 * j] = cur[j] - (acc[j] + acc2[j]);
     } else {
       // A_rc -= L_rk L_ck^T
       const double* Lr = T + (int64_t)r * NB * b + k * NB;
@@ -263,8 +320,12 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      const int blk = (tk.op == 0 || tk.op == 3) ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
-      st_release(&ver[blk], k + 1);
+      if (tk.op == 4) st_release(&wv[c * nb + r], r - c + 1);
+      else if (tk.op == 5) st_release(&wv[c * nb + r], k - c + 1);
+      else {
+        const int blk = (tk.op == 0 || tk.op == 3) ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
+        st_release(&ver[blk], k + 1);
+      }
     }
     // the log-determinant part is off the critical chain: after publishing
     if (tk.op == 0 || tk.op == 3) dag_logdet(S2, ldparts + it.ldslot + k);
@@ -300,17 +361,15 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
     __syncthreads();                               // previous unit done with X
     for (int e = tid; e < PR * b; e += blockDim.x)
       X[e] = load_f64(src, ref.dt, (int64_t)r0 * b + e) * s_in;
-    // rows r0.. of I L^{-T} vanish left of column r0: skip those blocks
-    const int cb0 = it.identity ? r0 / NB : 0;
-    for (int cb = cb0; cb < b / NB; ++cb) {
+    for (int cb = 0; cb < b / NB; ++cb) {
       for (int e = tid; e < NB * NB; e += blockDim.x)
         Dv[(e / NB) * (NB + 1) + e % NB] = it.dinv[(int64_t)cb * NB * NB + e];
       __syncthreads();
       double acc[NQ], acc2[NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) { acc[q] = X[r * b + cb * NB + cx + LPR * q]; acc2[q] = 0.0; }
-      const int ch0 = cb0 * NB / PK;
-      const int nch = cb * NB / PK - ch0;
+      const int ch0 = 0;
+      const int nch = cb * NB / PK;
       double pre[NB * PK / 128];
       if (nch > 0) {
 #pragma unroll
@@ -474,6 +533,13 @@ std::vector<DagTask> potrf_dag_tasks(int nb) {
   auto add = [&](int op, int r, int c, int k) {
     v.push_back(DagTask{(uint8_t)op, (uint8_t)r, (uint8_t)c, (uint8_t)k});
   };
+  // W: per step k, the solves V(k, j) of row k of Y, then the updates
+  // E(r, k, j) of the rows below with it
+  auto wtasks = [&](int k) {
+    for (int j = 0; j < k; ++j) add(4, k, j, 0);
+    for (int r = k + 1; r < nb; ++r)
+      for (int j = 0; j <= k; ++j) add(5, r, j, k);
+  };
   add(0, 0, 0, 0);
   for (int r = 2; r < nb; ++r) add(1, r, 0, 0);
   for (int k = 0; k + 1 < nb; ++k) {
@@ -482,7 +548,9 @@ std::vector<DagTask> potrf_dag_tasks(int nb) {
     for (int r = k + 3; r < nb; ++r) add(1, r, k + 1, k + 1);
     for (int c = k + 2; c < nb; ++c)
       for (int r = c; r < nb; ++r) add(2, r, c, k);
+    wtasks(k);
   }
+  for (int j = 0; j + 1 < nb; ++j) add(4, nb - 1, j, 0);
   return v;
 }
 

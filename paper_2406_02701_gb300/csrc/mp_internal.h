@@ -61,11 +61,13 @@ struct ItemPotrf {
   int32_t pad_;
   int64_t row0;       // global row of the tile's first row
   double* dinv;       // b/32 inverses of the 32 x 32 diagonal blocks (row-major)
-  int32_t* ver;       // (b/32)^2 per-block progress counters
+  double* w;          // b x b: W = L^{-T} of the tile (upper triangular)
+  int32_t* ver;       // 2 (b/32)^2 progress counters: factor blocks, then blocks of W
 };
 struct DagTask {
   uint8_t op;         // 0 factor (0, 0), 1 solve (r, k), 2 update (r, c), 3 solve (k, k-1) +
-                      //   update and factor (k, k)
+                      //   update and factor (k, k), 4 solve of W block (c, r), 5 update of
+                      //   W block (c, r) with column k
   uint8_t r, c, k;
 };
 
@@ -74,9 +76,7 @@ struct ItemPanel {
   int32_t tile;       // A_ik
   int32_t diag;       // L_kk
   int32_t amax;       // amax slot of the result
-  int32_t identity;   // 1: tile is the identity (rows r >= r0 of X are 0 left of r0)
   int32_t mat;        // matrix of the plan (host bookkeeping)
-  int32_t pad_;
   double* dinv;       // (b/32) inverses of the diagonal 32-blocks of L_kk
   double* x;          // b x b float64 scratch
 };
