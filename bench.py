@@ -164,6 +164,68 @@ def oracle_sample(cfg, pmap, steps: int, repeats: int = 1, warmup: int = 0):
     return out
 
 
+def measured_peaks():
+    """Measured denominators (HBM copy GB/s, cuBLAS bf16 TFLOP/s)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "of measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/ (kernel -> bytes); None where no capture of the current kernel
+# exists.
+TRAFFIC_BYTES_PER_LAUNCH = {}
+
+
+def kernel_rooflines(prof, chol_ms, peak64, b):
+    """Roofline of the hot kernels of one factorisation; the dominant one
+    (largest share of the instrumented run) first."""
+    peaks, which = measured_peaks()
+    bf16 = peaks["bf16_tflops_sustained"]
+    # FP32-kind products are three TF32 MMAs; TF32 runs at the nominal
+    # TF32/BF16 dense ratio 1.1/2.25 of the BF16 rate
+    tf32x3 = bf16 * (1.1 / 2.25) / 3.0
+    kinds = {
+        "potrf_tile": ("k_potrf_dag", "alu", peak64,
+                       "FP64 DFMA loop probe in this run (mp_probe_fp64_peak); flops: POTRF b^3/3 + "
+                       "inverse b^3/3 per diagonal tile"),
+        "panel_trsm_first": ("k_panel_trsm (chain)", "alu", peak64, "FP64 DFMA loop probe in this run"),
+        "panel_trsm": ("k_panel_trsm (bulk)", "alu", peak64, "FP64 DFMA loop probe in this run"),
+        "update_tc_3xtf32": ("k_update_tc (FP32 kind, 3 TF32 MMAs)", "tensor", tf32x3,
+                             f"bf16_tflops_sustained {which} x 1.1/2.25 / 3"),
+        "update_tc_lowp": ("k_update_tc (BF16/FP16/E4M3 kinds)", "tensor", bf16,
+                           f"bf16_tflops_sustained {which}"),
+        "panel_ozaki_gemm": ("k_oz_gemm", "tensor", bf16,
+                             f"bf16_tflops_sustained {which}; achieved counts the TRSM flops b^3 per tile"),
+    }
+    out = []
+    for cls, (kname, bound, peak, src) in kinds.items():
+        v = prof.get(cls)
+        if not v or not v["launches"] or v["ms"] <= 0 or not peak:
+            continue
+        ach = v["flops"] / (v["ms"] * 1e-3) / 1e12
+        r = {"bound": bound, "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "frac": ach / peak, "peak_source": src,
+             "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(kname.split(" ")[0]),
+             "launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+             "flops_per_launch": v["flops"] / v["launches"],
+             "share_of_chol": v["ms"] / chol_ms if chol_ms else None}
+        if cls == "panel_ozaki_gemm":
+            # 8 digits per operand, 36 digit products of 2 b^3 flops each per tile
+            r["executed_tflops"] = ach * 72.0
+            r["executed_frac"] = ach * 72.0 / peak
+        out.append(r)
+    out.sort(key=lambda r: -(r["share_of_chol"] or 0))
+    if not out:
+        return None
+    dom = dict(out[0])
+    dom["others"] = out[1:]
+    return dom
+
+
 def make_map(ctx, cfg, dsorted, eps):
     n, b = cfg["n"], cfg["b"]
     nt = -(-n // b)
@@ -429,14 +491,7 @@ def ours(args, cfg):
     # kernel breakdown (one instrumented factorisation, CUDA events on the stream)
     prof = T.profile()
     chol_ms = sum(v["ms"] for v in prof.values())
-    peak64 = ctx.fp64_peak()
-    tr = prof["panel_trsm"]
-    achieved = tr["flops"] / (tr["ms"] * 1e-3) / 1e12 if tr["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_panel_trsm, bulk launches (FP64 DFMA)",
-                "achieved": achieved,
-                "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64 if peak64 else None,
-                "peak_source": "DFMA loop probe measured in this run (mp_probe_fp64_peak)",
-                "traffic": None, "share_of_chol": tr["ms"] / chol_ms if chol_ms else None}
+    roofline = kernel_rooflines(prof, chol_ms, ctx.fp64_peak(), b)
     breakdown = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
                      "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] > 0 and v["flops"] > 0 else None}
                  for k, v in prof.items() if v["launches"]}

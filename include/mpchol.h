@@ -263,16 +263,18 @@ mp_status mp_tmat_stats(mp_tmat* t, int64_t* chol_kernels, int64_t* gen_kernels,
                         int64_t* loglik_kernels);
 
 /* Runs the factorisation once with direct launches and a CUDA event after
- * every launch, and returns per kernel class c (0 diagonal-tile POTRF task
- * graph, 1 panel TRSM, 2 panel rounding, 3 FP64 updates, 4 CUDA-core
- * lower-precision updates, 5 tensor-core updates, 6 E4M3 target rounding,
- * 7 other, 8 panel TRSM of the first tile of each step (the lookahead
- * chain's part), 9 integer-digit panel products, 10 their digit splits): h_ms[c] summed event time, h_launches[c]
- * launches, h_flops[c] algorithmic flops (POTRF b^3/3 per tile, TRSM b^3
- * per tile, GEMM 2b^3, SYRK b^2(b+1)).  Arrays hold nclass >=
- * MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as mp_chol).
- * Synchronous. */
-#define MP_PROFILE_CLASSES 11
+ * every launch, and returns per kernel class c (0 diagonal-tile task graph:
+ * POTRF and W = L^{-T}, 1 panel TRSM, 2 panel rounding, 3 FP64 updates,
+ * 4 CUDA-core lower-precision updates, 5 tensor-core updates of FP32 kind
+ * (three TF32 products), 6 E4M3 target rounding, 7 other, 8 panel TRSM of
+ * the first tile of each step (the lookahead chain's part), 9 integer-digit
+ * panel products, 10 their digit splits, 11 tensor-core updates of 16- and
+ * 8-bit kinds): h_ms[c] summed event time, h_launches[c] launches,
+ * h_flops[c] algorithmic flops (diagonal tile 2b^3/3 for the factor and
+ * its inverse, TRSM b^3 per tile, GEMM 2b^3, SYRK b^2(b+1)).  Arrays hold
+ * nclass >= MP_PROFILE_CLASSES entries.  Leaves the matrix factored (as
+ * mp_chol).  Synchronous. */
+#define MP_PROFILE_CLASSES 12
 mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, int64_t* h_launches,
                           double* h_flops);
 

@@ -1701,7 +1701,7 @@ int op_class(const Launch& L) {
     case OP_ROUND: return 2;
     case OP_UPD64: return 3;
     case OP_UPD32: return 4;
-    case OP_TC: return 5;
+    case OP_TC: return L.kb == F32 ? 5 : 11;
     case OP_FP8R: return 6;
     case OP_OZG: return 9;
     case OP_OZA:
@@ -1737,7 +1737,7 @@ extern "C" mp_status mp_chol_profile(mp_tmat* t, int32_t nclass, float* h_ms, in
     if (c == 7 && L.count == 0) continue;
     h_launches[c] += 1;
     switch (L.op) {
-      case OP_POTRF_DAG: h_flops[c] += L.count * b * b * b / 3.0; break;
+      case OP_POTRF_DAG: h_flops[c] += L.count * 2.0 * b * b * b / 3.0; break;  // POTRF + L^{-1}
       case OP_PANEL: h_flops[c] += L.count * b * b * b; break;  // incl. L_kk^{-T} rows
       case OP_OZG: h_flops[c] += L.count * b * b * b; break;    // the solve it stands for
       case OP_UPD64:

@@ -275,8 +275,8 @@ class TiledMatrix:
         return dict(chol=a.value, generate=g.value, loglik=l.value)
 
     PROFILE_CLASSES = ["potrf_tile", "panel_trsm", "panel_round", "update_f64", "update_simt",
-                       "update_tc", "fp8_round", "other", "panel_trsm_first", "panel_ozaki_gemm",
-                       "ozaki_split"]
+                       "update_tc_3xtf32", "fp8_round", "other", "panel_trsm_first", "panel_ozaki_gemm",
+                       "ozaki_split", "update_tc_lowp"]
 
     def profile(self):
         k = len(self.PROFILE_CLASSES)
