@@ -240,6 +240,8 @@ struct mp_tmat {
   int ws_nrhs = 0;
   double *zp = nullptr, *x = nullptr, *r = nullptr, *w = nullptr, *d = nullptr;
   double *rowabs = nullptr, *red = nullptr;
+  double* rpart = nullptr;          // residual partial products: nt * nt * b * nrhs
+  float* rpabs = nullptr;           // residual partial absolute sums: nt * nt * b
   int *active = nullptr, *iters = nullptr, *any = nullptr;
   cudaGraphExec_t ll_exec = nullptr;
   int64_t ll_kernels = 0;
@@ -1245,6 +1247,11 @@ static mp_status ensure_ws(mp_tmat* t, int nrhs) {
   if ((st = A((void**)&t->w, sizeof(double) * N * nrhs))) return st;
   if ((st = A((void**)&t->d, sizeof(double) * N * nrhs))) return st;
   if ((st = A((void**)&t->rowabs, sizeof(double) * N))) return st;
+  if (P.keep_sigma) {
+    const size_t nt = (size_t)P.mats[0].nt;
+    if ((st = A((void**)&t->rpart, sizeof(double) * nt * nt * P.b * nrhs))) return st;
+    if ((st = A((void**)&t->rpabs, sizeof(float) * nt * nt * P.b))) return st;
+  }
   if ((st = A((void**)&t->red, sizeof(double) * (5 * nrhs + 2)))) return st;
   if ((st = A((void**)&t->active, sizeof(int) * nrhs))) return st;
   if ((st = A((void**)&t->iters, sizeof(int) * nrhs))) return st;
@@ -1327,22 +1334,35 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
     const SolvePlan fwd_rw = build_solve(P, {t->r}, {t->w}, {N}, {nrhs}, 0);
     const SolvePlan bwd_wx = build_solve(P, {t->w}, {t->x}, {N}, {nrhs}, 1);
     const SolvePlan bwd_wd = build_solve(P, {t->w}, {t->d}, {N}, {nrhs}, 1);
-    std::vector<ItemResid> res;
+    std::vector<ItemResTile> rtiles;
+    std::vector<ItemResRow> rrows;
     for (int i = 0; i < M.nt && refine_iters > 0; ++i) {
-      ItemResid it{};
-      it.mat = 0;
-      it.ti = i;
-      it.nt = M.nt;
-      it.sig = P.d_sig;
-      it.x = t->x;
-      it.z = t->zp;
-      it.r = t->r;
-      it.rowabs = t->rowabs;
-      it.ld = N;
-      it.nrhs = nrhs;
-      res.push_back(it);
+      for (int j = 0; j <= i; ++j) {
+        ItemResTile it{};
+        it.tile = M.sig[(size_t)i * M.nt + j];
+        it.ti = i;
+        it.tj = j;
+        it.nt = M.nt;
+        it.x = t->x;
+        it.part = t->rpart;
+        it.pabs = t->rpabs;
+        it.ld = N;
+        it.nrhs = nrhs;
+        rtiles.push_back(it);
+      }
+      ItemResRow r{};
+      r.ti = i;
+      r.nt = M.nt;
+      r.part = t->rpart;
+      r.pabs = t->rpabs;
+      r.z = t->zp;
+      r.r = t->r;
+      r.rowabs = t->rowabs;
+      r.ld = N;
+      r.nrhs = nrhs;
+      rrows.push_back(r);
     }
-    size_t res_off = P.push(res);
+    const size_t rtiles_off = P.push(rtiles), rrows_off = P.push(rrows);
     size_t bytes = P.h_items.size();
     if (bytes > t->d_sitems_cap) {
       P.raw_free(t->d_sitems);
@@ -1359,7 +1379,8 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
            *snorm = red + 4 * nrhs;
     const int64_t n = M.n;
     const char* db = t->d_sitems;
-    const ItemResid* ri = reinterpret_cast<const ItemResid*>(db + res_off);
+    const ItemResTile* rti = reinterpret_cast<const ItemResTile*>(db + rtiles_off);
+    const ItemResRow* rro = reinterpret_cast<const ItemResRow*>(db + rrows_off);
     mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
       launch_copy_pad(d_z, ldz, t->zp, N, n, N, nrhs, nullptr, s);
       launch_copy_pad(t->zp, N, t->r, N, N, N, nrhs, nullptr, s);
@@ -1371,7 +1392,8 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
         run_solve(P, db, bwd_wx, nullptr, s);
         launch_colmax(t->zp, n, N, nrhs, zmax, nullptr, s);
         for (int itr = 0; itr < refine_iters; ++itr) {
-          launch_residual(P.arena(), ri, (int)res.size(), nrhs, itr == 0, t->any, s);
+          launch_residual(P.arena(), rti, (int)rtiles.size(), rro, (int)rrows.size(), nrhs, itr == 0,
+                          t->any, s);
           if (itr == 0) launch_colmax(t->rowabs, n, N, 1, snorm, t->any, s);
           launch_colmax(t->r, n, N, nrhs, rmax, t->any, s);
           launch_colmax(t->x, n, N, nrhs, xmax, t->any, s);

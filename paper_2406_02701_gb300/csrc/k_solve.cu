@@ -360,74 +360,164 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
   }
 }
 
-// r_i = z_i - sum_j Sigma_ij x_j for 32 rows of block row ti, in chunks of
-// 32 rows x 128 columns of Sigma staged through shared memory.
-constexpr int RW = 128;
+// Residual pass 1: one CTA per lower tile of Sigma (float64).  The tile's
+// columns are split into G = max(1, b / 512) groups of at most 512; the
+// eight warps are spread over the groups and take rows round-robin.  For a
+// row, a lane loads its 16 (or fewer) entries (the next row's loads are
+// issued before the current row's arithmetic), adds their products with
+// x_j into the row's dot product (reduced across the warp) and their
+// products with x_i[row] into per-column accumulators (the transposed
+// product).  Column accumulators are combined across the warps of a group
+// in warp order; row dots across groups in group order.  Absolute sums
+// (first iteration only) use FP32: they only scale the stopping tolerance.
+constexpr int RES_NCOL = 16;
 template <int RC>
-__global__ void __launch_bounds__(256) k_residual(Arena A, const ItemResid* __restrict__ items,
-                                                  int want_rowabs, const int* gate) {
+__global__ void __launch_bounds__(256) k_residual_tile(Arena A, const ItemResTile* __restrict__ items,
+                                                       int want_abs, const int* gate) {
   if (gated(gate)) return;
-  __shared__ double blk[32][RW + 1];
-  __shared__ double xs[RW][RC];
-  const ItemResid it = items[blockIdx.x];
-  const int b = A.b, tid = threadIdx.x;
-  const int lr0 = blockIdx.y * 32;                // local row offset in block row ti
-  const int64_t g0 = (int64_t)it.ti * b + lr0;    // global row
-  const int row = tid / 8, part = tid % 8;        // 8 threads per row, 16 columns each
+  extern __shared__ double rsm[];
+  const ItemResTile it = items[blockIdx.x];
+  const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = b > 512 ? b / 512 : 1;              // column groups
+  const int W = 8 / G;                              // warps per group
+  const int g = warp / W, wl = warp % W;
+  const int gw = b / G;                             // columns per group
+  const int ncol = gw / 32;                         // columns per lane (<= 16)
+  const int cbase = g * gw;
+  const bool diag = it.ti == it.tj;
+  double* xj = rsm;                                 // [b][RC]
+  double* xi = xj + (size_t)b * RC;                 // [b][RC]
+  double* yrow = xi + (size_t)b * RC;               // [G][b][RC]
+  double* csum = yrow + (size_t)G * b * RC;         // [b][RC]
+  float* arow = reinterpret_cast<float*>(csum + (size_t)b * RC);   // [G][b]
+  float* acol = arow + (size_t)G * b;                               // [b]
+  const double* S = tile_ptr<double>(A, it.tile);
+  const double* xjg = it.x + (int64_t)it.tj * b;
+  const double* xig = it.x + (int64_t)it.ti * b;
   for (int c0 = 0; c0 < it.nrhs; c0 += RC) {
     const int nc = min(RC, it.nrhs - c0);
-    double acc[RC], acc2[RC];
+    const bool abs_now = want_abs && c0 == 0;
+    __syncthreads();
+    for (int e = tid; e < b * RC; e += blockDim.x) {
+      const int t = e / RC, c = e % RC;
+      xj[e] = c < nc ? xjg[(int64_t)(c0 + c) * it.ld + t] : 0.0;
+      xi[e] = c < nc ? xig[(int64_t)(c0 + c) * it.ld + t] : 0.0;
+      csum[e] = 0.0;
+    }
+    if (abs_now)
+      for (int e = tid; e < b; e += blockDim.x) acol[e] = 0.f;
+    __syncthreads();
+    double cacc[RES_NCOL][RC];
+    float cabs[RES_NCOL];
 #pragma unroll
-    for (int c = 0; c < RC; ++c) { acc[c] = 0.0; acc2[c] = 0.0; }
-    double rabs = 0.0;
-    for (int tj = 0; tj < it.nt; ++tj) {
-      const bool lower = tj <= it.ti;
-      const int tile = lower ? it.sig[it.ti * it.nt + tj] : it.sig[tj * it.nt + it.ti];
-      const double* S = tile_ptr<double>(A, tile);
-      for (int cc0 = 0; cc0 < b; cc0 += RW) {
-        __syncthreads();
-        for (int e = tid; e < 32 * RW; e += blockDim.x) {
-          if (tj > it.ti) {
-            // upper part: Sigma_ij = Sigma_ji^T; consecutive threads read a row of S
-            int cc = e / 32, rr = e % 32;
-            blk[rr][cc] = S[(int64_t)(cc0 + cc) * b + lr0 + rr];
-          } else {
-            int rr = e / RW, cc = e % RW;
-            int gr = lr0 + rr, gc = cc0 + cc;
-            blk[rr][cc] = (tj < it.ti || gc <= gr) ? S[(int64_t)gr * b + gc] : S[(int64_t)gc * b + gr];
-          }
-        }
-        for (int e = tid; e < RW * RC; e += blockDim.x) {
-          int t = e / RC, c = e % RC;
-          xs[t][c] = c < nc ? it.x[(int64_t)(c0 + c) * it.ld + (int64_t)tj * b + cc0 + t] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int q = 0; q < RW / 8; q += 2) {
-          const int cc = part + 8 * q, cc2 = cc + 8;
-          const double v = blk[row][cc], v2 = blk[row][cc2];
-          if (want_rowabs && c0 == 0) rabs += fabs(v) + fabs(v2);
+    for (int m = 0; m < RES_NCOL; ++m) {
+      cabs[m] = 0.f;
 #pragma unroll
-          for (int c = 0; c < RC; ++c) {
-            acc[c] += v * xs[cc][c];
-            acc2[c] += v2 * xs[cc2][c];
-          }
+      for (int c = 0; c < RC; ++c) cacc[m][c] = 0.0;
+    }
+    double cur[RES_NCOL], nxt[RES_NCOL];
+    int r = wl;
+#pragma unroll
+    for (int m = 0; m < RES_NCOL; ++m)
+      cur[m] = (m < ncol && r < b) ? S[(int64_t)r * b + cbase + lane + 32 * m] : 0.0;
+    for (; r < b; r += W) {
+      const int rn = r + W;
+#pragma unroll
+      for (int m = 0; m < RES_NCOL; ++m)
+        nxt[m] = (m < ncol && rn < b) ? S[(int64_t)rn * b + cbase + lane + 32 * m] : 0.0;
+      // a diagonal tile holds its lower half: row r uses columns <= r, and
+      // the transposed product takes the columns < r
+      double dot[RC];
+#pragma unroll
+      for (int c = 0; c < RC; ++c) dot[c] = 0.0;
+      float ra = 0.f;
+#pragma unroll
+      for (int m = 0; m < RES_NCOL; ++m) {
+        const int col = cbase + lane + 32 * m;
+        const double sv = (m < ncol && (!diag || col <= r)) ? cur[m] : 0.0;
+        const double tv = (!diag || col < r) ? sv : 0.0;
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+          dot[c] += sv * xj[(m < ncol ? col : 0) * RC + c];
+          cacc[m][c] += tv * xi[r * RC + c];
+        }
+        if (abs_now) {
+          ra += fabsf((float)sv);
+          cabs[m] += fabsf((float)tv);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < RC; ++c) dot[c] = warp_sum(dot[c]);
+      if (abs_now)
+        for (int o = 16; o > 0; o >>= 1) ra += __shfl_xor_sync(0xffffffffu, ra, o);
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < RC; ++c) yrow[((size_t)g * b + r) * RC + c] = dot[c];
+        if (abs_now) arow[(size_t)g * b + r] = ra;
+      }
+#pragma unroll
+      for (int m = 0; m < RES_NCOL; ++m) cur[m] = nxt[m];
+    }
+    // column sums: the warps of a group add in warp order
+    for (int w = 0; w < W; ++w) {
+      if (wl == w) {
+#pragma unroll
+        for (int m = 0; m < RES_NCOL; ++m) {
+          if (m >= ncol) break;
+          const int col = cbase + lane + 32 * m;
+#pragma unroll
+          for (int c = 0; c < RC; ++c) csum[col * RC + c] += cacc[m][c];
+          if (abs_now) acol[col] += cabs[m];
+        }
+      }
+      __syncthreads();
+    }
+    // write the partials
+    double* pr = it.part + ((size_t)(it.ti * it.nt + it.tj) * it.nrhs) * b;
+    double* pc = it.part + ((size_t)(it.tj * it.nt + it.ti) * it.nrhs) * b;
+    for (int e = tid; e < b * nc; e += blockDim.x) {
+      const int c = e / b, t = e % b;
+      double v = 0.0;
+      for (int q = 0; q < G; ++q) v += yrow[((size_t)q * b + t) * RC + c];
+      if (diag) pr[(size_t)(c0 + c) * b + t] = v + csum[t * RC + c];
+      else {
+        pr[(size_t)(c0 + c) * b + t] = v;
+        pc[(size_t)(c0 + c) * b + t] = csum[t * RC + c];
+      }
+    }
+    if (abs_now) {
+      float* ar = it.pabs + (size_t)(it.ti * it.nt + it.tj) * b;
+      float* ac = it.pabs + (size_t)(it.tj * it.nt + it.ti) * b;
+      for (int t = tid; t < b; t += blockDim.x) {
+        float v = 0.f;
+        for (int q = 0; q < G; ++q) v += arow[(size_t)q * b + t];
+        if (diag) ar[t] = v + acol[t];
+        else {
+          ar[t] = v;
+          ac[t] = acol[t];
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < RC; ++c) acc[c] += acc2[c];
-    for (int o = 4; o > 0; o >>= 1) {
-#pragma unroll
-      for (int c = 0; c < RC; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-      rabs += __shfl_xor_sync(0xffffffffu, rabs, o);
-    }
-    if (part == 0) {
-      const int64_t g = g0 + row;
-      for (int c = 0; c < nc; ++c)
-        it.r[(int64_t)(c0 + c) * it.ld + g] = it.z[(int64_t)(c0 + c) * it.ld + g] - acc[c];
-      if (want_rowabs && c0 == 0) it.rowabs[g] = rabs;
-    }
+  }
+}
+
+// Residual pass 2: r_i = z_i - sum_j part(i, j), j in increasing order.
+__global__ void __launch_bounds__(256) k_residual_rows(int b, const ItemResRow* __restrict__ items,
+                                                       int want_abs, const int* gate) {
+  if (gated(gate)) return;
+  const ItemResRow it = items[blockIdx.x];
+  const int t = blockIdx.y * blockDim.x + threadIdx.x;
+  if (t >= b) return;
+  const int64_t g = (int64_t)it.ti * b + t;
+  for (int c = 0; c < it.nrhs; ++c) {
+    double acc = 0.0;
+    for (int j = 0; j < it.nt; ++j) acc += it.part[((size_t)(it.ti * it.nt + j) * it.nrhs + c) * b + t];
+    it.r[(int64_t)c * it.ld + g] = it.z[(int64_t)c * it.ld + g] - acc;
+  }
+  if (want_abs && it.rowabs) {
+    double a = 0.0;
+    for (int j = 0; j < it.nt; ++j) a += (double)it.pabs[(size_t)(it.ti * it.nt + j) * b + t];
+    it.rowabs[g] = a;
   }
 }
 
@@ -567,12 +657,21 @@ void launch_solve_dag(const Arena& A, const ItemSolveDag* items, const SolveTask
   else k_solve_dag<RCMAX><<<grid, 256, smem, s>>>(A, items, tasks, ntasks, ticket, trans, gate);
 }
 
-void launch_residual(const Arena& A, const ItemResid* items, int count, int nrhs,
-                     int want_rowabs, const int* gate, cudaStream_t s) {
-  if (count <= 0) return;
-  dim3 grid(count, A.b / 32);
-  if (nrhs == 1) k_residual<1><<<grid, 256, 0, s>>>(A, items, want_rowabs, gate);
-  else k_residual<RCMAX><<<grid, 256, 0, s>>>(A, items, want_rowabs, gate);
+void launch_residual(const Arena& A, const ItemResTile* tiles, int ntiles, const ItemResRow* rows,
+                     int nrows, int nrhs, int want_rowabs, const int* gate, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  const int b = A.b, G = b > 512 ? b / 512 : 1;
+  const int rc = nrhs == 1 ? 1 : 4;
+  const size_t smem = sizeof(double) * (size_t)b * rc * (3 + G) + sizeof(float) * (size_t)b * (G + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_residual_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_residual_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  if (rc == 1) k_residual_tile<1><<<ntiles, 256, smem, s>>>(A, tiles, want_rowabs, gate);
+  else k_residual_tile<4><<<ntiles, 256, smem, s>>>(A, tiles, want_rowabs, gate);
+  k_residual_rows<<<dim3(nrows, (b + 255) / 256), 256, 0, s>>>(b, rows, want_rowabs, gate);
 }
 
 void launch_logdet(const double* ldparts, const int32_t* ldoff, const int32_t* ldcnt, int nmat,

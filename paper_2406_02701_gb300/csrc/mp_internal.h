@@ -175,20 +175,32 @@ struct ItemSolveDag {
 // (40-51), 32-row block p (52-59).
 typedef uint64_t SolveTask;
 
-// Residual rows of one block row of a matrix: r_i = z_i - sum_j S_ij x_j.
-struct ItemResid {
-  int32_t mat;
-  int32_t ti;         // block row
-  int32_t nt;
-  int32_t pad_;
-  const int32_t* sig; // nt*nt tile ids of the float64 Sigma copy (lower)
-  const double* x;    // N x nrhs, ld
-  const double* z;    // N x nrhs, ld
-  double* r;          // N x nrhs, ld
-  double* rowabs;     // N: sum_j |S_ij| (for ||Sigma||_inf)
+// Refinement residual r = z - Sigma x from the float64 copy of Sigma's lower
+// tiles.  Pass 1, one item per lower tile (i, j): its row product
+// Sigma_ij x_j into part(i, j) and, for i > j, its transposed product
+// Sigma_ij^T x_i into part(j, i) (a diagonal tile's upper half is its lower
+// half transposed), so every tile is read once.  Pass 2, one item per tile
+// row i: r_i = z_i - sum_j part(i, j), j in increasing order.  part(i, j)
+// holds b x nrhs doubles at ((i nt + j) nrhs + c) b; pabs the same for the
+// absolute row sums (float, one column; NULL: not wanted).
+struct ItemResTile {
+  int32_t tile;       // Sigma tile (FP64)
+  int32_t ti, tj, nt;
+  const double* x;    // N x nrhs (column stride ld)
+  double* part;
+  float* pabs;
   int64_t ld;
-  int32_t nrhs;
-  int32_t pad2_;
+  int32_t nrhs, pad_;
+};
+struct ItemResRow {
+  int32_t ti, nt;
+  const double* part;
+  const float* pabs;
+  const double* z;    // N x nrhs (column stride ld)
+  double* r;          // N x nrhs (column stride ld)
+  double* rowabs;     // N: sum_j |Sigma_ij| (NULL: not wanted)
+  int64_t ld;
+  int32_t nrhs, pad_;
 };
 
 // ---- host launchers (each .cu file exports its own) -----------------------
@@ -236,8 +248,8 @@ void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
 std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int p_blocks, int trans);
 void launch_solve_dag(const Arena& A, const ItemSolveDag* items, const SolveTask* tasks, int ntasks,
                       int* ticket, int trans, int nrhs_max, const int* gate, cudaStream_t s);
-void launch_residual(const Arena& A, const ItemResid* items, int count, int nrhs,
-                     int want_rowabs, const int* gate, cudaStream_t s);
+void launch_residual(const Arena& A, const ItemResTile* tiles, int ntiles, const ItemResRow* rows,
+                     int nrows, int nrhs, int want_rowabs, const int* gate, cudaStream_t s);
 void launch_logdet(const double* ldparts, const int32_t* ldoff, const int32_t* ldcnt, int nmat,
                    double* logdet, cudaStream_t s);
 void launch_colmax(const double* v, int64_t n, int64_t ld, int nrhs, double* out,
