@@ -40,7 +40,7 @@ constexpr int NB = 32;   // inner block of the diagonal tile
 // R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Writes L and the
 // inverse to global memory; info gets the first pivot that is not > 0.
 __device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk, int b,
-                           double* dinv, long long* info, long long row0) {
+                           double* dinv, long long* info, long long row0, const uint16_t* tri) {
   const int tid = threadIdx.x, lane = tid & 31;
   constexpr int NO = 224;                        // threads of warps 1-7
   __shared__ double rps[NB];                     // 1 / L_cc
@@ -70,20 +70,22 @@ __device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk,
       const int t = tid - 32;
       if (c >= 1 && t < c) R[c - 1][t] *= rps[c - 1];
       asm volatile("bar.sync 1, %0;" ::"r"(NO));
-      // trailing rows c+2.. on columns c+2..r, then inverse rows c.. on columns < c
+      // compact enumeration (the FP64 pipe charges a warp instruction in
+      // full however many lanes it masks): trailing rows c+2.. on columns
+      // c+2..r through the triangle table, then inverse rows c.. on columns < c
       const int m = NB - 2 - c;
       const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
       const int total = ntri + (c >= 1 ? (NB - c) * c : 0);
+      const float rc = c >= 1 ? 1.f / (float)c : 0.f;
       for (int e = t; e < total; e += NO) {
         if (e < ntri) {
-          int rr = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-          while (rr * (rr + 1) / 2 > e) --rr;
-          while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-          const int r = c + 2 + rr, j = c + 2 + (e - rr * (rr + 1) / 2);
+          const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
+          const int r = c + 2 + rr, j = c + 2 + cc;
           S[r][j] -= S[r][c] * S[j][c];
         } else {
           const int q = e - ntri;
-          const int r = c + q / c, j = q % c;
+          const int qr = (int)(((float)q + 0.5f) * rc);   // q / c, exact for q < 2^12
+          const int r = c + qr, j = q - qr * c;
           R[r][j] -= S[r][c - 1] * R[c - 1][j];
         }
       }
@@ -116,14 +118,14 @@ __device__ __forceinline__ void dag_solve(const double (*Ab)[NB + 1], const doub
                                           double out[4]) {
   const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
   double acc[4] = {};
-  // four independent accumulation chains; q beyond 8 j + 7 is inactive in
-  // the whole warp for column group j
+  // four independent accumulation chains; D[c][q] = 0 for q > c, so column
+  // group j stops at q = 8 j + 7 (a bound uniform over the warp)
 #pragma unroll 4
   for (int q = 0; q < NB; ++q) {
     const double a = Ab[ty][q];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (q <= 8 * j + 7 && q <= tx + 8 * j) acc[j] += a * D[tx + 8 * j][q];
+    for (int j = 0; j < 4; ++j)   // D is lower triangular with exact zeros above
+      if (q <= 8 * j + 7) acc[j] += a * D[tx + 8 * j][q];
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) out[j] = acc[j];
@@ -160,9 +162,13 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
   __shared__ double S1[NB][NB + 1];
   __shared__ double S2[NB][NB + 1];
   __shared__ int s_t, s_ok;
+  // lower triangle of a 32 x 32 block in row order: entry e -> (row, col)
+  __shared__ uint16_t tri[NB * (NB + 1) / 2];
   const int b = A.b, nb = b / NB, tid = threadIdx.x;
   const int ty = tid / 8, tx = tid % 8;
   const int total = ntasks * count;
+  for (int r = 0; r < NB; ++r)
+    for (int c = tid; c <= r; c += blockDim.x) tri[r * (r + 1) / 2 + c] = (uint16_t)(r << 8 | c);
   for (;;) {
     if (tid == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
@@ -220,12 +226,9 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
           __threadfence();
           st_release(&ver[k * nb + k - 1], k);
         }
-        // A_kk -= X X^T on the lower triangle (528 entries)
+        // A_kk -= X X^T on the lower triangle (528 entries, table order)
         for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) {
-          int rr = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-          while (rr * (rr + 1) / 2 > e) --rr;
-          while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-          const int cc = e - rr * (rr + 1) / 2;
+          const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
           double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
           for (int q = 0; q < NB; q += 2) {
@@ -237,11 +240,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       }
       __syncthreads();
       dag_factor(S2, S1, Tk, b, it.dinv + (int64_t)k * NB * NB, info + it.mat,
-                 it.row0 + (long long)k * NB);
-      // W_kk = Dinv_k^T; the blocks of W left of it are zero
+                 it.row0 + (long long)k * NB, tri);
+      // W_kk = Dinv_k^T (the blocks of W left of it are zeroed after publishing)
       double* Wk = it.w + (int64_t)k * NB * b;
       for (int e = tid; e < NB * NB; e += blockDim.x) Wk[(int64_t)(e / NB) * b + k * NB + e % NB] = S1[e % NB][e / NB];
-      for (int e = tid; e < NB * k * NB; e += blockDim.x) Wk[(int64_t)(e / (k * NB)) * b + e % (k * NB)] = 0.0;
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * NB * b + k * NB;
@@ -327,8 +329,13 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         st_release(&ver[blk], k + 1);
       }
     }
-    // the log-determinant part is off the critical chain: after publishing
-    if (tk.op == 0 || tk.op == 3) dag_logdet(S2, ldparts + it.ldslot + k);
+    // off the critical chain, after publishing: the log-determinant part and
+    // the zero blocks of W left of W_kk (no task reads them)
+    if (tk.op == 0 || tk.op == 3) {
+      dag_logdet(S2, ldparts + it.ldslot + k);
+      double* Wk = it.w + (int64_t)k * NB * b;
+      for (int e = tid; e < NB * k * NB; e += blockDim.x) Wk[(int64_t)(e / (k * NB)) * b + e % (k * NB)] = 0.0;
+    }
   }
 }
 
