@@ -103,6 +103,8 @@ struct MatDesc {
                                             // (bit d: rounded copy in format d; bit 5:
                                             // TF32 hi/lo split)
   std::vector<int32_t> linv;                // nt: FP64 tile holding L_ii^{-T}
+  std::vector<int32_t> linv_hi, linv_lo;    // nt each: its FP32 hi/lo parts (-1: all-FP64 matrix)
+  bool mixed = false;                       // some tile stored below FP64
   int32_t ldoff = 0;
   double* dinv = nullptr;                   // nt * (b/32) blocks of 32x32
 };
@@ -323,6 +325,15 @@ mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
     }
   M.linv.assign(nt, -1);
   for (int i = 0; i < nt; ++i) M.linv[i] = new_tile(P, F64);
+  for (int i = 0; i < nt; ++i)
+    for (int j = 0; j <= i; ++j) M.mixed |= dt(i, j) != F64;
+  M.linv_hi.assign(nt, -1);
+  M.linv_lo.assign(nt, -1);
+  if (M.mixed)
+    for (int i = 0; i < nt; ++i) {
+      M.linv_hi[i] = new_tile(P, F32);
+      M.linv_lo[i] = new_tile(P, F32);
+    }
   if (P.keep_sigma) {
     M.sig.assign((size_t)nt * nt, -1);
     for (int i = 0; i < nt; ++i)
@@ -384,6 +395,10 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         it.row0 = (int64_t)s * b;
         it.dinv = M.dinv + (int64_t)s * nbb * 1024;
         it.w = (double*)(P.pool[F64] + (size_t)P.h_tiles[M.linv[s]].idx * b * b * 8);
+        if (M.mixed) {
+          it.whi = (float*)(P.pool[F32] + (size_t)P.h_tiles[M.linv_hi[s]].idx * b * b * 4);
+          it.wlo = (float*)(P.pool[F32] + (size_t)P.h_tiles[M.linv_lo[s]].idx * b * b * 4);
+        }
         it.ver = P.d_dag + 32 + (int64_t)m * 2 * nbb * nbb;
         items.push_back(it);
       }
@@ -767,6 +782,8 @@ mp_status finish_plan(Plan& P) {
       P.ltab_off.push_back((int64_t)ltab.size());
       ltab.insert(ltab.end(), M.tile.begin(), M.tile.end());
       ltab.insert(ltab.end(), M.linv.begin(), M.linv.end());
+      ltab.insert(ltab.end(), M.linv_hi.begin(), M.linv_hi.end());
+      ltab.insert(ltab.end(), M.linv_lo.begin(), M.linv_lo.end());
       P.scnt_off.push_back((int64_t)cnt);
       cnt += (size_t)M.nt * (nbb + 1);
     }
@@ -1206,6 +1223,7 @@ SolvePlan build_solve(Plan& P, const std::vector<double*>& in, const std::vector
     it.ld = ld[m];
     it.nt = M.nt;
     it.nrhs = nrhs[m];
+    it.ffdiag = M.mixed ? 1 : 0;
     sp.nrhs_max = std::max(sp.nrhs_max, nrhs[m]);
     items.push_back(it);
     nts.push_back(M.nt);

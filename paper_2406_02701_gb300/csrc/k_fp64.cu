@@ -242,8 +242,16 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       dag_factor(S2, S1, Tk, b, it.dinv + (int64_t)k * NB * NB, info + it.mat,
                  it.row0 + (long long)k * NB, tri);
       // W_kk = Dinv_k^T (the blocks of W left of it are zeroed after publishing)
-      double* Wk = it.w + (int64_t)k * NB * b;
-      for (int e = tid; e < NB * NB; e += blockDim.x) Wk[(int64_t)(e / NB) * b + k * NB + e % NB] = S1[e % NB][e / NB];
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int64_t o = (int64_t)k * NB * b + (int64_t)(e / NB) * b + k * NB + e % NB;
+        const double v = S1[e % NB][e / NB];
+        it.w[o] = v;
+        if (it.whi) {
+          const float h = (float)v;
+          it.whi[o] = h;
+          it.wlo[o] = (float)(v - (double)h);
+        }
+      }
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * NB * b + k * NB;
@@ -269,7 +277,15 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       double out[4];
       dag_solve(S0, S1, out);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Wb[(int64_t)ty * b + tx + 8 * j] = out[j];
+      for (int j = 0; j < 4; ++j) {
+        const int64_t o = (int64_t)c * NB * b + r * NB + (int64_t)ty * b + tx + 8 * j;
+        Wb[(int64_t)ty * b + tx + 8 * j] = out[j];
+        if (it.whi) {
+          const float h = (float)out[j];
+          it.whi[o] = h;
+          it.wlo[o] = (float)(out[j] - (double)h);
+        }
+      }
     } else if (tk.op == 5) {
       // W_jr -= W_jk L_rk^T (the first update, k = j, starts from zero)
       const double* Wj = it.w + (int64_t)c * NB * b + k * NB;

@@ -81,17 +81,21 @@ __global__ void k_morton_gather(const unsigned long long* __restrict__ keys,
   out[2 * i + 1] = in[2 * p + 1];
 }
 
-// Matérn covariance of two locations (closed forms, x = r / range).
-__device__ __forceinline__ double entry(const ItemGen& it, double xi, double yi, double xj,
-                                        double yj, int64_t gi, int64_t gj) {
+// Matérn covariance of two locations (closed forms, x = r / range).  x is
+// r times the rounded reciprocal of the range (GB300's FP64 pipe makes a
+// division cost about ten FP64 operations): one more rounding than r /
+// range, i.e. |dx| <= 2 ulp(x), which exp(-x) carries as a relative error
+// of at most 2 x 2^-52.
+__device__ __forceinline__ double entry(const ItemGen& it, double inv_range, double xi, double yi,
+                                        double xj, double yj, int64_t gi, int64_t gj) {
   if (gi >= it.n || gj >= it.n) return gi == gj ? 1.0 : 0.0;
   double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
   double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-  double x = __ddiv_rn(r, it.range);
+  double x = __dmul_rn(r, inv_range);
   double poly;
   if (it.nu == 0.5) poly = 1.0;
   else if (it.nu == 1.5) poly = __dadd_rn(1.0, x);
-  else poly = __dadd_rn(__dadd_rn(1.0, x), __ddiv_rn(__dmul_rn(x, x), 3.0));
+  else poly = __dadd_rn(__dadd_rn(1.0, x), __dmul_rn(__dmul_rn(x, x), 1.0 / 3.0));
   double v = __dmul_rn(__dmul_rn(it.sigma2, poly), exp(-x));
   if (gi == gj) v = __dadd_rn(v, it.nugget);
   return v;
@@ -121,12 +125,13 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
   __syncthreads();
   const int dt = A.tiles[it.tile].dt;
   char* dst = tile_bytes(A, it.tile);
+  const double inv_range = 1.0 / it.range;
   double mx = 0.0;
   double inv_s = 1.0;
   if (!AMAX && dt == E4M3) inv_s = 1.0 / e4m3_scale(amax_value(&A.amax[it.tile]));
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
-    double v = entry(it, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
+    double v = entry(it, inv_range, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
     int64_t off = (int64_t)(r0 + r) * b + c;
     if (AMAX) {
       mx = fmax(mx, fabs(v));
@@ -170,10 +175,11 @@ __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __rest
     rx[2 * r + 1] = g < it.n ? it.locs[2 * g + 1] : 0.0;
   }
   __syncthreads();
+  const double inv_range = 1.0 / it.range;
   double ss = 0.0;
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
-    double v = entry(it, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
+    double v = entry(it, inv_range, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
     ss += v * v;
   }
   __shared__ double red[8];

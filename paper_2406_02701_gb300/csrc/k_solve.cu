@@ -71,7 +71,7 @@ __device__ __forceinline__ void ff_madd(float& hi, float& lo, float a, float h, 
   lo += err + e + a * l;
 }
 
-constexpr int MLP = 16;   // loads a thread issues before using them
+constexpr int MLP = 32;   // loads a thread issues before using them
 
 // Diagonal block: out_i[p] from in_i with X = L_ii^{-T} (float64).
 template <int RCT>
@@ -152,6 +152,109 @@ __device__ void solve_diag(const Arena& A, const ItemSolveDag& it, int i, int p,
   }
 }
 
+// (hi, lo) += (xh + xl)(vh + vl) to about 2^-46: xh vh exactly as p + e,
+// the cross terms once rounded, xl vl dropped.
+__device__ __forceinline__ void ff_madd2(float& hi, float& lo, float xh, float xl, float vh, float vl) {
+  const float p = xh * vh;
+  const float e = fmaf(xh, vh, -p);
+  const float cross = fmaf(xh, vl, xl * vh);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb);
+  hi = s;
+  lo += err + e + cross;
+}
+
+// Diagonal block in float-float from W's FP32 hi/lo parts (mixed factors):
+// same data flow as solve_diag, the products on the FP32 pipe.
+template <int RCT>
+__device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int p, int trans,
+                              double* vs, double* part) {
+  const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = it.nt;
+  const float* Xh = tile_ptr<float>(A, it.linv[nt + i]);
+  const float* Xl = tile_ptr<float>(A, it.linv[2 * nt + i]);
+  const double* v = it.in + (int64_t)i * b;
+  double* o = it.out + (int64_t)i * b;
+  float2* vsf = reinterpret_cast<float2*>(vs);
+  const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
+  for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
+    const int nc = min(RCT, it.nrhs - c0);
+    __syncthreads();
+    for (int e = tid; e < (t1 - t0) * RCT; e += blockDim.x) {
+      const int t = t0 + e / RCT, c = e % RCT;
+      const double x = c < nc ? __ldcg(v + (int64_t)(c0 + c) * it.ld + t) : 0.0;
+      const float h = (float)x;
+      vsf[t * RCT + c] = make_float2(h, (float)(x - (double)h));
+    }
+    __syncthreads();
+    float hi[RCT], lo[RCT];
+#pragma unroll
+    for (int c = 0; c < RCT; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
+    if (!trans) {
+      const int r = p * 32 + lane;
+      const int nk = t1 / 8;
+      for (int k0 = 0; k0 < nk; k0 += MLP) {
+        float xh[MLP], xl[MLP];
+#pragma unroll
+        for (int u = 0; u < MLP; ++u) {
+          const int t = warp + 8 * (k0 + u);
+          const bool ok = k0 + u < nk && t <= r;
+          xh[u] = ok ? Xh[(int64_t)t * b + r] : 0.f;
+          xl[u] = ok ? Xl[(int64_t)t * b + r] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < MLP; ++u) {
+          if (k0 + u >= nk) break;
+          const int t = warp + 8 * (k0 + u);
+#pragma unroll
+          for (int c = 0; c < RCT; ++c) {
+            const float2 w = vsf[t * RCT + c];
+            ff_madd2(hi[c], lo[c], xh[u], xl[u], w.x, w.y);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < RCT; ++c) part[(warp * 32 + lane) * RCT + c] = (double)hi[c] + (double)lo[c];
+      __syncthreads();
+      if (warp == 0) {
+        for (int c = 0; c < nc; ++c) {
+          double sum = 0.0;
+          for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
+          o[(int64_t)(c0 + c) * it.ld + r] = sum;
+        }
+      }
+    } else {
+      const int r = p * 32 + (tid >> 3), sg = tid & 7;
+      const int nk = (b - p * 32) / 8;
+      for (int k0 = 0; k0 < nk; k0 += MLP) {
+        float xh[MLP], xl[MLP];
+#pragma unroll
+        for (int u = 0; u < MLP; ++u) {
+          const int t = p * 32 + sg + 8 * (k0 + u);
+          const bool ok = k0 + u < nk && t >= r;
+          xh[u] = ok ? Xh[(int64_t)r * b + t] : 0.f;
+          xl[u] = ok ? Xl[(int64_t)r * b + t] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < MLP; ++u) {
+          if (k0 + u >= nk) break;
+          const int t = p * 32 + sg + 8 * (k0 + u);
+#pragma unroll
+          for (int c = 0; c < RCT; ++c) {
+            const float2 w = vsf[t * RCT + c];
+            ff_madd2(hi[c], lo[c], xh[u], xl[u], w.x, w.y);
+          }
+        }
+      }
+      for (int c = 0; c < nc; ++c) {
+        double sum = (double)hi[c] + (double)lo[c];
+        for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+        if (sg == 0) o[(int64_t)(c0 + c) * it.ld + r] = sum;
+      }
+    }
+  }
+}
+
 // Off-diagonal block, tiles stored in FP32 or below (DT), float-float sums.
 template <int RCT, int DT>
 __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, int b, int p,
@@ -168,9 +271,10 @@ __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, i
     for (int k0 = 0; k0 < nk; k0 += MLP) {
       float a[MLP];
 #pragma unroll
-      for (int u = 0; u < MLP; ++u) a[u] = tval<DT>(L, row + sg + 8 * (k0 + u)) * scf;
+      for (int u = 0; u < MLP; ++u) a[u] = k0 + u < nk ? tval<DT>(L, row + sg + 8 * (k0 + u)) * scf : 0.f;
 #pragma unroll
       for (int u = 0; u < MLP; ++u) {
+        if (k0 + u >= nk) break;                   // uniform: nk = b / 8 for every thread
         const int t = sg + 8 * (k0 + u);
 #pragma unroll
         for (int c = 0; c < RCT; ++c) {
@@ -194,9 +298,11 @@ __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, i
     for (int k0 = 0; k0 < nk; k0 += MLP) {
       float a[MLP];
 #pragma unroll
-      for (int u = 0; u < MLP; ++u) a[u] = tval<DT>(L, (int64_t)(warp + 8 * (k0 + u)) * b + q) * scf;
+      for (int u = 0; u < MLP; ++u)
+        a[u] = k0 + u < nk ? tval<DT>(L, (int64_t)(warp + 8 * (k0 + u)) * b + q) * scf : 0.f;
 #pragma unroll
       for (int u = 0; u < MLP; ++u) {
+        if (k0 + u >= nk) break;
         const int t = warp + 8 * (k0 + u);
 #pragma unroll
         for (int c = 0; c < RCT; ++c) {
@@ -234,11 +340,13 @@ __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, in
     for (int k0 = 0; k0 < nk; k0 += MLP) {
       double a[MLP];
 #pragma unroll
-      for (int u = 0; u < MLP; ++u) a[u] = L[row + sg + 8 * (k0 + u)];
+      for (int u = 0; u < MLP; ++u) a[u] = k0 + u < nk ? L[row + sg + 8 * (k0 + u)] : 0.0;
 #pragma unroll
-      for (int u = 0; u < MLP; ++u)
+      for (int u = 0; u < MLP; ++u) {
+        if (k0 + u >= nk) break;
 #pragma unroll
         for (int c = 0; c < RCT; ++c) acc[c] += a[u] * vs[(sg + 8 * (k0 + u)) * RCT + c];
+      }
     }
     for (int c = 0; c < nc; ++c) {
       double sum = acc[c];
@@ -254,11 +362,13 @@ __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, in
     for (int k0 = 0; k0 < nk; k0 += MLP) {
       double a[MLP];
 #pragma unroll
-      for (int u = 0; u < MLP; ++u) a[u] = L[(int64_t)(warp + 8 * (k0 + u)) * b + q];
+      for (int u = 0; u < MLP; ++u) a[u] = k0 + u < nk ? L[(int64_t)(warp + 8 * (k0 + u)) * b + q] : 0.0;
 #pragma unroll
-      for (int u = 0; u < MLP; ++u)
+      for (int u = 0; u < MLP; ++u) {
+        if (k0 + u >= nk) break;
 #pragma unroll
         for (int c = 0; c < RCT; ++c) acc[c] += a[u] * vs[(warp + 8 * (k0 + u)) * RCT + c];
+      }
     }
 #pragma unroll
     for (int c = 0; c < RCT; ++c) part[(warp * 32 + lane) * RCT + c] = acc[c];
@@ -349,7 +459,10 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
     }
     __syncthreads();
     if (!s_ok) break;
-    if (op == 0) solve_diag<RCT>(A, it, i, p, trans, vs, part);
+    if (op == 0) {
+      if (it.ffdiag) solve_diag_ff<RCT>(A, it, i, p, trans, vs, part);
+      else solve_diag<RCT>(A, it, i, p, trans, vs, part);
+    }
     else solve_off<RCT>(A, it, i, j, p, trans, vs, part);
     __syncthreads();
     if (tid == 0) {

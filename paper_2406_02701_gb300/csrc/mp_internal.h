@@ -62,6 +62,8 @@ struct ItemPotrf {
   int64_t row0;       // global row of the tile's first row
   double* dinv;       // b/32 inverses of the 32 x 32 diagonal blocks (row-major)
   double* w;          // b x b: W = L^{-T} of the tile (upper triangular)
+  float* whi;         // W as FP32 hi + lo pair (upper part only; NULL: not wanted)
+  float* wlo;
   int32_t* ver;       // 2 (b/32)^2 progress counters: factor blocks, then blocks of W
 };
 struct DagTask {
@@ -163,12 +165,15 @@ struct ItemGen {
 // finished 32-row blocks of out_i.
 struct ItemSolveDag {
   const int32_t* tiles;   // nt x nt tile ids of the factor (lower part)
-  const int32_t* linv;    // nt tile ids of L_ii^{-T} (FP64, upper triangular)
+  const int32_t* linv;    // nt tile ids of L_ii^{-T} (FP64, upper triangular), then nt ids
+                          // of its FP32 hi parts and nt of its lo parts (ffdiag)
   double* in;             // N x nrhs (column stride ld), consumed
   double* out;            // N x nrhs (column stride ld)
   int* cnt;
   int64_t ld;
   int32_t nt, nrhs;
+  int32_t ffdiag;         // 1: diagonal steps in float-float from the hi/lo parts
+  int32_t pad_;
 };
 // Task of the solve graph: matrix (bits 0-23), op (24-27: 0 diagonal block,
 // 1 off-diagonal block), target tile row i (28-39), source tile row j

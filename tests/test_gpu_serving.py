@@ -79,13 +79,20 @@ def _drive(srv, reqs):
 def test_admission_respects_the_budget_and_release_frees(ctx):
     from paper_2406_02701_gb300 import mpchol, serving
     reqs = serving.make_requests(5, 1e6, seed=9, sizes=(1000,), weights=(1,))
-    # n = 1000 (tile 128) needs about 9 MB: a 12 MB budget admits one at a
-    # time, evicting the previous request's kept factor
-    srv = mpchol.Server(ctx, hbm_budget=12 << 20, max_slots=4, eps=1e-6)
+    # footprint of one request (n = 1000, tile 128), measured alone
+    probe = mpchol.Server(ctx, hbm_budget=8 << 30, max_slots=1, eps=1e-6)
+    _drive(probe, reqs[:1])
+    one = probe.stats()["bytes"]
+    probe.close()
+    assert one > 0
+    # a budget of 1.5 requests admits one at a time, evicting the previous
+    # request's kept factor
+    budget = int(1.5 * one)
+    srv = mpchol.Server(ctx, hbm_budget=budget, max_slots=4, eps=1e-6)
     ids, done, peak = _drive(srv, reqs)
     assert peak == 1
     assert all(r["status"] == 0 for r in done.values())
-    assert srv.stats()["bytes"] <= 12 << 20
+    assert srv.stats()["bytes"] <= budget
     for rid in ids:
         srv.release(rid)
     assert srv.stats()["bytes"] == 0 and srv.stats()["kept"] == 0
