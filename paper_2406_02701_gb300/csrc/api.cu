@@ -522,12 +522,19 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
     };
     // panel tiles stored in FP32 or below take X = A W on the tensor cores
     // (Ozaki mode); the others keep the FP64 solve
-    auto split_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemOzA>& oza,
-                           std::vector<ItemOz>& ozg) {
+    auto split_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemRound>& round,
+                           std::vector<ItemOzA>& oza, std::vector<ItemOz>& ozg) {
       if (!P.ozaki) return;
       std::vector<ItemPanel> native;
-      for (const ItemPanel& it : panel) {
-        if (P.h_tiles[it.tile].dt == F64) { native.push_back(it); continue; }
+      std::vector<ItemRound> rest_round;
+      for (size_t k = 0; k < panel.size(); ++k) {
+        const ItemPanel& it = panel[k];
+        const ItemRound& rd = round[k];
+        if (P.h_tiles[it.tile].dt == F64) {
+          native.push_back(it);
+          rest_round.push_back(rd);
+          continue;
+        }
         const int64_t q = (it.x - P.d_panel) / ((int64_t)b * b);
         const int m = it.mat;
         ItemOzA a{};
@@ -541,14 +548,25 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         g.sigma = a.sigma;
         g.tau = P.d_tau + (par * P.mats.size() + m) * (int64_t)b;
         g.x = it.x;
+        // rounding fused into the product unless an E4M3 scale (from the
+        // tile's amax) is involved
+        bool e4 = P.h_tiles[it.tile].dt == E4M3;
+        for (int d = 0; d < MAX_SHADOW; ++d) e4 |= rd.shadow[d] >= 0 && P.h_tiles[rd.shadow[d]].dt == E4M3;
+        g.fuse = e4 ? 0 : 1;
+        g.tile = it.tile;
+        for (int d = 0; d < MAX_SHADOW; ++d) g.shadow[d] = rd.shadow[d];
+        g.hi = rd.hi;
+        g.lo = rd.lo;
         ozg.push_back(g);
+        if (e4) rest_round.push_back(rd);
       }
       panel.swap(native);
+      round.swap(rest_round);
     };
     auto emit_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemRound>& round, int st) {
       std::vector<ItemOzA> oza;
       std::vector<ItemOz> ozg;
-      split_panel(panel, oza, ozg);
+      split_panel(panel, round, oza, ozg);
       if (!oza.empty()) add(OP_OZA, P.push(oza), (int)oza.size(), 0, st);
       if (!panel.empty()) add(OP_PANEL, P.push(panel), (int)panel.size(), 0, st);
       if (!ozg.empty()) add(OP_OZG, P.push(ozg), (int)ozg.size(), 0, st);

@@ -243,9 +243,11 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* bempty = bfull + OZ_BSTG;
   uint64_t* accf = bempty + OZ_BSTG;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
-  const ItemOz it = items[blockIdx.x];
+  // grid (column block, row block, tile): the CTAs that share a row strip of
+  // A's digits run next to each other, so the strip is read from DRAM once
+  const ItemOz it = items[blockIdx.z];
   const int b = A.b;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.z * OZ_BN;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * OZ_BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_ASTG; ++s) { mb_init(&afull[s], 1); mb_init(&aempty[s], 1); }
@@ -329,8 +331,28 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = m0 + warp * 32 + lane;
   const float sg = it.sigma[row];
+  // staging of the warp's 32 x 32 chunk (the ring buffers are free once every
+  // MMA has completed): float64 X, or the scaled float-float pair when fused
   double (*Sx)[33] = reinterpret_cast<double (*)[33]>(smem + warp * 32 * 33 * sizeof(double));
+  float2 (*Sf)[33] = reinterpret_cast<float2 (*)[33]>(smem + warp * 32 * 33 * sizeof(double));
   float mx = 0.f;
+  // fused rounding (no E4M3 target or shadow): the tile, its shadow copies
+  // and its TF32 split come straight from the float-float value
+  int tdt = -1, sdt[MAX_SHADOW];
+  char* tdst = nullptr;
+  char* sdst[MAX_SHADOW];
+  float* thi = nullptr;
+  float* tlo = nullptr;
+  if (it.fuse) {
+    tdt = A.tiles[it.tile].dt;
+    tdst = tile_bytes(A, it.tile);
+#pragma unroll
+    for (int q = 0; q < MAX_SHADOW; ++q) {
+      sdt[q] = it.shadow[q] >= 0 ? A.tiles[it.shadow[q]].dt : -1;
+      sdst[q] = it.shadow[q] >= 0 ? tile_bytes(A, it.shadow[q]) : nullptr;
+    }
+    if (it.hi >= 0) { thi = tile_ptr<float>(A, it.hi); tlo = tile_ptr<float>(A, it.lo); }
+  }
 #pragma unroll 1
   for (int h = 0; h < OZ_BN / 32; ++h) {
     // levels from the smallest (l = S-1) to the largest, in float-float
@@ -352,13 +374,41 @@ __global__ void __launch_bounds__(128, 1)
         lo[j] += e;
       }
     }
-    if (have) {
-      // stage the warp's 32 x 32 chunk in shared memory (the ring buffers are
-      // free once every MMA has completed), then write rows with lanes over
-      // columns: coalesced
+    if (!have) continue;
+    if (it.fuse) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const float st = sg * it.tau[n0 + h * 32 + j];   // power of two: scaling is exact
+        Sf[lane][j] = make_float2(hi[j] * st, lo[j] * st);
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const float2 p = Sf[rr][lane];
+        const int64_t o = (int64_t)(m0 + warp * 32 + rr) * b + n0 + h * 32 + lane;
+        float stored;
+        if (tdt == F32) {
+          stored = __fadd_rn(p.x, p.y);              // the float-float value rounded once
+          reinterpret_cast<float*>(tdst)[o] = stored;
+        } else {
+          store_round(tdst, tdt, o, (double)p.x + (double)p.y);
+          stored = load_f32(tdst, tdt, o);
+        }
+#pragma unroll
+        for (int q = 0; q < MAX_SHADOW; ++q)
+          if (sdst[q]) store_round_f32(sdst[q], sdt[q], o, stored);
+        if (thi) {
+          uint32_t hb;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(stored));
+          thi[o] = __uint_as_float(hb);
+          tlo[o] = stored - __uint_as_float(hb);
+        }
+      }
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float st = sg * it.tau[n0 + h * 32 + j];
         Sx[lane][j] = (double)(hi[j] * st) + (double)(lo[j] * st);
       }
       __syncwarp();
@@ -415,7 +465,7 @@ void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const CUtens
     cudaFuncSetAttribute(k_oz_gemm<OZ_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_oz_gemm<OZ_S><<<dim3(count, A.b / 128, A.b / OZ_BN), 128, smem, s>>>(A, items, mapA, mapB);
+  k_oz_gemm<OZ_S><<<dim3(A.b / OZ_BN, A.b / 128, count), 128, smem, s>>>(A, items, mapA, mapB);
 }
 
 }  // namespace mp

@@ -152,7 +152,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // KIND: 0 BF16, 1 FP16, 2 E4M3, 3 FP32 as three TF32 products.
 template <int KIND, int STAGES>
 __global__ void __launch_bounds__(128, 1)
-    k_update_tc(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap) {
+    k_update_tc(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap,
+                int sub_fast) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int NA = KIND == 3 ? 2 : 1;              // operand slices per side
   constexpr int STAGE_BYTES = 2 * NA * TC_BUF;
@@ -163,9 +164,13 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* accf = empty + STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
 
-  const ItemTC it = items[blockIdx.x];
+  // grid (sub-block, target) when the targets fit in grid.y: the sub-blocks
+  // of one target, which share operand strips, run next to each other
+  const bool sub_major = sub_fast != 0;
+  const ItemTC it = items[sub_major ? blockIdx.y : blockIdx.x];
   const int b = A.b, nsub = b / TC_BM;
-  const int rb = blockIdx.y / nsub, cb = blockIdx.y % nsub;
+  const int sb = sub_major ? blockIdx.x : blockIdx.y;
+  const int rb = sb / nsub, cb = sb % nsub;
   if (it.syrk && cb > rb) return;                  // strictly above the diagonal
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -339,7 +344,8 @@ void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap
     attr = true;
   }
   const int nsub = A.b / TC_BM;
-  k_update_tc<KIND, STAGES><<<dim3(count, nsub * nsub), 128, smem, s>>>(A, items, map);
+  if (count <= 65535) k_update_tc<KIND, STAGES><<<dim3(nsub * nsub, count), 128, smem, s>>>(A, items, map, 1);
+  else k_update_tc<KIND, STAGES><<<dim3(count, nsub * nsub), 128, smem, s>>>(A, items, map, 0);
 }
 
 }  // namespace

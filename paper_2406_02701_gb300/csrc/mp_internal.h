@@ -131,10 +131,13 @@ struct ItemOz {             // X = A W for one panel tile
   int32_t a[OZ_SMAX];       // digit tiles of A
   int32_t w[OZ_SMAX];       // digit tiles of W^T
   int32_t amax;
-  int32_t pad_;
+  int32_t fuse;             // 1: round X into the tile, its shadows and TF32 splits here
+  int32_t tile;             // (fuse) the panel tile
+  int32_t shadow[MAX_SHADOW];
+  int32_t hi, lo;
   const float* sigma;
   const float* tau;
-  double* x;                // b x b float64 result
+  double* x;                // b x b float64 result (when not fused)
 };
 
 // Rounds an E4M3 target from its FP32 scratch with the new scale.
