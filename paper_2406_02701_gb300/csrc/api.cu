@@ -167,6 +167,8 @@ struct Plan {
   size_t d_items_cap = 0;
   std::vector<Launch> chol;          // full factorisation
   std::vector<size_t> step_begin;    // index into chol of each step's first launch
+  std::vector<int64_t> first_split;  // per step: launch splitting its first panel tiles' digits
+                                     // (issued by the previous step's bulk), or -1
   cudaGraphExec_t chol_exec = nullptr;
   int64_t chol_kernels = 0;
   bool factored = false;
@@ -362,6 +364,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
   int64_t max_v = 0;
   P.chol.clear();
   P.step_begin.clear();
+  P.first_split.assign(maxnt + 1, -1);
   {
     const std::vector<DagTask> tasks = potrf_dag_tasks(nbb);
     P.dag_tasks_off = P.push(tasks);
@@ -563,11 +566,12 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
       panel.swap(native);
       round.swap(rest_round);
     };
-    auto emit_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemRound>& round, int st) {
+    auto emit_panel = [&](std::vector<ItemPanel>& panel, std::vector<ItemRound>& round, int st,
+                          bool split_done) {
       std::vector<ItemOzA> oza;
       std::vector<ItemOz> ozg;
       split_panel(panel, round, oza, ozg);
-      if (!oza.empty()) add(OP_OZA, P.push(oza), (int)oza.size(), 0, st);
+      if (!oza.empty() && !split_done) add(OP_OZA, P.push(oza), (int)oza.size(), 0, st);
       if (!panel.empty()) add(OP_PANEL, P.push(panel), (int)panel.size(), 0, st);
       if (!ozg.empty()) add(OP_OZG, P.push(ozg), (int)ozg.size(), 0, st);
       if (!round.empty()) add(OP_ROUND, P.push(round), (int)round.size(), 0, st);
@@ -581,7 +585,9 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         if (P.mats[m].nt > s + 1) panel_items(m, s + 1, panel, round);
       if (s >= 1) wait(ev(s - 1, 2), 0);
       amax_reset(P.amax_panel0 + slot0, nfirst, 0);
-      emit_panel(panel, round, 0);
+      // from step 1 on, the bulk of the previous step split this tile's rows
+      // right after finishing it
+      emit_panel(panel, round, 0, P.ozaki && s >= 1);
       rec(ev(s, 1), 0);
       for (int m = 0; m < (int)P.mats.size(); ++m)
         if (P.mats[m].nt > s + 1) add_update(syrk, m, s + 1, s + 1);
@@ -596,7 +602,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         for (int i = s + 2; i < P.mats[m].nt; ++i) panel_items(m, i, panel, round);
       wait(ev(s, 0), 1);
       amax_reset(P.amax_panel0 + slot0 + nfirst, nrest, 1);
-      emit_panel(panel, round, 1);
+      emit_panel(panel, round, 1, false);
       Group col, rest;
       for (int m = 0; m < (int)P.mats.size(); ++m)
         for (int i = s + 2; i < P.mats[m].nt; ++i) add_update(col, m, i, s + 1);
@@ -606,6 +612,29 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
       wait(ev(s, 1), 1);
       amax_reset(P.amax_v0, vslot, 1);
       emit(col, 1);
+      // Ozaki mode: digits of the next step's first panel tiles (s+2, s+1),
+      // final after these column updates, split here off the critical chain
+      if (P.ozaki) {
+        const int64_t nslot0 = ((s + 1) & 1) * P.pslots;
+        std::vector<ItemOzA> nxt;
+        int64_t nf = 0;
+        for (int m = 0; m < (int)P.mats.size(); ++m) {
+          auto& M = P.mats[m];
+          if (M.nt <= s + 2) continue;
+          const int64_t q = nslot0 + nf++;
+          const int tile = M.tile[(s + 2) * M.nt + s + 1];
+          if (P.h_tiles[tile].dt == F64) continue;
+          ItemOzA a{};
+          a.tile = tile;
+          for (int d = 0; d < OZ_SMAX; ++d) a.slices[d] = P.slot_oz[q][d];
+          a.sigma = P.d_sigma + q * b;
+          nxt.push_back(a);
+        }
+        if (!nxt.empty()) {
+          P.first_split[s + 1] = (int64_t)P.chol.size();
+          add(OP_OZA, P.push(nxt), (int)nxt.size(), 0, 1);
+        }
+      }
       rec(ev(s, 2), 1);
       emit(rest, 1);
       rec(ev(s, 3), 1);
@@ -1168,6 +1197,8 @@ mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1) {
   if (!t->generated) return fail(P.ctx, MP_ERR_STATE, "matrix not generated or loaded");
   CK(P.ctx, cudaSetDevice(P.ctx->device));
   if (k0 == 0) run_launch(P, P.chol[0], P.stream);   // info reset
+  // the digit split of step k0's first panel tiles is issued by step k0-1
+  if (k0 >= 1 && k0 < k1 && P.first_split[k0] >= 0) run_launch(P, P.chol[P.first_split[k0]], P.stream);
   for (size_t l = P.step_begin[k0]; l < P.step_begin[k1]; ++l) run_launch(P, P.chol[l], P.stream);
   if (k1 == nt) {
     run_launch(P, P.chol.back(), P.stream);

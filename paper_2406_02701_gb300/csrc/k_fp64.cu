@@ -77,18 +77,34 @@ __device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk,
       const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
       const int total = ntri + (c >= 1 ? (NB - c) * c : 0);
       const float rc = c >= 1 ? 1.f / (float)c : 0.f;
-      for (int e = t; e < total; e += NO) {
+      // at most three elements per thread (total <= 3 * 224); the updates of
+      // one column touch distinct entries and read only columns c, c - 1 and
+      // row c - 1 of R, so all operands are loaded before any store
+      double* dst[3];
+      double x0[3], x1[3], x2[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int e = t + u * NO;
+        dst[u] = nullptr;
         if (e < ntri) {
           const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
           const int r = c + 2 + rr, j = c + 2 + cc;
-          S[r][j] -= S[r][c] * S[j][c];
-        } else {
+          dst[u] = &S[r][j];
+          x1[u] = S[r][c];
+          x2[u] = S[j][c];
+        } else if (e < total) {
           const int q = e - ntri;
           const int qr = (int)(((float)q + 0.5f) * rc);   // q / c, exact for q < 2^12
           const int r = c + qr, j = q - qr * c;
-          R[r][j] -= S[r][c - 1] * R[c - 1][j];
+          dst[u] = &R[r][j];
+          x1[u] = S[r][c - 1];
+          x2[u] = R[c - 1][j];
         }
+        if (dst[u]) x0[u] = *dst[u];
       }
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (dst[u]) *dst[u] = x0[u] - x1[u] * x2[u];
     }
   }
   __syncthreads();
