@@ -314,8 +314,11 @@ typedef struct {
  * (b = 0 lets the library's tuner choose from the request sizes): one tile
  * arena for all matrices and one merged schedule -- generation,
  * factorisation, solve, refinement and log-likelihood of every request --
- * captured as a single CUDA graph.  Pointers in `reqs` are borrowed and
- * must stay valid for the plan's lifetime.  Synchronous. */
+ * captured as a single CUDA graph.  Panel solves follow mp_tmat_create's
+ * default (integer-digit tensor-core products for tiles stored in FP32 or
+ * below), so each request's result is bit-identical to its evaluation
+ * alone.  Pointers in `reqs` are borrowed and must stay valid for the
+ * plan's lifetime.  Synchronous. */
 mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
                           void* stream, mp_batch** out);
 void mp_batch_destroy(mp_batch* batch);

@@ -1580,6 +1580,7 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
   B->P.ctx = ctx;
   B->P.b = b;
   B->P.stream = (cudaStream_t)stream;
+  B->P.ozaki = true;     // panel tiles stored in FP32 or below: digit products, as mp_tmat's default
   B->count = count;
   B->reqs.assign(reqs, reqs + count);
   Plan& P = B->P;

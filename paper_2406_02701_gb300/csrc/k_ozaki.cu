@@ -37,6 +37,7 @@ namespace mp {
 namespace {
 
 constexpr int OZ_BN = 64;                  // output columns per CTA
+constexpr int OZ_S_MAX_ORDER = 8;          // digits per operand (the kernels' S)
 constexpr uint32_t OZ_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -224,6 +225,14 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(Arena A, const ItemOzW* _
 }
 
 constexpr int OZ_ACH = 128 * 128;          // A digit chunk: 128 rows x 128 bytes
+
+// Order in which a K chunk's A digits are consumed: digit p pairs with the
+// S - p digits of W, so large and small amounts of MMA work alternate
+// (0, S-1, 1, S-2, ...) and the ring never waits on several short chunks in
+// a row.  Digit 0 comes first: it opens every level's accumulator.
+__device__ __forceinline__ int oz_digit_order(int pi) {
+  return (pi & 1) ? OZ_S_MAX_ORDER - 1 - (pi >> 1) : (pi >> 1);
+}
 constexpr int OZ_BCH = OZ_BN * 128;        // W digit chunk: 64 rows x 128 bytes
 constexpr int OZ_ASTG = 4;                 // A ring slots
 constexpr int OZ_BSTG = 2;                 // W ring slots (S chunks each)
@@ -233,6 +242,7 @@ __global__ void __launch_bounds__(128, 1)
     k_oz_gemm(Arena A, const ItemOz* __restrict__ items, const __grid_constant__ CUtensorMap mapA,
               const __grid_constant__ CUtensorMap mapB) {
   static_assert(S * OZ_BN <= 512, "levels exceed tensor memory");
+  static_assert(S == OZ_S_MAX_ORDER, "digit order table is for S digits");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* bring = smem;                                   // OZ_BSTG x S x OZ_BCH
@@ -284,8 +294,9 @@ __global__ void __launch_bounds__(128, 1)
         tma2d(bring + (sb * S + q) * OZ_BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
       ++nb;
 #pragma unroll 1
-      for (int p = 0; p < S; ++p) {
-        const int i = kt * S + p, sa = i % OZ_ASTG;
+      for (int pi = 0; pi < S; ++pi) {
+        const int p = oz_digit_order(pi);
+        const int i = kt * S + pi, sa = i % OZ_ASTG;
         if (i >= OZ_ASTG && !(ok = mb_wait(&aempty[sa], ((i / OZ_ASTG) - 1) & 1, A.err))) break;
         mb_expect(&afull[sa], OZ_ACH);
         tma2d(aring + sa * OZ_ACH, &mapA, kt * 64, aidx[p] * b + m0, &afull[sa]);
@@ -306,8 +317,9 @@ __global__ void __launch_bounds__(128, 1)
       if (!(ok = mb_wait(&bfull[sb], (kt / OZ_BSTG) & 1, A.err))) break;
       const uint32_t b0 = su32(bring + sb * S * OZ_BCH);
 #pragma unroll 1
-      for (int p = 0; p < S; ++p) {
-        const int i = kt * S + p, sa = i % OZ_ASTG;
+      for (int pi = 0; pi < S; ++pi) {
+        const int p = oz_digit_order(pi);
+        const int i = kt * S + pi, sa = i % OZ_ASTG;
         if (!(ok = mb_wait(&afull[sa], (i / OZ_ASTG) & 1, A.err))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = su32(aring + sa * OZ_ACH);

@@ -157,8 +157,8 @@ def test_batch_512_requests(ctx):
     bad = [k for k in range(len(specs)) if st[k] != 0]
     for k in [0, 7, 100, 333, 511] + bad[:2]:
         s = specs[k]
-        # the batch plan solves panels by FP64 substitution: same path, same bits
-        T = mpchol.TiledMatrix(ctx, s["n"], b, s["map"], ozaki=False)
+        # the batch plan takes the library's default panel solve: same path, same bits
+        T = mpchol.TiledMatrix(ctx, s["n"], b, s["map"])
         T.generate(s["locs"], s["sigma2"], s["range"], s["nu"], s["nugget"])
         info, _ = T.chol()
         one, _, _ = T.loglik(s["zt"])

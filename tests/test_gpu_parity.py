@@ -408,7 +408,7 @@ def test_batch_equals_single_evaluations(ctx):
         dl = torch.from_numpy(locs).to(DEV)
         zt = torch.from_numpy(np.ascontiguousarray(z.T)).to(DEV)
         reqs.append(dict(n=n, map=pmap, locs=dl, zt=zt, sigma2=1.0, range=a, nu=nu, nugget=1e-2))
-        s = _run(ctx, n, b, pmap, locs, z, nu, a, 1.0, 1e-2)
+        s = _run(ctx, n, b, pmap, locs, z, nu, a, 1.0, 1e-2, ozaki=True)   # the batch's panel solve
         singles.append(s)
         S = OM.covariance(locs, nu, a, 1.0, 1e-2)
         try:
