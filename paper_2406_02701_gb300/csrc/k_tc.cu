@@ -6,13 +6,14 @@
 //   FP32         kind::tf32    three products of hi/lo splits,
 //                              A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
 //                              where hi = A rounded to TF32 and lo = A - hi
-// One CTA computes a 128 x 128 sub-tile of the target with the full
-// contraction K = b.  Warp 0 (one lane) streams 128-byte-wide K slices of
-// the operand tiles into shared memory with TMA (128-byte swizzle, one
-// tensor map per format pool; no multicast), warp 1 (one lane) issues the
-// MMAs into a 128-column FP32 accumulator in tensor memory, and all four
-// warps read the accumulator back (each its 32 lanes) and apply the update
-// to the target tile in global memory:
+A work unit is a 128 x 128 sub-tile of a target with the full contraction
+// K = b; one persistent CTA per SM runs units back to back.  Warp 0 (one
+// lane) streams 128-byte-wide K slices of the operand tiles into shared
+// memory with TMA (128-byte swizzle, one tensor map per format pool; no
+// multicast), warp 1 (one lane) issues the MMAs into one of two 128-column
+// FP32 accumulators in tensor memory, and warps 2-5 read the other one back
+// (each its lane quarter) and apply the update to the target tile in global
+// memory:
 //   FP64 target (SYRK into the diagonal)  C -= acc            (float64)
 //   FP32 target                           C = C - acc         (one FP32 sub,
 //                                         correctly rounded)
@@ -20,9 +21,11 @@
 //   E4M3 target                           FP32 scratch + amax (rounded by
 //                                         k_fp8_round with the new scale)
 // Every mbarrier wait is bounded: when it runs out the CTA records the
-// failure in the arena's error word, lets the MMAs it issued complete, frees
-// its tensor memory and returns.
+// failure in the arena's error word, lets the copies and MMAs it issued
+// complete, frees its tensor memory and returns.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "mp_device.cuh"
 
@@ -150,43 +153,47 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // KIND: 0 BF16, 1 FP16, 2 E4M3, 3 FP32 as three TF32 products.
+// Persistent variant: one CTA per SM walks the work units (target tile,
+// 128 x 128 sub-block; the sub-blocks of one target next to each other) in
+// a fixed round-robin order.  Warp 0 streams K slices through a STAGES-deep
+// ring that runs on across units, warp 1 issues the MMAs into one of two
+// 128-column tensor-memory accumulators, and warps 2-5 drain the other one
+// (each its lane quarter) and update the target, so a unit's epilogue
+// overlaps the next unit's MMAs.  Barriers: full/empty per ring slot,
+// accf (accumulator complete) and acce (accumulator read back, 4 arrivals)
+// per accumulator.  Every wait is bounded (on expiry: error word, then the
+// roles stop; issued MMAs are waited for before tensor memory is freed).
 template <int KIND, int STAGES>
-__global__ void __launch_bounds__(128, 1)
-    k_update_tc(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap,
-                int sub_fast) {
+__global__ void __launch_bounds__(192, 1)
+    k_update_tc_p(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap,
+                  int count) {
   extern __shared__ uint8_t smem_raw[];
-  constexpr int NA = KIND == 3 ? 2 : 1;              // operand slices per side
+  constexpr int NA = KIND == 3 ? 2 : 1;
   constexpr int STAGE_BYTES = 2 * NA * TC_BUF;
-  constexpr int KCH = KIND == 2 ? 128 : KIND == 3 ? 32 : 64;   // elements per slice
+  constexpr int KCH = KIND == 2 ? 128 : KIND == 3 ? 32 : 64;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  float* stage_c = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);     // 4 x [32][33]
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage_c + 4 * 32 * 33);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
-
-  // grid (sub-block, target) when the targets fit in grid.y: the sub-blocks
-  // of one target, which share operand strips, run next to each other
-  const bool sub_major = sub_fast != 0;
-  const ItemTC it = items[sub_major ? blockIdx.y : blockIdx.x];
-  const int b = A.b, nsub = b / TC_BM;
-  const int sb = sub_major ? blockIdx.x : blockIdx.y;
-  const int rb = sb / nsub, cb = sb % nsub;
-  if (it.syrk && cb > rb) return;                  // strictly above the diagonal
+  uint64_t* accf = empty + STAGES;        // [2]
+  uint64_t* acce = accf + 2;              // [2]
+  uint64_t* fin = acce + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  const int b = A.b, nsub = b / TC_BM, nsub2 = nsub * nsub;
+  const int KT = b / KCH;
+  const int units = count * nsub2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(accf, 1);
+    for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+    for (int q = 0; q < 2; ++q) { mbar_init(&accf[q], 1); mbar_init(&acce[q], 4); }
+    mbar_init(fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tslot)),
-                 "r"(TC_BN)
+                 "r"(2 * TC_BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -194,158 +201,188 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int KT = b / KCH;
-
-  if (warp == 0 && lane == 0) {
-    // producer: TMA of the K slices
-    const int ya0 = A.tiles[it.a].idx * b + rb * TC_BM;
-    const int yb0 = A.tiles[it.b].idx * b + cb * TC_BN;
-    const int ya1 = NA == 2 ? A.tiles[it.a2].idx * b + rb * TC_BM : 0;
-    const int yb1 = NA == 2 ? A.tiles[it.b2].idx * b + cb * TC_BN : 0;
-    int issued = 0;
-    bool ok = true;
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % STAGES;
-      if (kt >= STAGES && !(ok = mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1, A.err))) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(st, &tmap, kt * KCH, ya0, &full[s]);
-      if (NA == 2) tma_load_2d(st + TC_BUF, &tmap, kt * KCH, ya1, &full[s]);
-      tma_load_2d(st + NA * TC_BUF, &tmap, kt * KCH, yb0, &full[s]);
-      if (NA == 2) tma_load_2d(st + (NA + 1) * TC_BUF, &tmap, kt * KCH, yb1, &full[s]);
-      ++issued;
-    }
-    if (!ok) {
-      // let the copies already in flight land before the CTA's memory goes away
-      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-        mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1, nullptr);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    for (int kt = 0; kt < KT; ++kt) {
-      const int s = kt % STAGES;
-      if (!mbar_wait(&full[s], (kt / STAGES) & 1, A.err)) break;
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t a1 = a0 + TC_BUF;
-      const uint32_t b0 = a0 + NA * TC_BUF;
-      const uint32_t b1 = b0 + TC_BUF;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {                 // 32 bytes of K per MMA
-        const uint32_t off = kk * 32;
-        const uint32_t acc = (kt | kk) != 0;
-        mma<KIND>(tmem, smem_desc(a0 + off), smem_desc(b0 + off), acc);
-        if (KIND == 3) {
-          mma<KIND>(tmem, smem_desc(a0 + off), smem_desc(b1 + off), 1);
-          mma<KIND>(tmem, smem_desc(a1 + off), smem_desc(b0 + off), 1);
+  // unit u -> (item, rb, cb); SYRK units strictly above the diagonal are skipped
+  auto unit = [&](int u, ItemTC& it, int& rb, int& cb) {
+    it = items[u / nsub2];
+    const int sb = u % nsub2;
+    rb = sb / nsub;
+    cb = sb % nsub;
+    return !(it.syrk && cb > rb);
+  };
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        ItemTC it;
+        int rb, cb;
+        if (!unit(u, it, rb, cb)) continue;
+        const int ya0 = A.tiles[it.a].idx * b + rb * TC_BM;
+        const int yb0 = A.tiles[it.b].idx * b + cb * TC_BN;
+        const int ya1 = NA == 2 ? A.tiles[it.a2].idx * b + rb * TC_BM : 0;
+        const int yb1 = NA == 2 ? A.tiles[it.b2].idx * b + cb * TC_BN : 0;
+        for (int kt = 0; kt < KT; ++kt, ++g) {
+          const int q = g % STAGES;
+          if (g >= STAGES && !(ok = mbar_wait(&empty[q], ((g / STAGES) - 1) & 1, A.err))) break;
+          uint8_t* st = smem + q * STAGE_BYTES;
+          mbar_expect_tx(&full[q], STAGE_BYTES);
+          tma_load_2d(st, &tmap, kt * KCH, ya0, &full[q]);
+          if (NA == 2) tma_load_2d(st + TC_BUF, &tmap, kt * KCH, ya1, &full[q]);
+          tma_load_2d(st + NA * TC_BUF, &tmap, kt * KCH, yb0, &full[q]);
+          if (NA == 2) tma_load_2d(st + (NA + 1) * TC_BUF, &tmap, kt * KCH, yb1, &full[q]);
         }
       }
-      mma_commit(&empty[s]);                           // frees the stage when done
+      if (!ok)   // let the copies in flight land before the CTA's memory goes away
+        for (int h = (g > STAGES ? g - STAGES : 0); h < g; ++h)
+          mbar_wait(&full[h % STAGES], (h / STAGES) & 1, nullptr);
     }
-    mma_commit(accf);                                  // all issued MMAs complete
-  }
-  __syncwarp();
-
-  // epilogue: every warp reads its 32 accumulator lanes
-  const bool have = mbar_wait(accf, 0, A.err);
-  tc_fence_after();
-  const TileRef rc = A.tiles[it.c];
-  char* pc = tile_bytes(A, it.c);
-  const float sab = (float)(A.scale[it.a] * A.scale[it.b]);
-  const double sc = A.scale[it.c];
-  // each warp stages a 32 x 32 chunk of its rows through shared memory (the
-  // pipeline buffers are free once every MMA has completed) and updates the
-  // target row by row, lanes over columns: coalesced reads and writes
-  float (*S)[33] = reinterpret_cast<float (*)[33]>(smem + warp * 32 * 33 * sizeof(float));
-  float mx = 0.f;
-#pragma unroll 1
-  for (int ch = 0; ch < TC_BN / 32; ++ch) {
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + ch * 32, v);
-    if (!have) continue;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int g = 0, t = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        ItemTC it;
+        int rb, cb;
+        if (!unit(u, it, rb, cb)) continue;
+        const int buf = t & 1;
+        if (t >= 2 && !(ok = mbar_wait(&acce[buf], ((t / 2) - 1) & 1, A.err))) break;
+        tc_fence_after();
+        const uint32_t acc_t = tmem + (uint32_t)(buf * TC_BN);
+        for (int kt = 0; kt < KT; ++kt, ++g) {
+          const int q = g % STAGES;
+          if (!(ok = mbar_wait(&full[q], (g / STAGES) & 1, A.err))) break;
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + q * STAGE_BYTES);
+          const uint32_t a1 = a0 + TC_BUF;
+          const uint32_t b0 = a0 + NA * TC_BUF;
+          const uint32_t b1 = b0 + TC_BUF;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) S[lane][j] = v[j] * sab;
-    __syncwarp();
-    const int col = cb * TC_BN + ch * 32 + lane;
-    const int row0 = rb * TC_BM + warp * 32;
-    // rows of this chunk strictly above the diagonal of a SYRK target: none
-    // when the chunk starts at or left of the row
-    const int rlo = it.syrk ? max(0, cb * TC_BN + ch * 32 - row0) : 0;
-    const int64_t o0 = (int64_t)row0 * b + col;
-    // all 32 loads are issued before the arithmetic (one memory round trip)
-    if (rc.dt == F32) {
-      float* c = reinterpret_cast<float*>(pc) + o0;
-      float cur[32];
-#pragma unroll
-      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.f;
-#pragma unroll
-      for (int rr = 0; rr < 32; ++rr)    // one correctly rounded FP32 subtraction
-        if (rr >= rlo) c[(int64_t)rr * b] = __fsub_rn(cur[rr], S[rr][lane]);
-    } else if (rc.dt == F64) {
-      double* c = reinterpret_cast<double*>(pc) + o0;
-      double cur[32];
-#pragma unroll
-      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.0;
-#pragma unroll
-      for (int rr = 0; rr < 32; ++rr)
-        if (rr >= rlo) c[(int64_t)rr * b] = cur[rr] - (double)S[rr][lane];
-    } else {
-      float cur[32];
-#pragma unroll
-      for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? load_f32(pc, rc.dt, o0 + (int64_t)rr * b) : 0.f;
-      if (rc.dt == E4M3) {
-        const float fs = (float)sc;
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr)
-          if (rr >= rlo) {
-            const float w = cur[rr] * fs - S[rr][lane];
-            it.v[o0 + (int64_t)rr * b] = w;
-            mx = fmaxf(mx, fabsf(w));
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint32_t acc = (kt | kk) != 0;
+            mma<KIND>(acc_t, smem_desc(a0 + off), smem_desc(b0 + off), acc);
+            if (KIND == 3) {
+              mma<KIND>(acc_t, smem_desc(a0 + off), smem_desc(b1 + off), 1);
+              mma<KIND>(acc_t, smem_desc(a1 + off), smem_desc(b0 + off), 1);
+            }
           }
-      } else {
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr)
-          if (rr >= rlo) store_round_f32(pc, rc.dt, o0 + (int64_t)rr * b, cur[rr] - S[rr][lane]);
+          mma_commit(&empty[q]);
+        }
+        if (!ok) break;
+        mma_commit(&accf[buf]);
+        ++t;
       }
+      // every MMA issued has completed before tensor memory is freed
+      mma_commit(fin);
+      mbar_wait(fin, 0, A.err);
     }
-    __syncwarp();
-  }
-  if (rc.dt == E4M3) {
-    __shared__ float red[4];
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < 4; ++w) mx = fmaxf(mx, red[w]);
-      atomic_max_pos(&A.amax[it.vslot], (double)mx);
+  } else {
+    // epilogue warps 2-5: lane quarter qr = warp % 4 of the accumulator
+    const int qr = warp & 3;
+    float (*S)[33] = reinterpret_cast<float (*)[33]>(stage_c + (warp - 2) * 32 * 33);
+    int t = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      ItemTC it;
+      int rb, cb;
+      if (!unit(u, it, rb, cb)) continue;
+      const int buf = t & 1;
+      if (!mbar_wait(&accf[buf], (t / 2) & 1, A.err)) break;
+      tc_fence_after();
+      const TileRef rc = A.tiles[it.c];
+      char* pc = tile_bytes(A, it.c);
+      const float sab = (float)(A.scale[it.a] * A.scale[it.b]);
+      const double sc = A.scale[it.c];
+      float mx = 0.f;
+#pragma unroll 1
+      for (int ch = 0; ch < TC_BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(buf * TC_BN + ch * 32), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) S[lane][j] = v[j] * sab;
+        __syncwarp();
+        const int col = cb * TC_BN + ch * 32 + lane;
+        const int row0 = rb * TC_BM + qr * 32;
+        const int rlo = it.syrk ? max(0, cb * TC_BN + ch * 32 - row0) : 0;
+        const int64_t o0 = (int64_t)row0 * b + col;
+        if (rc.dt == F32) {
+          float* c = reinterpret_cast<float*>(pc) + o0;
+          float cur[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.f;
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr)    // one correctly rounded FP32 subtraction
+            if (rr >= rlo) c[(int64_t)rr * b] = __fsub_rn(cur[rr], S[rr][lane]);
+        } else if (rc.dt == F64) {
+          double* c = reinterpret_cast<double*>(pc) + o0;
+          double cur[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? c[(int64_t)rr * b] : 0.0;
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr)
+            if (rr >= rlo) c[(int64_t)rr * b] = cur[rr] - (double)S[rr][lane];
+        } else {
+          float cur[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) cur[rr] = rr >= rlo ? load_f32(pc, rc.dt, o0 + (int64_t)rr * b) : 0.f;
+          if (rc.dt == E4M3) {
+            const float fs = (float)sc;
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+              if (rr >= rlo) {
+                const float w = cur[rr] * fs - S[rr][lane];
+                it.v[o0 + (int64_t)rr * b] = w;
+                mx = fmaxf(mx, fabsf(w));
+              }
+          } else {
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+              if (rr >= rlo) store_round_f32(pc, rc.dt, o0 + (int64_t)rr * b, cur[rr] - S[rr][lane]);
+          }
+        }
+        __syncwarp();
+      }
+      // this warp's quarter of the accumulator is read: hand it back
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[buf])) : "memory");
+      ++t;
+      if (rc.dt == E4M3) {
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomic_max_pos(&A.amax[it.vslot], (double)mx);
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN)
                  : "memory");
   }
 }
 
 template <int KIND, int STAGES>
-constexpr size_t tc_smem() {
-  return (size_t)STAGES * 2 * (KIND == 3 ? 2 : 1) * TC_BUF + 8 * (2 * STAGES + 1) + 16 + 1024;
+constexpr size_t tc_smem_p() {
+  return (size_t)STAGES * 2 * (KIND == 3 ? 2 : 1) * TC_BUF + 4 * 32 * 33 * sizeof(float) +
+         8 * (2 * STAGES + 5) + 16 + 1024;
 }
 
 template <int KIND, int STAGES>
 void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap& map,
                cudaStream_t s) {
-  static bool attr = false;
-  constexpr size_t smem = tc_smem<KIND, STAGES>();
-  if (!attr) {
-    cudaFuncSetAttribute(k_update_tc<KIND, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  static int sms = 0;
+  constexpr size_t smem = tc_smem_p<KIND, STAGES>();
+  if (!sms) {
+    cudaFuncSetAttribute(k_update_tc_p<KIND, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const int nsub = A.b / TC_BM;
-  if (count <= 65535) k_update_tc<KIND, STAGES><<<dim3(nsub * nsub, count), 128, smem, s>>>(A, items, map, 1);
-  else k_update_tc<KIND, STAGES><<<dim3(count, nsub * nsub), 128, smem, s>>>(A, items, map, 0);
+  const int64_t units = (int64_t)count * nsub * nsub;
+  const int grid = (int)std::min<int64_t>(units, sms);
+  k_update_tc_p<KIND, STAGES><<<grid, 192, smem, s>>>(A, items, map, count);
 }
 
 }  // namespace
