@@ -6,7 +6,7 @@
 //   FP32         kind::tf32    three products of hi/lo splits,
 //                              A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
 //                              where hi = A rounded to TF32 and lo = A - hi
-A work unit is a 128 x 128 sub-tile of a target with the full contraction
+// A work unit is a 128 x 128 sub-tile of a target with the full contraction
 // K = b; one persistent CTA per SM runs units back to back.  Warp 0 (one
 // lane) streams 128-byte-wide K slices of the operand tiles into shared
 // memory with TMA (128-byte swizzle, one tensor map per format pool; no
