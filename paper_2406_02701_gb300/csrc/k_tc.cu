@@ -163,8 +163,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // accf (accumulator complete) and acce (accumulator read back, 4 arrivals)
 // per accumulator.  Every wait is bounded (on expiry: error word, then the
 // roles stop; issued MMAs are waited for before tensor memory is freed).
-template <int KIND, int STAGES>
-__global__ void __launch_bounds__(192, 1)
+template <int KIND, int STAGES, int MINB>
+__global__ void __launch_bounds__(192, MINB)
     k_update_tc_p(Arena A, const ItemTC* __restrict__ items, const __grid_constant__ CUtensorMap tmap,
                   int count) {
   extern __shared__ uint8_t smem_raw[];
@@ -367,13 +367,16 @@ constexpr size_t tc_smem_p() {
          8 * (2 * STAGES + 5) + 16 + 1024;
 }
 
-template <int KIND, int STAGES>
+// FP32 kind: three MMAs per K step keep the tensor cores busy, one CTA per
+// SM with a 3-slot ring; 16- and 8-bit kinds are epilogue-bound, two CTAs
+// per SM with a 2-slot ring each.
+template <int KIND, int STAGES, int MINB>
 void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap& map,
                cudaStream_t s) {
   static int sms = 0;
   constexpr size_t smem = tc_smem_p<KIND, STAGES>();
   if (!sms) {
-    cudaFuncSetAttribute(k_update_tc_p<KIND, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_update_tc_p<KIND, STAGES, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int dev = 0;
     cudaGetDevice(&dev);
@@ -381,8 +384,8 @@ void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap
   }
   const int nsub = A.b / TC_BM;
   const int64_t units = (int64_t)count * nsub * nsub;
-  const int grid = (int)std::min<int64_t>(units, sms);
-  k_update_tc_p<KIND, STAGES><<<grid, 192, smem, s>>>(A, items, map, count);
+  const int grid = (int)std::min<int64_t>(units, (int64_t)MINB * sms);
+  k_update_tc_p<KIND, STAGES, MINB><<<grid, 192, smem, s>>>(A, items, map, count);
 }
 
 }  // namespace
@@ -393,10 +396,10 @@ void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
                       const CUtensorMap& map, cudaStream_t s) {
   if (count <= 0) return;
   switch (kind) {
-    case BF16: launch_tc<0, 3>(A, items, count, map, s); break;
-    case F16: launch_tc<1, 3>(A, items, count, map, s); break;
-    case E4M3: launch_tc<2, 3>(A, items, count, map, s); break;
-    default: launch_tc<3, 3>(A, items, count, map, s); break;
+    case BF16: launch_tc<0, 2, 2>(A, items, count, map, s); break;
+    case F16: launch_tc<1, 2, 2>(A, items, count, map, s); break;
+    case E4M3: launch_tc<2, 2, 2>(A, items, count, map, s); break;
+    default: launch_tc<3, 3, 1>(A, items, count, map, s); break;
   }
 }
 
