@@ -106,7 +106,7 @@ struct MatDesc {
   std::vector<int32_t> linv_hi, linv_lo;    // nt each: its FP32 hi/lo parts (-1: all-FP64 matrix)
   bool mixed = false;                       // some tile stored below FP64
   int32_t ldoff = 0;
-  double* dinv = nullptr;                   // nt * (b/32) blocks of 32x32
+  double* dinv = nullptr;                   // nt * (b/dag_nb) blocks of dag_nb x dag_nb
 };
 
 struct Plan {
@@ -122,7 +122,8 @@ struct Plan {
   // arena
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
-  int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix (b/32)^2 counters
+  int dag_nb = 32;                 // block of the diagonal-tile task graph (16 or 32)
+  int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
   std::vector<int64_t> ltab_off;
   int* d_scnt = nullptr;           // solve task graph: ticket, then per matrix nt (b/32 + 1) counters
@@ -358,7 +359,7 @@ mp_status add_matrix(Plan& P, int64_t n, const uint8_t* map) {
 // and panel amax slots alternate between two sets by step parity, so the
 // chain of step k+1 never touches what the bulk of step k reads.
 void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
-  const int b = P.b, nbb = b / 32;
+  const int b = P.b, nbb = b / P.dag_nb;
   int maxnt = 0;
   for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
   int64_t max_v = 0;
@@ -396,7 +397,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         it.mat = m;
         it.ldslot = M.ldoff + s * nbb;
         it.row0 = (int64_t)s * b;
-        it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+        it.dinv = M.dinv + (int64_t)s * nbb * P.dag_nb * P.dag_nb;
         it.w = (double*)(P.pool[F64] + (size_t)P.h_tiles[M.linv[s]].idx * b * b * 8);
         if (M.mixed) {
           it.whi = (float*)(P.pool[F32] + (size_t)P.h_tiles[M.linv_hi[s]].idx * b * b * 4);
@@ -448,7 +449,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
       it.diag = M.tile[s * nt + s];
       it.mat = m;
       it.amax = (int)(P.amax_panel0 + q);
-      it.dinv = M.dinv + (int64_t)s * nbb * 1024;
+      it.w = (const double*)(P.pool[F64] + (size_t)P.h_tiles[M.linv[s]].idx * b * b * 8);
       it.x = P.d_panel + q * (int64_t)b * b;
       panel.push_back(it);
       ItemRound r{};
@@ -729,7 +730,12 @@ mp_status make_tensor_maps(Plan& P) {
 
 // Allocates the arena and scratch of a plan whose matrices were added.
 mp_status finish_plan(Plan& P) {
-  const int b = P.b, nbb = b / 32;
+  // the block of the diagonal tile's task graph depends on b alone (a batch
+  // and a single matrix of the same b factor bit-identically): 16-blocks
+  // shorten the critical chain; at b = 1024 they make 91k tasks per tile and
+  // at b <= 256 the chain is short anyway, so those keep 32-blocks
+  P.dag_nb = (P.b >= 384 && P.b <= 768) ? 16 : 32;
+  const int b = P.b, nbb = b / 32, ndb = b / P.dag_nb;
   {
     int64_t panel_slots = 0, v_slots = 0;
     count_scratch(P, &panel_slots, &v_slots);
@@ -795,16 +801,16 @@ mp_status finish_plan(Plan& P) {
   for (auto& M : P.mats) {
     M.ldoff = ldo;
     ldoff.push_back(ldo);
-    ldcnt.push_back(M.nt * nbb);
-    ldo += M.nt * nbb;
-    ninv += (int64_t)M.nt * nbb;
+    ldcnt.push_back(M.nt * ndb);
+    ldo += M.nt * ndb;
+    ninv += (int64_t)M.nt * ndb;
   }
-  if (mp_status st = P.alloc(&p, sizeof(double) * 1024 * ninv)) return st;
+  if (mp_status st = P.alloc(&p, sizeof(double) * P.dag_nb * P.dag_nb * ninv)) return st;
   P.d_dinv_all = (double*)p;
   int64_t io = 0;
   for (auto& M : P.mats) {
-    M.dinv = P.d_dinv_all + io * 1024;
-    io += (int64_t)M.nt * nbb;
+    M.dinv = P.d_dinv_all + io * P.dag_nb * P.dag_nb;
+    io += (int64_t)M.nt * ndb;
   }
   const int nm = (int)P.mats.size();
   if (mp_status st = P.alloc(&p, sizeof(double) * std::max(ldo, 1))) return st;
@@ -819,7 +825,7 @@ mp_status finish_plan(Plan& P) {
   P.d_logdet = (double*)p;
   if (mp_status st = P.alloc(&p, sizeof(int))) return st;
   P.d_err = (int*)p;
-  P.dag_bytes = sizeof(int) * (32 + (size_t)nm * 2 * nbb * nbb);
+  P.dag_bytes = sizeof(int) * (32 + (size_t)nm * 2 * ndb * ndb);
   if (mp_status st = P.alloc(&p, P.dag_bytes)) return st;
   P.d_dag = (int*)p;
   {
@@ -903,7 +909,7 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
     case OP_POTRF_DAG:
       cudaMemsetAsync(P.d_dag, 0, P.dag_bytes, s);
       launch_potrf_dag(A, P.item<ItemPotrf>(L.off), L.count, P.item<DagTask>(P.dag_tasks_off),
-                       P.dag_ntasks, P.d_dag, P.d_ldparts, P.d_info, s);
+                       P.dag_ntasks, P.d_dag, P.d_ldparts, P.d_info, P.dag_nb, s);
       break;
     case OP_PANEL:
       // the bulk panel leaves SMs free for the chain running beside it

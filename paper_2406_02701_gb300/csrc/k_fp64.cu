@@ -3,7 +3,7 @@
 // tile by tile, as in the tiled extension of Sec. 7).
 //
 // The FP64 diagonal tile (b x b, b a multiple of 64) is factored by a
-// blocked right-looking Cholesky over 32 x 32 blocks, run as a task graph
+// blocked right-looking Cholesky over 16 x 16 or 32 x 32 blocks, run as a task graph
 // by one persistent launch (k_potrf_dag): per block column k, one CTA
 // factors block (k, k) in shared memory (adding 2 sum log L_tt to the
 // log-determinant partials, flagging the first pivot that is not > 0, and
@@ -12,7 +12,10 @@
 // task starting as soon as its input blocks are final.
 // The panel solve X = A_ik L_kk^{-T} keeps 16 rows of the panel tile in
 // shared memory in float64 and sweeps L_kk's 32-column blocks left to right:
-// acc = A[:, c] - X[:, <c] L[c, <c]^T, then X[:, c] = acc Dinv_c^T.  The
+// acc = A[:, c] - X[:, <c] L[c, <c]^T, then X[:, c] = acc Dinv_c^T, with
+// Dinv_c^T read from the diagonal 32-block of W = L_kk^{-T} (the diagonal
+// blocks of a triangular matrix's inverse are the inverses of its diagonal
+// blocks).  The
 // float64 result goes to a scratch slot; `panel_round` then rounds it once
 // into the tile's format (E4M3: scale from the tile's amax) and into the
 // tile's shadow copy, the operand form that lower-precision updates read.
@@ -28,7 +31,16 @@ namespace mp {
 
 namespace {
 
-constexpr int NB = 32;   // inner block of the diagonal tile
+constexpr int NB = 32;   // column block of the panel solve's sweep
+
+// The task graph is instantiated for blocks DB = 16 and 32.  A block
+// product runs on 256 threads, DJ outputs each, DTX threads along a row.
+template <int DB>
+struct DagShape {
+  static_assert(DB == 16 || DB == 32, "task-graph block must be 16 or 32");
+  static constexpr int DJ = DB * DB / 256;
+  static constexpr int DTX = DB / DJ;
+};
 
 // Block (k, k) in S: Cholesky factor in place (lower part) and the block's
 // inverse Y = L^{-1} in R, in one right-looking sweep run as a two-stage
@@ -39,31 +51,32 @@ constexpr int NB = 32;   // inner block of the diagonal tile
 // the inverse: Y[c-1, .] = R[c-1, .] / L_{c-1,c-1}, then
 // R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Writes L and the
 // inverse to global memory; info gets the first pivot that is not > 0.
-__device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk, int b,
+template <int DB>
+__device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk, int b,
                            double* dinv, long long* info, long long row0, const uint16_t* tri) {
   const int tid = threadIdx.x, lane = tid & 31;
   constexpr int NO = 224;                        // threads of warps 1-7
-  __shared__ double rps[NB];                     // 1 / L_cc
-  for (int e = tid; e < NB * NB; e += blockDim.x) R[e / NB][e % NB] = (e / NB == e % NB) ? 1.0 : 0.0;
+  __shared__ double rps[DB];                     // 1 / L_cc
+  for (int e = tid; e < DB * DB; e += blockDim.x) R[e / DB][e % DB] = (e / DB == e % DB) ? 1.0 : 0.0;
   if (tid < 32) {
     const double d = S[0][0];
     if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + 1);
     const double rp = rsqrt(d);
     if (lane == 0) { S[0][0] = d * rp; rps[0] = rp; }
-    else S[lane][0] *= rp;
+    else if (lane < DB) S[lane][0] *= rp;
   }
-  for (int c = 0; c < NB; ++c) {
+  for (int c = 0; c < DB; ++c) {
     __syncthreads();
     if (tid < 32) {
-      if (c + 1 < NB) {
+      if (c + 1 < DB) {
         const int n = c + 1;
         double v = 0.0;
-        if (lane >= n) v = S[lane][n] - S[lane][c] * S[n][c];
+        if (lane >= n && lane < DB) v = S[lane][n] - S[lane][c] * S[n][c];
         const double d = __shfl_sync(0xffffffffu, v, n);
         if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + n + 1);
         const double rp = rsqrt(d);
         if (lane == n) S[n][n] = d * rp;           // sqrt(d) = d / sqrt(d)
-        else if (lane > n) S[lane][n] = v * rp;
+        else if (lane > n && lane < DB) S[lane][n] = v * rp;
         if (lane == 0) rps[n] = rp;
       }
     } else {
@@ -73,17 +86,18 @@ __device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk,
       // compact enumeration (the FP64 pipe charges a warp instruction in
       // full however many lanes it masks): trailing rows c+2.. on columns
       // c+2..r through the triangle table, then inverse rows c.. on columns < c
-      const int m = NB - 2 - c;
+      const int m = DB - 2 - c;
       const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
-      const int total = ntri + (c >= 1 ? (NB - c) * c : 0);
+      const int total = ntri + (c >= 1 ? (DB - c) * c : 0);
       const float rc = c >= 1 ? 1.f / (float)c : 0.f;
-      // at most three elements per thread (total <= 3 * 224); the updates of
+      // at most UPT elements per thread (total <= UPT * 224); the updates of
       // one column touch distinct entries and read only columns c, c - 1 and
       // row c - 1 of R, so all operands are loaded before any store
-      double* dst[3];
-      double x0[3], x1[3], x2[3];
+      constexpr int UPT = DB == 32 ? 3 : 1;
+      double* dst[UPT];
+      double x0[UPT], x1[UPT], x2[UPT];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
+      for (int u = 0; u < UPT; ++u) {
         const int e = t + u * NO;
         dst[u] = nullptr;
         if (e < ntri) {
@@ -103,52 +117,55 @@ __device__ void dag_factor(double (*S)[NB + 1], double (*R)[NB + 1], double* Tk,
         if (dst[u]) x0[u] = *dst[u];
       }
 #pragma unroll
-      for (int u = 0; u < 3; ++u)
+      for (int u = 0; u < UPT; ++u)
         if (dst[u]) *dst[u] = x0[u] - x1[u] * x2[u];
     }
   }
   __syncthreads();
-  if (tid < NB) R[NB - 1][tid] *= rps[NB - 1];
+  if (tid < DB) R[DB - 1][tid] *= rps[DB - 1];
   __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
+  for (int e = tid; e < DB * DB; e += blockDim.x) {
+    const int r = e / DB, c = e % DB;
     if (c <= r) Tk[(int64_t)r * b + c] = S[r][c];
     dinv[e] = R[r][c];
   }
 }
 
-// 2 sum log L_tt of the block in S: one log per lane of warp 0, fixed-order
-// butterfly sum.
-__device__ void dag_logdet(double (*S)[NB + 1], double* ldpart) {
+// 2 sum log L_tt of the block in S: one log per lane of warp 0 (lanes past
+// the block add zero), fixed-order butterfly sum.
+template <int DB>
+__device__ void dag_logdet(double (*S)[DB + 1], double* ldpart) {
   if (threadIdx.x < 32) {
-    double lg = log(S[threadIdx.x][threadIdx.x]);
+    double lg = threadIdx.x < DB ? log(S[threadIdx.x][threadIdx.x]) : 0.0;
     for (int o = 16; o > 0; o >>= 1) lg += __shfl_xor_sync(0xffffffffu, lg, o);
     if (threadIdx.x == 0) *ldpart = 2.0 * lg;
   }
 }
 
-// X = A Dinv^T for a 32 x 32 block (Dinv lower triangular): X[i][j] =
+// X = A Dinv^T for a DB x DB block (Dinv lower triangular): X[i][j] =
 // sum_{t <= j} A[i][t] Dinv[j][t].  Thread (ty, tx) returns row ty,
-// columns tx + 8 q.
-__device__ __forceinline__ void dag_solve(const double (*Ab)[NB + 1], const double (*D)[NB + 1],
-                                          double out[4]) {
-  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
-  double acc[4] = {};
-  // four independent accumulation chains; D[c][q] = 0 for q > c, so column
-  // group j stops at q = 8 j + 7 (a bound uniform over the warp)
+// columns tx + DTX q.
+template <int DB>
+__device__ __forceinline__ void dag_solve(const double (*Ab)[DB + 1], const double (*D)[DB + 1],
+                                          double out[DagShape<DB>::DJ]) {
+  constexpr int DJ = DagShape<DB>::DJ, DTX = DagShape<DB>::DTX;
+  const int ty = threadIdx.x / DTX, tx = threadIdx.x % DTX;
+  double acc[DJ] = {};
+  // DJ independent accumulation chains; D[c][q] = 0 for q > c, so column
+  // group j stops at q = DTX j + DTX - 1 (a bound uniform over the warp)
 #pragma unroll 4
-  for (int q = 0; q < NB; ++q) {
+  for (int q = 0; q < DB; ++q) {
     const double a = Ab[ty][q];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)   // D is lower triangular with exact zeros above
-      if (q <= 8 * j + 7) acc[j] += a * D[tx + 8 * j][q];
+    for (int j = 0; j < DJ; ++j)   // D is lower triangular with exact zeros above
+      if (q <= DTX * j + DTX - 1) acc[j] += a * D[tx + DTX * j][q];
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) out[j] = acc[j];
+  for (int j = 0; j < DJ; ++j) out[j] = acc[j];
 }
 
 // One persistent launch factors the FP64 diagonal tile of every item as a
-// task graph over its 32 x 32 blocks (nb = b / 32) and forms
+// task graph over its DB x DB blocks (nb = b / DB) and forms
 // W = L^{-T} (the operand of the panel products and of the solves):
 //   F(0)       factor block (0, 0): L_00, Dinv_0 = L_00^{-1}, log-det part
 //   G(k)       k >= 1, the critical chain: L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T
@@ -170,20 +187,22 @@ __device__ __forceinline__ void dag_solve(const double (*Ab)[NB + 1], const doub
 // deadlock, whatever the number of co-resident CTAs.  Blocks written by
 // other CTAs are read through L2 (ld.global.cg); every wait is bounded and
 // reports through the error word.
+template <int DB>
 __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __restrict__ items,
                                                    int count, const DagTask* __restrict__ tasks,
                                                    int ntasks, int* ticket, double* ldparts,
                                                    long long* info) {
-  __shared__ double S0[NB][NB + 1];
-  __shared__ double S1[NB][NB + 1];
-  __shared__ double S2[NB][NB + 1];
+  constexpr int DJ = DagShape<DB>::DJ, DTX = DagShape<DB>::DTX;
+  __shared__ double S0[DB][DB + 1];
+  __shared__ double S1[DB][DB + 1];
+  __shared__ double S2[DB][DB + 1];
   __shared__ int s_t, s_ok;
-  // lower triangle of a 32 x 32 block in row order: entry e -> (row, col)
-  __shared__ uint16_t tri[NB * (NB + 1) / 2];
-  const int b = A.b, nb = b / NB, tid = threadIdx.x;
-  const int ty = tid / 8, tx = tid % 8;
+  // lower triangle of a DB x DB block in row order: entry e -> (row, col)
+  __shared__ uint16_t tri[DB * (DB + 1) / 2];
+  const int b = A.b, nb = b / DB, tid = threadIdx.x;
+  const int ty = tid / DTX, tx = tid % DTX;
   const int total = ntasks * count;
-  for (int r = 0; r < NB; ++r)
+  for (int r = 0; r < DB; ++r)
     for (int c = tid; c <= r; c += blockDim.x) tri[r * (r + 1) / 2 + c] = (uint16_t)(r << 8 | c);
   for (;;) {
     if (tid == 0) s_t = atomicAdd(ticket, 1);
@@ -218,36 +237,36 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     if (!s_ok) break;
     double* T = tile_ptr<double>(A, it.tile);
     if (tk.op == 0 || tk.op == 3) {
-      double* Tk = T + (int64_t)k * NB * b + k * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) S2[e / NB][e % NB] = __ldcg(Tk + (int64_t)(e / NB) * b + e % NB);
+      double* Tk = T + (int64_t)k * DB * b + k * DB;
+      for (int e = tid; e < DB * DB; e += blockDim.x) S2[e / DB][e % DB] = __ldcg(Tk + (int64_t)(e / DB) * b + e % DB);
       if (tk.op == 3) {
         // L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T, published before the rest
-        double* Tl = T + (int64_t)k * NB * b + (k - 1) * NB;
-        const double* D = it.dinv + (int64_t)(k - 1) * NB * NB;
-        for (int e = tid; e < NB * NB; e += blockDim.x) {
-          S0[e / NB][e % NB] = __ldcg(Tl + (int64_t)(e / NB) * b + e % NB);
-          S1[e / NB][e % NB] = __ldcg(D + e);
+        double* Tl = T + (int64_t)k * DB * b + (k - 1) * DB;
+        const double* D = it.dinv + (int64_t)(k - 1) * DB * DB;
+        for (int e = tid; e < DB * DB; e += blockDim.x) {
+          S0[e / DB][e % DB] = __ldcg(Tl + (int64_t)(e / DB) * b + e % DB);
+          S1[e / DB][e % DB] = __ldcg(D + e);
         }
         __syncthreads();
-        double out[4];
-        dag_solve(S0, S1, out);
+        double out[DJ];
+        dag_solve<DB>(S0, S1, out);
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          S0[ty][tx + 8 * j] = out[j];
-          Tl[(int64_t)ty * b + tx + 8 * j] = out[j];
+        for (int j = 0; j < DJ; ++j) {
+          S0[ty][tx + DTX * j] = out[j];
+          Tl[(int64_t)ty * b + tx + DTX * j] = out[j];
         }
         __syncthreads();
         if (tid == 0) {
           __threadfence();
           st_release(&ver[k * nb + k - 1], k);
         }
-        // A_kk -= X X^T on the lower triangle (528 entries, table order)
-        for (int e = tid; e < NB * (NB + 1) / 2; e += blockDim.x) {
+        // A_kk -= X X^T on the lower triangle (DB (DB + 1) / 2 entries, table order)
+        for (int e = tid; e < DB * (DB + 1) / 2; e += blockDim.x) {
           const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
           double a0 = 0.0, a1 = 0.0;
 #pragma unroll 8
-          for (int q = 0; q < NB; q += 2) {
+          for (int q = 0; q < DB; q += 2) {
             a0 += S0[rr][q] * S0[cc][q];
             a1 += S0[rr][q + 1] * S0[cc][q + 1];
           }
@@ -255,12 +274,12 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         }
       }
       __syncthreads();
-      dag_factor(S2, S1, Tk, b, it.dinv + (int64_t)k * NB * NB, info + it.mat,
-                 it.row0 + (long long)k * NB, tri);
+      dag_factor<DB>(S2, S1, Tk, b, it.dinv + (int64_t)k * DB * DB, info + it.mat,
+                 it.row0 + (long long)k * DB, tri);
       // W_kk = Dinv_k^T (the blocks of W left of it are zeroed after publishing)
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int64_t o = (int64_t)k * NB * b + (int64_t)(e / NB) * b + k * NB + e % NB;
-        const double v = S1[e % NB][e / NB];
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        const int64_t o = (int64_t)k * DB * b + (int64_t)(e / DB) * b + k * DB + e % DB;
+        const double v = S1[e % DB][e / DB];
         it.w[o] = v;
         if (it.whi) {
           const float h = (float)v;
@@ -270,32 +289,32 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       }
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
-      double* Tr = T + (int64_t)r * NB * b + k * NB;
-      const double* D = it.dinv + (int64_t)k * NB * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        S0[e / NB][e % NB] = __ldcg(Tr + (int64_t)(e / NB) * b + e % NB);
-        S1[e / NB][e % NB] = __ldcg(D + e);
+      double* Tr = T + (int64_t)r * DB * b + k * DB;
+      const double* D = it.dinv + (int64_t)k * DB * DB;
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        S0[e / DB][e % DB] = __ldcg(Tr + (int64_t)(e / DB) * b + e % DB);
+        S1[e / DB][e % DB] = __ldcg(D + e);
       }
       __syncthreads();
-      double out[4];
-      dag_solve(S0, S1, out);
+      double out[DJ];
+      dag_solve<DB>(S0, S1, out);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Tr[(int64_t)ty * b + tx + 8 * j] = out[j];
+      for (int j = 0; j < DJ; ++j) Tr[(int64_t)ty * b + tx + DTX * j] = out[j];
     } else if (tk.op == 4) {
       // W_jr = W_jr Dinv_r^T
-      double* Wb = it.w + (int64_t)c * NB * b + r * NB;
-      const double* D = it.dinv + (int64_t)r * NB * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        S0[e / NB][e % NB] = __ldcg(Wb + (int64_t)(e / NB) * b + e % NB);
-        S1[e / NB][e % NB] = __ldcg(D + e);
+      double* Wb = it.w + (int64_t)c * DB * b + r * DB;
+      const double* D = it.dinv + (int64_t)r * DB * DB;
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        S0[e / DB][e % DB] = __ldcg(Wb + (int64_t)(e / DB) * b + e % DB);
+        S1[e / DB][e % DB] = __ldcg(D + e);
       }
       __syncthreads();
-      double out[4];
-      dag_solve(S0, S1, out);
+      double out[DJ];
+      dag_solve<DB>(S0, S1, out);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t o = (int64_t)c * NB * b + r * NB + (int64_t)ty * b + tx + 8 * j;
-        Wb[(int64_t)ty * b + tx + 8 * j] = out[j];
+      for (int j = 0; j < DJ; ++j) {
+        const int64_t o = (int64_t)c * DB * b + r * DB + (int64_t)ty * b + tx + DTX * j;
+        Wb[(int64_t)ty * b + tx + DTX * j] = out[j];
         if (it.whi) {
           const float h = (float)out[j];
           it.whi[o] = h;
@@ -304,52 +323,52 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       }
     } else if (tk.op == 5) {
       // W_jr -= W_jk L_rk^T (the first update, k = j, starts from zero)
-      const double* Wj = it.w + (int64_t)c * NB * b + k * NB;
-      const double* Lr = T + (int64_t)r * NB * b + k * NB;
-      double* Wb = it.w + (int64_t)c * NB * b + r * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        S0[e / NB][e % NB] = __ldcg(Wj + (int64_t)(e / NB) * b + e % NB);
-        S1[e / NB][e % NB] = __ldcg(Lr + (int64_t)(e / NB) * b + e % NB);
+      const double* Wj = it.w + (int64_t)c * DB * b + k * DB;
+      const double* Lr = T + (int64_t)r * DB * b + k * DB;
+      double* Wb = it.w + (int64_t)c * DB * b + r * DB;
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        S0[e / DB][e % DB] = __ldcg(Wj + (int64_t)(e / DB) * b + e % DB);
+        S1[e / DB][e % DB] = __ldcg(Lr + (int64_t)(e / DB) * b + e % DB);
       }
-      double cur[4];
+      double cur[DJ];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cur[j] = k == c ? 0.0 : __ldcg(Wb + (int64_t)ty * b + tx + 8 * j);
+      for (int j = 0; j < DJ; ++j) cur[j] = k == c ? 0.0 : __ldcg(Wb + (int64_t)ty * b + tx + DTX * j);
       __syncthreads();
-      double acc[4] = {}, acc2[4] = {};
-      for (int q = 0; q < NB; q += 2) {
+      double acc[DJ] = {}, acc2[DJ] = {};
+      for (int q = 0; q < DB; q += 2) {
         const double a = S0[ty][q], a2 = S0[ty][q + 1];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[j] += a * S1[tx + 8 * j][q];
-          acc2[j] += a2 * S1[tx + 8 * j][q + 1];
+        for (int j = 0; j < DJ; ++j) {
+          acc[j] += a * S1[tx + DTX * j][q];
+          acc2[j] += a2 * S1[tx + DTX * j][q + 1];
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Wb[(int64_t)ty * b + tx + 8 * j] = cur[j] - (acc[j] + acc2[j]);
+      for (int j = 0; j < DJ; ++j) Wb[(int64_t)ty * b + tx + DTX * j] = cur[j] - (acc[j] + acc2[j]);
     } else {
       // A_rc -= L_rk L_ck^T
-      const double* Lr = T + (int64_t)r * NB * b + k * NB;
-      const double* Lc = T + (int64_t)c * NB * b + k * NB;
-      double* Trc = T + (int64_t)r * NB * b + c * NB;
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        S0[e / NB][e % NB] = __ldcg(Lr + (int64_t)(e / NB) * b + e % NB);
-        S1[e / NB][e % NB] = __ldcg(Lc + (int64_t)(e / NB) * b + e % NB);
+      const double* Lr = T + (int64_t)r * DB * b + k * DB;
+      const double* Lc = T + (int64_t)c * DB * b + k * DB;
+      double* Trc = T + (int64_t)r * DB * b + c * DB;
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        S0[e / DB][e % DB] = __ldcg(Lr + (int64_t)(e / DB) * b + e % DB);
+        S1[e / DB][e % DB] = __ldcg(Lc + (int64_t)(e / DB) * b + e % DB);
       }
-      double cur[4];
+      double cur[DJ];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cur[j] = __ldcg(Trc + (int64_t)ty * b + tx + 8 * j);
+      for (int j = 0; j < DJ; ++j) cur[j] = __ldcg(Trc + (int64_t)ty * b + tx + DTX * j);
       __syncthreads();
-      double acc[4] = {}, acc2[4] = {};
-      for (int q = 0; q < NB; q += 2) {
+      double acc[DJ] = {}, acc2[DJ] = {};
+      for (int q = 0; q < DB; q += 2) {
         const double a = S0[ty][q], a2 = S0[ty][q + 1];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[j] += a * S1[tx + 8 * j][q];
-          acc2[j] += a2 * S1[tx + 8 * j][q + 1];
+        for (int j = 0; j < DJ; ++j) {
+          acc[j] += a * S1[tx + DTX * j][q];
+          acc2[j] += a2 * S1[tx + DTX * j][q + 1];
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Trc[(int64_t)ty * b + tx + 8 * j] = cur[j] - (acc[j] + acc2[j]);
+      for (int j = 0; j < DJ; ++j) Trc[(int64_t)ty * b + tx + DTX * j] = cur[j] - (acc[j] + acc2[j]);
     }
     __syncthreads();
     if (tid == 0) {
@@ -364,9 +383,9 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     // off the critical chain, after publishing: the log-determinant part and
     // the zero blocks of W left of W_kk (no task reads them)
     if (tk.op == 0 || tk.op == 3) {
-      dag_logdet(S2, ldparts + it.ldslot + k);
-      double* Wk = it.w + (int64_t)k * NB * b;
-      for (int e = tid; e < NB * k * NB; e += blockDim.x) Wk[(int64_t)(e / (k * NB)) * b + e % (k * NB)] = 0.0;
+      dag_logdet<DB>(S2, ldparts + it.ldslot + k);
+      double* Wk = it.w + (int64_t)k * DB * b;
+      for (int e = tid; e < DB * k * DB; e += blockDim.x) Wk[(int64_t)(e / (k * DB)) * b + e % (k * DB)] = 0.0;
     }
   }
 }
@@ -401,8 +420,9 @@ __global__ void __launch_bounds__(128) k_panel_trsm(Arena A, const ItemPanel* __
     for (int e = tid; e < PR * b; e += blockDim.x)
       X[e] = load_f64(src, ref.dt, (int64_t)r0 * b + e) * s_in;
     for (int cb = 0; cb < b / NB; ++cb) {
+      // Dv[i][j] = Dinv_cb[i][j] = W[cb NB + j][cb NB + i]
       for (int e = tid; e < NB * NB; e += blockDim.x)
-        Dv[(e / NB) * (NB + 1) + e % NB] = it.dinv[(int64_t)cb * NB * NB + e];
+        Dv[(e % NB) * (NB + 1) + e / NB] = it.w[(int64_t)(cb * NB + e / NB) * b + cb * NB + e % NB];
       __syncthreads();
       double acc[NQ], acc2[NQ];
 #pragma unroll
@@ -594,7 +614,8 @@ std::vector<DagTask> potrf_dag_tasks(int nb) {
 }
 
 void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const DagTask* tasks,
-                      int ntasks, int* ticket, double* ldparts, long long* info, cudaStream_t s) {
+                      int ntasks, int* ticket, double* ldparts, long long* info, int db,
+                      cudaStream_t s) {
   if (count <= 0) return;
   static int sms = 0;
   if (!sms) {
@@ -603,8 +624,13 @@ void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const D
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const int64_t total = (int64_t)ntasks * count;
-  const int grid = (int)std::min<int64_t>(total, std::max<int64_t>(16, std::min<int64_t>(2 * sms, total / 8)));
-  k_potrf_dag<<<grid, 256, 0, s>>>(A, items, count, tasks, ntasks, ticket, ldparts, info);
+  // one CTA per SM while few tiles share the launch (a CTA on the critical
+  // chain then has its SM's FP64 pipe to itself); two when many do
+  const int per_sm = count > 4 ? 2 : 1;
+  const int grid =
+      (int)std::min<int64_t>(total, std::max<int64_t>(16, std::min<int64_t>(per_sm * sms, total / 8)));
+  if (db == 16) k_potrf_dag<16><<<grid, 256, 0, s>>>(A, items, count, tasks, ntasks, ticket, ldparts, info);
+  else k_potrf_dag<32><<<grid, 256, 0, s>>>(A, items, count, tasks, ntasks, ticket, ldparts, info);
 }
 
 namespace {

@@ -52,19 +52,24 @@ __host__ __device__ inline char* tile_bytes(const Arena& A, int id) {
 
 // ---- work items -----------------------------------------------------------
 
-// Factorisation of one FP64 diagonal tile by the 32 x 32-block task graph
-// (k_potrf_dag); ver and the launch's ticket are zero when it starts.
+// Factorisation of one FP64 diagonal tile by a task graph over its NB x NB
+// blocks, NB = 16 or 32 (k_potrf_dag); ver and the launch's ticket are zero
+// when it starts.  One SM's FP64 pipe retires about two lane-FMAs per clock,
+// so the block solve and update on the graph's critical chain cost NB^3 on
+// a single SM while the chain of pivots (one per column) does not depend on
+// NB: 16 keeps the chain short when few tiles share a launch, 32 has fewer
+// tasks when many do.
 struct ItemPotrf {
   int32_t tile;       // FP64 diagonal tile
   int32_t mat;        // matrix index (info word)
-  int32_t ldslot;     // first of b/32 log-determinant partial slots
+  int32_t ldslot;     // first of b/NB log-determinant partial slots
   int32_t pad_;
   int64_t row0;       // global row of the tile's first row
-  double* dinv;       // b/32 inverses of the 32 x 32 diagonal blocks (row-major)
+  double* dinv;       // b/NB inverses of the diagonal blocks (row-major)
   double* w;          // b x b: W = L^{-T} of the tile (upper triangular)
   float* whi;         // W as FP32 hi + lo pair (upper part only; NULL: not wanted)
   float* wlo;
-  int32_t* ver;       // 2 (b/32)^2 progress counters: factor blocks, then blocks of W
+  int32_t* ver;       // 2 (b/NB)^2 progress counters: factor blocks, then blocks of W
 };
 struct DagTask {
   uint8_t op;         // 0 factor (0, 0), 1 solve (r, k), 2 update (r, c), 3 solve (k, k-1) +
@@ -79,7 +84,8 @@ struct ItemPanel {
   int32_t diag;       // L_kk
   int32_t amax;       // amax slot of the result
   int32_t mat;        // matrix of the plan (host bookkeeping)
-  double* dinv;       // (b/32) inverses of the diagonal 32-blocks of L_kk
+  const double* w;    // W = L_kk^{-T} (b x b); its diagonal 32-blocks are the
+                      // transposed inverses of L_kk's diagonal 32-blocks
   double* x;          // b x b float64 scratch
 };
 
@@ -229,7 +235,8 @@ void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* p
 // k_fp64.cu
 std::vector<DagTask> potrf_dag_tasks(int nb);
 void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const DagTask* tasks,
-                      int ntasks, int* ticket, double* ldparts, long long* info, cudaStream_t s);
+                      int ntasks, int* ticket, double* ldparts, long long* info, int db,
+                      cudaStream_t s);
 // reserve_sms: SMs left free by the persistent grid (for concurrent work)
 void launch_panel_trsm(const Arena& A, const ItemPanel* items, int count, int reserve_sms,
                        cudaStream_t s);
