@@ -174,10 +174,11 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-# DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/ (kernel -> bytes); None where no capture of the current kernel
-# exists.
-TRAFFIC_BYTES_PER_LAUNCH = {}
+# DRAM bytes (read + write) per launch, dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the kernel as it is now on
+# this workload (kernel -> bytes); absent where no capture of the current
+# kernel exists.
+TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1212160 + 512}
 
 
 def kernel_rooflines(prof, chol_ms, peak64, b):
@@ -194,9 +195,9 @@ def kernel_rooflines(prof, chol_ms, peak64, b):
                        "inverse b^3/3 per diagonal tile"),
         "panel_trsm_first": ("k_panel_trsm (chain)", "alu", peak64, "FP64 DFMA loop probe in this run"),
         "panel_trsm": ("k_panel_trsm (bulk)", "alu", peak64, "FP64 DFMA loop probe in this run"),
-        "update_tc_3xtf32": ("k_update_tc (FP32 kind, 3 TF32 MMAs)", "tensor", tf32x3,
+        "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 MMAs)", "tensor", tf32x3,
                              f"bf16_tflops_sustained {which} x 1.1/2.25 / 3"),
-        "update_tc_lowp": ("k_update_tc (BF16/FP16/E4M3 kinds)", "tensor", bf16,
+        "update_tc_lowp": ("k_update_tc_p (BF16/FP16/E4M3 kinds)", "tensor", bf16,
                            f"bf16_tflops_sustained {which}"),
         "panel_ozaki_gemm": ("k_oz_gemm", "tensor", bf16,
                              f"bf16_tflops_sustained {which}; achieved counts the TRSM flops b^3 per tile"),
