@@ -1017,6 +1017,7 @@ mp_status mp_ctx_create(int device, mp_ctx** out) {
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
     return fail(nullptr, MP_ERR_ARG, "no CUDA device %d", device);
   CK(nullptr, cudaSetDevice(device));
+  if (init_gen_tables() != 0) return fail(nullptr, MP_ERR_CUDA, "cannot set the generation tables");
   mp_ctx* c = new mp_ctx;
   c->device = device;
   *out = c;

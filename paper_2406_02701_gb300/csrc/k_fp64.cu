@@ -180,7 +180,8 @@ __device__ __forceinline__ void dag_solve(const double (*Ab)[DB + 1], const doub
 // F and G also write W_kk = Dinv_k^T and zero the blocks of W left of it.
 // ver[r nb + c] counts the operations finished on block (r, c) of the
 // factor (its c updates, then the factorisation or solve); ver[nb^2 +
-// j nb + r] those on block (j, r) of W (its r - j updates, then the solve).
+// j nb + r] those on block (j, r) of W (its r - j updates, then the solve;
+// 1 once the diagonal block W_jj is written).
 // CTAs take tasks by an atomic ticket in a fixed topological order (every
 // task's inputs come earlier in the order), so a task only ever waits on
 // tasks that running CTAs have already taken: the schedule cannot
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
   __shared__ double S0[DB][DB + 1];
   __shared__ double S1[DB][DB + 1];
   __shared__ double S2[DB][DB + 1];
-  __shared__ int s_t, s_ok;
+  __shared__ int s_t, s_ok, s_ok2;
   // lower triangle of a DB x DB block in row order: entry e -> (row, col)
   __shared__ uint16_t tri[DB * (DB + 1) / 2];
   const int b = A.b, nb = b / DB, tid = threadIdx.x;
@@ -217,9 +218,8 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     if (tid == 0) {
       bool ok;
       if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err);
-      else if (tk.op == 3)   // G(k): F(k-1), block (k, k-1) and (k, k) updated up to k-2
-        ok = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err) && dag_wait(&ver[k * nb + k - 1], k - 1, A.err) &&
-             dag_wait(&ver[k * nb + k], k - 1, A.err);
+      else if (tk.op == 3)   // G(k): blocks (k, k-1) and (k, k) updated up to k-2 (F(k-1) below)
+        ok = dag_wait(&ver[k * nb + k - 1], k - 1, A.err) && dag_wait(&ver[k * nb + k], k - 1, A.err);
       else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err) && dag_wait(&ver[r * nb + k], k, A.err);
       else if (tk.op == 2)
         ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         ok = dag_wait(&ver[r * nb + r], r + 1, A.err) && dag_wait(&wv[c * nb + r], r - c, A.err);
       else                   // E(r, k, j = c): L_rk, W_jk final; the previous update of W_jr
         ok = dag_wait(&ver[r * nb + k], k + 1, A.err) &&
-             (k == c ? dag_wait(&ver[c * nb + c], c + 1, A.err) : dag_wait(&wv[c * nb + k], k - c + 1, A.err)) &&
+             (k == c ? dag_wait(&wv[c * nb + c], 1, A.err) : dag_wait(&wv[c * nb + k], k - c + 1, A.err)) &&
              dag_wait(&wv[c * nb + r], k - c, A.err);
       if (!ok) atomicExch(A.err, 1);
       s_ok = ok;
@@ -240,13 +240,19 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       double* Tk = T + (int64_t)k * DB * b + k * DB;
       for (int e = tid; e < DB * DB; e += blockDim.x) S2[e / DB][e % DB] = __ldcg(Tk + (int64_t)(e / DB) * b + e % DB);
       if (tk.op == 3) {
-        // L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T, published before the rest
+        // L_{k,k-1} = A_{k,k-1} Dinv_{k-1}^T, published before the rest; the
+        // two blocks of A are final before F(k-1) ends, so they are read
+        // first and only Dinv_{k-1} waits for it
         double* Tl = T + (int64_t)k * DB * b + (k - 1) * DB;
         const double* D = it.dinv + (int64_t)(k - 1) * DB * DB;
-        for (int e = tid; e < DB * DB; e += blockDim.x) {
-          S0[e / DB][e % DB] = __ldcg(Tl + (int64_t)(e / DB) * b + e % DB);
-          S1[e / DB][e % DB] = __ldcg(D + e);
+        for (int e = tid; e < DB * DB; e += blockDim.x) S0[e / DB][e % DB] = __ldcg(Tl + (int64_t)(e / DB) * b + e % DB);
+        if (tid == 0) {
+          s_ok2 = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err);
+          if (!s_ok2) atomicExch(A.err, 1);
         }
+        __syncthreads();
+        if (!s_ok2) break;
+        for (int e = tid; e < DB * DB; e += blockDim.x) S1[e / DB][e % DB] = __ldcg(D + e);
         __syncthreads();
         double out[DJ];
         dag_solve<DB>(S0, S1, out);
@@ -276,17 +282,6 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       __syncthreads();
       dag_factor<DB>(S2, S1, Tk, b, it.dinv + (int64_t)k * DB * DB, info + it.mat,
                  it.row0 + (long long)k * DB, tri);
-      // W_kk = Dinv_k^T (the blocks of W left of it are zeroed after publishing)
-      for (int e = tid; e < DB * DB; e += blockDim.x) {
-        const int64_t o = (int64_t)k * DB * b + (int64_t)(e / DB) * b + k * DB + e % DB;
-        const double v = S1[e % DB][e / DB];
-        it.w[o] = v;
-        if (it.whi) {
-          const float h = (float)v;
-          it.whi[o] = h;
-          it.wlo[o] = (float)(v - (double)h);
-        }
-      }
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * DB * b + k * DB;
@@ -380,9 +375,25 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         st_release(&ver[blk], k + 1);
       }
     }
-    // off the critical chain, after publishing: the log-determinant part and
+    // off the critical chain, after publishing: W_kk = Dinv_k^T (published on
+    // its own counter, read by the E(r, k, k)), the log-determinant part and
     // the zero blocks of W left of W_kk (no task reads them)
     if (tk.op == 0 || tk.op == 3) {
+      for (int e = tid; e < DB * DB; e += blockDim.x) {
+        const int64_t o = (int64_t)k * DB * b + (int64_t)(e / DB) * b + k * DB + e % DB;
+        const double v = S1[e % DB][e / DB];
+        it.w[o] = v;
+        if (it.whi) {
+          const float h = (float)v;
+          it.whi[o] = h;
+          it.wlo[o] = (float)(v - (double)h);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(&wv[k * nb + k], 1);
+      }
       dag_logdet<DB>(S2, ldparts + it.ldslot + k);
       double* Wk = it.w + (int64_t)k * DB * b;
       for (int e = tid; e < DB * k * DB; e += blockDim.x) Wk[(int64_t)(e / (k * DB)) * b + e % (k * DB)] = 0.0;

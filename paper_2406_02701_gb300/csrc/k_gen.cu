@@ -7,16 +7,28 @@
 //
 // Generation (the Matérn model of Sec. 6.2 in its half-integer closed
 // forms): every entry of a lower tile is computed in float64 from the two
-// locations and rounded once into the tile's format.  E4M3 tiles first get
+// locations and rounded once into the tile's format.  exp(-x) follows Tang's
+// table-driven method (fewer FP64 operations than the general exp; the
+// kernel is bound by the FP64 pipe).  E4M3 tiles first get
 // the tile's amax from a separate pass (`gen_amax`), then the power-of-two
-// scale.  Rows/columns beyond n are identity padding.  The float64
-// arithmetic is written with explicit _rn intrinsics so that no fused
-// multiply-add changes the rounding of the distance or the polynomial.
+// scale.  Rows/columns beyond n are identity padding.  The distance is
+// written with explicit _rn intrinsics (no contraction into fused
+// multiply-adds); the polynomial and exp use fused multiply-adds on purpose.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
 #include "mp_device.cuh"
 
 namespace mp {
 
 namespace {
+
+// e^{-x} tables (set per device by init_gen_tables): [0, 32) 2^{j/32}
+// rounded to double, [32, 64) the remainders 2^{j/32} - hi, [64] the head of
+// ln2/32 with 37 significant bits, [65] ln2/32 - head, [66] 32/ln2.
+constexpr int GEN_TAB = 67;
+__constant__ double c_gen_tab[GEN_TAB];
 
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
   uint32_t k = 0;
@@ -81,22 +93,53 @@ __global__ void k_morton_gather(const unsigned long long* __restrict__ keys,
   out[2 * i + 1] = in[2 * p + 1];
 }
 
-// Matérn covariance of two locations (closed forms, x = r / range).  x is
-// r times the rounded reciprocal of the range (GB300's FP64 pipe makes a
-// division cost about ten FP64 operations): one more rounding than r /
-// range, i.e. |dx| <= 2 ulp(x), which exp(-x) carries as a relative error
-// of at most 2 x 2^-52.
-__device__ __forceinline__ double entry(const ItemGen& it, double inv_range, double xi, double yi,
-                                        double xj, double yj, int64_t gi, int64_t gj) {
+// e^{-x} for x >= 0 by Tang's table-driven method (P. T. P. Tang,
+// "Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15, 1989): -x = k ln2/32 + r with
+// k = rint(-32 x / ln2) and |r| <= ln2/64 (k times the 37-bit head of
+// ln2/32 is exact for |k| < 2^16, i.e. x <= 700); k = 32 m + j and
+// e^{-x} = 2^m 2^{j/32} (1 + p), p = e^r - 1 from its Taylor polynomial of
+// degree 6 (truncation below r^7/7! < 4e-18), 2^{j/32} = T_hi + T_lo, the
+// sum T_hi + (T_lo + T_hi p) rounded once: about 0.55 ulp.  Beyond 700 (and
+// for NaN) the library exp.
+__device__ __forceinline__ double exp_neg(double x, const double* tab) {
+  if (!(x <= 700.0)) return exp(-x);
+  const double shifter = 6755399441055744.0;           // 1.5 * 2^52
+  const double t = fma(-x, tab[66], shifter);           // low bits: k
+  const int k = __double2loint(t);
+  const double kd = t - shifter;
+  const double r = fma(-kd, tab[65], fma(-kd, tab[64], -x));
+  const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
+  const double p = fma(r * r, q, r);
+  const int m = k >> 5, j = k & 31;
+  const double th = tab[j];
+  const double v = th + fma(th, p, tab[32 + j]);   // in [0.98, 2.03]
+  // times 2^m (m >= -1010: the result stays normal) on the exponent field
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)m << 52));
+}
+
+// Matérn covariance of two locations (closed forms, x = r / range):
+// sigma^2 e^{-x} (nu = 1/2), sigma^2 (1 + x) e^{-x} (3/2),
+// sigma^2 (1 + x + x^2/3) e^{-x} (5/2).
+// r = s rsqrt(s) for s = dx^2 + dy^2 > 0 (rsqrt within 1 ulp: r within
+// 1.5 ulp); x is r times the rounded reciprocal of the range (GB300's FP64
+// pipe makes a division cost about ten FP64 operations): |dx| <= 3 ulp(x),
+// which exp(-x) carries as a relative error of at most 3 x 2^-53.
+__device__ __forceinline__ double entry(const ItemGen& it, double inv_range, const double* tab,
+                                        double xi, double yi, double xj, double yj, int64_t gi,
+                                        int64_t gj) {
   if (gi >= it.n || gj >= it.n) return gi == gj ? 1.0 : 0.0;
   double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
-  double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+  const double s2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  double r = s2 > 0.0 ? __dmul_rn(s2, rsqrt(s2)) : 0.0;
   double x = __dmul_rn(r, inv_range);
+  // sigma^2 times the closed-form polynomial, Horner with fused multiply-adds
+  const double s = it.sigma2;
   double poly;
-  if (it.nu == 0.5) poly = 1.0;
-  else if (it.nu == 1.5) poly = __dadd_rn(1.0, x);
-  else poly = __dadd_rn(__dadd_rn(1.0, x), __dmul_rn(__dmul_rn(x, x), 1.0 / 3.0));
-  double v = __dmul_rn(__dmul_rn(it.sigma2, poly), exp(-x));
+  if (it.nu == 0.5) poly = s;
+  else if (it.nu == 1.5) poly = fma(s, x, s);
+  else poly = fma(x, fma(x, s * (1.0 / 3.0), s), s);
+  double v = __dmul_rn(poly, exp_neg(x, tab));
   if (gi == gj) v = __dadd_rn(v, it.nugget);
   return v;
 }
@@ -106,6 +149,8 @@ constexpr int GEN_ROWS = 16;
 template <bool AMAX>
 __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __restrict__ items) {
   extern __shared__ double sloc[];           // b column points (x, y) + GEN_ROWS row points
+  __shared__ double tab[GEN_TAB];
+  for (int e = threadIdx.x; e < GEN_TAB; e += blockDim.x) tab[e] = c_gen_tab[e];
   const ItemGen it = items[blockIdx.x];
   const int b = A.b;
   const int r0 = blockIdx.y * GEN_ROWS;
@@ -131,7 +176,8 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
   if (!AMAX && dt == E4M3) inv_s = 1.0 / e4m3_scale(amax_value(&A.amax[it.tile]));
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
-    double v = entry(it, inv_range, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
+    double v = entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r,
+                     gj0 + c);
     int64_t off = (int64_t)(r0 + r) * b + c;
     if (AMAX) {
       mx = fmax(mx, fabs(v));
@@ -159,6 +205,8 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
 __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __restrict__ items,
                                                     double* __restrict__ partial) {
   extern __shared__ double sloc[];
+  __shared__ double tab[GEN_TAB];
+  for (int e = threadIdx.x; e < GEN_TAB; e += blockDim.x) tab[e] = c_gen_tab[e];
   const ItemGen it = items[blockIdx.x];
   const int r0 = blockIdx.y * GEN_ROWS;
   const int64_t gi0 = (int64_t)it.ti * b + r0, gj0 = (int64_t)it.tj * b;
@@ -179,7 +227,8 @@ __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __rest
   double ss = 0.0;
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
-    double v = entry(it, inv_range, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
+    double v = entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r,
+                     gj0 + c);
     ss += v * v;
   }
   __shared__ double red[8];
@@ -202,6 +251,28 @@ __global__ void k_reduce_norms(const ItemGen* __restrict__ items, int count, int
 }
 
 }  // namespace
+
+// The e^{-x} tables of the current device, from long double arithmetic on
+// the host (2^{j/32} as a double plus its remainder; ln2/32 as a 37-bit head
+// plus its remainder).
+int init_gen_tables() {
+  double h[GEN_TAB];
+  for (int j = 0; j < 32; ++j) {
+    const long double v = std::exp2((long double)j / 32.0L);
+    h[j] = (double)v;
+    h[32 + j] = (double)(v - (long double)h[j]);
+  }
+  const long double l = std::log(2.0L) / 32.0L;
+  double head = (double)l;
+  uint64_t u;
+  std::memcpy(&u, &head, sizeof(u));
+  u &= ~(uint64_t)0xFFFF;   // 53 - 16 = 37 significant bits
+  std::memcpy(&head, &u, sizeof(u));
+  h[64] = head;
+  h[65] = (double)(l - (long double)head);
+  h[66] = (double)(32.0L / std::log(2.0L));
+  return cudaMemcpyToSymbol(c_gen_tab, h, sizeof(h)) == cudaSuccess ? 0 : 1;
+}
 
 void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,
                        double* norms, cudaStream_t s) {

@@ -227,6 +227,8 @@ void launch_morton_gather(const unsigned long long* keys, const double* in, int6
                           double* out, int64_t* perm, cudaStream_t s);
 void launch_gen_amax(const Arena& A, const ItemGen* items, int count, cudaStream_t s);
 void launch_generate(const Arena& A, const ItemGen* items, int count, cudaStream_t s);
+// Uploads the generation kernels' e^{-x} tables to the current device; 0 on success.
+int init_gen_tables();
 // Frobenius norm of every generated lower tile into norms[ti * nt + tj]
 // (partial: count * b/16 doubles of scratch).
 void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,
