@@ -60,7 +60,6 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
   for (int e = tid; e < DB * DB; e += blockDim.x) R[e / DB][e % DB] = (e / DB == e % DB) ? 1.0 : 0.0;
   if (tid < 32) {
     const double d = S[0][0];
-    if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + 1);
     const double rp = rsqrt(d);
     if (lane == 0) { S[0][0] = d * rp; rps[0] = rp; }
     else if (lane < DB) S[lane][0] *= rp;
@@ -69,11 +68,13 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
     __syncthreads();
     if (tid < 32) {
       if (c + 1 < DB) {
+        // every lane forms the pivot itself (broadcast reads, no shuffle on
+        // the chain); the pivot test is made once after the sweep
         const int n = c + 1;
+        const double snc = S[n][c];
+        const double d = S[n][n] - snc * snc;
         double v = 0.0;
-        if (lane >= n && lane < DB) v = S[lane][n] - S[lane][c] * S[n][c];
-        const double d = __shfl_sync(0xffffffffu, v, n);
-        if (lane == 0 && !(d > 0.0)) atomicMin(info, row0 + n + 1);
+        if (lane > n && lane < DB) v = S[lane][n] - S[lane][c] * snc;
         const double rp = rsqrt(d);
         if (lane == n) S[n][n] = d * rp;           // sqrt(d) = d / sqrt(d)
         else if (lane > n && lane < DB) S[lane][n] = v * rp;
@@ -123,6 +124,10 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
   }
   __syncthreads();
   if (tid < DB) R[DB - 1][tid] *= rps[DB - 1];
+  // a pivot d that is not > 0 leaves L_cc = d rsqrt(d) NaN (d < 0, NaN) or
+  // 0 * inf = NaN (d = 0): the first diagonal entry that is not > 0 is the
+  // first failed pivot
+  if (tid < DB && !(S[tid][tid] > 0.0)) atomicMin(info, row0 + tid + 1);
   __syncthreads();
   for (int e = tid; e < DB * DB; e += blockDim.x) {
     const int r = e / DB, c = e % DB;
