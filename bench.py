@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--eps", type=float, default=1e-6)
-    p.add_argument("--cpu-steps", type=int, default=3, help="oracle factorisation steps sampled")
+    p.add_argument("--cpu-steps", type=int, default=7, help="oracle factorisation steps sampled")
     p.add_argument("--panel", default="ozaki", choices=["fp64", "ozaki"],
                    help="panel solve of tiles stored in FP32 or below: FP64 substitution, or "
                         "integer-digit products on the tensor cores")
@@ -178,7 +178,7 @@ def measured_peaks():
 # dram__bytes_write.sum from one ncu capture of the kernel as it is now on
 # this workload (kernel -> bytes); absent where no capture of the current
 # kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1212160 + 512}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1210368 + 2560}
 
 
 def kernel_rooflines(prof, chol_ms, peak64, b):
@@ -258,7 +258,9 @@ def reference_arm(args, cfg):
         S = OM.covariance(locs, cfg["nu"], cfg["range"], cfg["sigma2"], cfg["nugget"])
         pmap = OC.guarded_map(OC.tile_norms(S, b), spec[4], spec[2], spec[3], args.eps)
         del S
-    steps = max(1, min(args.cpu_steps, nt))
+    # each of the K + W repeats samples 3 steps (about 5 s on 16 cores), so
+    # that the whole run stays within a few minutes
+    steps = max(1, min(3, args.cpu_steps, nt))
     res = oracle_sample(cfg, pmap, steps, repeats=args.steps, warmup=args.warmup)
     secs = sum(r[0] for r in res)
     fl = sum(r[1] for r in res)
