@@ -268,7 +268,9 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
           Tl[(int64_t)ty * b + tx + DTX * j] = out[j];
         }
         __syncthreads();
-        if (tid == 0) {
+        // published by the last thread, which has no share of the update
+        // below when DB = 16 (136 entries): the fence overlaps the update
+        if (tid == blockDim.x - 1) {
           __threadfence();
           st_release(&ver[k * nb + k - 1], k);
         }

@@ -176,50 +176,63 @@ __global__ void __launch_bounds__(256) k_oz_split_rows(Arena A, const ItemOzA* _
 // MMA's K-major B operand: row n of a digit tile is column n of W) and the
 // column bounds tau.  One CTA: 32 columns x 64 rows; the column bound is
 // taken over all b rows by every CTA of the column block (same value).
+// The digits of v = W / tau come from the integer N = rint(v 2^(6S)) (round
+// half to even): its balanced base-64 digits, least significant first, in
+// [-32, 31], the leading one in [-64, 64].  They represent exactly the value
+// that S successive steps d = rint(64 r), r = 64 r - d represent (both are
+// the nearest multiple of 2^(-6S), ties to even), with integer arithmetic in
+// place of 4 FP64 operations per digit.
 template <int S>
 __global__ void __launch_bounds__(256) k_oz_split_cols(Arena A, const ItemOzW* __restrict__ items) {
+  static_assert(S <= 8, "N = v 2^(6S) must fit in 63 bits");
   __shared__ double tr[32][65];
-  __shared__ double cmax[8][32];
+  __shared__ unsigned long long cmax[8][32];
+  __shared__ double cscale[32];
   const ItemOzW it = items[blockIdx.x];
   const int b = A.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n0 = blockIdx.y * 32, k0 = blockIdx.z * 64;
   const double* W = tile_ptr<double>(A, it.wtile);
-  double mx = 0.0;
-  for (int k = warp; k < b; k += 8) mx = fmax(mx, fabs(W[(int64_t)k * b + n0 + lane]));
+  // largest |W| of the column: the bit patterns of magnitudes order like the
+  // values (finite doubles), so an integer maximum does
+  unsigned long long mx = 0;
+  for (int k = warp; k < b; k += 8)
+    mx = max(mx, (unsigned long long)__double_as_longlong(W[(int64_t)k * b + n0 + lane]) & 0x7fffffffffffffffull);
   cmax[warp][lane] = mx;
   __syncthreads();
   if (warp == 0) {
-    for (int w = 1; w < 8; ++w) mx = fmax(mx, cmax[w][lane]);
-    const double t = pow2_above_d(mx);
+    for (int w = 1; w < 8; ++w) mx = max(mx, cmax[w][lane]);
+    const double t = pow2_above_d(__longlong_as_double((long long)mx));
     if (blockIdx.z == 0) it.tau[n0 + lane] = (float)t;
-    cmax[0][lane] = 1.0 / t;                  // exact: a power of two
+    cscale[lane] = ldexp(1.0, 6 * S) / t;     // exact: powers of two
   }
   __syncthreads();
-  // tr[n][k] = W[k0 + k][n0 + n] / tau_n
+  // tr[n][k] = W[k0 + k][n0 + n] 2^(6S) / tau_n
   for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
     const int k = e / 32, n = e % 32;
-    tr[n][k] = W[(int64_t)(k0 + k) * b + n0 + n] * cmax[0][n];
+    tr[n][k] = W[(int64_t)(k0 + k) * b + n0 + n] * cscale[n];
   }
   __syncthreads();
   // thread: row n = e / 16 of W^T, four consecutive k (8-byte stores)
   for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
     const int n = e / 16, kq = (e % 16) * 4;
-    double v[4];
+    int dg[S][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = tr[n][kq + j];
+    for (int j = 0; j < 4; ++j) {
+      long long m = __double2ll_rn(tr[n][kq + j]);
+#pragma unroll
+      for (int q = S - 1; q > 0; --q) {
+        const long long d = ((m + 32) & 63) - 32;
+        dg[q][j] = (int)d;
+        m = (m - d) >> 6;                     // exact: m - d is a multiple of 64
+      }
+      dg[0][j] = (int)m;
+    }
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      float d[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const double t = v[j] * 64.0;
-        const double r = rint(t);
-        v[j] = t - r;                         // exact
-        d[j] = (float)r;
-      }
       uint2* dst = reinterpret_cast<uint2*>(tile_ptr<__nv_bfloat16>(A, it.slices[q]) +
                                             (int64_t)(n0 + n) * b + k0 + kq);
-      *dst = make_uint2(pack_bf16x2(d[0], d[1]), pack_bf16x2(d[2], d[3]));
+      *dst = make_uint2(pack_bf16x2((float)dg[q][0], (float)dg[q][1]),
+                        pack_bf16x2((float)dg[q][2], (float)dg[q][3]));
     }
   }
 }
