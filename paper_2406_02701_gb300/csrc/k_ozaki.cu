@@ -77,15 +77,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// kind::f16, D = FP32, A = B = BF16, K-major, M = 128, N = 64
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
+// kind::f16, D = FP32, A = B = BF16, K-major, M = 128, N = n (a multiple of
+// 16, at most 256)
+__device__ __forceinline__ uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc,
+                                         uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -336,13 +339,20 @@ __global__ void __launch_bounds__(128, 1)
         if (!(ok = mb_wait(&afull[sa], (i / OZ_ASTG) & 1, A.err))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = su32(aring + sa * OZ_ACH);
-#pragma unroll 1
-        for (int q = 0; q < S - p; ++q) {
+        // A_p against W digits q = 0 .. S-1-p in one product per 256
+        // columns: the digits lie one after another in the ring (OZ_BN rows
+        // each) and level l sits at tensor-memory column l * OZ_BN, so the
+        // product of A_p with digits q0 .. q0+nq-1 lands on levels
+        // p+q0 .. p+q0+nq-1 (fewer, wider MMAs: A_p is read once per 256
+        // columns instead of once per digit)
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
-            mma_bf16(tmem + (uint32_t)(p + q) * OZ_BN, sdesc(a0 + kk * 32),
-                     sdesc(b0 + q * OZ_BCH + kk * 32), acc);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
+#pragma unroll 1
+          for (int q0 = 0; q0 < S - p; q0 += 256 / OZ_BN) {
+            const int nq = min(256 / OZ_BN, S - p - q0);
+            mma_bf16(tmem + (uint32_t)(p + q0) * OZ_BN, sdesc(a0 + kk * 32),
+                     sdesc(b0 + q0 * OZ_BCH + kk * 32), acc, oz_idesc(nq * OZ_BN));
           }
         }
         commit(&aempty[sa]);
