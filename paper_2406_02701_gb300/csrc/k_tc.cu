@@ -100,15 +100,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 }
 
 // Instruction descriptor: D = FP32, A/B format code `fmt`, both K-major,
-// M = 128, N = 128.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+// M = 128, N = n.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int n = TC_BN) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(TC_BM >> 4) << 24);
 }
 
-template <int KIND>
+template <int KIND, int N = TC_BN>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  constexpr uint32_t idesc = instr_desc(KIND == 0 ? 1u : KIND == 1 ? 0u : KIND == 2 ? 0u : 2u);
+  constexpr uint32_t idesc = instr_desc(KIND == 0 ? 1u : KIND == 1 ? 0u : KIND == 2 ? 0u : 2u, N);
   if constexpr (KIND == 0 || KIND == 1) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -152,7 +152,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// KIND: 0 BF16, 1 FP16, 2 E4M3, 3 FP32 as three TF32 products.
+// KIND: 0 BF16, 1 FP16, 2 E4M3, 3 FP32 as three TF32 products.  The FP32
+// kind's accumulator is 256 columns wide: per K step one MMA of A_hi
+// against [B_hi | B_lo] (N = 256: hi*hi into the first 128 columns, hi*lo
+// into the second) and one of A_lo against B_hi into the second; the
+// epilogue adds the two halves.
 // Persistent variant: one CTA per SM walks the work units (target tile,
 // 128 x 128 sub-block; the sub-blocks of one target next to each other) in
 // a fixed round-robin order.  Warp 0 streams K slices through a STAGES-deep
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(192, MINB)
   constexpr int NA = KIND == 3 ? 2 : 1;
   constexpr int STAGE_BYTES = 2 * NA * TC_BUF;
   constexpr int KCH = KIND == 2 ? 128 : KIND == 3 ? 32 : 64;
+  constexpr int ACC_COLS = KIND == 3 ? 2 * TC_BN : TC_BN;   // tensor-memory columns per accumulator
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* stage_c = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);     // 4 x [32][33]
   uint64_t* full = reinterpret_cast<uint64_t*>(stage_c + 4 * 32 * 33);
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(192, MINB)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tslot)),
-                 "r"(2 * TC_BN)
+                 "r"(2 * ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(192, MINB)
         const int buf = t & 1;
         if (t >= 2 && !(ok = mbar_wait(&acce[buf], ((t / 2) - 1) & 1, A.err))) break;
         tc_fence_after();
-        const uint32_t acc_t = tmem + (uint32_t)(buf * TC_BN);
+        const uint32_t acc_t = tmem + (uint32_t)(buf * ACC_COLS);
         for (int kt = 0; kt < KT; ++kt, ++g) {
           const int q = g % STAGES;
           if (!(ok = mbar_wait(&full[q], (g / STAGES) & 1, A.err))) break;
@@ -255,15 +260,16 @@ __global__ void __launch_bounds__(192, MINB)
           const uint32_t a0 = smem_u32(smem + q * STAGE_BYTES);
           const uint32_t a1 = a0 + TC_BUF;
           const uint32_t b0 = a0 + NA * TC_BUF;
-          const uint32_t b1 = b0 + TC_BUF;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t off = kk * 32;
             const uint32_t acc = (kt | kk) != 0;
-            mma<KIND>(acc_t, smem_desc(a0 + off), smem_desc(b0 + off), acc);
-            if (KIND == 3) {
-              mma<KIND>(acc_t, smem_desc(a0 + off), smem_desc(b1 + off), 1);
-              mma<KIND>(acc_t, smem_desc(a1 + off), smem_desc(b0 + off), 1);
+            if constexpr (KIND == 3) {
+              // B_hi and B_lo are adjacent in the slot: one 256-row operand
+              mma<KIND, 2 * TC_BN>(acc_t, smem_desc(a0 + off), smem_desc(b0 + off), acc);
+              mma<KIND>(acc_t + TC_BN, smem_desc(a1 + off), smem_desc(b0 + off), 1);
+            } else {
+              mma<KIND>(acc_t, smem_desc(a0 + off), smem_desc(b0 + off), acc);
             }
           }
           mma_commit(&empty[q]);
@@ -296,7 +302,13 @@ __global__ void __launch_bounds__(192, MINB)
 #pragma unroll 1
       for (int ch = 0; ch < TC_BN / 32; ++ch) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(buf * TC_BN + ch * 32), v);
+        tmem_ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(buf * ACC_COLS + ch * 32), v);
+        if constexpr (KIND == 3) {   // + the hi*lo + lo*hi half
+          float w[32];
+          tmem_ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(buf * ACC_COLS + TC_BN + ch * 32), w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) S[lane][j] = v[j] * sab;
         __syncwarp();
@@ -356,7 +368,7 @@ __global__ void __launch_bounds__(192, MINB)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS)
                  : "memory");
   }
 }
