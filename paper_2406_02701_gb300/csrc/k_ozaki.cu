@@ -30,6 +30,8 @@
 // while both are resident.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "mp_device.cuh"
 
 namespace mp {
@@ -250,35 +252,51 @@ __device__ __forceinline__ int oz_digit_order(int pi) {
   return (pi & 1) ? OZ_S_MAX_ORDER - 1 - (pi >> 1) : (pi >> 1);
 }
 constexpr int OZ_BCH = OZ_BN * 128;        // W digit chunk: 64 rows x 128 bytes
-constexpr int OZ_ASTG = 4;                 // A ring slots
+constexpr int OZ_ASTG = 3;                 // A ring slots
 constexpr int OZ_BSTG = 2;                 // W ring slots (S chunks each)
+constexpr int OZ_STAGE = 32 * 33 * 8;      // epilogue staging per warp (32 x 33 float2 / double)
 
+// Persistent: a work unit is (tile z, 128-row block y, OZ_BN-column block x),
+// x fastest, so that the CTAs working on one row strip of A's digits run
+// side by side; CTA i takes units i, i + gridDim.x, ...  Warp 0 (lane 0)
+// streams the K chunks of W's and A's digits through two rings that run on
+// across units, warp 1 (lane 0) issues the MMAs of a unit once the epilogue
+// has read the previous unit's levels out of tensor memory, and warps 2-5
+// (lane quarter warp % 4) read the levels into float-float registers, hand
+// tensor memory back, then round and store, so one unit's stores overlap
+// the next unit's MMAs.  Barriers: afull/aempty, bfull/bempty per ring slot,
+// accf (a unit's MMAs complete), tfree (levels read, 4 arrivals), fin.
+// Every wait is bounded (on expiry: error word, the roles stop; copies in
+// flight land and issued MMAs complete before tensor memory is freed).
 template <int S>
-__global__ void __launch_bounds__(128, 1)
-    k_oz_gemm(Arena A, const ItemOz* __restrict__ items, const __grid_constant__ CUtensorMap mapA,
-              const __grid_constant__ CUtensorMap mapB) {
+__global__ void __launch_bounds__(192, 1)
+    k_oz_gemm(Arena A, const ItemOz* __restrict__ items, int count,
+              const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB) {
   static_assert(S * OZ_BN <= 512, "levels exceed tensor memory");
   static_assert(S == OZ_S_MAX_ORDER, "digit order table is for S digits");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* bring = smem;                                   // OZ_BSTG x S x OZ_BCH
   uint8_t* aring = bring + OZ_BSTG * S * OZ_BCH;           // OZ_ASTG x OZ_ACH
-  uint64_t* afull = reinterpret_cast<uint64_t*>(aring + OZ_ASTG * OZ_ACH);
+  uint8_t* stage = aring + OZ_ASTG * OZ_ACH;               // 4 x OZ_STAGE
+  uint64_t* afull = reinterpret_cast<uint64_t*>(stage + 4 * OZ_STAGE);
   uint64_t* aempty = afull + OZ_ASTG;
   uint64_t* bfull = aempty + OZ_ASTG;
   uint64_t* bempty = bfull + OZ_BSTG;
   uint64_t* accf = bempty + OZ_BSTG;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
-  // grid (column block, row block, tile): the CTAs that share a row strip of
-  // A's digits run next to each other, so the strip is read from DRAM once
-  const ItemOz it = items[blockIdx.z];
+  uint64_t* tfree = accf + 1;
+  uint64_t* fin = tfree + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   const int b = A.b;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * OZ_BN;
+  const int nnb = b / OZ_BN, nmb = b / 128;
+  const int units = count * nnb * nmb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_ASTG; ++s) { mb_init(&afull[s], 1); mb_init(&aempty[s], 1); }
     for (int s = 0; s < OZ_BSTG; ++s) { mb_init(&bfull[s], 1); mb_init(&bempty[s], 1); }
     mb_init(accf, 1);
+    mb_init(tfree, 4);
+    mb_init(fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
@@ -294,185 +312,213 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   const int KT = b / 64;
-  if (warp == 0 && lane == 0) {
-    // producer: per K chunk, the S chunks of W^T, then the S chunks of A
-    int32_t aidx[S], widx[S];
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: per K chunk, the S chunks of W^T, then the S chunks of A
+      bool ok = true;
+      int na = 0, nb = 0;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const ItemOz& it = items[u / (nnb * nmb)];
+        const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * OZ_BN;
+        int32_t aidx[S], widx[S];
 #pragma unroll
-    for (int p = 0; p < S; ++p) { aidx[p] = A.tiles[it.a[p]].idx; widx[p] = A.tiles[it.w[p]].idx; }
-    bool ok = true;
-    int na = 0, nb = 0;
-    for (int kt = 0; kt < KT && ok; ++kt) {
-      const int sb = kt % OZ_BSTG;
-      if (kt >= OZ_BSTG && !(ok = mb_wait(&bempty[sb], ((kt / OZ_BSTG) - 1) & 1, A.err))) break;
-      mb_expect(&bfull[sb], S * OZ_BCH);
+        for (int p = 0; p < S; ++p) { aidx[p] = A.tiles[it.a[p]].idx; widx[p] = A.tiles[it.w[p]].idx; }
+        for (int kt = 0; kt < KT && ok; ++kt) {
+          const int sb = nb % OZ_BSTG;
+          if (nb >= OZ_BSTG && !(ok = mb_wait(&bempty[sb], ((nb / OZ_BSTG) - 1) & 1, A.err))) break;
+          mb_expect(&bfull[sb], S * OZ_BCH);
 #pragma unroll
-      for (int q = 0; q < S; ++q)
-        tma2d(bring + (sb * S + q) * OZ_BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
-      ++nb;
+          for (int q = 0; q < S; ++q)
+            tma2d(bring + (sb * S + q) * OZ_BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
+          ++nb;
 #pragma unroll 1
-      for (int pi = 0; pi < S; ++pi) {
-        const int p = oz_digit_order(pi);
-        const int i = kt * S + pi, sa = i % OZ_ASTG;
-        if (i >= OZ_ASTG && !(ok = mb_wait(&aempty[sa], ((i / OZ_ASTG) - 1) & 1, A.err))) break;
-        mb_expect(&afull[sa], OZ_ACH);
-        tma2d(aring + sa * OZ_ACH, &mapA, kt * 64, aidx[p] * b + m0, &afull[sa]);
-        ++na;
-      }
-    }
-    if (!ok) {
-      // let the copies in flight land before the CTA exits
-      for (int i = (na > OZ_ASTG ? na - OZ_ASTG : 0); i < na; ++i)
-        mb_wait(&afull[i % OZ_ASTG], (i / OZ_ASTG) & 1, nullptr);
-      for (int k = (nb > OZ_BSTG ? nb - OZ_BSTG : 0); k < nb; ++k)
-        mb_wait(&bfull[k % OZ_BSTG], (k / OZ_BSTG) & 1, nullptr);
-    }
-  } else if (warp == 1 && lane == 0) {
-    bool ok = true;
-    for (int kt = 0; kt < KT && ok; ++kt) {
-      const int sb = kt % OZ_BSTG;
-      if (!(ok = mb_wait(&bfull[sb], (kt / OZ_BSTG) & 1, A.err))) break;
-      const uint32_t b0 = su32(bring + sb * S * OZ_BCH);
-#pragma unroll 1
-      for (int pi = 0; pi < S; ++pi) {
-        const int p = oz_digit_order(pi);
-        const int i = kt * S + pi, sa = i % OZ_ASTG;
-        if (!(ok = mb_wait(&afull[sa], (i / OZ_ASTG) & 1, A.err))) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = su32(aring + sa * OZ_ACH);
-        // A_p against W digits q = 0 .. S-1-p in one product per 256
-        // columns: the digits lie one after another in the ring (OZ_BN rows
-        // each) and level l sits at tensor-memory column l * OZ_BN, so the
-        // product of A_p with digits q0 .. q0+nq-1 lands on levels
-        // p+q0 .. p+q0+nq-1 (fewer, wider MMAs: A_p is read once per 256
-        // columns instead of once per digit)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
-#pragma unroll 1
-          for (int q0 = 0; q0 < S - p; q0 += 256 / OZ_BN) {
-            const int nq = min(256 / OZ_BN, S - p - q0);
-            mma_bf16(tmem + (uint32_t)(p + q0) * OZ_BN, sdesc(a0 + kk * 32),
-                     sdesc(b0 + q0 * OZ_BCH + kk * 32), acc, oz_idesc(nq * OZ_BN));
+          for (int pi = 0; pi < S; ++pi) {
+            const int p = oz_digit_order(pi);
+            const int sa = na % OZ_ASTG;
+            if (na >= OZ_ASTG && !(ok = mb_wait(&aempty[sa], ((na / OZ_ASTG) - 1) & 1, A.err))) break;
+            mb_expect(&afull[sa], OZ_ACH);
+            tma2d(aring + sa * OZ_ACH, &mapA, kt * 64, aidx[p] * b + m0, &afull[sa]);
+            ++na;
           }
         }
-        commit(&aempty[sa]);
       }
-      commit(&bempty[sb]);
+      if (!ok) {
+        // let the copies in flight land before the CTA exits
+        for (int i = (na > OZ_ASTG ? na - OZ_ASTG : 0); i < na; ++i)
+          mb_wait(&afull[i % OZ_ASTG], (i / OZ_ASTG) & 1, nullptr);
+        for (int k = (nb > OZ_BSTG ? nb - OZ_BSTG : 0); k < nb; ++k)
+          mb_wait(&bfull[k % OZ_BSTG], (k / OZ_BSTG) & 1, nullptr);
+      }
     }
-    commit(accf);
-  }
-  __syncwarp();
-  const bool have = mb_wait(accf, 0, A.err);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + lane;
-  const float sg = it.sigma[row];
-  // staging of the warp's 32 x 32 chunk (the ring buffers are free once every
-  // MMA has completed): float64 X, or the scaled float-float pair when fused
-  double (*Sx)[33] = reinterpret_cast<double (*)[33]>(smem + warp * 32 * 33 * sizeof(double));
-  float2 (*Sf)[33] = reinterpret_cast<float2 (*)[33]>(smem + warp * 32 * 33 * sizeof(double));
-  float mx = 0.f;
-  // fused rounding (no E4M3 target or shadow): the tile, its shadow copies
-  // and its TF32 split come straight from the float-float value
-  int tdt = -1, sdt[MAX_SHADOW];
-  char* tdst = nullptr;
-  char* sdst[MAX_SHADOW];
-  float* thi = nullptr;
-  float* tlo = nullptr;
-  if (it.fuse) {
-    tdt = A.tiles[it.tile].dt;
-    tdst = tile_bytes(A, it.tile);
-#pragma unroll
-    for (int q = 0; q < MAX_SHADOW; ++q) {
-      sdt[q] = it.shadow[q] >= 0 ? A.tiles[it.shadow[q]].dt : -1;
-      sdst[q] = it.shadow[q] >= 0 ? tile_bytes(A, it.shadow[q]) : nullptr;
-    }
-    if (it.hi >= 0) { thi = tile_ptr<float>(A, it.hi); tlo = tile_ptr<float>(A, it.lo); }
-  }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      int na = 0, nb = 0, t = 0;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++t) {
+        // the epilogue has read the previous unit's levels
+        if (t >= 1 && !(ok = mb_wait(tfree, (t - 1) & 1, A.err))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kt = 0; kt < KT && ok; ++kt) {
+          const int sb = nb % OZ_BSTG;
+          if (!(ok = mb_wait(&bfull[sb], (nb / OZ_BSTG) & 1, A.err))) break;
+          const uint32_t b0 = su32(bring + sb * S * OZ_BCH);
 #pragma unroll 1
-  for (int h = 0; h < OZ_BN / 32; ++h) {
-    // levels from the smallest (l = S-1) to the largest, in float-float
-    float hi[32], lo[32];
+          for (int pi = 0; pi < S; ++pi) {
+            const int p = oz_digit_order(pi);
+            const int sa = na % OZ_ASTG;
+            if (!(ok = mb_wait(&afull[sa], (na / OZ_ASTG) & 1, A.err))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = su32(aring + sa * OZ_ACH);
+            // A_p against W digits q = 0 .. S-1-p in one product per 256
+            // columns: the digits lie one after another in the ring (OZ_BN
+            // rows each) and level l sits at tensor-memory column l * OZ_BN,
+            // so the product of A_p with digits q0 .. q0+nq-1 lands on levels
+            // p+q0 .. p+q0+nq-1 (A_p is read once per 256 columns)
 #pragma unroll
-    for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
 #pragma unroll 1
-    for (int l = S - 1; l >= 0; --l) {
-      float v[32];
-      ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(l * OZ_BN + h * 32), v);
-      const float scl = ldexpf(1.f, -6 * (l + 2));
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float x = v[j] * scl;             // exact: the level sum is an integer < 2^24
-        const float s = hi[j] + x;              // two-sum
-        const float bb = s - hi[j];
-        const float e = (hi[j] - (s - bb)) + (x - bb);
-        hi[j] = s;
-        lo[j] += e;
+              for (int q0 = 0; q0 < S - p; q0 += 256 / OZ_BN) {
+                const int nq = min(256 / OZ_BN, S - p - q0);
+                mma_bf16(tmem + (uint32_t)(p + q0) * OZ_BN, sdesc(a0 + kk * 32),
+                         sdesc(b0 + q0 * OZ_BCH + kk * 32), acc, oz_idesc(nq * OZ_BN));
+              }
+            }
+            commit(&aempty[sa]);
+            ++na;
+          }
+          if (!ok) break;
+          commit(&bempty[sb]);
+          ++nb;
+        }
+        if (!ok) break;
+        commit(accf);
       }
+      // every MMA issued has completed before tensor memory is freed
+      commit(fin);
+      mb_wait(fin, 0, A.err);
     }
-    if (!have) continue;
-    if (it.fuse) {
+  } else {
+    // epilogue warps 2-5: lane quarter qr = warp % 4 of the accumulator
+    const int qr = warp & 3;
+    double (*Sx)[33] = reinterpret_cast<double (*)[33]>(stage + (warp - 2) * OZ_STAGE);
+    float2 (*Sf)[33] = reinterpret_cast<float2 (*)[33]>(stage + (warp - 2) * OZ_STAGE);
+    int t = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++t) {
+      const ItemOz it = items[u / (nnb * nmb)];
+      const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * OZ_BN;
+      if (!mb_wait(accf, t & 1, A.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // levels from the smallest (l = S-1) to the largest, in float-float
+      float hi[OZ_BN], lo[OZ_BN];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float st = sg * it.tau[n0 + h * 32 + j];   // power of two: scaling is exact
-        Sf[lane][j] = make_float2(hi[j] * st, lo[j] * st);
+      for (int j = 0; j < OZ_BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+#pragma unroll 1
+      for (int l = S - 1; l >= 0; --l) {
+        const float scl = ldexpf(1.f, -6 * (l + 2));
+#pragma unroll
+        for (int h = 0; h < OZ_BN / 32; ++h) {
+          float v[32];
+          ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(l * OZ_BN + h * 32), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float x = v[j] * scl;           // exact: the level sum is an integer < 2^24
+            const float s = hi[h * 32 + j] + x;   // two-sum
+            const float bb = s - hi[h * 32 + j];
+            const float e = (hi[h * 32 + j] - (s - bb)) + (x - bb);
+            hi[h * 32 + j] = s;
+            lo[h * 32 + j] += e;
+          }
+        }
       }
+      // tensor memory read: the next unit's MMAs may start
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tfree)) : "memory");
+      const int row = m0 + qr * 32 + lane;
+      const float sg = it.sigma[row];
+      float mx = 0.f;
+      // fused rounding (no E4M3 target or shadow): the tile, its shadow
+      // copies and its TF32 split come straight from the float-float value
+      int tdt = -1, sdt[MAX_SHADOW];
+      char* tdst = nullptr;
+      char* sdst[MAX_SHADOW];
+      float* thi = nullptr;
+      float* tlo = nullptr;
+      if (it.fuse) {
+        tdt = A.tiles[it.tile].dt;
+        tdst = tile_bytes(A, it.tile);
+#pragma unroll
+        for (int q = 0; q < MAX_SHADOW; ++q) {
+          sdt[q] = it.shadow[q] >= 0 ? A.tiles[it.shadow[q]].dt : -1;
+          sdst[q] = it.shadow[q] >= 0 ? tile_bytes(A, it.shadow[q]) : nullptr;
+        }
+        if (it.hi >= 0) { thi = tile_ptr<float>(A, it.hi); tlo = tile_ptr<float>(A, it.lo); }
+      }
+#pragma unroll
+      for (int h = 0; h < OZ_BN / 32; ++h) {
+        if (it.fuse) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float st = sg * it.tau[n0 + h * 32 + j];   // power of two: scaling is exact
+            Sf[lane][j] = make_float2(hi[h * 32 + j] * st, lo[h * 32 + j] * st);
+          }
+          __syncwarp();
 #pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const float2 p = Sf[rr][lane];
-        const int64_t o = (int64_t)(m0 + warp * 32 + rr) * b + n0 + h * 32 + lane;
-        float stored;
-        if (tdt == F32) {
-          stored = __fadd_rn(p.x, p.y);              // the float-float value rounded once
-          reinterpret_cast<float*>(tdst)[o] = stored;
+          for (int rr = 0; rr < 32; ++rr) {
+            const float2 p = Sf[rr][lane];
+            const int64_t o = (int64_t)(m0 + qr * 32 + rr) * b + n0 + h * 32 + lane;
+            float stored;
+            if (tdt == F32) {
+              stored = __fadd_rn(p.x, p.y);              // the float-float value rounded once
+              reinterpret_cast<float*>(tdst)[o] = stored;
+            } else {
+              store_round(tdst, tdt, o, (double)p.x + (double)p.y);
+              stored = load_f32(tdst, tdt, o);
+            }
+#pragma unroll
+            for (int q = 0; q < MAX_SHADOW; ++q)
+              if (sdst[q]) store_round_f32(sdst[q], sdt[q], o, stored);
+            if (thi) {
+              uint32_t hb;
+              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(stored));
+              thi[o] = __uint_as_float(hb);
+              tlo[o] = stored - __uint_as_float(hb);
+            }
+          }
+          __syncwarp();
         } else {
-          store_round(tdst, tdt, o, (double)p.x + (double)p.y);
-          stored = load_f32(tdst, tdt, o);
-        }
 #pragma unroll
-        for (int q = 0; q < MAX_SHADOW; ++q)
-          if (sdst[q]) store_round_f32(sdst[q], sdt[q], o, stored);
-        if (thi) {
-          uint32_t hb;
-          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(stored));
-          thi[o] = __uint_as_float(hb);
-          tlo[o] = stored - __uint_as_float(hb);
-        }
-      }
-      __syncwarp();
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float st = sg * it.tau[n0 + h * 32 + j];
-        Sx[lane][j] = (double)(hi[j] * st) + (double)(lo[j] * st);
-      }
-      __syncwarp();
+          for (int j = 0; j < 32; ++j) {
+            const float st = sg * it.tau[n0 + h * 32 + j];
+            Sx[lane][j] = (double)(hi[h * 32 + j] * st) + (double)(lo[h * 32 + j] * st);
+          }
+          __syncwarp();
 #pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const double xv = Sx[rr][lane];
-        it.x[(int64_t)(m0 + warp * 32 + rr) * b + n0 + h * 32 + lane] = xv;
-        mx = fmaxf(mx, fabsf((float)xv));
+          for (int rr = 0; rr < 32; ++rr) {
+            const double xv = Sx[rr][lane];
+            it.x[(int64_t)(m0 + qr * 32 + rr) * b + n0 + h * 32 + lane] = xv;
+            mx = fmaxf(mx, fabsf((float)xv));
+          }
+          __syncwarp();
+        }
       }
-      __syncwarp();
+      if (!it.fuse) {
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomic_max_pos(&A.amax[it.amax], (double)mx);
+      }
     }
   }
-  __shared__ float red[4];
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) red[warp] = mx;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 4; ++w) mx = fmaxf(mx, red[w]);
-    atomic_max_pos(&A.amax[it.amax], (double)mx);
-  }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 template <int S>
 constexpr size_t oz_smem() {
-  return (size_t)OZ_BSTG * S * OZ_BCH + (size_t)OZ_ASTG * OZ_ACH +
-         8 * (2 * OZ_ASTG + 2 * OZ_BSTG + 1) + 16 + 1024;
+  return (size_t)OZ_BSTG * S * OZ_BCH + (size_t)OZ_ASTG * OZ_ACH + 4 * (size_t)OZ_STAGE +
+         8 * (2 * OZ_ASTG + 2 * OZ_BSTG + 3) + 16 + 1024;
 }
 
 }  // namespace
@@ -500,7 +546,15 @@ void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const CUtens
     cudaFuncSetAttribute(k_oz_gemm<OZ_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_oz_gemm<OZ_S><<<dim3(A.b / OZ_BN, A.b / 128, count), 128, smem, s>>>(A, items, mapA, mapB);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int64_t units = (int64_t)count * (A.b / OZ_BN) * (A.b / 128);
+  const int grid = (int)std::min<int64_t>(units, sms);
+  k_oz_gemm<OZ_S><<<grid, 192, smem, s>>>(A, items, count, mapA, mapB);
 }
 
 }  // namespace mp
