@@ -315,6 +315,33 @@ def test_mixed_loglik_matches_oracle(ctx, far, refine, ozaki):
         assert np.all(err_gpu < 1e-4)
 
 
+@pytest.mark.parametrize("far,refine,ozaki", [(I.BF16, 10, True), (I.BF16, 10, False), (I.F32, 0, True)])
+def test_mixed_loglik_matches_oracle_b384(ctx, far, refine, ozaki):
+    """b = 384: the diagonal tiles factor as task graphs over 16 x 16 blocks
+    (32 x 32 below b = 384); 6 tiles, 304 padding rows."""
+    n, b = 2000, 384
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, far, 2)
+    a = 0.1 if not refine else 0.03
+    locs, _ = OM.morton_order(I.points(n, 37))
+    z = I.rhs(n, 2, 37)
+    S = OM.covariance(locs, 0.5, a, 1.0, 1e-4)
+    ex = OC.exact_loglik(S, z)
+    tl = OC.tiled_loglik(S, z, b, pmap, refine_iters=refine)
+    r = _run(ctx, n, b, pmap, locs, z, 0.5, a, 1.0, 1e-4, refine=refine, ozaki=ozaki)
+    assert r["info"] == 0
+    err_gpu = np.abs(r["ll"] - ex["loglik"]) / np.abs(ex["loglik"])
+    tol = np.maximum(10 * err_gpu, 1e-9)
+    assert np.all(np.abs(r["ll"] - tl["loglik"]) / np.abs(tl["loglik"]) <= tol)
+    ld_err = abs(r["logdet"] - ex["logdet"]) / abs(ex["logdet"])
+    assert math.isclose(r["logdet"], tl["logdet"], rel_tol=max(1e-9, 10 * ld_err))
+    if refine:
+        assert np.all(tl["iters"] < refine)
+        assert np.all(np.abs(r["iters"] - tl["iters"]) <= 1)
+        assert np.allclose(r["quad"], ex["quad"], rtol=1e-10)
+        assert np.all(err_gpu < 1e-4)
+
+
 def test_trsm_forward_backward(ctx):
     """mp_trsm against the oracle's tiled solves applied to the GPU's own
     factor (downloaded tile by tile), so only the solve is compared."""
@@ -343,11 +370,14 @@ def test_trsm_forward_backward(ctx):
         assert np.allclose(Bt.cpu().numpy().T, ref[:n], rtol=1e-11, atol=1e-11 * np.abs(ref).max())
 
 
-def test_not_spd_reports_first_bad_row(ctx):
-    n, b = 512, 128
+@pytest.mark.parametrize("n,b,bad", [(512, 128, 300), (768, 384, 401)])
+def test_not_spd_reports_first_bad_row(ctx, n, b, bad):
+    """b = 128: 32 x 32 blocks; b = 384: 16 x 16 blocks (row 401 is column
+    1 of the second block of the second diagonal tile)."""
     T = _mk(ctx, n, b, None)
     d = np.ones(n)
-    d[300] = -2.0
+    d[bad] = -2.0
+    d[bad + 40] = -1.0           # a later failure must not mask the first
     for i in range(n // b):
         for j in range(i + 1):
             blk = np.zeros((b, b))
@@ -356,9 +386,9 @@ def test_not_spd_reports_first_bad_row(ctx):
             T.set_tile(i, j, blk)
     info, _ = T.chol()
     torch.cuda.synchronize()
-    assert int(info.item()) == 301
+    assert int(info.item()) == bad + 1
     _, oinfo = OC.potrf_textbook(np.diag(d))
-    assert oinfo == 301
+    assert oinfo == bad + 1
 
 
 @pytest.mark.parametrize("dt", [I.F64, I.F32, I.BF16, I.F16, I.E4M3])
