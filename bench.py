@@ -178,7 +178,7 @@ def measured_peaks():
 # dram__bytes_write.sum from one ncu capture of the kernel as it is now on
 # this workload (kernel -> bytes); absent where no capture of the current
 # kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1210368 + 2560}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1269760 + 2816}
 
 
 def kernel_rooflines(prof, chol_ms, peak64, b):
