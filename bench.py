@@ -195,7 +195,7 @@ def kernel_rooflines(prof, chol_ms, peak64, b):
                        "inverse b^3/3 per diagonal tile"),
         "panel_trsm_first": ("k_panel_trsm (chain)", "alu", peak64, "FP64 DFMA loop probe in this run"),
         "panel_trsm": ("k_panel_trsm (bulk)", "alu", peak64, "FP64 DFMA loop probe in this run"),
-        "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 MMAs)", "tensor", tf32x3,
+        "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 products)", "tensor", tf32x3,
                              f"bf16_tflops_sustained {which} x 1.1/2.25 / 3"),
         "update_tc_lowp": ("k_update_tc_p (BF16/FP16/E4M3 kinds)", "tensor", bf16,
                            f"bf16_tflops_sustained {which}"),
