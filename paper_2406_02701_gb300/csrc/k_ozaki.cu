@@ -5,9 +5,12 @@
 //
 //   rows of A:    a = sigma_r sum_p d_p 2^(-6(p+1)),  p < S
 //   columns of W: w = tau_c   sum_q e_q 2^(-6(q+1)),  q < S
-// with sigma_r, tau_c powers of two bounding the row / column and the
-// digits taken by rounding to nearest: |d_0| <= 64, every later digit
-// <= 32, so a digit is an integer of at most 7 bits, exact in BF16.  For one
+// with sigma_r, tau_c powers of two bounding the row / column; the digits
+// represent the entry rounded to the nearest multiple of 2^(-6S) (ties to
+// even) with |d_0| <= 64 and every later digit <= 32, so a digit is an
+// integer of at most 7 bits, exact in BF16 (A: S steps d = rint(64 r) on
+// the FP32 pipe; W: the balanced base-64 digits of rint(w 2^(6S) / tau_c)
+// in integer arithmetic -- the same represented value).  For one
 // level l = p + q the products d_p e_q summed over K = b are integers of
 // magnitude at most K 2^12 (l = 0) or K (l + 3) 2^10 (l >= 1); for S = 8 and
 // K <= 1024 that is below 2^24, so every level accumulates exactly in an
@@ -23,11 +26,12 @@
 // bounds sit far below the FP32/BF16 rounding the panel result then
 // receives.
 //
-// Data movement of the product (one CTA = 128 rows x 64 columns of X):
-// per K chunk of 64, the S digit chunks of W^T (S x 8 KB) are loaded once
-// into a two-slot ring and the S digit chunks of A (16 KB each) stream
-// through a four-slot ring; every A chunk meets all W chunks it pairs with
-// while both are resident.
+// Data movement of the product (one work unit = 128 rows x 64 columns of
+// X; persistent CTAs walk the units): per K chunk of 64, the S digit chunks
+// of W^T (S x 8 KB, adjacent in shared memory) are loaded once into a
+// two-slot ring and the S digit chunks of A (16 KB each) stream through a
+// three-slot ring; A_p meets the W digits 0 .. S-1-p it pairs with in one
+// MMA per 256 columns, whose output columns are exactly levels p .. S-1.
 #include <cuda.h>
 
 #include <algorithm>

@@ -5,13 +5,17 @@
 //   E4M3         kind::f8f6f4  scaled codes; FP32 sum times s_a s_b
 //   FP32         kind::tf32    three products of hi/lo splits,
 //                              A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
-//                              where hi = A rounded to TF32 and lo = A - hi
+//                              where hi = A rounded to TF32 and lo = A - hi,
+//                              in two MMAs per K step (A_hi against
+//                              [B_hi | B_lo] with N = 256, A_lo against B_hi)
+//                              into a 256-column accumulator whose halves
+//                              the epilogue adds
 // A work unit is a 128 x 128 sub-tile of a target with the full contraction
 // K = b; one persistent CTA per SM runs units back to back.  Warp 0 (one
 // lane) streams 128-byte-wide K slices of the operand tiles into shared
 // memory with TMA (128-byte swizzle, one tensor map per format pool; no
-// multicast), warp 1 (one lane) issues the MMAs into one of two 128-column
-// FP32 accumulators in tensor memory, and warps 2-5 read the other one back
+// multicast), warp 1 (one lane) issues the MMAs into one of two FP32
+// accumulators in tensor memory, and warps 2-5 read the other one back
 // (each its lane quarter) and apply the update to the target tile in global
 // memory:
 //   FP64 target (SYRK into the diagonal)  C -= acc            (float64)
