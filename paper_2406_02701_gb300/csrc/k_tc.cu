@@ -296,6 +296,19 @@ __global__ void __launch_bounds__(192, MINB)
       int rb, cb;
       if (!unit(u, it, rb, cb)) continue;
       const int buf = t & 1;
+      {
+        // pull this lane quarter's 32 target rows into L2 while the unit's
+        // MMAs run (the read-modify-write below then meets no DRAM latency)
+        const TileRef rp = A.tiles[it.c];
+        const char* base = tile_bytes(A, it.c);
+        const int es = (int)esize(rp.dt);
+        const int lpr = TC_BN * es / 128;              // 128-byte lines per row
+        const int64_t r0 = (int64_t)rb * TC_BM + qr * 32;
+        for (int e = lane; e < 32 * lpr; e += 32) {
+          const char* ptr = base + ((r0 + e / lpr) * b + cb * TC_BN) * es + (e % lpr) * 128;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+        }
+      }
       if (!mbar_wait(&accf[buf], (t / 2) & 1, A.err)) break;
       tc_fence_after();
       const TileRef rc = A.tiles[it.c];
