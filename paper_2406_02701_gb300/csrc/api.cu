@@ -140,6 +140,7 @@ struct Plan {
   float* d_sigma = nullptr;        // row bounds per panel slot (b each)
   float* d_tau = nullptr;          // column bounds per parity x matrix (b each)
   CUtensorMap tmap_bf16_64;        // BF16 pool, box 128 bytes x 64 rows (digit products)
+  CUtensorMap tmap_bf16_32;        // BF16 pool, box 128 bytes x 32 rows (single-tile digit products)
   // operand forms of the panel tiles, per panel slot of a step
   std::vector<std::array<int32_t, NDT>> slot_shadow;
   std::vector<int32_t> slot_hi, slot_lo;
@@ -723,6 +724,11 @@ mp_status make_tensor_maps(Plan& P) {
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return fail(P.ctx, MP_ERR_CUDA, "tensor map (64 rows): error %d", (int)r);
+      cuuint32_t box32[2] = {(cuuint32_t)(128 / es), 32};
+      r = encode(&P.tmap_bf16_32, ty, 2, P.pool[d], dims, strides, box32, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(P.ctx, MP_ERR_CUDA, "tensor map (32 rows): error %d", (int)r);
     }
   }
   return MP_OK;
@@ -894,7 +900,7 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
     case OP_OZA: launch_oz_split_rows(A, P.item<ItemOzA>(L.off), L.count, s); break;
     case OP_OZW: launch_oz_split_cols(A, P.item<ItemOzW>(L.off), L.count, s); break;
     case OP_OZG:
-      launch_oz_gemm(A, P.item<ItemOz>(L.off), L.count, P.tmap[BF16], P.tmap_bf16_64, s);
+      launch_oz_gemm(A, P.item<ItemOz>(L.off), L.count, P.tmap[BF16], P.tmap_bf16_64, P.tmap_bf16_32, s);
       break;
     case OP_REC: if (s2) cudaEventRecord(P.events[L.count], s); break;
     case OP_WAIT: if (s2) cudaStreamWaitEvent(s, P.events[L.count], 0); break;

@@ -42,7 +42,6 @@ namespace mp {
 
 namespace {
 
-constexpr int OZ_BN = 64;                  // output columns per CTA
 constexpr int OZ_S_MAX_ORDER = 8;          // digits per operand (the kernels' S)
 constexpr uint32_t OZ_WAIT_LIMIT = 1u << 22;
 
@@ -255,12 +254,11 @@ constexpr int OZ_ACH = 128 * 128;          // A digit chunk: 128 rows x 128 byte
 __device__ __forceinline__ int oz_digit_order(int pi) {
   return (pi & 1) ? OZ_S_MAX_ORDER - 1 - (pi >> 1) : (pi >> 1);
 }
-constexpr int OZ_BCH = OZ_BN * 128;        // W digit chunk: 64 rows x 128 bytes
 constexpr int OZ_ASTG = 3;                 // A ring slots
 constexpr int OZ_BSTG = 2;                 // W ring slots (S chunks each)
 constexpr int OZ_STAGE = 32 * 33 * 8;      // epilogue staging per warp (32 x 33 float2 / double)
 
-// Persistent: a work unit is (tile z, 128-row block y, OZ_BN-column block x),
+// Persistent: a work unit is (tile z, 128-row block y, BN-column block x),
 // x fastest, so that the CTAs working on one row strip of A's digits run
 // side by side; CTA i takes units i, i + gridDim.x, ...  Warp 0 (lane 0)
 // streams the K chunks of W's and A's digits through two rings that run on
@@ -272,16 +270,18 @@ constexpr int OZ_STAGE = 32 * 33 * 8;      // epilogue staging per warp (32 x 33
 // accf (a unit's MMAs complete), tfree (levels read, 4 arrivals), fin.
 // Every wait is bounded (on expiry: error word, the roles stop; copies in
 // flight land and issued MMAs complete before tensor memory is freed).
-template <int S>
+template <int S, int BN>
 __global__ void __launch_bounds__(192, 1)
     k_oz_gemm(Arena A, const ItemOz* __restrict__ items, int count,
               const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB) {
-  static_assert(S * OZ_BN <= 512, "levels exceed tensor memory");
+  static_assert(S * BN <= 512 && (S * BN) % 32 == 0, "levels exceed tensor memory");
+  constexpr int BCH = BN * 128;            // W digit chunk: BN rows x 128 bytes
+  constexpr uint32_t TCOLS = S * BN;       // tensor-memory columns (a power of two)
   static_assert(S == OZ_S_MAX_ORDER, "digit order table is for S digits");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* bring = smem;                                   // OZ_BSTG x S x OZ_BCH
-  uint8_t* aring = bring + OZ_BSTG * S * OZ_BCH;           // OZ_ASTG x OZ_ACH
+  uint8_t* bring = smem;                                   // OZ_BSTG x S x BCH
+  uint8_t* aring = bring + OZ_BSTG * S * BCH;           // OZ_ASTG x OZ_ACH
   uint8_t* stage = aring + OZ_ASTG * OZ_ACH;               // 4 x OZ_STAGE
   uint64_t* afull = reinterpret_cast<uint64_t*>(stage + 4 * OZ_STAGE);
   uint64_t* aempty = afull + OZ_ASTG;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* fin = tfree + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   const int b = A.b;
-  const int nnb = b / OZ_BN, nmb = b / 128;
+  const int nnb = b / BN, nmb = b / 128;
   const int units = count * nnb * nmb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "r"(512)
+                 "r"(TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -323,17 +323,17 @@ __global__ void __launch_bounds__(192, 1)
       int na = 0, nb = 0;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const ItemOz& it = items[u / (nnb * nmb)];
-        const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * OZ_BN;
+        const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * BN;
         int32_t aidx[S], widx[S];
 #pragma unroll
         for (int p = 0; p < S; ++p) { aidx[p] = A.tiles[it.a[p]].idx; widx[p] = A.tiles[it.w[p]].idx; }
         for (int kt = 0; kt < KT && ok; ++kt) {
           const int sb = nb % OZ_BSTG;
           if (nb >= OZ_BSTG && !(ok = mb_wait(&bempty[sb], ((nb / OZ_BSTG) - 1) & 1, A.err))) break;
-          mb_expect(&bfull[sb], S * OZ_BCH);
+          mb_expect(&bfull[sb], S * BCH);
 #pragma unroll
           for (int q = 0; q < S; ++q)
-            tma2d(bring + (sb * S + q) * OZ_BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
+            tma2d(bring + (sb * S + q) * BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
           ++nb;
 #pragma unroll 1
           for (int pi = 0; pi < S; ++pi) {
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int kt = 0; kt < KT && ok; ++kt) {
           const int sb = nb % OZ_BSTG;
           if (!(ok = mb_wait(&bfull[sb], (nb / OZ_BSTG) & 1, A.err))) break;
-          const uint32_t b0 = su32(bring + sb * S * OZ_BCH);
+          const uint32_t b0 = su32(bring + sb * S * BCH);
 #pragma unroll 1
           for (int pi = 0; pi < S; ++pi) {
             const int p = oz_digit_order(pi);
@@ -374,18 +374,18 @@ __global__ void __launch_bounds__(192, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = su32(aring + sa * OZ_ACH);
             // A_p against W digits q = 0 .. S-1-p in one product per 256
-            // columns: the digits lie one after another in the ring (OZ_BN
-            // rows each) and level l sits at tensor-memory column l * OZ_BN,
+            // columns: the digits lie one after another in the ring (BN
+            // rows each) and level l sits at tensor-memory column l * BN,
             // so the product of A_p with digits q0 .. q0+nq-1 lands on levels
             // p+q0 .. p+q0+nq-1 (A_p is read once per 256 columns)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
 #pragma unroll 1
-              for (int q0 = 0; q0 < S - p; q0 += 256 / OZ_BN) {
-                const int nq = min(256 / OZ_BN, S - p - q0);
-                mma_bf16(tmem + (uint32_t)(p + q0) * OZ_BN, sdesc(a0 + kk * 32),
-                         sdesc(b0 + q0 * OZ_BCH + kk * 32), acc, oz_idesc(nq * OZ_BN));
+              for (int q0 = 0; q0 < S - p; q0 += 256 / BN) {
+                const int nq = min(256 / BN, S - p - q0);
+                mma_bf16(tmem + (uint32_t)(p + q0) * BN, sdesc(a0 + kk * 32),
+                         sdesc(b0 + q0 * BCH + kk * 32), acc, oz_idesc(nq * BN));
               }
             }
             commit(&aempty[sa]);
@@ -410,20 +410,20 @@ __global__ void __launch_bounds__(192, 1)
     int t = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x, ++t) {
       const ItemOz it = items[u / (nnb * nmb)];
-      const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * OZ_BN;
+      const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * BN;
       if (!mb_wait(accf, t & 1, A.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // levels from the smallest (l = S-1) to the largest, in float-float
-      float hi[OZ_BN], lo[OZ_BN];
+      float hi[BN], lo[BN];
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+      for (int j = 0; j < BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
 #pragma unroll 1
       for (int l = S - 1; l >= 0; --l) {
         const float scl = ldexpf(1.f, -6 * (l + 2));
 #pragma unroll
-        for (int h = 0; h < OZ_BN / 32; ++h) {
+        for (int h = 0; h < BN / 32; ++h) {
           float v[32];
-          ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(l * OZ_BN + h * 32), v);
+          ld32(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(l * BN + h * 32), v);
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float x = v[j] * scl;           // exact: the level sum is an integer < 2^24
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(192, 1)
         if (it.hi >= 0) { thi = tile_ptr<float>(A, it.hi); tlo = tile_ptr<float>(A, it.lo); }
       }
 #pragma unroll
-      for (int h = 0; h < OZ_BN / 32; ++h) {
+      for (int h = 0; h < BN / 32; ++h) {
         if (it.fuse) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -516,12 +516,12 @@ __global__ void __launch_bounds__(192, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
-template <int S>
+template <int S, int BN>
 constexpr size_t oz_smem() {
-  return (size_t)OZ_BSTG * S * OZ_BCH + (size_t)OZ_ASTG * OZ_ACH + 4 * (size_t)OZ_STAGE +
+  return (size_t)OZ_BSTG * S * BN * 128 + (size_t)OZ_ASTG * OZ_ACH + 4 * (size_t)OZ_STAGE +
          8 * (2 * OZ_ASTG + 2 * OZ_BSTG + 3) + 16 + 1024;
 }
 
@@ -541,24 +541,32 @@ void launch_oz_split_cols(const Arena& A, const ItemOzW* items, int count, cudaS
   k_oz_split_cols<OZ_S><<<dim3(count, A.b / 32, A.b / 64), 256, 0, s>>>(A, items);
 }
 
-void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const CUtensorMap& mapA,
+template <int BN>
+void oz_gemm_launch(const Arena& A, const ItemOz* items, int count, const CUtensorMap& mapA,
                     const CUtensorMap& mapB, cudaStream_t s) {
-  if (count <= 0) return;
-  constexpr size_t smem = oz_smem<OZ_S>();
+  constexpr size_t smem = oz_smem<OZ_S, BN>();
   static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_oz_gemm<OZ_S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
   static int sms = 0;
-  if (!sms) {
+  if (!attr) {
+    cudaFuncSetAttribute(k_oz_gemm<OZ_S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    attr = true;
   }
-  const int64_t units = (int64_t)count * (A.b / OZ_BN) * (A.b / 128);
+  const int64_t units = (int64_t)count * (A.b / BN) * (A.b / 128);
   const int grid = (int)std::min<int64_t>(units, sms);
-  k_oz_gemm<OZ_S><<<grid, 192, smem, s>>>(A, items, count, mapA, mapB);
+  k_oz_gemm<OZ_S, BN><<<grid, 192, smem, s>>>(A, items, count, mapA, mapB);
+}
+
+// One tile (the critical chain's first panel tile): 128 x 32 units, twice as
+// many CTAs as 128 x 64 units; several tiles: 128 x 64 units (fewer, wider
+// MMAs per output column).
+void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const CUtensorMap& mapA,
+                    const CUtensorMap& mapB64, const CUtensorMap& mapB32, cudaStream_t s) {
+  if (count <= 0) return;
+  if (count == 1) oz_gemm_launch<32>(A, items, count, mapA, mapB32, s);
+  else oz_gemm_launch<64>(A, items, count, mapA, mapB64, s);
 }
 
 }  // namespace mp

@@ -254,7 +254,8 @@ int oz_slices(int b);
 void launch_oz_split_rows(const Arena& A, const ItemOzA* items, int count, cudaStream_t s);
 void launch_oz_split_cols(const Arena& A, const ItemOzW* items, int count, cudaStream_t s);
 void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const struct CUtensorMap_st& mapA,
-                    const struct CUtensorMap_st& mapB, cudaStream_t s);
+                    const struct CUtensorMap_st& mapB64, const struct CUtensorMap_st& mapB32,
+                    cudaStream_t s);
 
 // k_tc.cu (kind: BF16, F16, E4M3, or F32 as three TF32 products; the map
 // is a const CUtensorMap& of the operands' pool)
