@@ -11,9 +11,9 @@
 // table-driven method (fewer FP64 operations than the general exp; the
 // kernel is bound by the FP64 pipe).  E4M3 tiles first get
 // the tile's amax from a separate pass (`gen_amax`), then the power-of-two
-// scale.  Rows/columns beyond n are identity padding.  The distance is
-// written with explicit _rn intrinsics (no contraction into fused
-// multiply-adds); the polynomial and exp use fused multiply-adds on purpose.
+// scale.  Rows/columns beyond n are identity padding.  The coordinate
+// differences are written with explicit _rn intrinsics; the squared
+// distance, the polynomial and exp use fused multiply-adds on purpose.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -24,10 +24,10 @@ namespace mp {
 
 namespace {
 
-// e^{-x} tables (set per device by init_gen_tables): [0, 32) 2^{j/32}
-// rounded to double, [32, 64) the remainders 2^{j/32} - hi, [64] the head of
-// ln2/32 with 37 significant bits, [65] ln2/32 - head, [66] 32/ln2.
-constexpr int GEN_TAB = 67;
+// e^{-x} tables (set per device by init_gen_tables): [0, 64) 2^{j/64}
+// rounded to double, [64, 128) the remainders 2^{j/64} - hi, [128] the head
+// of ln2/64 with 37 significant bits, [129] ln2/64 - head, [130] 64/ln2.
+constexpr int GEN_TAB = 131;
 __constant__ double c_gen_tab[GEN_TAB];
 
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
@@ -95,25 +95,25 @@ __global__ void k_morton_gather(const unsigned long long* __restrict__ keys,
 
 // e^{-x} for x >= 0 by Tang's table-driven method (P. T. P. Tang,
 // "Table-driven implementation of the exponential function in IEEE
-// floating-point arithmetic", ACM TOMS 15, 1989): -x = k ln2/32 + r with
-// k = rint(-32 x / ln2) and |r| <= ln2/64 (k times the 37-bit head of
-// ln2/32 is exact for |k| < 2^16, i.e. x <= 700); k = 32 m + j and
-// e^{-x} = 2^m 2^{j/32} (1 + p), p = e^r - 1 from its Taylor polynomial of
-// degree 6 (truncation below r^7/7! < 4e-18), 2^{j/32} = T_hi + T_lo, the
-// sum T_hi + (T_lo + T_hi p) rounded once: about 0.55 ulp.  Beyond 700 (and
-// for NaN) the library exp.
+// floating-point arithmetic", ACM TOMS 15, 1989) with a 64-entry table:
+// -x = k ln2/64 + r with k = rint(-64 x / ln2) and |r| <= ln2/128 (k times
+// the 37-bit head of ln2/64 is exact for |k| < 2^16, i.e. x <= 700);
+// k = 64 m + j and e^{-x} = 2^m 2^{j/64} (1 + p), p = e^r - 1 from its
+// Taylor polynomial of degree 5 (truncation below r^6/6! < 4e-17),
+// 2^{j/64} = T_hi + T_lo, the sum T_hi + (T_lo + T_hi p) rounded once:
+// within 0.8 ulp.  Beyond 700 (and for NaN) the library exp.
 __device__ __forceinline__ double exp_neg(double x, const double* tab) {
   if (!(x <= 700.0)) return exp(-x);
   const double shifter = 6755399441055744.0;           // 1.5 * 2^52
-  const double t = fma(-x, tab[66], shifter);           // low bits: k
+  const double t = fma(-x, tab[130], shifter);          // low bits: k
   const int k = __double2loint(t);
   const double kd = t - shifter;
-  const double r = fma(-kd, tab[65], fma(-kd, tab[64], -x));
-  const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
+  const double r = fma(-kd, tab[129], fma(-kd, tab[128], -x));
+  const double q = fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5);
   const double p = fma(r * r, q, r);
-  const int m = k >> 5, j = k & 31;
+  const int m = k >> 6, j = k & 63;
   const double th = tab[j];
-  const double v = th + fma(th, p, tab[32 + j]);   // in [0.98, 2.03]
+  const double v = th + fma(th, p, tab[64 + j]);   // in [0.99, 2.02]
   // times 2^m (m >= -1010: the result stays normal) on the exponent field
   return __longlong_as_double(__double_as_longlong(v) + ((long long)m << 52));
 }
@@ -121,8 +121,8 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
 // Matérn covariance of two locations (closed forms, x = r / range):
 // sigma^2 e^{-x} (nu = 1/2), sigma^2 (1 + x) e^{-x} (3/2),
 // sigma^2 (1 + x + x^2/3) e^{-x} (5/2).
-// r = s rsqrt(s) for s = dx^2 + dy^2 > 0 (rsqrt within 1 ulp: r within
-// 1.5 ulp); x is r times the rounded reciprocal of the range (GB300's FP64
+// r = s rsqrt(s) for s = dx^2 + dy^2 > 0 (one fused multiply-add; rsqrt
+// within 1 ulp: r within 1.5 ulp); x is r times the rounded reciprocal of the range (GB300's FP64
 // pipe makes a division cost about ten FP64 operations): |dx| <= 3 ulp(x),
 // which exp(-x) carries as a relative error of at most 3 x 2^-53.
 __device__ __forceinline__ double entry(const ItemGen& it, double inv_range, const double* tab,
@@ -130,7 +130,7 @@ __device__ __forceinline__ double entry(const ItemGen& it, double inv_range, con
                                         int64_t gj) {
   if (gi >= it.n || gj >= it.n) return gi == gj ? 1.0 : 0.0;
   double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
-  const double s2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  const double s2 = fma(dx, dx, __dmul_rn(dy, dy));
   double r = s2 > 0.0 ? __dmul_rn(s2, rsqrt(s2)) : 0.0;
   double x = __dmul_rn(r, inv_range);
   // sigma^2 times the closed-form polynomial, Horner with fused multiply-adds
@@ -253,24 +253,24 @@ __global__ void k_reduce_norms(const ItemGen* __restrict__ items, int count, int
 }  // namespace
 
 // The e^{-x} tables of the current device, from long double arithmetic on
-// the host (2^{j/32} as a double plus its remainder; ln2/32 as a 37-bit head
+// the host (2^{j/64} as a double plus its remainder; ln2/64 as a 37-bit head
 // plus its remainder).
 int init_gen_tables() {
   double h[GEN_TAB];
-  for (int j = 0; j < 32; ++j) {
-    const long double v = std::exp2((long double)j / 32.0L);
+  for (int j = 0; j < 64; ++j) {
+    const long double v = std::exp2((long double)j / 64.0L);
     h[j] = (double)v;
-    h[32 + j] = (double)(v - (long double)h[j]);
+    h[64 + j] = (double)(v - (long double)h[j]);
   }
-  const long double l = std::log(2.0L) / 32.0L;
+  const long double l = std::log(2.0L) / 64.0L;
   double head = (double)l;
   uint64_t u;
   std::memcpy(&u, &head, sizeof(u));
   u &= ~(uint64_t)0xFFFF;   // 53 - 16 = 37 significant bits
   std::memcpy(&head, &u, sizeof(u));
-  h[64] = head;
-  h[65] = (double)(l - (long double)head);
-  h[66] = (double)(32.0L / std::log(2.0L));
+  h[128] = head;
+  h[129] = (double)(l - (long double)head);
+  h[130] = (double)(64.0L / std::log(2.0L));
   return cudaMemcpyToSymbol(c_gen_tab, h, sizeof(h)) == cudaSuccess ? 0 : 1;
 }
 
