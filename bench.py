@@ -129,6 +129,24 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def max_over_ranks(values, ws, device=None):
+    """Each timing's maximum over the ranks (one all-reduce; the caller
+    brackets the timed region with barriers).  Identity for one rank."""
+    if ws == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job(ms_values, ws, flops_per_rank):
+    """Whole-job TFLOP/s for each time in ms: every rank did flops_per_rank
+    of work in (at most) that time."""
+    return [ws * flops_per_rank / (ms * 1e-3) / 1e12 for ms in ms_values]
+
+
 def cpu_cores():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         if os.environ.get(v):
@@ -453,13 +471,9 @@ def ours(args, cfg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_e2e = ee0.elapsed_time(ee1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = t.tolist()
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], ws, device=dev)
     F = chol_flops(n)
-    value = ws * F / (ms * 1e-3) / 1e12
-    value_e2e = ws * F / (ms_e2e * 1e-3) / 1e12
+    value, value_e2e = whole_job([ms, ms_e2e], ws, F)
     stats = T.stats()
     launches_per_step = (morton_launches(n) if cfg["morton"] else 0) + stats["generate"] + \
         stats["chol"] + 1 + stats["loglik"]
