@@ -97,19 +97,21 @@ const char* mp_version(void);
  *             8 * NT(NT+1)/2 * b^2 more bytes).  MP_TMAT_SIMT_UPDATES runs
  *             the lower-precision trailing updates on CUDA cores (FP32
  *             FMA) instead of the tcgen05 tensor cores (BF16/FP16/E4M3
- *             MMAs; FP32 products as three TF32 MMAs of hi/lo splits).
+ *             MMAs; FP32 products as three TF32 products of hi/lo splits
+ *             in two MMAs).
  *             MP_TMAT_STREAM_ALLOC allocates and frees the matrix's device
  *             memory with cudaMallocAsync / cudaFreeAsync on `stream` (and
  *             uploads with cudaMemcpyAsync), so that creating or destroying
  *             a matrix never waits for other streams' work.
  *             By default the panel solve of every panel tile stored in
  *             FP32 or below is the product X = A_ik W with W = L_kk^{-T}
- *             (FP64, from the identity solve), on the tensor cores: both operands are split into 8 integer digits of
- *             6 bits, every digit level accumulates exactly in FP32, and
- *             the levels are summed in float-float; the dropped levels
- *             bound the error by b (1 + 11/3) 2^-48 times the product of
- *             the row bound of A and the column bound of W, far below the
- *             FP32 rounding the result then receives.  FP64-stored panel
+ *             (FP64, formed with the diagonal tile's factorisation), on
+ *             the tensor cores: both operands are split into 8 integer
+ *             digits of 6 bits, every digit level accumulates exactly in
+ *             FP32, and the levels are summed in float-float; the dropped
+ *             levels bound the error by b (1 + 11/3) 2^-48 times the
+ *             product of the row bound of A and the column bound of W,
+ *             far below the FP32 rounding the result then receives.  FP64-stored panel
  *             tiles keep the FP64 solve.  MP_TMAT_FP64_PANEL solves every
  *             panel tile by FP64 substitution instead.
  *   stream  : stream all later calls on this matrix are ordered on.
@@ -187,8 +189,10 @@ mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p);
 /* --------------------------------------------------------- factorisation */
 
 /* Tiled right-looking Cholesky in place (Sec. 6.2 `chol`, tiled as in
- * Sec. 7): per step k, POTRF of the FP64 diagonal tile, FP64 TRSM of the
- * panel (result rounded to each tile's format), and the trailing
+ * Sec. 7): per step k, POTRF of the FP64 diagonal tile (with its inverse
+ * W = L_kk^{-T}), the panel TRSM (integer-digit tensor-core products with W
+ * by default, FP64 substitution with MP_TMAT_FP64_PANEL or for FP64-stored
+ * panel tiles; the result rounded to each tile's format), and the trailing
  * SYRK/GEMM updates, each in the precision min(p(target), max(p(A),
  * p(B))) with FP32 accumulation (FP64 for FP64 products).  The whole
  * schedule is one CUDA graph launch on the matrix's stream.
