@@ -111,9 +111,10 @@ const char* mp_version(void);
  *             FP32, and the levels are summed in float-float; the dropped
  *             levels bound the error by b (1 + 11/3) 2^-48 times the
  *             product of the row bound of A and the column bound of W,
- *             far below the FP32 rounding the result then receives.  FP64-stored panel
- *             tiles keep the FP64 solve.  MP_TMAT_FP64_PANEL solves every
- *             panel tile by FP64 substitution instead.
+ *             far below the FP32 rounding the result then receives.
+ *             FP64-stored panel tiles keep the FP64 solve.
+ *             MP_TMAT_FP64_PANEL solves every panel tile by FP64
+ *             substitution instead.
  *   stream  : stream all later calls on this matrix are ordered on.
  * The library allocates tile storage and workspace on the device (see
  * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
