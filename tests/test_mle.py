@@ -1,0 +1,86 @@
+"""Nelder-Mead driver (host logic on the CPU) and the Matérn MLE on the GPU
+against the oracle's exact log-likelihood (Sec. 6.2's MLE workload)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2406_02701_gb300.mle import nelder_mead
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_02701_gb300 import mpchol
+    return mpchol.Context(0)
+
+
+def _batch(f):
+    return lambda pts: [f(p) for p in pts]
+
+
+def test_nelder_mead_quadratic():
+    f = lambda x: (x[0] - 1.0) ** 2 + 10.0 * (x[1] + 2.0) ** 2
+    r = nelder_mead(_batch(f), [0.0, 0.0], step=0.5, max_iter=500, ftol=1e-14, xtol=1e-9)
+    assert np.allclose(r["x"], [1.0, -2.0], atol=1e-6)
+    assert r["f"] < 1e-11
+
+
+def test_nelder_mead_rosenbrock():
+    f = lambda x: 100.0 * (x[1] - x[0] ** 2) ** 2 + (1.0 - x[0]) ** 2
+    r = nelder_mead(_batch(f), [-1.2, 1.0], step=0.5, max_iter=2000, ftol=1e-15, xtol=1e-10)
+    assert np.allclose(r["x"], [1.0, 1.0], atol=1e-4)
+
+
+def test_speculative_batches_take_the_same_path():
+    """Evaluating the four candidates of an iteration together changes the
+    number of evaluations and round trips, not a single decision."""
+    calls = []
+    f = lambda x: math.sin(3 * x[0]) + (x[0] - 0.3) ** 2 + 2 * (x[1] - x[0] * x[1]) ** 2 + 0.1 * x[1] ** 2
+
+    def fb(pts):
+        calls.append(len(pts))
+        return [f(p) for p in pts]
+
+    a = nelder_mead(fb, [1.0, 1.0], max_iter=150, speculative=False)
+    calls.clear()
+    b = nelder_mead(fb, [1.0, 1.0], max_iter=150, speculative=True)
+    assert a["iters"] == b["iters"]
+    assert np.array_equal(a["simplex"], b["simplex"]) and np.array_equal(a["fvals"], b["fvals"])
+    assert b["rounds"] < a["rounds"] and b["evals"] > a["evals"]
+    assert all(c in (3, 4, 2) for c in calls)        # initial simplex, candidates, shrink
+
+
+@pytest.mark.gpu
+def test_matern_mle_matches_oracle_at_the_optimum(ctx):
+    import torch
+    from oracle import chol as OC
+    from oracle import matern as OM
+    import mpinputs as I
+    from paper_2406_02701_gb300.mle import MaternMLE
+    n, b, nu, nugget = 1024, 128, 0.5, 1e-4
+    locs = I.points(n, 41)
+    # one draw of the field at (range 0.1, sigma^2 1.2)
+    S0 = OM.covariance(locs, nu, 0.1, 1.2, nugget)
+    z = np.linalg.cholesky(S0) @ np.random.default_rng(41).standard_normal(n)
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.F32, 2)
+    mle = MaternMLE(ctx, locs, z, b, nu, nugget, pmap=pmap, lanes=4, refine_iters=10)
+    # lanes agree with one another (same layout, same parameters)
+    same = mle.loglik([(0.07, 0.9)] * 4)
+    assert len(set(same)) == 1
+    r = mle.fit(0.05, 0.5, max_iter=120)
+    mle.close()
+    assert r["iters"] < 120
+    rng_hat, s2_hat = r["range"], r["sigma2"]
+    # the GPU log-likelihood at the estimate is the oracle's exact one there
+    ex = OC.exact_loglik(OM.covariance(locs, nu, rng_hat, s2_hat, nugget), z.reshape(n, 1))
+    assert math.isclose(r["loglik"], float(ex["loglik"][0]), rel_tol=1e-9)
+    # and the estimate is a maximum of the exact log-likelihood
+    for dr, ds in [(1.02, 1), (0.98, 1), (1, 1.02), (1, 0.98)]:
+        e = OC.exact_loglik(OM.covariance(locs, nu, rng_hat * dr, s2_hat * ds, nugget), z.reshape(n, 1))
+        assert float(e["loglik"][0]) <= r["loglik"] + 1e-6 * abs(r["loglik"])
+    assert 0.05 < rng_hat < 0.2 and 0.6 < s2_hat < 2.4
+    torch.cuda.synchronize()
