@@ -25,10 +25,16 @@ import numpy as np
 ALPHA, GAMMA, RHO, SIGMA = 1.0, 2.0, 0.5, 0.5
 
 
-def nelder_mead(f_batch, x0, step=0.5, max_iter=200, ftol=1e-9, xtol=1e-7, speculative=False):
+REL_TOL = 1.490116119384765625e-08   # sqrt of the double epsilon, R optim's reltol
+
+
+def nelder_mead(f_batch, x0, step=0.5, max_iter=200, reltol=REL_TOL, xtol=None, speculative=False):
     """Minimises f over R^d.  f_batch maps a list of points (1-D arrays) to a
-    list of values.  Returns dict(x, f, iters, evals, simplex, fvals,
-    rounds) -- rounds counts the calls of f_batch (sequential round trips)."""
+    list of values.  Stops when the spread of f over the simplex is at most
+    reltol (|f_best| + reltol) (R optim's rule), or, with xtol, when every
+    vertex lies within xtol of the best one.  Returns dict(x, f, iters,
+    evals, simplex, fvals, rounds) -- rounds counts the calls of f_batch
+    (sequential round trips)."""
     x0 = np.asarray(x0, dtype=np.float64)
     d = x0.size
     simplex = [x0.copy()]
@@ -49,8 +55,9 @@ def nelder_mead(f_batch, x0, step=0.5, max_iter=200, ftol=1e-9, xtol=1e-7, specu
         order = np.argsort(fv, kind="stable")
         simplex = [simplex[k] for k in order]
         fv = [fv[k] for k in order]
-        if abs(fv[-1] - fv[0]) <= ftol * (abs(fv[0]) + ftol) and \
-                max(np.max(np.abs(x - simplex[0])) for x in simplex[1:]) <= xtol:
+        if abs(fv[-1] - fv[0]) <= reltol * (abs(fv[0]) + reltol):
+            break
+        if xtol is not None and max(np.max(np.abs(x - simplex[0])) for x in simplex[1:]) <= xtol:
             break
         it += 1
         xo = np.mean(simplex[:-1], axis=0)
@@ -152,9 +159,9 @@ class MaternMLE:
         ll = self.loglik([(math.exp(p[0]), math.exp(p[1])) for p in points])
         return [-v for v in ll]
 
-    def fit(self, range0, sigma2_0, step=0.5, max_iter=200, ftol=1e-10, xtol=1e-6, speculative=True):
+    def fit(self, range0, sigma2_0, step=0.5, max_iter=200, reltol=REL_TOL, speculative=True):
         r = nelder_mead(self.nll_log, [math.log(range0), math.log(sigma2_0)], step=step,
-                        max_iter=max_iter, ftol=ftol, xtol=xtol, speculative=speculative)
+                        max_iter=max_iter, reltol=reltol, speculative=speculative)
         r["range"], r["sigma2"] = math.exp(r["x"][0]), math.exp(r["x"][1])
         r["loglik"] = -r["f"]
         return r

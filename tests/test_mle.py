@@ -23,15 +23,27 @@ def _batch(f):
 
 def test_nelder_mead_quadratic():
     f = lambda x: (x[0] - 1.0) ** 2 + 10.0 * (x[1] + 2.0) ** 2
-    r = nelder_mead(_batch(f), [0.0, 0.0], step=0.5, max_iter=500, ftol=1e-14, xtol=1e-9)
+    r = nelder_mead(_batch(f), [0.0, 0.0], step=0.5, max_iter=500, reltol=1e-14)
     assert np.allclose(r["x"], [1.0, -2.0], atol=1e-6)
     assert r["f"] < 1e-11
 
 
 def test_nelder_mead_rosenbrock():
     f = lambda x: 100.0 * (x[1] - x[0] ** 2) ** 2 + (1.0 - x[0]) ** 2
-    r = nelder_mead(_batch(f), [-1.2, 1.0], step=0.5, max_iter=2000, ftol=1e-15, xtol=1e-10)
+    r = nelder_mead(_batch(f), [-1.2, 1.0], step=0.5, max_iter=2000, reltol=1e-15)
     assert np.allclose(r["x"], [1.0, 1.0], atol=1e-4)
+
+
+def test_stops_on_a_noisy_objective():
+    """R optim's relative rule ends the search when the values at the
+    vertices agree to about 1.5e-8, above the ~1e-10 relative differences of
+    two FP64-refined evaluations of a log-likelihood."""
+    g = lambda x: 850.0 + 40.0 * (x[0] + 2.3) ** 2 + 25.0 * (x[1] - 0.1) ** 2 + 3.0 * x[0] * x[1]
+    noisy = lambda x: g(x) * (1.0 + 1e-10 * math.sin(1e7 * (x[0] + 2 * x[1])))
+    r = nelder_mead(_batch(noisy), [-3.0, -0.7], step=0.5, max_iter=200)
+    assert r["iters"] < 200
+    ref = nelder_mead(_batch(g), [-3.0, -0.7], step=0.5, max_iter=2000, reltol=1e-15)
+    assert abs(r["f"] - ref["f"]) <= 1e-6 * abs(ref["f"])
 
 
 def test_speculative_batches_take_the_same_path():
@@ -71,9 +83,9 @@ def test_matern_mle_matches_oracle_at_the_optimum(ctx):
     # lanes agree with one another (same layout, same parameters)
     same = mle.loglik([(0.07, 0.9)] * 4)
     assert len(set(same)) == 1
-    r = mle.fit(0.05, 0.5, max_iter=120)
+    r = mle.fit(0.05, 0.5, max_iter=200)
     mle.close()
-    assert r["iters"] < 120
+    assert r["iters"] < 200
     rng_hat, s2_hat = r["range"], r["sigma2"]
     # the GPU log-likelihood at the estimate is the oracle's exact one there
     ex = OC.exact_loglik(OM.covariance(locs, nu, rng_hat, s2_hat, nugget), z.reshape(n, 1))
