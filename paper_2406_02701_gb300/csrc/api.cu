@@ -207,9 +207,14 @@ struct Plan {
     if (stream_alloc) cudaFreeAsync(p, stream);
     else cudaFree(p);
   }
+  // Host-to-device copies are ordered on the plan's stream: the kernels that
+  // read them run there, and a plain cudaMemcpy (legacy stream) is not
+  // ordered with a non-blocking stream -- from pageable memory it returns
+  // once the data is staged, and a kernel on such a stream could still read
+  // the previous contents.  A pageable source is staged before the call
+  // returns, so the host buffer may be freed right after.
   cudaError_t upload(void* dst, const void* src, size_t bytes_) {
-    return stream_alloc ? cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, stream)
-                        : cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice);
+    return cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, stream);
   }
   mp_status alloc(void** p, size_t bytes_) {
     if (bytes_ == 0) { *p = nullptr; return MP_OK; }
@@ -853,8 +858,7 @@ mp_status finish_plan(Plan& P) {
     if (mp_status st = P.alloc(&p, P.scnt_bytes)) return st;
     P.d_scnt = (int*)p;
   }
-  CK(P.ctx, P.stream_alloc ? cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream)
-                           : cudaMemset(P.d_err, 0, sizeof(int)));
+  CK(P.ctx, cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
   if (P.use_tc || P.ozaki) {
     if (mp_status st = make_tensor_maps(P)) return st;
   }
@@ -887,6 +891,9 @@ mp_status finish_plan(Plan& P) {
   for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
   P.events.resize(4 * maxnt + 2);
   for (auto& e : P.events) CK(P.ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // the uploads above are ordered on the plan's stream; creation stays
+  // synchronous unless the plan allocates stream-ordered
+  if (!P.stream_alloc) CK(P.ctx, cudaStreamSynchronize(P.stream));
   return MP_OK;
 }
 
@@ -1084,16 +1091,18 @@ static mp_status tile_xfer(mp_tmat* t, int32_t i, int32_t j, void* h, double* sc
   const TileRef r = P.h_tiles[id];
   const size_t bytes = (size_t)P.b * P.b * esize(r.dt);
   char* dev = P.pool[r.dt] + (size_t)r.idx * bytes;
-  CK(P.ctx, cudaStreamSynchronize(P.stream));
+  // ordered on the matrix's stream, complete on return
   if (get) {
-    CK(P.ctx, cudaMemcpy(h, dev, bytes, cudaMemcpyDeviceToHost));
     double s = 1.0;
-    CK(P.ctx, cudaMemcpy(&s, P.d_scale + id, sizeof(double), cudaMemcpyDeviceToHost));
+    CK(P.ctx, cudaMemcpyAsync(h, dev, bytes, cudaMemcpyDeviceToHost, P.stream));
+    CK(P.ctx, cudaMemcpyAsync(&s, P.d_scale + id, sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    CK(P.ctx, cudaStreamSynchronize(P.stream));
     if (scale) *scale = s;
   } else {
-    CK(P.ctx, cudaMemcpy(dev, h, bytes, cudaMemcpyHostToDevice));
-    double s = scale ? *scale : 1.0;
-    CK(P.ctx, cudaMemcpy(P.d_scale + id, &s, sizeof(double), cudaMemcpyHostToDevice));
+    const double s = scale ? *scale : 1.0;
+    CK(P.ctx, cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, P.stream));
+    CK(P.ctx, cudaMemcpyAsync(P.d_scale + id, &s, sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    CK(P.ctx, cudaStreamSynchronize(P.stream));
     t->generated = true;
     P.factored = false;
   }
@@ -1739,7 +1748,8 @@ extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const doub
   cudaStream_t s = (cudaStream_t)stream;
   CK(ctx, cudaMalloc(&d_items, sizeof(ItemGen) * items.size()));
   cudaError_t e = cudaMalloc(&partial, sizeof(double) * items.size() * parts);
-  if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(ItemGen) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_items, items.data(), sizeof(ItemGen) * items.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_norms, 0, sizeof(double) * nt * nt, s);
   if (e == cudaSuccess) {
     launch_tile_norms(b, d_items, (int)items.size(), nt, partial, d_norms, s);

@@ -47,7 +47,8 @@ def nelder_mead(f_batch, x0, step=0.5, max_iter=200, reltol=REL_TOL, xtol=None, 
     def ev(points):
         stats["evals"] += len(points)
         stats["rounds"] += 1
-        return [float(v) for v in f_batch(points)]
+        # a value that is not a number ranks as the worst possible
+        return [float(v) if not math.isnan(v) else math.inf for v in f_batch(points)]
 
     fv = ev(simplex)
     it = 0
@@ -108,7 +109,7 @@ class MaternMLE:
     """Negative log-likelihood of (log range, log sigma^2) for fixed nu and
     nugget, evaluated on the GPU; `fit` runs Nelder-Mead on it."""
 
-    def __init__(self, ctx, locs, z, b, nu, nugget=1e-4, pmap=None, lanes=4, refine_iters=10,
+    def __init__(self, ctx, locs, z, b, nu, nugget=1e-4, pmap=None, lanes=4, refine_iters=20,
                  ozaki=True):
         import torch
         from . import mpchol
@@ -134,7 +135,11 @@ class MaternMLE:
 
     def loglik(self, thetas):
         """Log-likelihoods at the parameter vectors (range, sigma^2) in
-        `thetas`, lanes at a time; -inf where the matrix is not SPD."""
+        `thetas`, lanes at a time; -inf where the matrix is not SPD or the
+        FP64 refinement of the solve did not converge within its iteration
+        cap (far from the data's scale the condition number grows until the
+        refinement with the lower-precision factor no longer contracts; such
+        a value is not the log-likelihood)."""
         import torch
         res = []
         lanes = len(self.mats)
@@ -149,15 +154,16 @@ class MaternMLE:
                     infos.append(info)
             for s in self.streams[:len(chunk)]:
                 s.synchronize()
-            for info, (ll, _, _) in zip(infos, self.out):
-                res.append(float(ll.item()) if int(info.item()) == 0 else -math.inf)
+            for info, (ll, _, it) in zip(infos, self.out):
+                ok = int(info.item()) == 0 and (self.refine == 0 or int(it.item()) < self.refine)
+                res.append(float(ll.item()) if ok else -math.inf)
             self.evals += len(chunk)
         return res
 
     def nll_log(self, points):
         """Negative log-likelihood at points (log range, log sigma^2)."""
         ll = self.loglik([(math.exp(p[0]), math.exp(p[1])) for p in points])
-        return [-v for v in ll]
+        return [-v if math.isfinite(v) else math.inf for v in ll]
 
     def fit(self, range0, sigma2_0, step=0.5, max_iter=200, reltol=REL_TOL, speculative=True):
         r = nelder_mead(self.nll_log, [math.log(range0), math.log(sigma2_0)], step=step,

@@ -77,22 +77,33 @@ def test_matern_mle_matches_oracle_at_the_optimum(ctx):
     # one draw of the field at (range 0.1, sigma^2 1.2)
     S0 = OM.covariance(locs, nu, 0.1, 1.2, nugget)
     z = np.linalg.cholesky(S0) @ np.random.default_rng(41).standard_normal(n)
+    zc = z.reshape(n, 1)
+
+    def exact(rng, s2):
+        return float(OC.exact_loglik(OM.covariance(locs, nu, rng, s2, nugget), zc)["loglik"][0])
+
+    # the oracle's own optimum (Nelder-Mead on the exact log-likelihood)
+    ref = nelder_mead(lambda pts: [-exact(math.exp(p[0]), math.exp(p[1])) for p in pts],
+                      [math.log(0.05), math.log(0.5)], max_iter=200, speculative=True)
+    ll_star = -ref["f"]
     nt = -(-n // b)
     pmap = I.band_map(nt, I.F64, I.F32, I.F32, 2)
-    mle = MaternMLE(ctx, locs, z, b, nu, nugget, pmap=pmap, lanes=4, refine_iters=10)
-    # lanes agree with one another (same layout, same parameters)
-    same = mle.loglik([(0.07, 0.9)] * 4)
-    assert len(set(same)) == 1
+    mle = MaternMLE(ctx, locs, z, b, nu, nugget, pmap=pmap, lanes=4, refine_iters=20)
+    # four lanes at four parameter vectors, each against the oracle
+    thetas = [(0.07, 0.9), (0.12, 1.5), (0.05, 0.6), (0.09, 1.1)]
+    got = mle.loglik(thetas)
+    for (rng, s2), g in zip(thetas, got):
+        want = exact(rng, s2)
+        assert abs(g - want) <= 1e-6 * abs(want), (rng, s2, g, want)
     r = mle.fit(0.05, 0.5, max_iter=200)
     mle.close()
-    assert r["iters"] < 200
-    rng_hat, s2_hat = r["range"], r["sigma2"]
-    # the GPU log-likelihood at the estimate is the oracle's exact one there
-    ex = OC.exact_loglik(OM.covariance(locs, nu, rng_hat, s2_hat, nugget), z.reshape(n, 1))
-    assert math.isclose(r["loglik"], float(ex["loglik"][0]), rel_tol=1e-9)
-    # and the estimate is a maximum of the exact log-likelihood
-    for dr, ds in [(1.02, 1), (0.98, 1), (1, 1.02), (1, 0.98)]:
-        e = OC.exact_loglik(OM.covariance(locs, nu, rng_hat * dr, s2_hat * ds, nugget), z.reshape(n, 1))
-        assert float(e["loglik"][0]) <= r["loglik"] + 1e-6 * abs(r["loglik"])
-    assert 0.05 < rng_hat < 0.2 and 0.6 < s2_hat < 2.4
+    print("gpu fit:", r["iters"], r["evals"], r["range"], r["sigma2"], r["loglik"], "oracle fit:",
+          ref["iters"], math.exp(ref["x"][0]), math.exp(ref["x"][1]), ll_star)
+    # the point found is as good as the oracle's optimum (the north-star
+    # tolerance for the FP32 map: 1e-6 relative), and its GPU value is the
+    # oracle's there
+    ll_hat = exact(r["range"], r["sigma2"])
+    assert ll_hat >= ll_star - 1e-6 * abs(ll_star)
+    assert abs(r["loglik"] - ll_hat) <= 1e-6 * abs(ll_hat)
+    assert 0.05 < r["range"] < 0.2 and 0.6 < r["sigma2"] < 2.4
     torch.cuda.synchronize()
