@@ -9,7 +9,8 @@ Multi-Precision Computations Package in R"):
   formats  -- rounding into FP32 / BF16 / FP16 / FP8-E4M3 from the format
               definitions (Sec. 2), per-tile power-of-two FP8 scales.
   matern   -- the Matérn covariance (Sec. 6.2) in its half-integer closed
-              forms, and Morton ordering of locations.
+              forms and, for any other nu, its definition through the
+              library Bessel function; Morton ordering of locations.
   chol     -- O-exact: the float64 Gaussian log-likelihood (Sec. 6.2);
               O-tiled: the tiled Cholesky with a per-tile precision map
               (the tiled multi-precision approach of Sec. 7), its
@@ -19,7 +20,7 @@ Multi-Precision Computations Package in R"):
 Every function is plain numpy/scipy in float64, except where a step's
 definition fixes a lower precision (FP32 accumulation of the tile products).
 Library routines used as steps: numpy's matmul and LAPACK Cholesky,
-scipy's triangular solve.
+scipy's triangular solve, scipy's K_nu and Gamma (general nu only).
 
 Parity pins live in tests/test_oracle_*.py.  Parity unpinned: none of these
 functions is left without a pin; the paper's own MLE numbers (Table 3) depend

@@ -12,6 +12,9 @@ function has the textbook closed forms, so with x = r / a:
     nu = 1/2:  sigma^2 exp(-x)
     nu = 3/2:  sigma^2 (1 + x) exp(-x)
     nu = 5/2:  sigma^2 (1 + x + x^2/3) exp(-x)
+For other nu, `matern_general` evaluates the definition with the library
+Bessel function (scipy.special.kv) as a step; C(0) = sigma^2 (the limit
+x^nu K_nu(x) -> 2^(nu-1) Gamma(nu)).
 The range a enters as given (no sqrt(2 nu) rescaling).  A nugget tau^2 is added
 on the diagonal (Sec. 6.2 adds a small diagonal term for single precision).
 
@@ -39,6 +42,25 @@ def matern_closed(r, nu: float, a: float, sigma2: float) -> np.ndarray:
     return sigma2 * poly * np.exp(-x)
 
 
+def matern_general(r, nu: float, a: float, sigma2: float) -> np.ndarray:
+    """Matérn covariance at distances r for any nu > 0 (the definition,
+    sigma^2 2^(1-nu) / Gamma(nu) x^nu K_nu(x), x = r / a; C(0) = sigma^2)."""
+    from scipy.special import gamma, kv
+    x = np.asarray(r, dtype=np.float64) / a
+    out = np.full(x.shape, float(sigma2))
+    pos = x > 0
+    xp = x[pos]
+    out[pos] = sigma2 * 2.0 ** (1.0 - nu) / gamma(nu) * xp ** nu * kv(nu, xp)
+    return out
+
+
+def matern(r, nu: float, a: float, sigma2: float) -> np.ndarray:
+    """Closed form for nu in {1/2, 3/2, 5/2}, the definition otherwise."""
+    if nu in (0.5, 1.5, 2.5):
+        return matern_closed(r, nu, a, sigma2)
+    return matern_general(r, nu, a, sigma2)
+
+
 def distances(locs_a: np.ndarray, locs_b: np.ndarray) -> np.ndarray:
     """Euclidean distances ||s_i - s_j|| between two point sets (float64)."""
     dx = locs_a[:, 0:1] - locs_b[:, 0][None, :]
@@ -49,7 +71,7 @@ def distances(locs_a: np.ndarray, locs_b: np.ndarray) -> np.ndarray:
 def covariance(locs: np.ndarray, nu: float, a: float, sigma2: float,
                nugget: float) -> np.ndarray:
     """Full n x n covariance Sigma_ij = C(||s_i - s_j||) + nugget [i == j]."""
-    S = matern_closed(distances(locs, locs), nu, a, sigma2)
+    S = matern(distances(locs, locs), nu, a, sigma2)
     S[np.diag_indices_from(S)] += nugget
     return S
 

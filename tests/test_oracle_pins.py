@@ -114,6 +114,30 @@ def test_matern_closed_form_matches_bessel_definition(nu):
     assert np.allclose(got, ref, rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_general_reduces_to_closed_forms(nu):
+    a, s2 = 0.07, 1.7
+    r = np.array([0.0, 1e-9, 0.002, 0.03, 0.2, 0.9])
+    assert np.allclose(M.matern_general(r, nu, a, s2), M.matern_closed(r, nu, a, s2), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("nu", [0.3, 1.0, 2.2])
+def test_matern_general_matches_integral_representation(nu):
+    """K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt, by adaptive
+    quadrature (independent of the library Bessel routine), and the r -> 0
+    limit sigma^2."""
+    from scipy.integrate import quad
+    a, s2 = 0.05, 1.3
+    for x in (0.05, 0.7, 3.0, 11.0):
+        tmax = math.acosh(800.0 / x) + 1.0          # the integrand is below e^-800 beyond
+        k, _ = quad(lambda t: math.exp(-x * math.cosh(t)) * math.cosh(nu * t), 0, tmax,
+                    epsabs=0, epsrel=1e-13, limit=200)
+        want = s2 * 2.0 ** (1.0 - nu) / math.gamma(nu) * x ** nu * k
+        assert math.isclose(float(M.matern_general(x * a, nu, a, s2)), want, rel_tol=1e-10)
+    assert float(M.matern_general(0.0, nu, a, s2)) == s2
+    assert math.isclose(float(M.matern_general(1e-12 * a, nu, a, s2)), s2, rel_tol=1e-6)
+
+
 def test_matern_landmarks():
     a, s2 = 0.05, 1.3
     e = math.exp(-1.0)
