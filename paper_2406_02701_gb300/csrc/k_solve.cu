@@ -21,7 +21,6 @@ namespace mp {
 
 namespace {
 
-constexpr int NB = 32;
 constexpr int RCMAX = 8;   // right-hand sides per pass (1 when there is one)
 
 __device__ __forceinline__ bool gated(const int* gate) { return gate && *gate == 0; }
