@@ -63,6 +63,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the norm-guard eps sweep")
+    p.add_argument("--no-fp8", action="store_true", help="skip the n=65536 E4M3 workload")
+    p.add_argument("--fp8-eps", type=float, default=1e-6, help="norm guard of the E4M3 map (2-D field)")
+    p.add_argument("--fp8-eps-ar1", type=float, default=1e-4, help="norm guard of the AR(1) check")
     p.add_argument("--batch-requests", type=int, default=512)
     p.add_argument("--serve-requests", type=int, default=36)
     p.add_argument("--serve-rate", type=float, default=6.0, help="Poisson arrivals per second")
@@ -209,8 +213,9 @@ def kernel_rooflines(prof, chol_ms, peak64, b):
     tf32x3 = bf16 * (1.1 / 2.25) / 3.0
     kinds = {
         "potrf_tile": ("k_potrf_dag", "alu", peak64,
-                       "FP64 DFMA loop probe in this run (mp_probe_fp64_peak); flops: POTRF b^3/3 + "
-                       "inverse b^3/3 per diagonal tile"),
+                       "FP64 DFMA loop probe in this run (mp_probe_fp64_peak); achieved counts the "
+                       "method's POTRF b^3/3 per diagonal tile (executed_tflops adds the b^3/3 of "
+                       "the inverse W = L^-T it also forms)"),
         "panel_trsm_first": ("k_panel_trsm (chain)", "alu", peak64, "FP64 DFMA loop probe in this run"),
         "panel_trsm": ("k_panel_trsm (bulk)", "alu", peak64, "FP64 DFMA loop probe in this run"),
         "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 products)", "tensor", tf32x3,
@@ -225,13 +230,17 @@ def kernel_rooflines(prof, chol_ms, peak64, b):
         v = prof.get(cls)
         if not v or not v["launches"] or v["ms"] <= 0 or not peak:
             continue
-        ach = v["flops"] / (v["ms"] * 1e-3) / 1e12
+        flops = v["flops"] / 2.0 if cls == "potrf_tile" else v["flops"]
+        ach = flops / (v["ms"] * 1e-3) / 1e12
         r = {"bound": bound, "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
              "frac": ach / peak, "peak_source": src,
              "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(kname.split(" ")[0]),
              "launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
-             "flops_per_launch": v["flops"] / v["launches"],
+             "flops_per_launch": flops / v["launches"],
              "share_of_chol": v["ms"] / chol_ms if chol_ms else None}
+        if cls == "potrf_tile":
+            r["executed_tflops"] = ach * 2.0
+            r["executed_frac"] = ach * 2.0 / peak
         if cls == "panel_ozaki_gemm":
             # 8 digits per operand, 36 digit products of 2 b^3 flops each per tile
             r["executed_tflops"] = ach * 72.0
@@ -294,6 +303,191 @@ def reference_arm(args, cfg):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+EPS_SWEEP = (1e-6, 3e-6, 1e-5, 3e-5, 1e-4)
+
+
+def eps_sweep(ctx, cfg, dsorted, norms, zt, zmt, stream):
+    """The norm guard's eps against the work it saves (untimed in the step):
+    for each eps the map's tile counts, one factorisation graph and one full
+    step timed with CUDA events, and the log-likelihoods for the bench's z
+    and for a z drawn from the model (errors are taken against the FP64
+    oracle by the caller)."""
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    n, b = cfg["n"], cfg["b"]
+    nt = -(-n // b)
+    _, diag, near, far, band = cfg["map"]
+    out = []
+    for eps in EPS_SWEEP:
+        m = ctx.map_guarded(norms, band, near, far, eps)
+        low = int((m[np.tril_indices(nt, -1)] == far).sum())
+        T = mpchol.TiledMatrix(ctx, n, b, m, keep_sigma=True)
+        info = torch.zeros(1, dtype=torch.int64, device=zt.device)
+        ld = torch.zeros(1, dtype=torch.float64, device=zt.device)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(2):
+            ev[0].record(stream)
+            T.generate(dsorted, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+            ev[1].record(stream)
+            ctx.check(ctx.lib.mp_chol(T.h, mpchol._ptr(info), mpchol._ptr(ld)))
+            ev[2].record(stream)
+            ll, _, it = T.loglik(zt, refine_iters=cfg["refine"])
+            ev[3].record(stream)
+        llm, _, itm = T.loglik(zmt, refine_iters=cfg["refine"]) if zmt is not None else (None, None, None)
+        torch.cuda.synchronize()
+        chol_ms = ev[1].elapsed_time(ev[2])
+        out.append({"eps": eps, "far_tiles": low, "offdiag_tiles": nt * (nt - 1) // 2,
+                    "info": int(info.item()), "chol_graph_ms": chol_ms,
+                    "chol_graph_tflops": chol_flops(n) / (chol_ms * 1e-3) / 1e12,
+                    "step_ms": ev[0].elapsed_time(ev[3]),
+                    "refine_iters": int(it.max().item()), "logdet": float(ld.item()),
+                    "loglik": ll.cpu().numpy().tolist(),
+                    "loglik_model_z": llm.cpu().numpy().tolist() if llm is not None else None,
+                    "refine_iters_model_z": int(itm.max().item()) if itm is not None else None})
+        T.close()
+        del T
+    return out
+
+
+def oracle_reference(cfg, sorted_locs, z):
+    """O-exact for the bench workload (CPU-baseline leg: LAPACK on the host
+    cores, outside every timed region): log-determinant and log-likelihood
+    of the bench's z, and a z = L eps drawn from the model with its exact
+    log-likelihood (quad = ||eps||^2)."""
+    from oracle import chol as OC
+    t0 = time.perf_counter()
+    ex = OC.exact_loglik_field(sorted_locs, cfg["nu"], cfg["range"], cfg["sigma2"], cfg["nugget"],
+                               z, keep_factor=True)
+    eps = np.random.default_rng(99).standard_normal((sorted_locs.shape[0], 1))
+    zm = np.tril(ex.pop("L")) @ eps
+    llm = float(OC.loglik_value(sorted_locs.shape[0], ex["logdet"], float(eps[:, 0] @ eps[:, 0])))
+    return {"logdet": ex["logdet"], "loglik": [float(v) for v in ex["loglik"]], "z_model": zm,
+            "loglik_model_z": llm, "seconds": time.perf_counter() - t0, "cores": cpu_cores()}
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64))
+                        / np.abs(np.asarray(b, dtype=np.float64))))
+
+
+def fp8_workload(ctx, dev, eps_2d, eps_ar1, steps=3):
+    """The FP8 configuration: n = 65536, tile 1024, FP64 diagonal, FP32 for
+    |i - j| <= 2, E4M3 with per-tile scales beyond (where the norm guard
+    allows it), 16 right-hand sides, FP64 refinement.  (a) the 2-D Matérn
+    field (Morton-ordered uniform points, nu = 3/2, range 0.05, nugget 1e-4):
+    one step (Morton, generation, factorisation, solves with refinement)
+    timed over `steps` after a warm-up, its E4M3 tile count and refinement
+    sweeps; (b) the same sizes and map rule on the nu = 1/2 field of equally
+    spaced points on a line without nugget, whose covariance is AR(1): its
+    log-likelihood error against the closed form."""
+    import math
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    c = I.CONFIGS["mixed_fp8_n65536_b1024"]
+    n, b, nrhs = c["n"], c["b"], c["nrhs"]
+    nt = n // b
+    stream = torch.cuda.current_stream()
+    dl = torch.from_numpy(I.points(n, c["seed"])).to(dev)
+    zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, nrhs, c["seed"]).T)).to(dev)
+    ds, _ = ctx.morton_order(dl)
+    norms = ctx.tile_norms(n, b, ds, c["sigma2"], c["range"], c["nu"], c["nugget"]).cpu().numpy()
+    m = ctx.map_guarded(norms, 2, I.F32, I.E4M3, eps_2d)
+    low = int((m[np.tril_indices(nt, -1)] == I.E4M3).sum())
+    T = mpchol.TiledMatrix(ctx, n, b, m, keep_sigma=True)
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    ld = torch.zeros(1, dtype=torch.float64, device=dev)
+    sb = torch.empty_like(dl)
+    pb = torch.empty(n, dtype=torch.int64, device=dev)
+    ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step():
+        ctx.check(ctx.lib.mp_morton_order(ctx.h, n, mpchol._ptr(dl), mpchol._ptr(sb), mpchol._ptr(pb),
+                                          mpchol._stream(None)))
+        T.generate(sb, c["sigma2"], c["range"], c["nu"], c["nugget"])
+        ph[1].record(stream)
+        ctx.check(ctx.lib.mp_chol(T.h, mpchol._ptr(info), mpchol._ptr(ld)))
+        ph[2].record(stream)
+        return T.loglik(zt, refine_iters=c["refine"])
+
+    step()
+    torch.cuda.synchronize()
+    chol_ms = []
+    ph[0].record(stream)
+    for _ in range(steps):
+        ll, q, it = step()
+        torch.cuda.synchronize()
+        chol_ms.append(ph[1].elapsed_time(ph[2]))
+    ph[3].record(stream)
+    torch.cuda.synchronize()
+    # the synchronisations between steps are inside the bracket: the step
+    # time is their sum, each step's own time is what the events measure
+    ms = ph[0].elapsed_time(ph[3]) / steps
+    res = {"workload": "mixed_fp8_n65536_b1024", "n": n, "b": b, "nrhs": nrhs, "map": f"band2+guard(eps={eps_2d:g})",
+           "e4m3_tiles": low, "f32_tiles": int((m[np.tril_indices(nt, -1)] == I.F32).sum()),
+           "offdiag_tiles": nt * (nt - 1) // 2, "info": int(info.item()),
+           "ms_per_step": ms, "tflops_step": chol_flops(n) / (ms * 1e-3) / 1e12,
+           "chol_graph_ms": float(np.median(chol_ms)),
+           "chol_graph_tflops": chol_flops(n) / (float(np.median(chol_ms)) * 1e-3) / 1e12,
+           "refine_iters": it.cpu().numpy().tolist()}
+    T.close()
+    del T
+    # AR(1) closed form at the same sizes
+    a, s2 = 0.05, 1.0
+    h = 1.0 / n
+    rho = math.exp(-h / a)
+    z = I.ar1_rhs(n, nrhs, rho, s2, c["seed"])
+    dl1 = torch.from_numpy(I.points_line(n, h)).to(dev)
+    norms1 = ctx.tile_norms(n, b, dl1, s2, a, 0.5, 0.0).cpu().numpy()
+    m1 = ctx.map_guarded(norms1, 2, I.F32, I.E4M3, eps_ar1)
+    T1 = mpchol.TiledMatrix(ctx, n, b, m1, keep_sigma=True)
+    T1.generate(dl1, s2, a, 0.5, 0.0)
+    info1, ld1 = T1.chol()
+    ll1, _, it1 = T1.loglik(torch.from_numpy(np.ascontiguousarray(z.T)).to(dev), refine_iters=10)
+    torch.cuda.synchronize()
+    ldx = n * math.log(s2) + (n - 1) * math.log(1 - rho * rho)
+    qx = (z[0] ** 2 + np.sum((z[1:] - rho * z[:-1]) ** 2, axis=0) / (1 - rho * rho)) / s2
+    llx = -0.5 * n * math.log(2 * math.pi) - 0.5 * ldx - 0.5 * qx
+    res["ar1_closed_form"] = {
+        "what": "nu=1/2, range 0.05, no nugget, n equally spaced points on a line (AR(1)); 16 RHS "
+                "drawn from the model; same tile size, band and E4M3 guard",
+        "map": f"band2+guard(eps={eps_ar1:g})",
+        "e4m3_tiles": int((m1[np.tril_indices(nt, -1)] == I.E4M3).sum()), "info": int(info1.item()),
+        "loglik_rel_err_max": rel(ll1.cpu().numpy(), llx),
+        "logdet_rel_err": abs(ld1.item() - ldx) / abs(ldx),
+        "refine_iters": it1.cpu().numpy().tolist()}
+    T1.close()
+    return res
+
+
+def cusolver_context(dev, cfg, dsorted, stream):
+    """Context only: the vendor FP64 Cholesky (torch.linalg.cholesky, which
+    calls cuSOLVER's potrf) of the same covariance as one dense n x n FP64
+    matrix built with torch operations; timed with CUDA events after a
+    warm-up."""
+    import torch
+    if cfg["nu"] != 1.5:
+        return None
+    x = torch.cdist(dsorted, dsorted) / cfg["range"]
+    S = cfg["sigma2"] * (1.0 + x) * torch.exp(-x)
+    del x
+    S.diagonal().add_(cfg["nugget"])
+    L = torch.linalg.cholesky(S)
+    del L
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L = torch.linalg.cholesky(S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = S.shape[0]
+    del L, S
+    torch.cuda.empty_cache()
+    return {"what": "torch.linalg.cholesky (cuSOLVER potrf) of the dense FP64 covariance",
+            "ms": ms, "tflops": chol_flops(n) / (ms * 1e-3) / 1e12}
 
 
 def batch_run(ctx, args, dev):
@@ -513,6 +707,26 @@ def ours(args, cfg):
                      "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] > 0 and v["flops"] > 0 else None}
                  for k, v in prof.items() if v["launches"]}
 
+    # CPU-baseline leg, part 1: the FP64 oracle's log-likelihood of this
+    # workload (LAPACK on the host cores), and the mixed result for a z drawn
+    # from the model
+    ref, err = None, None
+    if not args.no_cpu_baseline and cfg["map"][0] == "band":
+        ref = oracle_reference(cfg, dsorted.cpu().numpy(), I.rhs(n, nrhs, cfg["seed"]))
+        zmt = torch.from_numpy(np.ascontiguousarray(ref["z_model"].T)).to(dev)
+        T.generate(sorted_buf if cfg["morton"] else dl, cfg["sigma2"], cfg["range"], cfg["nu"],
+                   cfg["nugget"])
+        ctx.check(ctx.lib.mp_chol(T.h, mpchol._ptr(info), mpchol._ptr(logdet)))
+        llm, _, itm = T.loglik(zmt, refine_iters=refine)
+        torch.cuda.synchronize()
+        err = {"reference": f"FP64 oracle: LAPACK dpotrf on {ref['cores']} host cores "
+                            f"({ref['seconds']:.1f} s, outside the timed region)",
+               "loglik_rel_err": rel(ll_mixed, ref["loglik"]),
+               "logdet_rel_err": abs(logdet_mixed - ref["logdet"]) / abs(ref["logdet"]),
+               "loglik_rel_err_model_z": rel(llm.cpu().numpy(), ref["loglik_model_z"]),
+               "refine_iters_model_z": int(itm.max().item()),
+               "target": 1e-6}
+
     # the all-FP64 GPU path on the same workload (speedup and error reference)
     fp64 = None
     if not args.no_fp64_path:
@@ -536,8 +750,34 @@ def ours(args, cfg):
         ll64 = ll64.cpu().numpy()
         fp64 = {"chol_ms": ms64, "tflops": F / (ms64 * 1e-3) / 1e12, "info": int(info64.item()),
                 "speedup_chol_only": ms64 / chol_ms if chol_ms else None,
+                "speedup_chol_graph": ms64 / phases["chol_graph_ms"],
                 "speedup_step": ms64 / ms,
-                "loglik_rel_err_mixed_vs_fp64": (np.abs(ll_mixed - ll64) / np.abs(ll64)).tolist()}
+                "loglik_rel_err_mixed_vs_fp64": (np.abs(ll_mixed - ll64) / np.abs(ll64)).tolist(),
+                "loglik_rel_err_vs_oracle": rel(ll64, ref["loglik"]) if ref else None}
+        T64.close()
+        del T64
+        fp64["cusolver_context"] = cusolver_context(dev, cfg, sorted_buf if cfg["morton"] else dl, stream)
+
+    sweep = None
+    if not args.no_sweep and cfg["map"][0] == "band":
+        norms = ctx.tile_norms(n, b, sorted_buf if cfg["morton"] else dl, cfg["sigma2"], cfg["range"],
+                               cfg["nu"], cfg["nugget"]).cpu().numpy()
+        sweep = eps_sweep(ctx, cfg, sorted_buf if cfg["morton"] else dl, norms, zt,
+                          torch.from_numpy(np.ascontiguousarray(ref["z_model"].T)).to(dev) if ref else None,
+                          stream)
+        if ref:
+            for e in sweep:
+                e["loglik_rel_err"] = rel(e["loglik"], ref["loglik"])
+                e["logdet_rel_err"] = abs(e["logdet"] - ref["logdet"]) / abs(ref["logdet"])
+                if e["loglik_model_z"] is not None:
+                    e["loglik_rel_err_model_z"] = rel(e["loglik_model_z"], ref["loglik_model_z"])
+        for e in sweep:
+            e.pop("loglik", None)
+            e.pop("loglik_model_z", None)
+
+    fp8 = None
+    if not args.no_fp8:
+        fp8 = fp8_workload(ctx, dev, args.fp8_eps, args.fp8_eps_ar1)
 
     batch = None
     if not args.no_batch:
@@ -576,6 +816,9 @@ def ours(args, cfg):
         "result": {"info": info_mixed, "loglik": ll_mixed.tolist(), "logdet": logdet_mixed,
                    "refine_iters": iters_mixed.tolist(), "plain_band_map": band_status},
         "fp64_path": fp64,
+        "error_vs_oracle": err,
+        "eps_sweep": sweep,
+        "fp8_workload": fp8,
         "chol_graph_tflops": F / (phases["chol_graph_ms"] * 1e-3) / 1e12,
         "serving": serve,
         "batch": batch,

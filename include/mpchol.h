@@ -165,8 +165,12 @@ mp_status mp_morton_order(mp_ctx* ctx, int64_t n, const double* d_locs_in,
  *     (use mp_morton_order).  The buffer (8 bytes per point of the limit,
  *     1 MiB) is held by every device that loads the library until exit.
  *   - The first call on a device looks the buffer's device address up
- *     (cudaGetSymbolAddress); make that first call before any stream
- *     capture that includes this entry point.
+ *     (cudaGetSymbolAddress), and so does the first call after a
+ *     cudaDeviceReset (the address belongs to the device's context); make
+ *     that first call before any stream capture that includes this entry
+ *     point.
+ *   - A CUDA error already pending when the call starts is reported as
+ *     MP_ERR_CUDA (and left pending) before anything is enqueued.
  *   - All calls share the one buffer: two calls whose work overlaps on the
  *     GPU (different streams, or different threads without ordering) race
  *     and corrupt each other's result; order them on one stream.

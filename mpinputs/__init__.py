@@ -37,6 +37,23 @@ def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
     return rng.standard_normal((n, nrhs))
 
 
+def ar1_rhs(n: int, nrhs: int, rho: float, sigma2: float, seed: int) -> np.ndarray:
+    """Right-hand sides drawn from the stationary AR(1) model with lag-one
+    correlation rho and variance sigma2, shape (n, nrhs): z_1 = sigma e_1,
+    z_i = rho z_{i-1} + sigma sqrt(1 - rho^2) e_i with e ~ N(0, 1) from
+    default_rng(seed + 1000) -- a field drawn from the covariance it is
+    evaluated under, as for an exponential covariance on equally spaced
+    points."""
+    e = np.random.default_rng(seed + 1000).standard_normal((n, nrhs))
+    z = np.empty((n, nrhs))
+    s = np.sqrt(sigma2)
+    c = s * np.sqrt(1.0 - rho * rho)
+    z[0] = s * e[0]
+    for i in range(1, n):
+        z[i] = rho * z[i - 1] + c * e[i]
+    return z
+
+
 def band_map(nt: int, diag: int, near: int, far: int, band: int) -> np.ndarray:
     """Per-tile precision map, shape (nt, nt), uint8, row-major; lower triangle used.
 

@@ -93,6 +93,37 @@ def exact_loglik(S: np.ndarray, z: np.ndarray, method: str = "lapack"):
     return dict(logdet=logdet, quad=quad, loglik=loglik_value(S.shape[0], logdet, quad), L=L)
 
 
+def exact_loglik_field(locs: np.ndarray, nu: float, a: float, sigma2: float, nugget: float,
+                       z: np.ndarray, rows: int = 2048, keep_factor: bool = False):
+    """O-exact for a Matérn field too large for `covariance` and its
+    temporaries: Sigma is built row block by row block into one float64
+    array, LAPACK's Cholesky (dpotrf) factors it in place and a triangular
+    solve gives w = L^{-1} z.  Same quantity as exact_loglik.  Returns
+    dict(logdet, quad[nrhs], loglik[nrhs]) and, with keep_factor, L (its
+    upper triangle holds what is left of Sigma)."""
+    from scipy.linalg import lapack
+    from . import matern as M
+    n = locs.shape[0]
+    z = np.asarray(z, dtype=np.float64).reshape(n, -1)
+    S = np.empty((n, n), order="F")
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        blk = M.matern(M.distances(locs[r0:r1], locs), nu, a, sigma2)
+        blk[np.arange(r1 - r0), np.arange(r0, r1)] += nugget
+        S[r0:r1] = blk
+        del blk
+    L, info = lapack.dpotrf(S, lower=1, clean=0, overwrite_a=1)
+    if info != 0:
+        raise np.linalg.LinAlgError(f"not SPD at row {info}")
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
+    w = sla.solve_triangular(L, z, lower=True, check_finite=False)
+    quad = np.sum(w * w, axis=0)
+    out = dict(logdet=logdet, quad=quad, loglik=loglik_value(n, logdet, quad))
+    if keep_factor:
+        out["L"] = L
+    return out
+
+
 # ----------------------------------------------------------------------------
 # tiled matrix with per-tile formats
 # ----------------------------------------------------------------------------

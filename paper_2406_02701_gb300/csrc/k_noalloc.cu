@@ -15,7 +15,11 @@
 // process exits.  In host code the array's name is only a host-side
 // placeholder; the device address is looked up once per device with
 // cudaGetSymbolAddress while that device is current, and that address is
-// what the kernels receive.
+// what the kernels receive.  The looked-up address belongs to the device's
+// current context: after a cudaDeviceReset the runtime creates a new
+// context (and loads the module again), so the cache records the context it
+// was filled in and looks the address up again when the context differs.
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/mpchol.h"
@@ -31,7 +35,35 @@ static __device__ __align__(256) unsigned long long g_sort_keys[MP_NOALLOC_MAX_P
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned long long* g_keys_addr[kMaxDevices] = {};
+struct KeysAddr {
+  void* ctx;                   // context the address was looked up in
+  unsigned long long* addr;
+};
+KeysAddr g_keys[kMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link
+// against libcuda); returns the calling thread's current context or null.
+void* current_context() {
+  typedef int (*Fn)(void**);
+  static Fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<Fn>(f);
+  }();
+  void* c = nullptr;
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
+
+mp_status cuda_fail(const char* what, cudaError_t e) {
+  char msg[256];
+  snprintf(msg, sizeof msg, "mp_morton_order_noalloc: %s: %s", what, cudaGetErrorString(e));
+  mp::set_error_text(msg);
+  return MP_ERR_CUDA;
+}
 
 }  // namespace
 
@@ -47,19 +79,29 @@ extern "C" mp_status mp_morton_order_noalloc(int64_t n, const double* d_locs_in,
     return MP_ERR_ARG;
   }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MP_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+  if (dev < 0 || dev >= kMaxDevices) {
+    mp::set_error_text("mp_morton_order_noalloc: device index beyond the library's table of 64");
+    return MP_ERR_ARG;
+  }
+  // an error left by earlier work would otherwise be reported as this
+  // call's: say so and leave it in place for its owner
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return cuda_fail("an earlier CUDA error is pending (not cleared)", e);
   unsigned long long* keys = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_keys_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_keys[dev].addr || !ctx || g_keys[dev].ctx != ctx) {
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_sort_keys) != cudaSuccess || !p) {
-        mp::set_error_text("mp_morton_order_noalloc: cudaGetSymbolAddress failed");
-        return MP_ERR_CUDA;
-      }
-      g_keys_addr[dev] = static_cast<unsigned long long*>(p);
+      e = cudaGetSymbolAddress(&p, g_sort_keys);
+      if (e != cudaSuccess || !p) return cuda_fail("cudaGetSymbolAddress", e);
+      // the look-up makes the runtime's context current when none was
+      g_keys[dev].ctx = ctx ? ctx : current_context();
+      g_keys[dev].addr = static_cast<unsigned long long*>(p);
     }
-    keys = g_keys_addr[dev];
+    keys = g_keys[dev].addr;
   }
   int64_t n2 = 1024;
   while (n2 < n) n2 <<= 1;
@@ -69,5 +111,6 @@ extern "C" mp_status mp_morton_order_noalloc(int64_t n, const double* d_locs_in,
   mp::launch_morton_keys(d_locs_in, n, n2, keys, s);
   mp::launch_bitonic(keys, n2, s);
   mp::launch_morton_gather(keys, d_locs_in, n, d_locs_out, d_perm, s);
-  return cudaPeekAtLastError() == cudaSuccess ? MP_OK : MP_ERR_CUDA;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? MP_OK : cuda_fail("kernel launch", e);
 }

@@ -30,6 +30,10 @@
 
 #include "../../include/mpchol.h"
 
+namespace mp {
+void set_error_text(const char* msg);
+}
+
 namespace {
 
 double now_s() {
@@ -88,6 +92,12 @@ extern "C" mp_status mp_map_bound(int64_t n, int32_t b, const double* h_sorted_l
                                   uint8_t* h_map) {
   if (n < 1 || b < 1 || !h_sorted_locs || !h_map || band < 0 || !(eps > 0)) return MP_ERR_ARG;
   if (!(c.range > 0) || !(c.sigma2 > 0)) return MP_ERR_ARG;
+  // the host covariance below has the closed forms only: another nu would
+  // silently bound the wrong covariance
+  if (!(c.nu == 0.5 || c.nu == 1.5 || c.nu == 2.5)) {
+    mp::set_error_text("mp_map_bound: nu must be 0.5, 1.5 or 2.5");
+    return MP_ERR_ARG;
+  }
   const int nt = (int)((n + b - 1) / b);
   std::vector<double> lo_x(nt), hi_x(nt), lo_y(nt), hi_y(nt);
   std::vector<int64_t> cnt(nt);

@@ -31,10 +31,12 @@ REL_TOL = 1.490116119384765625e-08   # sqrt of the double epsilon, R optim's rel
 def nelder_mead(f_batch, x0, step=0.5, max_iter=200, reltol=REL_TOL, xtol=None, speculative=False):
     """Minimises f over R^d.  f_batch maps a list of points (1-D arrays) to a
     list of values.  Stops when the spread of f over the simplex is at most
-    reltol (|f_best| + reltol) (R optim's rule), or, with xtol, when every
-    vertex lies within xtol of the best one.  Returns dict(x, f, iters,
-    evals, simplex, fvals, rounds) -- rounds counts the calls of f_batch
-    (sequential round trips)."""
+    reltol (|f(x0)| + reltol), the tolerance fixed once from the value at
+    the starting point (R optim's rule), or, with xtol, when every vertex
+    lies within xtol of the best one.  Returns dict(x, f, iters, evals,
+    simplex, fvals, rounds, converged) -- rounds counts the calls of
+    f_batch (sequential round trips); converged is False when max_iter, not
+    a stopping rule, ended the search."""
     x0 = np.asarray(x0, dtype=np.float64)
     d = x0.size
     simplex = [x0.copy()]
@@ -51,14 +53,20 @@ def nelder_mead(f_batch, x0, step=0.5, max_iter=200, reltol=REL_TOL, xtol=None, 
         return [float(v) if not math.isnan(v) else math.inf for v in f_batch(points)]
 
     fv = ev(simplex)
+    convtol = reltol * (abs(fv[0]) + reltol) if math.isfinite(fv[0]) else math.inf
     it = 0
-    while it < max_iter:
+    converged = False
+    while True:
         order = np.argsort(fv, kind="stable")
         simplex = [simplex[k] for k in order]
         fv = [fv[k] for k in order]
-        if abs(fv[-1] - fv[0]) <= reltol * (abs(fv[0]) + reltol):
+        if fv[-1] - fv[0] <= convtol:
+            converged = True
             break
         if xtol is not None and max(np.max(np.abs(x - simplex[0])) for x in simplex[1:]) <= xtol:
+            converged = True
+            break
+        if it >= max_iter:
             break
         it += 1
         xo = np.mean(simplex[:-1], axis=0)
@@ -102,7 +110,7 @@ def nelder_mead(f_batch, x0, step=0.5, max_iter=200, reltol=REL_TOL, xtol=None, 
         fv = [fv[0]] + fs
     k = int(np.argmin(fv))
     return dict(x=simplex[k], f=fv[k], iters=it, evals=stats["evals"], rounds=stats["rounds"],
-                simplex=np.array(simplex), fvals=np.array(fv))
+                simplex=np.array(simplex), fvals=np.array(fv), converged=converged)
 
 
 class MaternMLE:

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import mpinputs as I
+from oracle import chol as OC
 from oracle import matern as OM
 
 pytestmark = pytest.mark.gpu
@@ -83,11 +84,26 @@ def test_bench_workload_n16384_matches_fp64_path_and_sigma(ctx, ozaki):
     assert int(iters.item()) < 10
     err = abs(ll.item() - ll64.item()) / abs(ll64.item())
     assert err <= 1e-6, err
+    # against the FP64 oracle (LAPACK on the host): the bench's z ~ N(0, 1),
+    # and a z drawn from the model, z = L eps (then quad is about n and the
+    # log-determinant carries a larger share of the log-likelihood)
+    locs = ds.cpu().numpy()
+    z = I.rhs(n, 1, c["seed"])
+    ex = OC.exact_loglik_field(locs, c["nu"], c["range"], c["sigma2"], c["nugget"], z,
+                               keep_factor=True)
+    assert abs(ll.item() - ex["loglik"][0]) / abs(ex["loglik"][0]) <= 1e-6
+    assert abs(logdet.item() - ex["logdet"]) / abs(ex["logdet"]) <= 1e-6
+    eps = np.random.default_rng(99).standard_normal((n, 1))
+    zm = np.tril(ex.pop("L")) @ eps
+    llm, _, itm = T.loglik(torch.from_numpy(np.ascontiguousarray(zm.T)).cuda(), refine_iters=10)
+    torch.cuda.synchronize()
+    exm = OC.loglik_value(n, ex["logdet"], float(eps[:, 0] @ eps[:, 0]))
+    errm = abs(llm.item() - float(exm)) / abs(float(exm))
+    assert int(itm.item()) < 10 and errm <= 1e-6, errm
     # both quadratic forms carry a forward error of about kappa(Sigma) u64
     # (kappa ~ 1e7-1e8 here: nugget 1e-4 against a smooth kernel), so they
     # agree to that level, not to the last digits
     assert math.isclose(quad.item(), quad64.item(), rel_tol=1e-6)
-    locs = ds.cpu().numpy()
     _check_llt(T, locs, n, b, c, 2.0 ** -8, np.random.default_rng(3))
     _check_llt(T64, locs, n, b, c, 2.0 ** -50, np.random.default_rng(4))
 
@@ -127,6 +143,46 @@ def test_fp8_workload_n65536_16rhs_refinement(ctx, ozaki):
     q = quad.cpu().numpy()
     assert np.all(np.isfinite(q)) and np.all(q > 0)
     _check_llt(T, locs, n, b, c, 2.0 ** -4, np.random.default_rng(6), npairs=12)
+
+
+def test_fp8_map_ar1_closed_form_n65536(ctx):
+    """The FP8 workload's sizes and map rule -- n = 65536, tile 1024, FP64
+    diagonal, FP32 for |i - j| <= 2, E4M3 with a per-tile scale beyond where
+    the norm guard allows it, 16 right-hand sides, FP64 refinement -- on a
+    covariance whose log-likelihood has a closed form: the nu = 1/2 Matérn
+    (exponential) covariance on equally spaced points of a line, without a
+    nugget, is the AR(1) covariance sigma^2 rho^|i-j| with rho = exp(-h/a),
+    so log det = n log sigma^2 + (n-1) log(1 - rho^2) and
+    quad = (z_1^2 + sum_i (z_i - rho z_{i-1})^2 / (1 - rho^2)) / sigma^2.
+    The right-hand sides are drawn from that model.  Target: relative
+    log-likelihood error <= 1e-4 with E4M3 tiles present."""
+    from paper_2406_02701_gb300 import mpchol
+    n, b, nrhs, a, s2 = 65536, 1024, 16, 0.05, 1.0
+    h = 1.0 / n
+    rho = math.exp(-h / a)
+    locs = I.points_line(n, h)
+    z = I.ar1_rhs(n, nrhs, rho, s2, 21)
+    dl = torch.from_numpy(locs).cuda()
+    norms = ctx.tile_norms(n, b, dl, s2, a, 0.5, 0.0)
+    pmap = ctx.map_guarded(norms.cpu().numpy(), 2, I.F32, I.E4M3, 1e-4)
+    nt = n // b
+    low = int((pmap[np.tril_indices(nt, -1)] == I.E4M3).sum())
+    assert low > 0
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
+    T.generate(dl, s2, a, 0.5, 0.0)
+    info, logdet = T.chol()
+    ll, quad, iters = T.loglik(torch.from_numpy(np.ascontiguousarray(z.T)).cuda(), refine_iters=10)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    assert np.all(iters.cpu().numpy() < 10)
+    ld = n * math.log(s2) + (n - 1) * math.log(1 - rho * rho)
+    q = (z[0] ** 2 + np.sum((z[1:] - rho * z[:-1]) ** 2, axis=0) / (1 - rho * rho)) / s2
+    want = -0.5 * n * math.log(2 * math.pi) - 0.5 * ld - 0.5 * q
+    err = np.abs(ll.cpu().numpy() - want) / np.abs(want)
+    print(f"E4M3 tiles {low} of {nt * (nt - 1) // 2}; loglik rel err max {err.max():.3g}; "
+          f"logdet rel err {abs(logdet.item() - ld) / abs(ld):.3g}")
+    assert np.all(err <= 1e-4), err
+    assert np.allclose(quad.cpu().numpy(), q, rtol=1e-8)
 
 
 def test_batch_512_requests(ctx):

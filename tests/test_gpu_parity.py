@@ -189,12 +189,30 @@ def test_single_steps_match_oracle(ctx, far, mode):
     "ozaki" mode the panel tiles (stored in FP32 or below) are integer-digit
     tensor-core products A L_kk^{-T}, within the bound of _ozaki_bound of
     the float64 solve before their rounding."""
+    _single_steps(ctx, 640, 128, far, mode, 0.1)
+
+
+@pytest.mark.parametrize("mode", ["tcgen05", "ozaki"])
+@pytest.mark.parametrize("far", [I.BF16, I.E4M3])
+@pytest.mark.parametrize("n,b", [(2048, 512), (3072, 1024)], ids=["b512", "b1024"])
+def test_single_steps_match_oracle_large_tiles(ctx, n, b, far, mode):
+    """The same step-by-step comparison at the tile sizes of the full-size
+    workloads: at b = 512 and 1024 a tensor-core target holds 16 or 64
+    128 x 128 units and the products run over K = 512 or 1024 (several
+    units per tile, both TMEM accumulators in turn, the wide and the narrow
+    integer-digit panel kernels), and the diagonal tiles factor as task
+    graphs over 16 x 16 (b = 512) or 32 x 32 (b = 1024) blocks.  Range
+    0.05: at 0.1 the E4M3 far tiles of this 2048-point field are no longer
+    positive definite after rounding."""
+    _single_steps(ctx, n, b, far, mode, 0.05)
+
+
+def _single_steps(ctx, n, b, far, mode, a):
     simt, ozaki = mode == "cudacore", mode == "ozaki"
-    n, b = 640, 128
     nt = n // b
     pmap = I.band_map(nt, I.F64, I.F32, far, 1)
     locs, _ = OM.morton_order(I.points(n, 21))
-    S = OM.covariance(locs, 0.5, 0.1, 1.0, 1e-4)
+    S = OM.covariance(locs, 0.5, a, 1.0, 1e-4)
     state = OC.tiled_from_dense(S, b, pmap)
     T = _mk(ctx, n, b, pmap, simt=simt, ozaki=ozaki)
     for k in range(nt):

@@ -27,3 +27,14 @@ def test_bound_map_is_more_conservative_than_exact_norms():
     # every tile the bound puts in BF16 is also BF16 under the exact rule
     assert np.all((bound[lo] == I.BF16) <= (exact[lo] == I.BF16))
     assert (bound[lo] == I.BF16).sum() > 0
+
+
+def test_bound_map_rejects_nu_without_closed_form():
+    """The host bound evaluates the half-integer closed forms only; any other
+    nu is refused rather than bounded with the wrong covariance."""
+    from paper_2406_02701_gb300 import mpchol
+    locs, _ = OM.morton_order(I.points(600, 4))
+    for nu in (1.0, 0.3, 3.5):
+        with pytest.raises(mpchol.MPError) as e:
+            mpchol.map_bound(600, 128, locs, (1.0, 0.05, nu, 1e-4), 2, I.F32, I.BF16, 1e-6)
+        assert e.value.status == mpchol.MP_ERR_ARG

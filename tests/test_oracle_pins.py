@@ -408,3 +408,26 @@ def test_planted_missing_logdet_factor_is_caught(monkeypatch):
     monkeypatch.setattr(C, "step_potrf", half)
     with pytest.raises(AssertionError):
         test_ar1_closed_form_end_to_end(200, 64)
+
+
+def test_exact_loglik_field_matches_dense_and_ar1():
+    """The row-block O-exact for large fields: the same numbers as the dense
+    O-exact on a 2-D Matérn field, and the AR(1) closed form on a line."""
+    n = 900
+    locs, _ = M.morton_order(I.points(n, 6))
+    z = I.rhs(n, 3, 6)
+    S = M.covariance(locs, 2.5, 0.07, 1.4, 1e-3)
+    ref = C.exact_loglik(S, z)
+    got = C.exact_loglik_field(locs, 2.5, 0.07, 1.4, 1e-3, z, rows=128, keep_factor=True)
+    assert math.isclose(got["logdet"], ref["logdet"], rel_tol=1e-12)
+    assert np.allclose(got["loglik"], ref["loglik"], rtol=1e-12)
+    assert np.allclose(np.tril(got["L"]), ref["L"], rtol=0, atol=1e-12)
+    n, a, s2 = 1000, 0.05, 1.7
+    h = 1.0 / n
+    rho = math.exp(-h / a)
+    z = I.ar1_rhs(n, 2, rho, s2, 9)
+    r = C.exact_loglik_field(I.points_line(n, h), 0.5, a, s2, 0.0, z, rows=300)
+    for c in range(2):
+        logdet, quad = _ar1(n, h, a, s2, z[:, c])
+        assert math.isclose(r["logdet"], logdet, rel_tol=1e-11)
+        assert math.isclose(r["quad"][c], quad, rel_tol=1e-10)

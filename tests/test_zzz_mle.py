@@ -41,9 +41,24 @@ def test_stops_on_a_noisy_objective():
     g = lambda x: 850.0 + 40.0 * (x[0] + 2.3) ** 2 + 25.0 * (x[1] - 0.1) ** 2 + 3.0 * x[0] * x[1]
     noisy = lambda x: g(x) * (1.0 + 1e-10 * math.sin(1e7 * (x[0] + 2 * x[1])))
     r = nelder_mead(_batch(noisy), [-3.0, -0.7], step=0.5, max_iter=200)
-    assert r["iters"] < 200
+    assert r["iters"] < 200 and r["converged"]
     ref = nelder_mead(_batch(g), [-3.0, -0.7], step=0.5, max_iter=2000, reltol=1e-15)
     assert abs(r["f"] - ref["f"]) <= 1e-6 * abs(ref["f"])
+
+
+def test_tolerance_is_fixed_from_the_starting_value_and_cap_is_reported():
+    """R optim's Nelder-Mead fixes its tolerance once, reltol (|f(x0)| +
+    reltol) at the starting point: started far up a steep bowl the search
+    stops at a spread that a tolerance taken from the current best value
+    would not accept; a search ended by the iteration cap says so."""
+    f = lambda x: 1e6 * (x[0] ** 2 + x[1] ** 2) + 1.0
+    r = nelder_mead(_batch(f), [3.0, 4.0], step=0.5, max_iter=500, reltol=1e-6)
+    spread = r["fvals"].max() - r["fvals"].min()
+    assert r["converged"]
+    assert spread <= 1e-6 * (f([3.0, 4.0]) + 1e-6)
+    assert spread > 1e-6 * (abs(r["f"]) + 1e-6)
+    capped = nelder_mead(_batch(f), [3.0, 4.0], step=0.5, max_iter=5, reltol=1e-12)
+    assert capped["iters"] == 5 and not capped["converged"]
 
 
 def test_speculative_batches_take_the_same_path():
@@ -97,6 +112,7 @@ def test_matern_mle_matches_oracle_at_the_optimum(ctx):
         assert abs(g - want) <= 1e-6 * abs(want), (rng, s2, g, want)
     r = mle.fit(0.05, 0.5, max_iter=200)
     mle.close()
+    assert r["converged"], r["iters"]
     print("gpu fit:", r["iters"], r["evals"], r["range"], r["sigma2"], r["loglik"], "oracle fit:",
           ref["iters"], math.exp(ref["x"][0]), math.exp(ref["x"][1]), ll_star)
     # the point found is as good as the oracle's optimum (the north-star
