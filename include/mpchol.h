@@ -54,9 +54,12 @@ typedef enum {
  * per tile so that amax / s <= 448; a stored code c represents c * s. */
 typedef enum { MP_F64 = 0, MP_F32 = 1, MP_BF16 = 2, MP_F16 = 3, MP_E4M3 = 4 } mp_dtype;
 
-/* Matérn covariance parameters (Sec. 6.2): C(r) = sigma2 * M(r / range)
- * with the half-integer closed forms nu in {0.5, 1.5, 2.5}; `nugget` is
- * added to the diagonal.  Other nu give MP_ERR_ARG. */
+/* Matérn covariance parameters (Sec. 6.2): C(r) = sigma2 2^(1-nu) /
+ * Gamma(nu) x^nu K_nu(x), x = r / range (K_nu the modified Bessel function
+ * of the second kind; C(0) = sigma2), for 0 < nu <= 16: the half-integer
+ * closed forms for nu in {0.5, 1.5, 2.5}, a Chebyshev table of x^nu K_nu(x)
+ * (built on the host per nu, relative error about 1e-15) for any other nu.
+ * `nugget` is added to the diagonal.  Other nu give MP_ERR_ARG. */
 typedef struct {
   double sigma2;
   double range;
@@ -253,6 +256,11 @@ mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32_t nrhs,
  * (fixed reduction order).  Allocates a small scratch; synchronous. */
 mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const double* d_locs, mp_matern p,
                         double* d_norms, void* stream);
+
+/* The Matérn covariance C(r) of `p` (nugget not added) at count distances
+ * h_r, into h_out; host only, the same method as the generation kernels
+ * (closed forms or the per-nu Chebyshev table).  Synchronous. */
+mp_status mp_matern_host(mp_matern p, int64_t count, const double* h_r, double* h_out);
 
 /* Norm-guarded band precision map (host only).  The multi-precision tiled
  * extension (Sec. 7) leaves the choice of precisions open; this rule keeps

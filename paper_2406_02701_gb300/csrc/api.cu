@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include <array>
@@ -247,6 +248,11 @@ struct mp_tmat {
   int gen_n_amax = 0, gen_n_all = 0;
   char* d_gen = nullptr;
   size_t d_gen_cap = 0;
+  // Matérn table for nu without a closed form (device), the nu it holds
+  double* d_ktab = nullptr;
+  size_t d_ktab_cap = 0;
+  double ktab_nu = 0.0;
+  int ktab_e0 = 0;
   // loglik workspace + graph
   int ws_nrhs = 0;
   double *zp = nullptr, *x = nullptr, *r = nullptr, *w = nullptr, *d = nullptr;
@@ -265,6 +271,7 @@ struct mp_tmat {
     for (void* p : ws_allocs) P.raw_free(p);
     P.raw_free(d_gen);
     P.raw_free(d_sitems);
+    P.raw_free(d_ktab);
   }
 };
 
@@ -1160,6 +1167,10 @@ static mp_status build_gen_items(mp_tmat* t) {
       g.nu = t->cov.nu;
       g.nugget = t->cov.nugget;
       g.sigma64 = nullptr;
+      if (!matern_nu_closed(t->cov.nu)) {
+        g.ktab = t->d_ktab;
+        g.ke0 = t->ktab_e0;
+      }
       if (P.keep_sigma) {
         const TileRef r = P.h_tiles[M.sig[i * M.nt + j]];
         g.sigma64 = (double*)(P.pool[F64] + (size_t)r.idx * P.b * P.b * 8);
@@ -1183,15 +1194,58 @@ static mp_status build_gen_items(mp_tmat* t) {
   return MP_OK;
 }
 
-static bool valid_nu(double nu) { return nu == 0.5 || nu == 1.5 || nu == 2.5; }
+static bool valid_nu(double nu) { return matern_nu_valid(nu); }
+
+// Builds the Matérn table of nu on the host and uploads it into a device
+// buffer (grown with `alloc`, a stream-ordered or plain allocation) on
+// `stream`; the host table may be reused once the call returns (a copy
+// from pageable memory is staged before cudaMemcpyAsync returns).
+static mp_status upload_knu_table(mp_ctx* ctx, double nu, double** d_tab, size_t* cap, int* e0,
+                                  cudaStream_t stream,
+                                  const std::function<cudaError_t(void**, size_t)>& alloc) {
+  std::vector<double> tab;
+  if (matern_nu_table(nu, tab, e0)) return fail(ctx, MP_ERR_ARG, "nu must be in (0, 16]");
+  const size_t bytes = sizeof(double) * tab.size();
+  if (bytes > *cap) {
+    cudaError_t e = alloc((void**)d_tab, bytes);
+    if (e != cudaSuccess) return fail(ctx, MP_ERR_OOM, "Matérn table: %s", cudaGetErrorString(e));
+    *cap = bytes;
+  }
+  CK(ctx, cudaMemcpyAsync(*d_tab, tab.data(), bytes, cudaMemcpyHostToDevice, stream));
+  return MP_OK;
+}
 
 mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p) {
   if (!t || !d_locs) return fail(t ? t->P.ctx : nullptr, MP_ERR_ARG, "null argument");
   Plan& P = t->P;
-  if (!valid_nu(p.nu)) return fail(P.ctx, MP_ERR_ARG, "nu must be 0.5, 1.5 or 2.5");
+  if (!valid_nu(p.nu)) return fail(P.ctx, MP_ERR_ARG, "nu must be in (0, 16]");
   if (!(p.range > 0.0) || !(p.sigma2 > 0.0) || !(p.nugget >= 0.0))
     return fail(P.ctx, MP_ERR_ARG, "need range > 0, sigma2 > 0, nugget >= 0");
   CK(P.ctx, cudaSetDevice(P.ctx->device));
+  if (!matern_nu_closed(p.nu) && (!t->d_ktab || p.nu != t->ktab_nu)) {
+    size_t cap = t->d_ktab_cap;
+    bool freed = false;
+    mp_status st = upload_knu_table(P.ctx, p.nu, &t->d_ktab, &cap, &t->ktab_e0, P.stream,
+                                    [&](void** q, size_t bytes) {
+                                      P.raw_free(t->d_ktab);   // stream-ordered or synchronising
+                                      freed = true;
+                                      *q = nullptr;
+                                      return P.raw_alloc(q, bytes);
+                                    });
+    if (st) {
+      if (freed) {
+        if (t->d_ktab) P.raw_free(t->d_ktab);
+        t->d_ktab = nullptr;
+        t->d_ktab_cap = 0;
+      }
+      t->ktab_nu = 0.0;
+      t->gen_key.clear();
+      return st;
+    }
+    t->d_ktab_cap = cap;
+    t->ktab_nu = p.nu;
+    t->gen_key.clear();          // the items carry the table's pointer and octave
+  }
   std::vector<char> key(sizeof(void*) + sizeof(mp_matern));
   memcpy(key.data(), &d_locs, sizeof(void*));
   memcpy(key.data() + sizeof(void*), &p, sizeof(mp_matern));
@@ -1592,7 +1646,7 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
       return fail(ctx, MP_ERR_ARG, "request %d: bad n, pointers or nrhs", r);
     if (q.refine_iters != 0) return fail(ctx, MP_ERR_ARG, "request %d: batched refinement is not supported", r);
     if (!valid_nu(q.cov.nu) || !(q.cov.range > 0) || !(q.cov.sigma2 > 0) || !(q.cov.nugget >= 0))
-      return fail(ctx, MP_ERR_ARG, "request %d: bad covariance parameters", r);
+      return fail(ctx, MP_ERR_ARG, "request %d: bad covariance parameters (nu in (0, 16])", r);
     nmax = std::max(nmax, q.n);
   }
   if (b == 0) b = nmax <= 2048 ? 128 : 256;   // tuned choice for uneven small n
@@ -1625,6 +1679,23 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
   B->d_llbuf = (double*)p;
   if ((st = P.alloc(&p, sizeof(int32_t) * count))) { delete B; return st; }
   B->d_stbuf = (int32_t*)p;
+  // Matérn tables of the requests' nu without a closed form, one per value
+  std::vector<std::pair<double, std::pair<double*, int>>> ktabs;
+  for (int r = 0; r < count; ++r) {
+    const double nu = reqs[r].cov.nu;
+    if (matern_nu_closed(nu)) continue;
+    bool have = false;
+    for (auto& k : ktabs) have = have || k.first == nu;
+    if (have) continue;
+    double* d = nullptr;
+    size_t cap = 0;
+    int e0 = 0;
+    st = upload_knu_table(ctx, nu, &d, &cap, &e0, P.stream, [&](void** q, size_t bytes) {
+      return P.alloc(q, bytes) == MP_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+    });
+    if (st) { delete B; return st; }
+    ktabs.push_back({nu, {d, e0}});
+  }
   // generation items
   std::vector<ItemGen> gamax, gall;
   std::vector<ItemBatchCopy> cp;
@@ -1649,6 +1720,11 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
         g.range = reqs[r].cov.range;
         g.nu = reqs[r].cov.nu;
         g.nugget = reqs[r].cov.nugget;
+        for (auto& k : ktabs)
+          if (k.first == g.nu) {
+            g.ktab = k.second.first;
+            g.ke0 = k.second.second;
+          }
         if (P.h_tiles[g.tile].dt == E4M3) gamax.push_back(g);
         gall.push_back(g);
       }
@@ -1731,8 +1807,17 @@ extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const doub
   if (!ctx || !d_locs || !d_norms) return fail(ctx, MP_ERR_ARG, "null argument");
   if (n < 1 || b < 128 || b > 1024 || b % 128) return fail(ctx, MP_ERR_ARG, "bad n or b");
   if (!valid_nu(p.nu) || !(p.range > 0.0) || !(p.sigma2 > 0.0) || !(p.nugget >= 0.0))
-    return fail(ctx, MP_ERR_ARG, "bad covariance parameters");
+    return fail(ctx, MP_ERR_ARG, "bad covariance parameters (nu in (0, 16])");
   CK(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d_ktab = nullptr;
+  size_t kcap = 0;
+  int ke0 = 0;
+  if (!matern_nu_closed(p.nu)) {
+    mp_status st = upload_knu_table(ctx, p.nu, &d_ktab, &kcap, &ke0, s,
+                                    [](void** q, size_t bytes) { return cudaMalloc(q, bytes); });
+    if (st) return st;
+  }
   const int nt = (int)((n + b - 1) / b);
   std::vector<ItemGen> items;
   for (int i = 0; i < nt; ++i)
@@ -1740,14 +1825,18 @@ extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const doub
       ItemGen g{};
       g.ti = i; g.tj = j; g.locs = d_locs; g.n = n;
       g.sigma2 = p.sigma2; g.range = p.range; g.nu = p.nu; g.nugget = p.nugget;
+      g.ktab = d_ktab; g.ke0 = ke0;
       items.push_back(g);
     }
   const int parts = b / 16;
   ItemGen* d_items = nullptr;
   double* partial = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
-  CK(ctx, cudaMalloc(&d_items, sizeof(ItemGen) * items.size()));
-  cudaError_t e = cudaMalloc(&partial, sizeof(double) * items.size() * parts);
+  cudaError_t e = cudaMalloc(&d_items, sizeof(ItemGen) * items.size());
+  if (e != cudaSuccess) {
+    if (d_ktab) { cudaStreamSynchronize(s); cudaFree(d_ktab); }
+    return fail(ctx, MP_ERR_CUDA, "tile norms: %s", cudaGetErrorString(e));
+  }
+  e = cudaMalloc(&partial, sizeof(double) * items.size() * parts);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_items, items.data(), sizeof(ItemGen) * items.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_norms, 0, sizeof(double) * nt * nt, s);
@@ -1755,9 +1844,33 @@ extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const doub
     launch_tile_norms(b, d_items, (int)items.size(), nt, partial, d_norms, s);
     e = cudaStreamSynchronize(s);
   }
+  if (e != cudaSuccess) cudaStreamSynchronize(s);
   cudaFree(d_items);
   if (partial) cudaFree(partial);
+  if (d_ktab) cudaFree(d_ktab);
   if (e != cudaSuccess) return fail(ctx, MP_ERR_CUDA, "tile norms: %s", cudaGetErrorString(e));
+  return MP_OK;
+}
+
+extern "C" mp_status mp_matern_host(mp_matern p, int64_t count, const double* h_r, double* h_out) {
+  if (count < 0 || (count > 0 && (!h_r || !h_out))) return MP_ERR_ARG;
+  if (!valid_nu(p.nu) || !(p.range > 0.0) || !(p.sigma2 > 0.0)) {
+    set_error_text("mp_matern_host: need 0 < nu <= 16, range > 0, sigma2 > 0");
+    return MP_ERR_ARG;
+  }
+  std::vector<double> tab;
+  int e0 = 0;
+  const bool closed = matern_nu_closed(p.nu);
+  if (!closed && matern_nu_table(p.nu, tab, &e0)) return MP_ERR_ARG;
+  for (int64_t i = 0; i < count; ++i) {
+    const double x = h_r[i] / p.range;
+    if (closed) {
+      const double poly = p.nu == 0.5 ? 1.0 : p.nu == 1.5 ? 1.0 + x : 1.0 + x + x * x / 3.0;
+      h_out[i] = p.sigma2 * poly * std::exp(-x);
+    } else {
+      h_out[i] = p.sigma2 * matern_nu_host(tab.data(), e0, x);
+    }
+  }
   return MP_OK;
 }
 

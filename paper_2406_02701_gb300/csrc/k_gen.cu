@@ -5,18 +5,22 @@
 // sorted by a bitonic network (global passes for strides >= 1024, shared
 // memory for the rest).
 //
-// Generation (the Matérn model of Sec. 6.2 in its half-integer closed
-// forms): every entry of a lower tile is computed in float64 from the two
-// locations and rounded once into the tile's format.  exp(-x) follows Tang's
+// Generation (the Matérn model of Sec. 6.2; half-integer nu by the closed
+// forms, any other nu in (0, 16] from a Chebyshev table of x^nu K_nu(x)
+// built on the host, see matern_nu_table): every entry of a lower tile is
+// computed in float64 from the two locations and rounded once into the
+// tile's format.  exp(-x) follows Tang's
 // table-driven method (fewer FP64 operations than the general exp; the
 // kernel is bound by the FP64 pipe).  E4M3 tiles first get
 // the tile's amax from a separate pass (`gen_amax`), then the power-of-two
 // scale.  Rows/columns beyond n are identity padding.  The coordinate
 // differences are written with explicit _rn intrinsics; the squared
 // distance, the polynomial and exp use fused multiply-adds on purpose.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "mp_device.cuh"
 
@@ -118,6 +122,32 @@ __device__ __forceinline__ double exp_neg(double x, const double* tab) {
   return __longlong_as_double(__double_as_longlong(v) + ((long long)m << 52));
 }
 
+// Matérn correlation for nu without a closed form, from the table of
+// matern_nu_table: x = m 2^E (m in [1, 2)) lies in the half octave
+// 2 (E - e0) + (m >= 1.5), whose Chebyshev series in u = 4 (m - 1.25) or
+// 4 (m - 1.75) -- exact, the piece's centre and half-width being dyadic --
+// is summed by Clenshaw's recurrence.  Returns g(x) for x < 1 and g(x) e^x
+// for 1 <= x < 2^KNU_EMAX (the caller multiplies by e^{-x}); 1 below
+// 2^e0, where g differs from 1 by less than 2^-54.
+__device__ __forceinline__ double knu_table(const double* __restrict__ tab, int e0, double x) {
+  const int hi = __double2hiint(x);
+  const int E = ((hi >> 20) & 0x7ff) - 1023;
+  if (E < e0) return 1.0;
+  const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));
+  const int upper = m >= 1.5;
+  const double u = 4.0 * (m - (upper ? 1.75 : 1.25));
+  const double* c = tab + (2 * (E - e0) + upper) * KNU_COEF;
+  const double u2 = u + u;
+  double b1 = 0.0, b2 = 0.0;
+#pragma unroll
+  for (int k = KNU_COEF - 1; k >= 1; --k) {
+    const double t = fma(u2, b1, __ldg(c + k) - b2);
+    b2 = b1;
+    b1 = t;
+  }
+  return fma(u, b1, __ldg(c) - b2);
+}
+
 // Matérn covariance of two locations (closed forms, x = r / range):
 // sigma^2 e^{-x} (nu = 1/2), sigma^2 (1 + x) e^{-x} (3/2),
 // sigma^2 (1 + x + x^2/3) e^{-x} (5/2).
@@ -135,11 +165,20 @@ __device__ __forceinline__ double entry(const ItemGen& it, double inv_range, con
   double x = __dmul_rn(r, inv_range);
   // sigma^2 times the closed-form polynomial, Horner with fused multiply-adds
   const double s = it.sigma2;
-  double poly;
-  if (it.nu == 0.5) poly = s;
-  else if (it.nu == 1.5) poly = fma(s, x, s);
-  else poly = fma(x, fma(x, s * (1.0 / 3.0), s), s);
-  double v = __dmul_rn(poly, exp_neg(x, tab));
+  double v;
+  if (it.ktab) {
+    // general nu: g(x) below 1, g(x) e^x times e^{-x} from 1 to 2^KNU_EMAX
+    // (beyond, the correlation is below the smallest double)
+    if (x < 1.0) v = __dmul_rn(s, knu_table(it.ktab, it.ke0, x));
+    else if (x < (double)(1 << KNU_EMAX)) v = __dmul_rn(__dmul_rn(s, knu_table(it.ktab, it.ke0, x)), exp_neg(x, tab));
+    else v = 0.0;
+  } else {
+    double poly;
+    if (it.nu == 0.5) poly = s;
+    else if (it.nu == 1.5) poly = fma(s, x, s);
+    else poly = fma(x, fma(x, s * (1.0 / 3.0), s), s);
+    v = __dmul_rn(poly, exp_neg(x, tab));
+  }
   if (gi == gj) v = __dadd_rn(v, it.nugget);
   return v;
 }
@@ -251,6 +290,101 @@ __global__ void k_reduce_norms(const ItemGen* __restrict__ items, int count, int
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- general nu
+//
+// g(x) = 2^(1-nu) / Gamma(nu) x^nu K_nu(x) (g(0) = 1) at a node x > 0 from the
+// integral representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
+// by the trapezoidal rule, which converges geometrically for this
+// integrand (analytic in the strip |Im t| < pi/2 and decaying doubly
+// exponentially): step h = the power of two at most min(1/4, 1/(2 sqrt x),
+// 1/(nu + 2)) / 2, terms
+// summed with Kahan compensation until they fall below 1e-22 of the sum
+// past the integrand's peak.  For x >= 1 the factor e^x is folded in
+// (exp(-x (cosh t - 1)) in place of exp(-x cosh t), with cosh t - 1 =
+// 2 sinh^2(t/2) to keep it accurate), so that the table stays finite where
+// K_nu underflows.  The x^nu and cosh(nu t) factors are multiplied, not
+// added as logarithms (a logarithm of 30 carries 30 units of rounding).
+static double knu_node(double x, double nu) {
+  // a power of two at most half the step bound, so that every node t = k h
+  // is exact; nu t is then carried as p + e (e from a fused multiply-add)
+  // and cosh(p + e) = cosh p + e sinh p to first order
+  const double hb = 0.5 * std::fmin(std::fmin(0.25, 0.5 / std::sqrt(x)), 1.0 / (nu + 2.0));
+  const double h = std::ldexp(1.0, (int)std::floor(std::log2(hb)));
+  const bool scaled = x >= 1.0;
+  const double xn = std::pow(x, nu);
+  double sum = 0.0, comp = 0.0;
+  for (int k = 0; k < 1000000; ++k) {
+    const double t = k * h;
+    const double sh = std::sinh(0.5 * t);
+    const double y = scaled ? 2.0 * x * sh * sh : x * std::cosh(t);
+    const double p = nu * t, e = std::fma(nu, t, -p);
+    double term = xn * std::fma(e, std::sinh(p), std::cosh(p)) * std::exp(-y);
+    if (k == 0) term *= 0.5;
+    const double yk = term - comp;
+    const double tk = sum + yk;
+    comp = (tk - sum) - yk;
+    sum = tk;
+    if (k > 0 && term < 1e-22 * sum && y > nu * t + 5.0) break;
+  }
+  return std::exp2(1.0 - nu) / std::tgamma(nu) * sum * h;
+}
+
+bool matern_nu_closed(double nu) { return nu == 0.5 || nu == 1.5 || nu == 2.5; }
+bool matern_nu_valid(double nu) { return nu > 0.0 && nu <= KNU_NU_MAX; }
+
+// Chebyshev interpolation of g on each half octave at the KNU_COEF
+// Chebyshev points of the first kind; the angle of T_m at node j, m (2j+1)
+// pi / (2 KNU_COEF), is reduced as an integer before the cosine.  The
+// table starts at 2^e0 with e0 = min(-32, floor(-54 / (2 nu))): below it
+// both the regular part of g (1 - x^2 / (4 (nu - 1)) + ..., with an
+// x^2 log x term at nu = 1) and the singular part (a multiple of x^(2 nu))
+// differ from 1 by less than 2^-54, so g = 1 there.
+int matern_nu_table(double nu, std::vector<double>& coef, int* e0) {
+  if (!matern_nu_valid(nu)) return 1;
+  const int lo = std::max(-1022, std::min(-32, (int)std::floor(-54.0 / (2.0 * nu))));
+  const int pieces = 2 * (KNU_EMAX - lo);
+  coef.assign((size_t)pieces * KNU_COEF, 0.0);
+  const double pi = 3.14159265358979323846;
+  double f[KNU_COEF], cs[4 * KNU_COEF];
+  for (int q = 0; q < 4 * KNU_COEF; ++q) cs[q] = std::cos(pi * q / (2.0 * KNU_COEF));
+  for (int p = 0; p < pieces; ++p) {
+    const int E = lo + p / 2;
+    const double centre = (p & 1) ? 1.75 : 1.25;
+    for (int j = 0; j < KNU_COEF; ++j) {
+      const double u = cs[2 * j + 1];                 // cos((j + 1/2) pi / KNU_COEF)
+      f[j] = knu_node(std::ldexp(centre + 0.25 * u, E), nu);
+    }
+    for (int m = 0; m < KNU_COEF; ++m) {
+      double acc = 0.0;
+      for (int j = 0; j < KNU_COEF; ++j) acc += f[j] * cs[(m * (2 * j + 1)) % (4 * KNU_COEF)];
+      coef[(size_t)p * KNU_COEF + m] = (m == 0 ? 1.0 : 2.0) / KNU_COEF * acc;
+    }
+  }
+  *e0 = lo;
+  return 0;
+}
+
+double matern_nu_host(const double* coef, int e0, double x) {
+  if (!(x > 0.0)) return 1.0;
+  if (x >= std::ldexp(1.0, KNU_EMAX)) return 0.0;
+  int ex;
+  const double fr = std::frexp(x, &ex);            // x = fr 2^ex, fr in [0.5, 1)
+  const int E = ex - 1;
+  if (E < e0) return 1.0;
+  const double m = 2.0 * fr;
+  const int upper = m >= 1.5;
+  const double u = 4.0 * (m - (upper ? 1.75 : 1.25));
+  const double* c = coef + (size_t)(2 * (E - e0) + upper) * KNU_COEF;
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = KNU_COEF - 1; k >= 1; --k) {
+    const double t = 2.0 * u * b1 - b2 + c[k];
+    b2 = b1;
+    b1 = t;
+  }
+  const double g = u * b1 - b2 + c[0];
+  return x < 1.0 ? g : g * std::exp(-x);
+}
 
 // The e^{-x} tables of the current device, from long double arithmetic on
 // the host (2^{j/64} as a double plus its remainder; ln2/64 as a 37-bit head

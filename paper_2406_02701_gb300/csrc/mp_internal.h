@@ -162,6 +162,11 @@ struct ItemGen {
   int64_t n;
   double sigma2, range, nu, nugget;
   double* sigma64;    // optional float64 copy (b x b row-major) or null
+  // nu without a closed form: the Matérn table of matern_nu_table (device
+  // copy) and its first octave; null for nu in {1/2, 3/2, 5/2}
+  const double* ktab;
+  int32_t ke0;
+  int32_t kpad_;
 };
 
 // Solve items.  Diagonal: tile = L_ii^{-T} (FP64), xj = X-product of xi
@@ -229,6 +234,20 @@ void launch_gen_amax(const Arena& A, const ItemGen* items, int count, cudaStream
 void launch_generate(const Arena& A, const ItemGen* items, int count, cudaStream_t s);
 // Uploads the generation kernels' e^{-x} tables to the current device; 0 on success.
 int init_gen_tables();
+// Matérn correlation for nu without a closed form (host side of the
+// generation kernels): KNU_COEF Chebyshev coefficients per half octave
+// [2^E, 1.5 2^E) and [1.5 2^E, 2^(E+1)), E = e0 .. KNU_EMAX - 1, of
+// g(x) = 2^(1-nu) / Gamma(nu) x^nu K_nu(x) for x < 1 and of g(x) e^x for
+// x >= 1; g(x) = 1 below 2^e0 and 0 from 2^KNU_EMAX on.
+constexpr int KNU_COEF = 16;
+constexpr int KNU_EMAX = 10;
+constexpr double KNU_NU_MAX = 16.0;
+bool matern_nu_closed(double nu);          // nu in {1/2, 3/2, 5/2}
+bool matern_nu_valid(double nu);           // 0 < nu <= KNU_NU_MAX
+// Builds the table (0 on success); e0 receives the first octave.
+int matern_nu_table(double nu, std::vector<double>& coef, int* e0);
+// g(x) e^{-x} ... the correlation at x = r / range from a host table.
+double matern_nu_host(const double* coef, int e0, double x);
 // Frobenius norm of every generated lower tile into norms[ti * nt + tj]
 // (partial: count * b/16 doubles of scratch).
 void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,

@@ -63,6 +63,7 @@ _SIGS = {
     "mp_loglik": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
     "mp_tile_norms": (C.c_int, [P, C.c_int64, C.c_int32, P, mp_matern, P, P]),
     "mp_map_guarded": (C.c_int, [C.c_int32, P, C.c_int32, C.c_uint8, C.c_uint8, C.c_double, P]),
+    "mp_matern_host": (C.c_int, [mp_matern, C.c_int64, P, P]),
     "mp_tmat_stats": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "mp_chol_profile": (C.c_int, [P, C.c_int32, P, P, P]),
@@ -408,6 +409,19 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def matern_host(r, sigma2, range_, nu):
+    """C(r) by the library's host evaluation (closed forms or the per-nu
+    Chebyshev table of the generation kernels)."""
+    lib = load()
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1))
+    out = np.empty_like(r)
+    st = lib.mp_matern_host(mp_matern(sigma2, range_, nu, 0.0), r.size, r.ctypes.data_as(C.c_void_p),
+                            out.ctypes.data_as(C.c_void_p))
+    if st != MP_OK:
+        raise MPError(st, "mp_matern_host")
+    return out
 
 
 def map_bound(n, b, sorted_locs, cov, band, near, far, eps):

@@ -109,7 +109,7 @@ def _mixed_map(nt):
     return m
 
 
-@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5, 0.3, 1.0, 2.2])
 def test_generation_matches_oracle_every_format(ctx, nu):
     n, b = 700, 128              # 6 tiles per side, ragged last tile
     nt = -(-n // b)
@@ -143,6 +143,11 @@ def test_generation_matches_oracle_every_format(ctx, nu):
                 x = np.zeros((b, b))
                 x[:len(ri), :len(rj)] = d / 0.08
                 tol = (4 + 4 * x) * 2.0 ** -52 * np.abs(want) + 1e-300
+                if nu not in (0.5, 1.5, 2.5):
+                    # the oracle's K_nu (scipy) is good to a few 1e-14; the
+                    # library's table to about 1e-15 (pinned on the CPU
+                    # against forty-digit values)
+                    tol = tol + 1e-13 * np.abs(want)
                 if i == j:
                     tol = np.tril(tol)
                 assert np.all(np.abs(got - want) <= tol), (i, j, np.max(np.abs(got - want) - tol))
@@ -220,7 +225,8 @@ def _single_steps(ctx, n, b, far, mode, a):
         _load_state(T, state, nt)
         T.chol_steps(k, k + 1)
         torch.cuda.synchronize()
-        OC.step(state, k)
+        OC.step_potrf(state, k)
+        OC.step_trsm(state, k)
         # diagonal factor
         got, _, _ = T.get_tile(k, k)
         want = state.tiles[(k, k)].codes
@@ -243,7 +249,12 @@ def _single_steps(ctx, n, b, far, mode, a):
                     # error of a rounding boundary: at most 2 bound / ulp
                     frac += 2 * np.mean(np.minimum(ob / ulp(rt.values(), fmt), 0.5))
                 assert_close_fmt(got, rt.values(), fmt, extra=extra, frac=frac, what=f"trsm {i},{k}")
-        # trailing updates
+        # trailing updates, from the panel the GPU wrote: a panel entry that
+        # rounded one unit apart (allowed above) must not count against them
+        for i in range(k + 1, nt):
+            _, codes, sc = T.get_tile(i, k)
+            state.tiles[(i, k)] = OC.Tile(codes, state.tiles[(i, k)].fmt, sc)
+        OC.step_update(state, k)
         for j in range(k + 1, nt):
             for i in range(j, nt):
                 got, codes, s = T.get_tile(i, j)
