@@ -230,7 +230,7 @@ def bound_map(sorted_locs: np.ndarray, b: int, nu: float, a: float, sigma2: floa
     boxes of the two tiles' points (the Matérn covariance decreases with
     distance), and ||A||_F by its lower bound sqrt(n) (sigma2 + nugget)
     (the diagonal alone): a more conservative choice than guarded_map."""
-    from .matern import matern_closed
+    from .matern import matern
     n = sorted_locs.shape[0]
     nt = -(-n // b)
     boxes = []
@@ -249,7 +249,7 @@ def bound_map(sorted_locs: np.ndarray, b: int, nu: float, a: float, sigma2: floa
             xj0, xj1, yj0, yj1, cj = boxes[j]
             dx = max(0.0, max(xi0 - xj1, xj0 - xi1))
             dy = max(0.0, max(yi0 - yj1, yj0 - yi1))
-            B = math.sqrt(float(ci) * float(cj)) * float(matern_closed(math.sqrt(dx * dx + dy * dy), nu, a, sigma2))
+            B = math.sqrt(float(ci) * float(cj)) * float(matern(math.sqrt(dx * dx + dy * dy), nu, a, sigma2))
             m[i, j] = far if F.unit_roundoff(far) * B <= bound else near
     return m
 

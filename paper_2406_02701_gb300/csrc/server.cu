@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mpchol.h"
+#include "mp_internal.h"
 
 namespace mp {
 void set_error_text(const char* msg);
@@ -62,8 +63,10 @@ std::vector<int64_t> morton_perm(const double* locs, int64_t n) {
   return p;
 }
 
-double matern(double r, const mp_matern& c) {
+// C(r): the closed forms, or the generation kernels' table for other nu
+double matern(double r, const mp_matern& c, const std::vector<double>& tab, int e0) {
   double x = r / c.range;
+  if (!mp::matern_nu_closed(c.nu)) return c.sigma2 * mp::matern_nu_host(tab.data(), e0, x);
   double poly = c.nu == 0.5 ? 1.0 : c.nu == 1.5 ? 1.0 + x : 1.0 + x + x * x / 3.0;
   return c.sigma2 * poly * std::exp(-x);
 }
@@ -92,10 +95,10 @@ extern "C" mp_status mp_map_bound(int64_t n, int32_t b, const double* h_sorted_l
                                   uint8_t* h_map) {
   if (n < 1 || b < 1 || !h_sorted_locs || !h_map || band < 0 || !(eps > 0)) return MP_ERR_ARG;
   if (!(c.range > 0) || !(c.sigma2 > 0)) return MP_ERR_ARG;
-  // the host covariance below has the closed forms only: another nu would
-  // silently bound the wrong covariance
-  if (!(c.nu == 0.5 || c.nu == 1.5 || c.nu == 2.5)) {
-    mp::set_error_text("mp_map_bound: nu must be 0.5, 1.5 or 2.5");
+  std::vector<double> tab;
+  int e0 = 0;
+  if (!mp::matern_nu_valid(c.nu) || (!mp::matern_nu_closed(c.nu) && mp::matern_nu_table(c.nu, tab, &e0))) {
+    mp::set_error_text("mp_map_bound: nu must be in (0, 16]");
     return MP_ERR_ARG;
   }
   const int nt = (int)((n + b - 1) / b);
@@ -124,7 +127,7 @@ extern "C" mp_status mp_map_bound(int64_t n, int32_t b, const double* h_sorted_l
         else {
           double dx = std::max(0.0, std::max(lo_x[i] - hi_x[j], lo_x[j] - hi_x[i]));
           double dy = std::max(0.0, std::max(lo_y[i] - hi_y[j], lo_y[j] - hi_y[i]));
-          double B = std::sqrt((double)cnt[i] * (double)cnt[j]) * matern(std::sqrt(dx * dx + dy * dy), c);
+          double B = std::sqrt((double)cnt[i] * (double)cnt[j]) * matern(std::sqrt(dx * dx + dy * dy), c, tab, e0);
           m = uround(far_dt) * B <= bound ? far_dt : near_dt;
         }
       }
@@ -280,8 +283,7 @@ extern "C" mp_status mp_server_submit(mp_server* S, int64_t n, const double* h_l
                                       int32_t nrhs, int32_t refine_iters, mp_matern cov,
                                       int64_t* id) {
   if (!S || n < 1 || !h_locs || !h_z || nrhs < 1 || refine_iters < 0 || !id) return MP_ERR_ARG;
-  if (!(cov.nu == 0.5 || cov.nu == 1.5 || cov.nu == 2.5) || !(cov.range > 0) || !(cov.sigma2 > 0) ||
-      !(cov.nugget >= 0))
+  if (!mp::matern_nu_valid(cov.nu) || !(cov.range > 0) || !(cov.sigma2 > 0) || !(cov.nugget >= 0))
     return MP_ERR_ARG;
   Job* J = new Job;
   J->id = S->next_id++;

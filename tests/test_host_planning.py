@@ -29,15 +29,28 @@ def test_bound_map_is_more_conservative_than_exact_norms():
     assert (bound[lo] == I.BF16).sum() > 0
 
 
-def test_bound_map_rejects_nu_without_closed_form():
-    """The host bound evaluates the half-integer closed forms only; any other
-    nu is refused rather than bounded with the wrong covariance."""
+def test_bound_map_rejects_unsupported_nu():
+    """nu outside (0, 16] is refused rather than bounded with some other
+    covariance."""
     from paper_2406_02701_gb300 import mpchol
     locs, _ = OM.morton_order(I.points(600, 4))
-    for nu in (1.0, 0.3, 3.5):
+    for nu in (0.0, -1.0, 17.0):
         with pytest.raises(mpchol.MPError) as e:
             mpchol.map_bound(600, 128, locs, (1.0, 0.05, nu, 1e-4), 2, I.F32, I.BF16, 1e-6)
         assert e.value.status == mpchol.MP_ERR_ARG
+
+
+@pytest.mark.parametrize("nu", [0.3, 1.0, 2.2])
+def test_bound_map_general_nu_matches_oracle(nu):
+    """The bound map for nu without a closed form: the oracle's bound_map
+    with the covariance through scipy's K_nu gives the same map (a tile
+    whose bound sits within rounding of the threshold could differ; none
+    does here)."""
+    from paper_2406_02701_gb300 import mpchol
+    n, b = 3000, 256
+    locs, _ = OM.morton_order(I.points(n, 8))
+    got = mpchol.map_bound(n, b, locs, (1.0, 0.04, nu, 1e-4), 2, I.F32, I.BF16, 1e-6)
+    assert np.array_equal(got, OC.bound_map(locs, b, nu, 0.04, 1.0, 1e-4, 2, I.F32, I.BF16, 1e-6))
 
 
 @pytest.mark.parametrize("nu", [0.05, 0.3, 1.0, 2.2, 3.7, 7.5, 16.0])
