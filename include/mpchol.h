@@ -118,6 +118,15 @@ const char* mp_version(void);
  *             FP64-stored panel tiles keep the FP64 solve.
  *             MP_TMAT_FP64_PANEL solves every panel tile by FP64
  *             substitution instead.
+ *             Accuracy of the two update paths: the tensor cores' FP32
+ *             accumulation rounds toward zero, a bias of about 1e-6 of a
+ *             K = 512 product per update (measured), which refinement does
+ *             not remove from the log-determinant; MP_TMAT_SIMT_UPDATES
+ *             accumulates with IEEE FP32 fused multiply-adds (the method's
+ *             FP32 accumulation exactly, about 2.5x the factorisation time).
+ *             Keep one path for all updates of a matrix: SYRK on one and
+ *             GEMM on the other leaves a factor that FP64 refinement no
+ *             longer converges with at n = 65536.
  *   stream  : stream all later calls on this matrix are ordered on.
  * The library allocates tile storage and workspace on the device (see
  * mp_tmat_info for the byte count).  Rows/columns n..NT*b-1 are padding
@@ -218,6 +227,17 @@ mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet);
  * mp_chol is the same as mp_chol_steps(t, 0, NT) plus the outputs.
  * Asynchronous. */
 mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1);
+
+/* Budget of the bounded device-side waits of the task-graph kernels (the
+ * diagonal tile's factorisation and the triangular solves): a wait gives up
+ * after `polls` polls of about 64 ns each (0: the default, 2^21 polls,
+ * about 0.1-0.3 s), sets the matrix's error word and its kernel returns;
+ * mp_chol then reports -MP_ERR_TIMEOUT in d_info and mp_loglik writes NaN
+ * log-likelihoods until the matrix is factored again.  A small budget makes
+ * waits run out on purpose (failure handling can be tested without a
+ * hung GPU).  Waits for the matrix's stream, drops its captured graphs
+ * (recaptured at the next call).  Synchronous. */
+mp_status mp_tmat_set_wait_budget(mp_tmat* t, int32_t polls);
 
 /* Copies log det Sigma of the factorised matrix into d_out (1 float64).
  * MP_ERR_STATE if mp_chol has not been enqueued.  Asynchronous. */
@@ -414,6 +434,13 @@ mp_status mp_server_factor(mp_server* s, int64_t id, mp_tmat** t);
 
 /* Frees a finished request's device memory. */
 mp_status mp_server_release(mp_server* s, int64_t id);
+
+/* Failure injection for the admission path: the next `count` admissions
+ * fail their input allocation as if the device had no memory left (made on
+ * the host; the request's tiled matrix already exists and is freed by the
+ * failure path).  Those requests finish with MP_ERR_OOM; the others are
+ * unaffected.  Host only. */
+mp_status mp_server_inject_alloc_failures(mp_server* s, int32_t count);
 
 /* Queue length, requests on the GPU, kept factors, device bytes in use. */
 mp_status mp_server_stats(mp_server* s, int64_t* queued, int64_t* running, int64_t* kept,

@@ -124,6 +124,7 @@ struct Plan {
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
   int dag_nb = 32;                 // block of the diagonal-tile task graph (16 or 32)
+  int wait_polls = 0;              // task-graph wait budget (0: the kernels' default)
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
   std::vector<int64_t> ltab_off;
@@ -187,6 +188,7 @@ struct Plan {
     A.amax = d_amax;
     A.err = d_err;
     A.b = b;
+    A.wait_polls = wait_polls;
     return A;
   }
 
@@ -499,9 +501,10 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         g.f8.push_back(ItemFp8{tc_, vs, v});
         ++vslot;
       }
+      const bool tc_ok = P.use_tc;
       if (kd == F64) {
         g.u64.push_back(ItemUpd{tc_, ta, tb, i == j, v, vs, 0});
-      } else if (P.use_tc && kd == F32) {
+      } else if (tc_ok && kd == F32) {
         ItemTC u{};
         u.c = tc_;
         u.a = P.slot_hi[slot_of(m, i)];
@@ -515,7 +518,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
       } else {
         const int a = needs_round(pa, kd) ? form(m, i, kd) : ta;
         const int bb = needs_round(pb, kd) ? form(m, j, kd) : tb;
-        if (P.use_tc) {
+        if (tc_ok) {
           ItemTC u{};
           u.c = tc_;
           u.a = a;
@@ -1308,6 +1311,19 @@ mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet) {
   return check_launch(P.ctx);
 }
 
+mp_status mp_tmat_set_wait_budget(mp_tmat* t, int32_t polls) {
+  if (!t || polls < 0) return MP_ERR_ARG;
+  Plan& P = t->P;
+  if (polls == P.wait_polls) return MP_OK;
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  // the captured graphs hold the arena (and with it the budget) by value
+  CK(P.ctx, cudaStreamSynchronize(P.stream));
+  if (P.chol_exec) { cudaGraphExecDestroy(P.chol_exec); P.chol_exec = nullptr; }
+  if (t->ll_exec) { cudaGraphExecDestroy(t->ll_exec); t->ll_exec = nullptr; t->ll_key.clear(); }
+  P.wait_polls = polls;
+  return MP_OK;
+}
+
 mp_status mp_logdet(mp_tmat* t, double* d_out) {
   if (!t || !d_out) return MP_ERR_ARG;
   Plan& P = t->P;
@@ -1548,7 +1564,7 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
         }
         launch_dot(t->zp, t->x, N, N, nrhs, quad, s);
       }
-      launch_loglik(P.d_logdet, quad, n, nrhs, d_ll, s);
+      launch_loglik(P.d_logdet, quad, n, nrhs, d_ll, P.d_err, s);
       if (d_quad) cudaMemcpyAsync(d_quad, quad, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, s);
       if (d_iters) k_copy_iters<<<(nrhs + 127) / 128, 128, 0, s>>>(t->iters, d_iters, nrhs);
     }, &t->ll_exec, &t->ll_kernels);

@@ -222,19 +222,19 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     int* wv = ver + nb * nb;
     if (tid == 0) {
       bool ok;
-      if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err);
+      if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err, A.wait_polls);
       else if (tk.op == 3)   // G(k): blocks (k, k-1) and (k, k) updated up to k-2 (F(k-1) below)
-        ok = dag_wait(&ver[k * nb + k - 1], k - 1, A.err) && dag_wait(&ver[k * nb + k], k - 1, A.err);
-      else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err) && dag_wait(&ver[r * nb + k], k, A.err);
+        ok = dag_wait(&ver[k * nb + k - 1], k - 1, A.err, A.wait_polls) && dag_wait(&ver[k * nb + k], k - 1, A.err, A.wait_polls);
+      else if (tk.op == 1) ok = dag_wait(&ver[k * nb + k], k + 1, A.err, A.wait_polls) && dag_wait(&ver[r * nb + k], k, A.err, A.wait_polls);
       else if (tk.op == 2)
-        ok = dag_wait(&ver[r * nb + k], k + 1, A.err) && dag_wait(&ver[c * nb + k], k + 1, A.err) &&
-             dag_wait(&ver[r * nb + c], k, A.err);
+        ok = dag_wait(&ver[r * nb + k], k + 1, A.err, A.wait_polls) && dag_wait(&ver[c * nb + k], k + 1, A.err, A.wait_polls) &&
+             dag_wait(&ver[r * nb + c], k, A.err, A.wait_polls);
       else if (tk.op == 4)   // V(r, j = c): F(r) done, W_jr has its r - j updates
-        ok = dag_wait(&ver[r * nb + r], r + 1, A.err) && dag_wait(&wv[c * nb + r], r - c, A.err);
+        ok = dag_wait(&ver[r * nb + r], r + 1, A.err, A.wait_polls) && dag_wait(&wv[c * nb + r], r - c, A.err, A.wait_polls);
       else                   // E(r, k, j = c): L_rk, W_jk final; the previous update of W_jr
-        ok = dag_wait(&ver[r * nb + k], k + 1, A.err) &&
-             (k == c ? dag_wait(&wv[c * nb + c], 1, A.err) : dag_wait(&wv[c * nb + k], k - c + 1, A.err)) &&
-             dag_wait(&wv[c * nb + r], k - c, A.err);
+        ok = dag_wait(&ver[r * nb + k], k + 1, A.err, A.wait_polls) &&
+             (k == c ? dag_wait(&wv[c * nb + c], 1, A.err, A.wait_polls) : dag_wait(&wv[c * nb + k], k - c + 1, A.err, A.wait_polls)) &&
+             dag_wait(&wv[c * nb + r], k - c, A.err, A.wait_polls);
       if (!ok) atomicExch(A.err, 1);
       s_ok = ok;
     }
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         const double* D = it.dinv + (int64_t)(k - 1) * DB * DB;
         for (int e = tid; e < DB * DB; e += blockDim.x) S0[e / DB][e % DB] = __ldcg(Tl + (int64_t)(e / DB) * b + e % DB);
         if (tid == 0) {
-          s_ok2 = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err);
+          s_ok2 = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err, A.wait_polls);
           if (!s_ok2) atomicExch(A.err, 1);
         }
         __syncthreads();

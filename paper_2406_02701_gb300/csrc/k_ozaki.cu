@@ -119,12 +119,6 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float* v) {
 }
 
 // Smallest power of two >= x (1 for x = 0).
-__device__ __forceinline__ float pow2_above(float x) {
-  if (!(x > 0.f)) return 1.f;
-  int e;
-  float m = frexpf(x, &e);                    // x = m 2^e, m in [0.5, 1)
-  return m == 0.5f ? ldexpf(1.f, e - 1) : ldexpf(1.f, e);
-}
 __device__ __forceinline__ double pow2_above_d(double x) {
   if (!(x > 0.0)) return 1.0;
   int e;
@@ -159,13 +153,26 @@ __global__ void __launch_bounds__(256) k_oz_split_rows(Arena A, const ItemOzA* _
 #pragma unroll
     for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(load_f32(src, ref.dt, r0 + k + e) * sc));
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const float sig = pow2_above(mx);
+  // sigma = 2^es >= mx; a row whose largest entry is below 2^-126 (an
+  // FP32 subnormal, far from the diagonal of a long-range field) has an
+  // inverse bound beyond the float range, so it is scaled by the exponent
+  // (exact both ways)
+  int es = 0;
+  if (mx > 0.f) {
+    const float m = frexpf(mx, &es);          // mx = m 2^es, m in [0.5, 1)
+    if (m == 0.5f) es -= 1;
+  }
+  const float sig = ldexpf(1.f, es);
   if (lane == 0) it.sigma[row] = sig;
-  const float inv = 1.f / sig;                // exact: a power of two
+  const bool wide = es < -126;
+  const float inv = wide ? 0.f : ldexpf(1.f, -es);
   for (int k = lane * 4; k < b; k += 128) {
     float v[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = load_f32(src, ref.dt, r0 + k + e) * sc * inv;
+    for (int e = 0; e < 4; ++e) {
+      const float x = load_f32(src, ref.dt, r0 + k + e) * sc;
+      v[e] = wide ? ldexpf(x, -es) : x * inv;
+    }
 #pragma unroll
     for (int p = 0; p < S; ++p) {
       float d[4];

@@ -445,10 +445,10 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
       if (op == 0) {
         // the blocks of in_i this block reads: p' <= p (forward), p' >= p (backward)
         const int need = trans ? nt - 1 - i : i;
-        if (lane < P && (trans ? lane >= p : lane <= p)) ok = dag_wait(&cnt[i * (P + 1) + lane], need, A.err);
+        if (lane < P && (trans ? lane >= p : lane <= p)) ok = dag_wait(&cnt[i * (P + 1) + lane], need, A.err, A.wait_polls);
       } else if (lane == 0) {
         const int need = trans ? nt - 1 - j : j;
-        ok = dag_wait(&cnt[j * (P + 1) + P], P, A.err) && dag_wait(&cnt[i * (P + 1) + p], need, A.err);
+        ok = dag_wait(&cnt[j * (P + 1) + P], P, A.err, A.wait_polls) && dag_wait(&cnt[i * (P + 1) + p], need, A.err, A.wait_polls);
       }
       ok = __all_sync(0xffffffffu, ok);
       if (lane == 0) {
@@ -707,12 +707,16 @@ __global__ void k_dot(const double* a, const double* b, int64_t n, int64_t ld, d
   }
 }
 
+// A bounded wait that ran out in the factorisation or the solves leaves the
+// error word set: the log-likelihood is then NaN, not a number computed
+// from an unfinished solve.
 __global__ void k_loglik(const double* logdet, const double* quad, int64_t n, int nrhs,
-                         double* ll) {
+                         double* ll, const int* err) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nrhs) return;
   const double log2pi = 1.8378770664093454836;   // log(2 pi)
-  ll[c] = -0.5 * (double)n * log2pi - 0.5 * logdet[0] - 0.5 * quad[c];
+  ll[c] = *err ? __longlong_as_double(0x7ff8000000000000LL)
+               : -0.5 * (double)n * log2pi - 0.5 * logdet[0] - 0.5 * quad[c];
 }
 
 }  // namespace
@@ -819,8 +823,8 @@ void launch_dot(const double* a, const double* b, int64_t n, int64_t ld, int nrh
 }
 
 void launch_loglik(const double* logdet, const double* quad, int64_t n, int nrhs, double* ll,
-                   cudaStream_t s) {
-  k_loglik<<<(nrhs + 127) / 128, 128, 0, s>>>(logdet, quad, n, nrhs, ll);
+                   const int* err, cudaStream_t s) {
+  k_loglik<<<(nrhs + 127) / 128, 128, 0, s>>>(logdet, quad, n, nrhs, ll, err);
 }
 
 }  // namespace mp

@@ -106,8 +106,9 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 // Waits until *ver >= need; false on timeout or when another CTA gave up.
-__device__ __forceinline__ bool dag_wait(const int* ver, int need, const int* err) {
-  for (uint32_t i = 0; i < DAG_WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool dag_wait(const int* ver, int need, const int* err, int polls) {
+  const uint32_t limit = polls > 0 ? (uint32_t)polls : DAG_WAIT_LIMIT;
+  for (uint32_t i = 0; i < limit; ++i) {
     if (ld_acquire(ver) >= need) return true;
     if ((i & 63) == 63 && ld_acquire(err) != 0) return false;
     __nanosleep(64);

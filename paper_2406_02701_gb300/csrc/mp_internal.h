@@ -37,7 +37,7 @@ struct Arena {
   unsigned long long* amax;       // per tile: amax as float64 bits (atomicMax)
   int* err;                       // set to 1 when a bounded device wait ran out
   int b;
-  int pad_;
+  int wait_polls;                 // polls of a task-graph wait before it gives up (0: DAG_WAIT_LIMIT)
 };
 
 template <typename T>
@@ -301,7 +301,7 @@ void launch_copy_pad(const double* src, int64_t lds, double* dst, int64_t ldd, i
 void launch_dot(const double* a, const double* b, int64_t n, int64_t ld, int nrhs, double* out,
                 cudaStream_t s);
 void launch_loglik(const double* logdet, const double* quad, int64_t n, int nrhs, double* ll,
-                   cudaStream_t s);
+                   const int* err, cudaStream_t s);
 
 // k_gemm.cu
 void launch_gemm(int dt, int ta, int tb, int64_t m, int64_t n, int64_t k, double alpha,

@@ -167,6 +167,7 @@ struct mp_server {
   std::vector<Job*> jobs;               // all jobs by id order
   std::deque<Job*> kept;                // finished, unreleased (LRU order)
   int64_t next_id = 1;
+  int32_t inject_oom = 0;               // admissions whose input allocation is made to fail
 };
 
 namespace {
@@ -217,6 +218,10 @@ mp_status admit(mp_server* S, Job* J, int slot) {
                      (J->refine > 0 ? MP_TMAT_KEEP_SIGMA : 0) | MP_TMAT_STREAM_ALLOC, st, &J->t);
   if (s) return s;
   const size_t in_bytes = sizeof(double) * (2 * J->n + (size_t)J->n * J->nrhs + 2 * J->nrhs + 2);
+  if (S->inject_oom > 0) {   // a failed allocation, made on the host (the matrix exists already)
+    --S->inject_oom;
+    return MP_ERR_OOM;
+  }
   if (cudaMallocAsync((void**)&J->d_in, in_bytes, st) != cudaSuccess) return MP_ERR_OOM;
   int64_t tb = 0;
   mp_tmat_info(J->t, nullptr, nullptr, nullptr, &tb);
@@ -377,6 +382,12 @@ extern "C" mp_status mp_server_poll(mp_server* S, mp_serve_result* out, int32_t 
     S->slot_job[slot] = J;
     it = S->queue.erase(it);
   }
+  return MP_OK;
+}
+
+extern "C" mp_status mp_server_inject_alloc_failures(mp_server* S, int32_t count) {
+  if (!S || count < 0) return MP_ERR_ARG;
+  S->inject_oom = count;
   return MP_OK;
 }
 

@@ -59,6 +59,7 @@ _SIGS = {
     "mp_chol": (C.c_int, [P, P, P]),
     "mp_chol_steps": (C.c_int, [P, C.c_int32, C.c_int32]),
     "mp_logdet": (C.c_int, [P, P]),
+    "mp_tmat_set_wait_budget": (C.c_int, [P, C.c_int32]),
     "mp_trsm": (C.c_int, [P, C.c_int, P, C.c_int64, C.c_int32]),
     "mp_loglik": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
     "mp_tile_norms": (C.c_int, [P, C.c_int64, C.c_int32, P, mp_matern, P, P]),
@@ -78,6 +79,7 @@ _SIGS = {
     "mp_server_result": (C.c_int, [P, C.c_int64, P, P]),
     "mp_server_factor": (C.c_int, [P, C.c_int64, C.POINTER(P)]),
     "mp_server_release": (C.c_int, [P, C.c_int64]),
+    "mp_server_inject_alloc_failures": (C.c_int, [P, C.c_int32]),
     "mp_server_stats": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mp_map_bound": (C.c_int, [C.c_int64, C.c_int32, P, mp_matern, C.c_int32, C.c_uint8, C.c_uint8,
@@ -250,6 +252,10 @@ class TiledMatrix:
     def chol_steps(self, k0, k1):
         self.ctx.check(self.lib.mp_chol_steps(self.h, k0, k1))
 
+    def set_wait_budget(self, polls: int):
+        """Polls a task-graph wait makes before it gives up (0: default)."""
+        self.ctx.check(self.lib.mp_tmat_set_wait_budget(self.h, polls))
+
     def logdet(self, out):
         self.ctx.check(self.lib.mp_logdet(self.h, _ptr(out)))
 
@@ -393,6 +399,10 @@ class Server:
 
     def release(self, rid: int):
         self.ctx.check(self.lib.mp_server_release(self.h, rid))
+
+    def inject_alloc_failures(self, count: int):
+        """The next `count` admissions fail their allocation (host-made)."""
+        self.ctx.check(self.lib.mp_server_inject_alloc_failures(self.h, count))
 
     def stats(self):
         q, r, k, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
