@@ -68,8 +68,7 @@ def parse():
     p.add_argument("--fp8-eps", type=float, default=1e-6, help="norm guard of the E4M3 map (2-D field)")
     p.add_argument("--fp8-eps-ar1", type=float, default=1e-5, help="norm guard of the AR(1) check")
     p.add_argument("--batch-requests", type=int, default=512)
-    p.add_argument("--serve-requests", type=int, default=36)
-    p.add_argument("--serve-rate", type=float, default=6.0, help="Poisson arrivals per second")
+    p.add_argument("--serve-requests", type=int, default=48, help="burst that measures capacity")
     return p.parse_args()
 
 
@@ -521,70 +520,110 @@ def cusolver_context(dev, cfg, dsorted, stream):
 def batch_run(ctx, args, dev):
     """512 independent Matérn likelihoods (n ~ U{256..4096}, range ~ U[0.02,
     0.3], nu ~ U{1/2, 3/2, 5/2}), FP64 diagonal / FP32 band / BF16 where the
-    norm bound allows, Morton-ordered points, one CUDA graph launch for all
-    (generation, factorisation, solve, log-likelihood); timed over 3 launches
-    after one warm-up."""
+    norm bound allows (a map rule, rebuilt at each tile size), Morton-ordered
+    points, one CUDA graph launch for all (generation, factorisation, solve,
+    log-likelihood).  The autotuner picks the tile size and schedule flags
+    by timing candidate plans of this batch; the tuned plan and the default
+    schedule (b = 256, no flags) are each timed over 3 launches after one
+    warm-up."""
     import torch
     from paper_2406_02701_gb300 import mpchol
     reqs = I.batch_requests(args.batch_requests, seed=31)
-    b = 256
     specs = []
     flops = 0.0
     for r in reqs:
         n = r["n"]
         ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, r["seed"])).to(dev))
-        pmap = mpchol.map_bound(n, b, ds.cpu().numpy(), (r["sigma2"], r["range"], r["nu"], r["nugget"]),
-                                2, I.F32, I.BF16, 1e-6)
         zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, r["seed"]).T)).to(dev)
-        specs.append(dict(n=n, map=pmap, locs=ds, zt=zt, sigma2=r["sigma2"], range=r["range"],
-                          nu=r["nu"], nugget=r["nugget"]))
+        specs.append(dict(n=n, locs=ds, zt=zt, sigma2=r["sigma2"], range=r["range"], nu=r["nu"],
+                          nugget=r["nugget"], rule=(2, I.F32, I.BF16, 1e-6)))
         flops += chol_flops(n)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    B = mpchol.Batch(ctx, specs, b=b)
-    plan_s = time.perf_counter() - t0
-    ll, st = B.run()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(3):
-        B.run(ll, st)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 3
-    info = B.info()
-    ok = int((st.cpu().numpy() == 0).sum())
-    return {"requests": len(specs), "ok": ok, "ms_per_launch": ms, "solves_per_s": len(specs) / (ms * 1e-3),
-            "chol_tflops": flops / (ms * 1e-3) / 1e12, "plan_build_s": plan_s,
-            "device_bytes": info["bytes"], "b": info["b"]}
+    tuned = mpchol.tune_batch(ctx, specs)
+    tune_s = time.perf_counter() - t0
+
+    def timed(b, flags):
+        t1 = time.perf_counter()
+        B = mpchol.Batch(ctx, specs, b=b, flags=flags)
+        plan_s = time.perf_counter() - t1
+        ll, st = B.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            B.run(ll, st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        info = B.info()
+        ok = int((st.cpu().numpy() == 0).sum())
+        B.close()
+        return {"b": info["b"], "flags": info["flags"], "ok": ok, "ms_per_launch": ms,
+                "solves_per_s": len(specs) / (ms * 1e-3), "chol_tflops": flops / (ms * 1e-3) / 1e12,
+                "plan_build_s": plan_s, "device_bytes": info["bytes"]}
+
+    best = timed(tuned["b"], tuned["flags"])
+    default = timed(256, 0)
+    return {"requests": len(specs), **best,
+            "tuner": {"b": tuned["b"], "flags": tuned["flags"], "flags_names": flag_names(tuned["flags"]),
+                      "candidates_timed": tuned["tried"], "tuning_s": tune_s, "tuner_ms": tuned["ms"]},
+            "default_schedule": default}
+
+
+def flag_names(flags):
+    from paper_2406_02701_gb300 import mpchol
+    names = {mpchol.MP_TMAT_SIMT_UPDATES: "simt_updates", mpchol.MP_TMAT_FP64_PANEL: "fp64_panel",
+             mpchol.MP_TMAT_DAG16: "dag16", mpchol.MP_TMAT_DAG32: "dag32",
+             mpchol.MP_TMAT_LOWP_RING4: "lowp_ring4"}
+    return [v for k, v in names.items() if flags & k]
 
 
 def serving_run(ctx, args):
     """Continuous batching of a Poisson stream of likelihood requests:
     n in {2048, 8192, 32768} at 8:3:1, Matérn parameters drawn as in an MLE
     search, 1 RHS, 3 refinement sweeps at most, far tiles BF16 where the
-    norm bound allows (eps 1e-6)."""
+    norm bound allows (eps 1e-6), b and schedule per size from the
+    autotuner.  Capacity: a burst of requests all arriving at once; then
+    offered load swept from 0.2x to 1.2x of that capacity, p50/p99 latency
+    (arrival to result seen by the poller) and throughput at each level, and
+    the split of latency into admission (queueing and host planning up to
+    the moment the work is enqueued) and device time."""
     from paper_2406_02701_gb300 import mpchol, serving
-    reqs = serving.make_requests(args.serve_requests, args.serve_rate, seed=31)
     srv = mpchol.Server(ctx, hbm_budget=200 << 30, max_slots=8, eps=1e-6, far=mpchol.MP_BF16)
+    t0 = time.perf_counter()
+    srv.tune([2048, 8192, 32768], refine_iters=3)
+    tune_s = time.perf_counter() - t0
     warm = serving.make_requests(3, 1e6, seed=7, sizes=(2048,), weights=(1,))
     for r in warm:
         r["arrival"] = 0.0
     serving.run(srv, warm, refine_iters=3)
-    res, wall = serving.run(srv, reqs, refine_iters=3)
+    burst = serving.make_requests(args.serve_requests, 1e6, seed=31)
+    for r in burst:
+        r["arrival"] = 0.0
+    _, wall = serving.run(srv, burst, refine_iters=3)
+    capacity = len(burst) / wall
+    levels = []
+    for f in (0.2, 0.5, 0.8, 1.0, 1.2):
+        rate = f * capacity
+        count = int(min(150, max(40, round(6.0 * rate))))
+        reqs = serving.make_requests(count, rate, seed=1000 + int(100 * f))
+        res, wall = serving.run(srv, reqs, refine_iters=3)
+        lat = serving.latency_stats(res)
+        by_n = {}
+        for i, r in res.items():
+            by_n.setdefault(reqs[i]["n"], []).append(r)
+        split = {str(k): {"p50_ms": float(np.percentile([(r["t_done"] - r["t_submit"]) * 1e3 for r in v], 50)),
+                          "admission_p50_ms": float(np.percentile([(r["t_admit"] - r["t_submit"]) * 1e3 for r in v], 50)),
+                          "device_p50_ms": float(np.percentile([(r["t_done"] - r["t_admit"]) * 1e3 for r in v], 50)),
+                          "b": int(v[0]["b"]), "count": len(v)} for k, v in sorted(by_n.items())}
+        ok = sum(1 for r in res.values() if r["status"] == 0)
+        levels.append({"load": f, "rate_hz": rate, "requests": count, "ok": ok, "wall_s": wall,
+                       "solves_per_s": count / wall, **lat, "by_n": split})
     srv.close()
-    lat = serving.latency_stats(res)
-    by_n = {}
-    for i, r in res.items():
-        by_n.setdefault(reqs[i]["n"], []).append((r["t_done"] - r["t_submit"]) * 1e3)
-    ok = sum(1 for r in res.values() if r["status"] == 0)
-    low = sum(r["low_tiles"] for r in res.values())
-    tiles = sum(r["offdiag_tiles"] for r in res.values())
-    return {"requests": len(reqs), "ok": ok, "rate_hz": args.serve_rate, "wall_s": wall,
-            "solves_per_s": len(reqs) / wall, **lat,
-            "p50_ms_by_n": {str(k): float(np.percentile(v, 50)) for k, v in sorted(by_n.items())},
-            "bf16_offdiag_tile_share": low / tiles if tiles else 0.0,
-            "slots": 8, "mix": "n 2048/8192/32768 at 8:3:1, Poisson arrivals"}
+    return {"capacity_solves_per_s": capacity, "capacity_burst": len(burst), "tuning_s": tune_s,
+            "slots": 8, "mix": "n 2048/8192/32768 at 8:3:1, Poisson arrivals", "levels": levels}
 
 
 def morton_launches(n: int) -> int:

@@ -118,6 +118,11 @@ const char* mp_version(void);
  *             FP64-stored panel tiles keep the FP64 solve.
  *             MP_TMAT_FP64_PANEL solves every panel tile by FP64
  *             substitution instead.
+ *             MP_TMAT_DAG16 / MP_TMAT_DAG32 / MP_TMAT_LOWP_RING4 are
+ *             schedule choices (the autotuner's, see mp_tune_batch): they
+ *             change speed, not the arithmetic of any product, but the
+ *             task-graph block changes the summation order inside the
+ *             diagonal tiles, so results agree to rounding, not bits.
  *             Accuracy of the two update paths: the tensor cores' FP32
  *             accumulation rounds toward zero, a bias of about 1e-6 of a
  *             K = 512 product per update (measured), which refinement does
@@ -136,6 +141,9 @@ const char* mp_version(void);
 #define MP_TMAT_SIMT_UPDATES 2u  /* trailing updates on CUDA cores instead of tcgen05 */
 #define MP_TMAT_STREAM_ALLOC 4u  /* stream-ordered allocation on `stream` (no device sync) */
 #define MP_TMAT_FP64_PANEL 8u    /* panel solves by FP64 substitution (default: integer-digit tcgen05 products) */
+#define MP_TMAT_DAG16 32u        /* diagonal tile's task graph on 16 x 16 blocks (default: 16 for b in [384, 768], else 32) */
+#define MP_TMAT_DAG32 64u        /* ... on 32 x 32 blocks */
+#define MP_TMAT_LOWP_RING4 128u  /* 16-/8-bit tensor-core updates: 4-slot ring, 1 CTA per SM (default: 2-slot, 2 per SM) */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);
@@ -345,10 +353,22 @@ typedef struct {
   int32_t nrhs;           /* right-hand sides (>= 1)                          */
   int32_t refine_iters;   /* as in mp_loglik (0 = none)                       */
   mp_matern cov;          /* covariance parameters                            */
+  /* Precision map by rule, used when h_map is NULL and rule_eps > 0: the
+   * map of mp_map_bound(n, b, locations, cov, rule_band, rule_near,
+   * rule_far, rule_eps) at the plan's own b (the locations are read back
+   * from d_locs, which must then be in the order the matrix uses).  A map
+   * by rule follows b; an explicit h_map fixes it.  rule_eps = 0 with
+   * h_map NULL: all FP64. */
+  int32_t rule_band;
+  uint8_t rule_near, rule_far, rule_pad_[2];
+  double rule_eps;
 } mp_request;
 
 /* Builds a batch plan for `count` independent requests sharing tile size b
- * (b = 0 lets the library's tuner choose from the request sizes): one tile
+ * (b = 0: the autotuner picks b and the schedule flags, see mp_tune_batch,
+ * with its cache at the path in the environment variable MPCHOL_TUNE_CACHE
+ * when set; the first call for a new kind of batch then times candidate
+ * plans, several seconds): one tile
  * arena for all matrices and one merged schedule -- generation,
  * factorisation, solve, refinement and log-likelihood of every request --
  * captured as a single CUDA graph.  Panel solves follow mp_tmat_create's
@@ -359,6 +379,60 @@ typedef struct {
 mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
                           void* stream, mp_batch** out);
 void mp_batch_destroy(mp_batch* batch);
+
+/* mp_batch_create with explicit schedule flags: MP_TMAT_SIMT_UPDATES,
+ * MP_TMAT_FP64_PANEL, MP_TMAT_DAG16 or MP_TMAT_DAG32, MP_TMAT_LOWP_RING4
+ * (others give MP_ERR_ARG).  A request's result is bit-identical to its
+ * evaluation by mp_tmat_create with the same b and flags.  Synchronous. */
+mp_status mp_batch_create_ex(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
+                             uint32_t flags, void* stream, mp_batch** out);
+
+/* Schedule flags a batch plan was built with. */
+mp_status mp_batch_flags(mp_batch* batch, uint32_t* flags);
+
+/* ------------------------------------------------------------- autotuner */
+
+/* A schedule chosen by the autotuner: tile size, schedule flags (as for
+ * mp_tmat_create), the measured time of the workload it was chosen on,
+ * whether it came from the cache, and how many candidates were timed. */
+typedef struct {
+  int32_t b;
+  uint32_t flags;
+  double ms;
+  int32_t from_cache;
+  int32_t tried;
+} mp_tuned;
+
+/* Autotuner of batch plans (the tiled extension of Sec. 7 leaves tile sizes
+ * and schedules open; they are measured, not assumed).  Times whole batch
+ * graphs of these very requests (one warm-up and the best of two launches,
+ * CUDA events on `stream`) for candidate schedules, by coordinate descent
+ * from b = 256 with the default flags: every b in {128, 256, 384, 512} up
+ * to the largest request, then at the best b the other task-graph block,
+ * the FP64 panel solve, the 4-slot ring of the 16-/8-bit updates.  The
+ * fastest goes to *out.  cache_path (may be NULL: no cache) is a text file
+ * of "key b flags ms" lines; the key names the GPU (name, SM count) and the
+ * batch (request count, quartiles of n in steps of 256, share of tiles
+ * stored below FP32 in steps of 1/10, right-hand sides); a matching line is
+ * returned without timing, a new result is appended.  The requests'
+ * pointers must be valid (their data are read).  Allocates and frees each
+ * candidate plan; synchronous. */
+mp_status mp_tune_batch(mp_ctx* ctx, int32_t count, const mp_request* reqs, const char* cache_path,
+                        void* stream, mp_tuned* out);
+/* (A request with an explicit h_map fixes b: then mp_tune_batch and
+ * mp_batch_create with b = 0 give MP_ERR_ARG; give its map by rule.) */
+
+/* Autotuner of single-matrix evaluations (the server's and the MLE
+ * driver's): times one log-likelihood evaluation (generation, factorisation,
+ * solve with `refine_iters` FP64 refinement sweeps) of an n-point synthetic
+ * Matérn field (a jittered grid of the unit square, nu 3/2, range 0.05,
+ * nugget 1e-4, precision map of mp_map_bound with band 2, FP32 near tiles,
+ * far_dt where the bound allows it with eps) for b in {128, 256, 384, 512,
+ * 1024} up to n and, at the best b, the other task-graph block and the
+ * FP64 panel solve.  Cache as for mp_tune_batch (key: GPU, "tmat", n,
+ * far_dt, eps, refine_iters).  Synchronous. */
+mp_status mp_tune_tmat(mp_ctx* ctx, int64_t n, uint8_t far_dt, double eps, int32_t refine_iters,
+                       const char* cache_path, void* stream, mp_tuned* out);
 
 /* Device bytes held by a batch plan and the tile size it uses. */
 mp_status mp_batch_info(mp_batch* batch, int64_t* bytes, int32_t* b);
@@ -441,6 +515,15 @@ mp_status mp_server_release(mp_server* s, int64_t id);
  * failure path).  Those requests finish with MP_ERR_OOM; the others are
  * unaffected.  Host only. */
 mp_status mp_server_inject_alloc_failures(mp_server* s, int32_t count);
+
+/* Tunes the server's tile size and schedule for requests of the given
+ * sizes with mp_tune_tmat (its far_dt and eps, refine_iters as given);
+ * afterwards a request of order n takes the choice of the smallest tuned
+ * size >= n (the largest beyond all), instead of the fixed rule (b = 128
+ * up to n = 2048, 256 up to 8192, else 512).  cache_path as for
+ * mp_tune_batch.  Synchronous; call before submitting requests. */
+mp_status mp_server_tune(mp_server* s, const int64_t* sizes, int32_t count, int32_t refine_iters,
+                         const char* cache_path);
 
 /* Queue length, requests on the GPU, kept factors, device bytes in use. */
 mp_status mp_server_stats(mp_server* s, int64_t* queued, int64_t* running, int64_t* kept,

@@ -13,6 +13,7 @@
 // built once per plan and replayed as one CUDA graph launch.
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -124,6 +125,8 @@ struct Plan {
   std::vector<TileRef> h_tiles;
   int pool_count[NDT] = {};
   int dag_nb = 32;                 // block of the diagonal-tile task graph (16 or 32)
+  int dag_nb_req = 0;              // requested block (0: chosen by b)
+  bool lowp_ring4 = false;         // 16-/8-bit tensor-core updates: 4-slot ring, one CTA per SM
   int wait_polls = 0;              // task-graph wait budget (0: the kernels' default)
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
@@ -280,6 +283,7 @@ struct mp_tmat {
 struct mp_batch {
   Plan P;
   int count = 0;
+  uint32_t flags = 0;
   std::vector<mp_request> reqs;
   cudaGraphExec_t exec = nullptr;
   double* d_llbuf = nullptr;    // internal outputs
@@ -755,7 +759,7 @@ mp_status finish_plan(Plan& P) {
   // and a single matrix of the same b factor bit-identically): 16-blocks
   // shorten the critical chain; at b = 1024 they make 91k tasks per tile and
   // at b <= 256 the chain is short anyway, so those keep 32-blocks
-  P.dag_nb = (P.b >= 384 && P.b <= 768) ? 16 : 32;
+  P.dag_nb = P.dag_nb_req ? P.dag_nb_req : (P.b >= 384 && P.b <= 768) ? 16 : 32;
   const int b = P.b, nbb = b / 32, ndb = b / P.dag_nb;
   {
     int64_t panel_slots = 0, v_slots = 0;
@@ -944,7 +948,7 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
     case OP_TC: {
       // FP32 products read the TF32 splits from the FP32 pool; the others
       // read their own format's pool
-      launch_update_tc(A, L.kb, P.item<ItemTC>(L.off), L.count, P.tmap[L.kb], s);
+      launch_update_tc(A, L.kb, P.item<ItemTC>(L.off), L.count, P.tmap[L.kb], s, P.lowp_ring4);
       break;
     }
     case OP_FP8R: launch_fp8_round(A, P.item<ItemFp8>(L.off), L.count, s); break;
@@ -1073,6 +1077,12 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
   t->P.ozaki = (flags & MP_TMAT_FP64_PANEL) == 0;
   t->P.stream_alloc = (flags & MP_TMAT_STREAM_ALLOC) != 0;
+  if ((flags & MP_TMAT_DAG16) && (flags & MP_TMAT_DAG32)) {
+    delete t;
+    return fail(ctx, MP_ERR_ARG, "MP_TMAT_DAG16 and MP_TMAT_DAG32 exclude each other");
+  }
+  t->P.dag_nb_req = (flags & MP_TMAT_DAG16) ? 16 : (flags & MP_TMAT_DAG32) ? 32 : 0;
+  t->P.lowp_ring4 = (flags & MP_TMAT_LOWP_RING4) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
@@ -1654,7 +1664,19 @@ __global__ void k_batch_copy(const ItemBatchCopy* items) {
 
 extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
                                      void* stream, mp_batch** out) {
+  if (b != 0) return mp_batch_create_ex(ctx, count, reqs, b, 0, stream, out);
+  mp_tuned t{};
+  if (mp_status st = mp_tune_batch(ctx, count, reqs, getenv("MPCHOL_TUNE_CACHE"), stream, &t)) return st;
+  return mp_batch_create_ex(ctx, count, reqs, t.b, t.flags, stream, out);
+}
+
+extern "C" mp_status mp_batch_create_ex(mp_ctx* ctx, int32_t count, const mp_request* reqs, int32_t b,
+                                        uint32_t flags, void* stream, mp_batch** out) {
   if (!ctx || !reqs || !out || count < 1) return fail(ctx, MP_ERR_ARG, "bad batch arguments");
+  const uint32_t allowed = MP_TMAT_SIMT_UPDATES | MP_TMAT_FP64_PANEL | MP_TMAT_DAG16 | MP_TMAT_DAG32 |
+                           MP_TMAT_LOWP_RING4;
+  if ((flags & ~allowed) || ((flags & MP_TMAT_DAG16) && (flags & MP_TMAT_DAG32)))
+    return fail(ctx, MP_ERR_ARG, "bad batch schedule flags 0x%x", flags);
   int64_t nmax = 0;
   for (int r = 0; r < count; ++r) {
     const mp_request& q = reqs[r];
@@ -1665,19 +1687,40 @@ extern "C" mp_status mp_batch_create(mp_ctx* ctx, int32_t count, const mp_reques
       return fail(ctx, MP_ERR_ARG, "request %d: bad covariance parameters (nu in (0, 16])", r);
     nmax = std::max(nmax, q.n);
   }
-  if (b == 0) b = nmax <= 2048 ? 128 : 256;   // tuned choice for uneven small n
+  (void)nmax;
   if (b < 128 || b > 1024 || b % 128) return fail(ctx, MP_ERR_ARG, "b must be a multiple of 128 in [128, 1024]");
   CK(ctx, cudaSetDevice(ctx->device));
   mp_batch* B = new mp_batch;
   B->P.ctx = ctx;
   B->P.b = b;
   B->P.stream = (cudaStream_t)stream;
-  B->P.ozaki = true;     // panel tiles stored in FP32 or below: digit products, as mp_tmat's default
+  // the same plan options as mp_tmat_create's flags, so that a request gives
+  // the bits of its single evaluation with the same b and flags
+  B->P.ozaki = (flags & MP_TMAT_FP64_PANEL) == 0;
+  B->P.use_tc = (flags & MP_TMAT_SIMT_UPDATES) == 0;
+  B->P.dag_nb_req = (flags & MP_TMAT_DAG16) ? 16 : (flags & MP_TMAT_DAG32) ? 32 : 0;
+  B->P.lowp_ring4 = (flags & MP_TMAT_LOWP_RING4) != 0;
+  B->flags = flags;
   B->count = count;
   B->reqs.assign(reqs, reqs + count);
   Plan& P = B->P;
   mp_status st = MP_OK;
-  for (int r = 0; r < count && st == MP_OK; ++r) st = add_matrix(P, reqs[r].n, reqs[r].h_map);
+  for (int r = 0; r < count && st == MP_OK; ++r) {
+    const mp_request& q = reqs[r];
+    std::vector<uint8_t> rule_map;
+    if (!q.h_map && q.rule_eps > 0) {
+      // the bound map at this plan's b, from the request's locations
+      std::vector<double> h_locs(2 * (size_t)q.n);
+      cudaError_t e = cudaMemcpy(h_locs.data(), q.d_locs, sizeof(double) * 2 * q.n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) { st = fail(ctx, MP_ERR_CUDA, "request %d: locations: %s", r, cudaGetErrorString(e)); break; }
+      const int nt = (int)((q.n + b - 1) / b);
+      rule_map.resize((size_t)nt * nt);
+      st = mp_map_bound(q.n, b, h_locs.data(), q.cov, q.rule_band, q.rule_near, q.rule_far, q.rule_eps,
+                        rule_map.data());
+      if (st) { fail(ctx, st, "request %d: map rule", r); break; }
+    }
+    st = add_matrix(P, q.n, rule_map.empty() ? q.h_map : rule_map.data());
+  }
   if (st == MP_OK) st = finish_plan(P);
   if (st != MP_OK) { delete B; return st; }
   // workspace: padded vectors, outputs
@@ -1788,6 +1831,12 @@ extern "C" mp_status mp_batch_info(mp_batch* batch, int64_t* bytes, int32_t* b) 
   if (!batch) return MP_ERR_ARG;
   if (bytes) *bytes = batch->P.bytes;
   if (b) *b = batch->P.b;
+  return MP_OK;
+}
+
+extern "C" mp_status mp_batch_flags(mp_batch* batch, uint32_t* flags) {
+  if (!batch || !flags) return MP_ERR_ARG;
+  *flags = batch->flags;
   return MP_OK;
 }
 

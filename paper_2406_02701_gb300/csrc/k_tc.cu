@@ -421,13 +421,16 @@ void launch_tc(const Arena& A, const ItemTC* items, int count, const CUtensorMap
 
 // kind: BF16, F16, E4M3 or F32 (three TF32 products); map: the tensor map of
 // the operand pool (box 128 bytes x 128 rows, 128-byte swizzle).
+// ring4: the 16- and 8-bit kinds with a 4-slot ring and one CTA per SM
+// instead of a 2-slot ring and two CTAs per SM (a schedule choice of the
+// autotuner).
 void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
-                      const CUtensorMap& map, cudaStream_t s) {
+                      const CUtensorMap& map, cudaStream_t s, bool ring4) {
   if (count <= 0) return;
   switch (kind) {
-    case BF16: launch_tc<0, 2, 2>(A, items, count, map, s); break;
-    case F16: launch_tc<1, 2, 2>(A, items, count, map, s); break;
-    case E4M3: launch_tc<2, 2, 2>(A, items, count, map, s); break;
+    case BF16: ring4 ? launch_tc<0, 4, 1>(A, items, count, map, s) : launch_tc<0, 2, 2>(A, items, count, map, s); break;
+    case F16: ring4 ? launch_tc<1, 4, 1>(A, items, count, map, s) : launch_tc<1, 2, 2>(A, items, count, map, s); break;
+    case E4M3: ring4 ? launch_tc<2, 4, 1>(A, items, count, map, s) : launch_tc<2, 2, 2>(A, items, count, map, s); break;
     default: launch_tc<3, 3, 1>(A, items, count, map, s); break;
   }
 }

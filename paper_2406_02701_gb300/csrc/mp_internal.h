@@ -279,7 +279,7 @@ void launch_oz_gemm(const Arena& A, const ItemOz* items, int count, const struct
 // k_tc.cu (kind: BF16, F16, E4M3, or F32 as three TF32 products; the map
 // is a const CUtensorMap& of the operands' pool)
 void launch_update_tc(const Arena& A, int kind, const ItemTC* items, int count,
-                      const struct CUtensorMap_st& map, cudaStream_t s);
+                      const struct CUtensorMap_st& map, cudaStream_t s, bool ring4 = false);
 
 // k_solve.cu  (a non-null `gate` pointing at 0 turns a launch into a no-op)
 std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int p_blocks, int trans);

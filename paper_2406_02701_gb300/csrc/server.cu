@@ -144,6 +144,7 @@ struct Job {
   double t_submit = 0, t_admit = 0, t_done = 0;
   std::vector<double> locs, z;          // host copies (locs sorted at admission)
   int slot = -1;
+  uint32_t flags = 0;                   // schedule flags of its matrix
   int64_t bytes = 0;
   mp_tmat* t = nullptr;
   double* d_in = nullptr;               // device: sorted locs, z, outputs
@@ -168,11 +169,28 @@ struct mp_server {
   std::deque<Job*> kept;                // finished, unreleased (LRU order)
   int64_t next_id = 1;
   int32_t inject_oom = 0;               // admissions whose input allocation is made to fail
+  // tuned schedules by request size (ascending n): b and flags
+  std::vector<int64_t> tuned_n;
+  std::vector<int32_t> tuned_b;
+  std::vector<uint32_t> tuned_flags;
 };
 
 namespace {
 
 int pick_b(int64_t n) { return n <= 2048 ? 128 : n <= 8192 ? 256 : 512; }
+
+// Tile size and schedule flags of a request: the tuned choice of the
+// smallest tuned size >= n (the largest when n exceeds them all), else the
+// fixed rule.
+void pick_schedule(const mp_server* S, int64_t n, int* b, uint32_t* flags) {
+  *b = pick_b(n);
+  *flags = 0;
+  if (S->tuned_n.empty()) return;
+  size_t k = 0;
+  while (k + 1 < S->tuned_n.size() && S->tuned_n[k] < n) ++k;
+  *b = S->tuned_b[k];
+  *flags = S->tuned_flags[k];
+}
 
 // Device bytes of a request: tiles and workspace, estimated from the sizes
 // before the plan exists (FP64 worst case for the tiles, the Sigma copy,
@@ -215,7 +233,7 @@ mp_status admit(mp_server* S, Job* J, int slot) {
       if (map[(size_t)i * nt + j] == S->far_dt) ++J->n_low;
     }
   s = mp_tmat_create(S->ctx, J->n, J->b, map.data(),
-                     (J->refine > 0 ? MP_TMAT_KEEP_SIGMA : 0) | MP_TMAT_STREAM_ALLOC, st, &J->t);
+                     (J->refine > 0 ? MP_TMAT_KEEP_SIGMA : 0) | MP_TMAT_STREAM_ALLOC | J->flags, st, &J->t);
   if (s) return s;
   const size_t in_bytes = sizeof(double) * (2 * J->n + (size_t)J->n * J->nrhs + 2 * J->nrhs + 2);
   if (S->inject_oom > 0) {   // a failed allocation, made on the host (the matrix exists already)
@@ -296,7 +314,11 @@ extern "C" mp_status mp_server_submit(mp_server* S, int64_t n, const double* h_l
   J->nrhs = nrhs;
   J->refine = refine_iters;
   J->cov = cov;
-  J->b = pick_b(n);
+  {
+    int b = 0;
+    pick_schedule(S, n, &b, &J->flags);
+    J->b = b;
+  }
   J->locs.assign(h_locs, h_locs + 2 * n);
   J->z.assign(h_z, h_z + (size_t)n * nrhs);
   if (cudaMallocHost(&J->h_out, sizeof(double) * (2 * nrhs + 2)) != cudaSuccess ||
@@ -382,6 +404,28 @@ extern "C" mp_status mp_server_poll(mp_server* S, mp_serve_result* out, int32_t 
     S->slot_job[slot] = J;
     it = S->queue.erase(it);
   }
+  return MP_OK;
+}
+
+extern "C" mp_status mp_server_tune(mp_server* S, const int64_t* sizes, int32_t count,
+                                    int32_t refine_iters, const char* cache_path) {
+  if (!S || !sizes || count < 1 || refine_iters < 0) return MP_ERR_ARG;
+  std::vector<int64_t> ns(sizes, sizes + count);
+  std::sort(ns.begin(), ns.end());
+  ns.erase(std::unique(ns.begin(), ns.end()), ns.end());
+  std::vector<int32_t> bs;
+  std::vector<uint32_t> fs;
+  for (int64_t n : ns) {
+    if (n < 1) return MP_ERR_ARG;
+    mp_tuned t{};
+    mp_status st = mp_tune_tmat(S->ctx, n, S->far_dt, S->eps, refine_iters, cache_path, S->streams[0], &t);
+    if (st) return st;
+    bs.push_back(t.b);
+    fs.push_back(t.flags);
+  }
+  S->tuned_n = ns;
+  S->tuned_b = bs;
+  S->tuned_flags = fs;
   return MP_OK;
 }
 

@@ -20,6 +20,9 @@ MP_TMAT_KEEP_SIGMA = 1
 MP_TMAT_SIMT_UPDATES = 2
 MP_TMAT_STREAM_ALLOC = 4
 MP_TMAT_FP64_PANEL = 8
+MP_TMAT_DAG16 = 32
+MP_TMAT_DAG32 = 64
+MP_TMAT_LOWP_RING4 = 128
 ELEM_BYTES = {MP_F64: 8, MP_F32: 4, MP_BF16: 2, MP_F16: 2, MP_E4M3: 1}
 
 
@@ -38,7 +41,13 @@ class mp_serve_result(C.Structure):
 class mp_request(C.Structure):
     _fields_ = [("n", C.c_int64), ("h_map", C.c_void_p), ("d_locs", C.c_void_p),
                 ("d_z", C.c_void_p), ("nrhs", C.c_int32), ("refine_iters", C.c_int32),
-                ("cov", mp_matern)]
+                ("cov", mp_matern), ("rule_band", C.c_int32), ("rule_near", C.c_uint8),
+                ("rule_far", C.c_uint8), ("rule_pad_", C.c_uint8 * 2), ("rule_eps", C.c_double)]
+
+
+class mp_tuned(C.Structure):
+    _fields_ = [("b", C.c_int32), ("flags", C.c_uint32), ("ms", C.c_double), ("from_cache", C.c_int32),
+                ("tried", C.c_int32)]
 
 
 P = C.c_void_p
@@ -80,6 +89,11 @@ _SIGS = {
     "mp_server_factor": (C.c_int, [P, C.c_int64, C.POINTER(P)]),
     "mp_server_release": (C.c_int, [P, C.c_int64]),
     "mp_server_inject_alloc_failures": (C.c_int, [P, C.c_int32]),
+    "mp_server_tune": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_char_p]),
+    "mp_batch_create_ex": (C.c_int, [P, C.c_int32, P, C.c_int32, C.c_uint32, P, C.POINTER(P)]),
+    "mp_batch_flags": (C.c_int, [P, C.POINTER(C.c_uint32)]),
+    "mp_tune_batch": (C.c_int, [P, C.c_int32, P, C.c_char_p, P, P]),
+    "mp_tune_tmat": (C.c_int, [P, C.c_int64, C.c_uint8, C.c_double, C.c_int32, C.c_char_p, P, P]),
     "mp_server_stats": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mp_map_bound": (C.c_int, [C.c_int64, C.c_int32, P, mp_matern, C.c_int32, C.c_uint8, C.c_uint8,
@@ -201,7 +215,7 @@ class TiledMatrix:
     """mp_tmat: an n x n tiled matrix with a per-tile precision map."""
 
     def __init__(self, ctx: Context, n: int, b: int, pmap=None, keep_sigma=False, stream=None,
-                 simt_updates=False, ozaki=True):
+                 simt_updates=False, ozaki=True, flags=0):
         self.ctx, self.lib = ctx, ctx.lib
         self.n, self.b = n, b
         self.nt = -(-n // b)
@@ -212,7 +226,7 @@ class TiledMatrix:
             assert self._map.shape == (self.nt, self.nt)
         h = P()
         flags = ((MP_TMAT_KEEP_SIGMA if keep_sigma else 0) | (MP_TMAT_SIMT_UPDATES if simt_updates else 0)
-                 | (0 if ozaki else MP_TMAT_FP64_PANEL))
+                 | (0 if ozaki else MP_TMAT_FP64_PANEL) | flags)
         mp = None if self._map is None else self._map.ctypes.data_as(C.c_void_p)
         ctx.check(self.lib.mp_tmat_create(ctx.h, n, b, mp, flags, _stream(stream), C.byref(h)))
         self.h = h
@@ -311,34 +325,66 @@ class TiledMatrix:
         self.ctx.check(self.lib.mp_tile_set(self.h, i, j, raw.ctypes.data_as(C.c_void_p), scale))
 
 
+def _requests(reqs, keep):
+    arr = (mp_request * len(reqs))()
+    for k, r in enumerate(reqs):
+        m = r.get("map")
+        mp = None
+        if m is not None:
+            m = np.ascontiguousarray(np.asarray(m, dtype=np.uint8))
+            keep.append(m)
+            mp = m.ctypes.data
+        keep += [r["locs"], r["zt"]]
+        band, near, far, eps = r.get("rule", (0, 0, 0, 0.0))
+        arr[k] = mp_request(r["n"], mp, r["locs"].data_ptr(), r["zt"].data_ptr(), r["zt"].shape[0], 0,
+                            mp_matern(r["sigma2"], r["range"], r["nu"], r["nugget"]), band, near, far,
+                            (C.c_uint8 * 2)(), eps)
+    return arr
+
+
+def tune_batch(ctx: "Context", reqs, cache_path=None, stream=None):
+    """The autotuner's choice for these requests: dict(b, flags, ms, from_cache, tried)."""
+    keep = []
+    arr = _requests(reqs, keep)
+    t = mp_tuned()
+    ctx.check(ctx.lib.mp_tune_batch(ctx.h, len(reqs), arr, cache_path.encode() if cache_path else None,
+                                    _stream(stream), C.byref(t)))
+    return {k: getattr(t, k) for k, _ in mp_tuned._fields_}
+
+
+def tune_tmat(ctx: "Context", n, far=MP_BF16, eps=1e-6, refine_iters=0, cache_path=None, stream=None):
+    t = mp_tuned()
+    ctx.check(ctx.lib.mp_tune_tmat(ctx.h, n, far, eps, refine_iters,
+                                   cache_path.encode() if cache_path else None, _stream(stream), C.byref(t)))
+    return {k: getattr(t, k) for k, _ in mp_tuned._fields_}
+
+
 class Batch:
     """mp_batch: many log-likelihood requests in one CUDA graph."""
 
-    def __init__(self, ctx: Context, reqs, b=0, stream=None):
+    def __init__(self, ctx: Context, reqs, b=0, stream=None, flags=None):
+        """reqs: dicts with n, locs (device, n x 2), zt (device, nrhs x n),
+        sigma2, range, nu, nugget, and either map (explicit, at this b) or
+        rule = (band, near, far, eps) (the bound map at the plan's b).
+        b = 0: the library's autotuner picks b and the schedule flags."""
         self.ctx, self.lib = ctx, ctx.lib
         self._keep = []
-        arr = (mp_request * len(reqs))()
-        for k, r in enumerate(reqs):
-            m = r.get("map")
-            mp = None
-            if m is not None:
-                m = np.ascontiguousarray(np.asarray(m, dtype=np.uint8))
-                self._keep.append(m)
-                mp = m.ctypes.data
-            self._keep += [r["locs"], r["zt"]]
-            arr[k] = mp_request(r["n"], mp, r["locs"].data_ptr(), r["zt"].data_ptr(),
-                                r["zt"].shape[0], 0,
-                                mp_matern(r["sigma2"], r["range"], r["nu"], r["nugget"]))
+        self.arr = _requests(reqs, self._keep)
         h = P()
-        ctx.check(self.lib.mp_batch_create(ctx.h, len(reqs), arr, b, _stream(stream), C.byref(h)))
+        if flags is None:
+            ctx.check(self.lib.mp_batch_create(ctx.h, len(reqs), self.arr, b, _stream(stream), C.byref(h)))
+        else:
+            ctx.check(self.lib.mp_batch_create_ex(ctx.h, len(reqs), self.arr, b, flags, _stream(stream),
+                                                  C.byref(h)))
         self.h = h
         self.count = len(reqs)
         self.total_rhs = sum(r["zt"].shape[0] for r in reqs)
 
     def info(self):
-        by, b = C.c_int64(), C.c_int32()
+        by, b, f = C.c_int64(), C.c_int32(), C.c_uint32()
         self.ctx.check(self.lib.mp_batch_info(self.h, C.byref(by), C.byref(b)))
-        return dict(bytes=by.value, b=b.value)
+        self.ctx.check(self.lib.mp_batch_flags(self.h, C.byref(f)))
+        return dict(bytes=by.value, b=b.value, flags=f.value)
 
     def run(self, ll=None, status=None):
         import torch
@@ -399,6 +445,12 @@ class Server:
 
     def release(self, rid: int):
         self.ctx.check(self.lib.mp_server_release(self.h, rid))
+
+    def tune(self, sizes, refine_iters=0, cache_path=None):
+        """Autotunes b and the schedule flags for requests of these sizes."""
+        arr = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+        self.ctx.check(self.lib.mp_server_tune(self.h, arr.ctypes.data_as(C.c_void_p), arr.size, refine_iters,
+                                               cache_path.encode() if cache_path else None))
 
     def inject_alloc_failures(self, count: int):
         """The next `count` admissions fail their allocation (host-made)."""
