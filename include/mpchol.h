@@ -118,6 +118,11 @@ const char* mp_version(void);
  *             FP64-stored panel tiles keep the FP64 solve.
  *             MP_TMAT_FP64_PANEL solves every panel tile by FP64
  *             substitution instead.
+ *             MP_TMAT_DIRECT: mp_chol and mp_loglik enqueue their kernels
+ *             directly instead of capturing and replaying CUDA graphs, for
+ *             matrices that are factored once (capturing and instantiating
+ *             a graph of thousands of nodes costs more host time than its
+ *             replay saves; the server uses it).  Same kernels, same bits.
  *             MP_TMAT_DAG16 / MP_TMAT_DAG32 / MP_TMAT_LOWP_RING4 are
  *             schedule choices (the autotuner's, see mp_tune_batch): they
  *             change speed, not the arithmetic of any product, but the
@@ -144,6 +149,7 @@ const char* mp_version(void);
 #define MP_TMAT_DAG16 32u        /* diagonal tile's task graph on 16 x 16 blocks (default: 16 for b in [384, 768], else 32) */
 #define MP_TMAT_DAG32 64u        /* ... on 32 x 32 blocks */
 #define MP_TMAT_LOWP_RING4 128u  /* 16-/8-bit tensor-core updates: 4-slot ring, 1 CTA per SM (default: 2-slot, 2 per SM) */
+#define MP_TMAT_DIRECT 256u      /* mp_chol / mp_loglik launch directly instead of capturing CUDA graphs */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);

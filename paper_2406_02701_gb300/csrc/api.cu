@@ -127,6 +127,7 @@ struct Plan {
   int dag_nb = 32;                 // block of the diagonal-tile task graph (16 or 32)
   int dag_nb_req = 0;              // requested block (0: chosen by b)
   bool lowp_ring4 = false;         // 16-/8-bit tensor-core updates: 4-slot ring, one CTA per SM
+  bool no_graph = false;           // factorisation and solves launched directly (no capture)
   int wait_polls = 0;              // task-graph wait budget (0: the kernels' default)
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
@@ -903,7 +904,7 @@ mp_status finish_plan(Plan& P) {
   CK(P.ctx, cudaStreamCreateWithPriority(&P.cap2, cudaStreamNonBlocking, lo_pri));
   int maxnt = 0;
   for (auto& M : P.mats) maxnt = std::max(maxnt, M.nt);
-  P.events.resize(4 * maxnt + 2);
+  P.events.resize(4 * maxnt + 4);     // last four: chain fork/join, direct-launch fork/join
   for (auto& e : P.events) CK(P.ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   // the uploads above are ordered on the plan's stream; creation stays
   // synchronous unless the plan allocates stream-ordered
@@ -961,6 +962,20 @@ void run_launch(const Plan& P, const Launch& L, cudaStream_t s0, cudaStream_t s2
 
 // Enqueues the factorisation schedule on `s` with the bulk work forked to
 // the plan's second stream (inside a graph capture: two graph branches).
+void run_chol_forked(const Plan& P, cudaStream_t s);
+
+// Direct launches (no graph) with the same two-stream structure: the
+// chain on the high-priority stream, the bulk on the low-priority one,
+// ordered after and before the work of the plan's stream.
+void run_chol_direct(const Plan& P) {
+  cudaEvent_t fork = P.events[P.events.size() - 4], join = P.events[P.events.size() - 3];
+  cudaEventRecord(fork, P.stream);
+  cudaStreamWaitEvent(P.cap, fork, 0);
+  run_chol_forked(P, P.cap);
+  cudaEventRecord(join, P.cap);
+  cudaStreamWaitEvent(P.stream, join, 0);
+}
+
 void run_chol_forked(const Plan& P, cudaStream_t s) {
   cudaEvent_t fork = P.events[P.events.size() - 2], join = P.events.back();
   cudaEventRecord(fork, s);
@@ -1083,6 +1098,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   }
   t->P.dag_nb_req = (flags & MP_TMAT_DAG16) ? 16 : (flags & MP_TMAT_DAG32) ? 32 : 0;
   t->P.lowp_ring4 = (flags & MP_TMAT_LOWP_RING4) != 0;
+  t->P.no_graph = (flags & MP_TMAT_DIRECT) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
@@ -1308,13 +1324,17 @@ mp_status mp_chol(mp_tmat* t, int64_t* d_info, double* d_logdet) {
   Plan& P = t->P;
   if (!t->generated) return fail(P.ctx, MP_ERR_STATE, "matrix not generated or loaded");
   CK(P.ctx, cudaSetDevice(P.ctx->device));
-  if (!P.chol_exec) {
-    mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
-      run_chol_forked(P, s);
-    }, &P.chol_exec, &P.chol_kernels);
-    if (st) return st;
+  if (P.no_graph) {
+    run_chol_direct(P);
+  } else {
+    if (!P.chol_exec) {
+      mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
+        run_chol_forked(P, s);
+      }, &P.chol_exec, &P.chol_kernels);
+      if (st) return st;
+    }
+    if (mp_status st = launch_graph(P.ctx, P.chol_exec, P.stream)) return st;
   }
-  if (mp_status st = launch_graph(P.ctx, P.chol_exec, P.stream)) return st;
   if (d_info) k_info_out<<<1, 32, 0, P.stream>>>(P.d_info, P.d_err, (long long*)d_info, 1);
   if (d_logdet) CK(P.ctx, cudaMemcpyAsync(d_logdet, P.d_logdet, sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
   P.factored = true;
@@ -1550,7 +1570,7 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
     const char* db = t->d_sitems;
     const ItemResTile* rti = reinterpret_cast<const ItemResTile*>(db + rtiles_off);
     const ItemResRow* rro = reinterpret_cast<const ItemResRow*>(db + rrows_off);
-    mp_status st = capture_graph(P.ctx, P.cap, [&](cudaStream_t s) {
+    auto body = [&](cudaStream_t s) {
       launch_copy_pad(d_z, ldz, t->zp, N, n, N, nrhs, nullptr, s);
       launch_copy_pad(t->zp, N, t->r, N, N, N, nrhs, nullptr, s);
       k_refine_init<<<1, 128, 0, s>>>(t->active, t->iters, t->any, nrhs);
@@ -1577,7 +1597,12 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
       launch_loglik(P.d_logdet, quad, n, nrhs, d_ll, P.d_err, s);
       if (d_quad) cudaMemcpyAsync(d_quad, quad, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, s);
       if (d_iters) k_copy_iters<<<(nrhs + 127) / 128, 128, 0, s>>>(t->iters, d_iters, nrhs);
-    }, &t->ll_exec, &t->ll_kernels);
+    };
+    if (P.no_graph) {       // one-shot matrices: direct launches, no capture
+      body(P.stream);
+      return check_launch(P.ctx);
+    }
+    mp_status st = capture_graph(P.ctx, P.cap, body, &t->ll_exec, &t->ll_kernels);
     if (st) return st;
     t->ll_key = key;
   }

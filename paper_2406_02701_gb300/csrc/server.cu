@@ -233,7 +233,8 @@ mp_status admit(mp_server* S, Job* J, int slot) {
       if (map[(size_t)i * nt + j] == S->far_dt) ++J->n_low;
     }
   s = mp_tmat_create(S->ctx, J->n, J->b, map.data(),
-                     (J->refine > 0 ? MP_TMAT_KEEP_SIGMA : 0) | MP_TMAT_STREAM_ALLOC | J->flags, st, &J->t);
+                     (J->refine > 0 ? MP_TMAT_KEEP_SIGMA : 0) | MP_TMAT_STREAM_ALLOC | MP_TMAT_DIRECT | J->flags, st,
+                     &J->t);
   if (s) return s;
   const size_t in_bytes = sizeof(double) * (2 * J->n + (size_t)J->n * J->nrhs + 2 * J->nrhs + 2);
   if (S->inject_oom > 0) {   // a failed allocation, made on the host (the matrix exists already)

@@ -23,6 +23,7 @@ MP_TMAT_FP64_PANEL = 8
 MP_TMAT_DAG16 = 32
 MP_TMAT_DAG32 = 64
 MP_TMAT_LOWP_RING4 = 128
+MP_TMAT_DIRECT = 256
 ELEM_BYTES = {MP_F64: 8, MP_F32: 4, MP_BF16: 2, MP_F16: 2, MP_E4M3: 1}
 
 

@@ -107,6 +107,8 @@ def test_schedule_flags_leave_the_arithmetic_alone(ctx):
     base, ld0 = ll(0)
     ring, ld1 = ll(mpchol.MP_TMAT_LOWP_RING4)
     assert np.array_equal(ring, base) and ld1 == ld0
+    direct, ldd = ll(mpchol.MP_TMAT_DIRECT)         # no graph capture: same kernels, same bits
+    assert np.array_equal(direct, base) and ldd == ld0
     d32, ld2 = ll(mpchol.MP_TMAT_DAG32)
     assert np.allclose(d32, base, rtol=1e-9) and abs(ld2 - ld0) <= 1e-9 * abs(ld0)
     f64, _ = ll(mpchol.MP_TMAT_FP64_PANEL)
