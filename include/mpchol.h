@@ -263,6 +263,21 @@ mp_status mp_logdet(mp_tmat* t, double* d_out);
  * column-major float64 with leading dimension ldb >= n.  Asynchronous. */
 mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, int32_t nrhs);
 
+/* Solve with the factor, Sigma X = B (R's `solve` through the Cholesky
+ * factor, Sec. 4.1's operation list): X = L^-T (L^-1 B) by two mp_trsm
+ * calls, FP64 arithmetic on the exactly upcast tiles, no refinement (the
+ * result carries the factor's lower-precision rounding; mp_loglik refines).
+ * d_B: n x nrhs column-major, ld >= n, overwritten by X.  Right-hand sides
+ * go through in chunks of 2048 (bounded workspace).  Waits for the
+ * matrix's stream between chunks; asynchronous after the last. */
+mp_status mp_solve(mp_tmat* t, double* d_B, int64_t ldb, int32_t nrhs);
+
+/* Inverse from the factor, (L L^T)^-1 = L^-T L^-1 (R's `chol2inv`, Sec. 4.1):
+ * d_out n x n column-major (ld >= n) receives the inverse of the matrix the
+ * factor represents, column block by column block (identity columns solved
+ * with mp_solve).  n^3 FP64 work; as mp_solve otherwise. */
+mp_status mp_chol2inv(mp_tmat* t, double* d_out, int64_t ldo);
+
 /* Gaussian log-likelihood (Sec. 6.2):
  *   loglik = -n/2 log(2 pi) - logdet/2 - quad/2
  * for each of nrhs right-hand sides z (d_z: n x nrhs column-major float64,
@@ -342,7 +357,14 @@ mp_status mp_probe_fp64_peak(int device, double* h_tflops);
  * op(B) is k x n, C is m x n.  Products accumulate in FP32 (FP64 for
  * MP_F64); alpha, beta and the final sum are applied in float64 for
  * MP_F64/MP_F32 targets and FP32 otherwise; the result is rounded once
- * to `dtype` (E4M3 codes with scale 1, satfinite).  Asynchronous on
+ * to `dtype` (E4M3 codes with scale 1, satfinite).  BF16, FP16, E4M3 and
+ * FP32 run on the tcgen05 tensor cores (FP32 as three TF32 products of
+ * hi/lo splits): the operands are packed into K-major tiles of a stream-
+ * ordered workspace (about (m + n) k element bytes, twice for FP32, plus
+ * 4 m n), each 128 x 128 output block accumulates up to K = 4096 in tensor
+ * memory (whose FP32 accumulation rounds toward zero), and blocks of K
+ * are added with IEEE FP32 subtractions.  FP64 (and sizes beyond the
+ * tile layout's limits) runs on the CUDA cores.  Asynchronous on
  * `stream`. */
 mp_status mp_gemm(mp_ctx* ctx, mp_dtype dtype, char ta, char tb, int64_t m, int64_t n,
                   int64_t k, double alpha, const void* d_A, int64_t lda, const void* d_B,

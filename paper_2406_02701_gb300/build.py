@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpchol.so")
 SOURCES = ["api.cu", "k_gen.cu", "k_fp64.cu", "k_update.cu", "k_solve.cu", "k_gemm.cu",
-           "k_tc.cu", "k_ozaki.cu", "k_peak.cu", "k_noalloc.cu", "server.cu", "tune.cu"]
+           "k_tc.cu", "k_ozaki.cu", "k_peak.cu", "k_noalloc.cu", "server.cu", "tune.cu", "k_gemm_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I" + os.path.join(ROOT, "include")]

@@ -1463,6 +1463,43 @@ __global__ void k_copy_iters(const int* src, int32_t* dst, int nrhs) {
 }
 }  // namespace
 
+namespace {
+__global__ void k_identity(double* d, int64_t n, int64_t ld, int64_t c0, int64_t cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * cols) return;
+  const int64_t r = idx % n, c = idx / n;
+  d[r + c * ld] = r == c0 + c ? 1.0 : 0.0;
+}
+constexpr int32_t SOLVE_CHUNK = 2048;   // right-hand sides per solve (bounds the workspace)
+}  // namespace
+
+extern "C" mp_status mp_solve(mp_tmat* t, double* d_B, int64_t ldb, int32_t nrhs) {
+  if (!t || !d_B || nrhs < 1) return MP_ERR_ARG;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += SOLVE_CHUNK) {
+    const int32_t nc = std::min(SOLVE_CHUNK, nrhs - c0);
+    double* B = d_B + (int64_t)c0 * ldb;
+    if (mp_status st = mp_trsm(t, 0, B, ldb, nc)) return st;
+    if (mp_status st = mp_trsm(t, 1, B, ldb, nc)) return st;
+  }
+  return MP_OK;
+}
+
+extern "C" mp_status mp_chol2inv(mp_tmat* t, double* d_out, int64_t ldo) {
+  if (!t || !d_out) return MP_ERR_ARG;
+  Plan& P = t->P;
+  const int64_t n = P.mats[0].n;
+  if (ldo < n) return fail(P.ctx, MP_ERR_ARG, "ldo must be >= n");
+  if (!P.factored) return fail(P.ctx, MP_ERR_STATE, "mp_chol has not been called");
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  for (int64_t c0 = 0; c0 < n; c0 += SOLVE_CHUNK) {
+    const int64_t nc = std::min<int64_t>(SOLVE_CHUNK, n - c0);
+    double* B = d_out + c0 * ldo;
+    k_identity<<<(unsigned)((n * nc + 255) / 256), 256, 0, P.stream>>>(B, n, ldo, c0, nc);
+    if (mp_status st = mp_solve(t, B, ldo, (int32_t)nc)) return st;
+  }
+  return MP_OK;
+}
+
 extern "C" mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, int32_t nrhs) {
   if (!t || !d_B) return MP_ERR_ARG;
   Plan& P = t->P;
@@ -1626,6 +1663,14 @@ extern "C" mp_status mp_gemm(mp_ctx* ctx, mp_dtype dtype, char ta, char tb, int6
   if (m >= (int64_t)65535 * 64 || n >= (int64_t)65535 * 64)
     return fail(ctx, MP_ERR_ARG, "m or n too large");
   CK(ctx, cudaSetDevice(ctx->device));
+  if (dtype != MP_F64 && k > 0 && !getenv("MPCHOL_GEMM_SIMT")) {
+    // BF16, FP16, E4M3, FP32 (three TF32 products) on the tcgen05 tensor cores
+    const int rc = launch_gemm_tc((int)dtype, a, bb, m, n, k, alpha, d_A, lda, d_B, ldb, beta, d_C, ldc,
+                                  (cudaStream_t)stream);
+    if (rc == 1) return fail(ctx, MP_ERR_OOM, "mp_gemm: workspace allocation failed");
+    if (rc == 2) return fail(ctx, MP_ERR_CUDA, "mp_gemm: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == 0) return check_launch(ctx);
+  }
   launch_gemm((int)dtype, a, bb, m, n, k, alpha, d_A, lda, d_B, ldb, beta, d_C, ldc,
               (cudaStream_t)stream);
   return check_launch(ctx);

@@ -226,19 +226,21 @@ __global__ void __launch_bounds__(192, MINB)
         ItemTC it;
         int rb, cb;
         if (!unit(u, it, rb, cb)) continue;
-        const int ya0 = A.tiles[it.a].idx * b + rb * TC_BM;
-        const int yb0 = A.tiles[it.b].idx * b + cb * TC_BN;
-        const int ya1 = NA == 2 ? A.tiles[it.a2].idx * b + rb * TC_BM : 0;
-        const int yb1 = NA == 2 ? A.tiles[it.b2].idx * b + cb * TC_BN : 0;
-        for (int kt = 0; kt < KT; ++kt, ++g) {
+        // a unit contracts over it.kspan consecutive operand tiles (1 in
+        // the factorisation; the standalone product spans several)
+        const int span = it.kspan > 1 ? it.kspan : 1;
+        for (int kt = 0; kt < KT * span; ++kt, ++g) {
+          const int tk = kt / KT, kx = (kt % KT) * KCH;
+          const int ya0 = A.tiles[it.a + tk].idx * b + rb * TC_BM;
+          const int yb0 = A.tiles[it.b + tk].idx * b + cb * TC_BN;
           const int q = g % STAGES;
           if (g >= STAGES && !(ok = mbar_wait(&empty[q], ((g / STAGES) - 1) & 1, A.err))) break;
           uint8_t* st = smem + q * STAGE_BYTES;
           mbar_expect_tx(&full[q], STAGE_BYTES);
-          tma_load_2d(st, &tmap, kt * KCH, ya0, &full[q]);
-          if (NA == 2) tma_load_2d(st + TC_BUF, &tmap, kt * KCH, ya1, &full[q]);
-          tma_load_2d(st + NA * TC_BUF, &tmap, kt * KCH, yb0, &full[q]);
-          if (NA == 2) tma_load_2d(st + (NA + 1) * TC_BUF, &tmap, kt * KCH, yb1, &full[q]);
+          tma_load_2d(st, &tmap, kx, ya0, &full[q]);
+          if (NA == 2) tma_load_2d(st + TC_BUF, &tmap, kx, A.tiles[it.a2 + tk].idx * b + rb * TC_BM, &full[q]);
+          tma_load_2d(st + NA * TC_BUF, &tmap, kx, yb0, &full[q]);
+          if (NA == 2) tma_load_2d(st + (NA + 1) * TC_BUF, &tmap, kx, A.tiles[it.b2 + tk].idx * b + cb * TC_BN, &full[q]);
         }
       }
       if (!ok)   // let the copies in flight land before the CTA's memory goes away
@@ -257,7 +259,8 @@ __global__ void __launch_bounds__(192, MINB)
         if (t >= 2 && !(ok = mbar_wait(&acce[buf], ((t / 2) - 1) & 1, A.err))) break;
         tc_fence_after();
         const uint32_t acc_t = tmem + (uint32_t)(buf * ACC_COLS);
-        for (int kt = 0; kt < KT; ++kt, ++g) {
+        const int span = it.kspan > 1 ? it.kspan : 1;
+        for (int kt = 0; kt < KT * span; ++kt, ++g) {
           const int q = g % STAGES;
           if (!(ok = mbar_wait(&full[q], (g / STAGES) & 1, A.err))) break;
           tc_fence_after();

@@ -116,7 +116,7 @@ struct ItemTC {
   int32_t c, a, b, a2, b2;
   int32_t syrk;
   int32_t vslot;
-  int32_t pad_;
+  int32_t kspan;      // contraction over tiles a .. a+kspan-1 with b .. b+kspan-1 (0, 1: one tile)
   float* v;
 };
 
@@ -304,6 +304,11 @@ void launch_loglik(const double* logdet, const double* quad, int64_t n, int nrhs
                    const int* err, cudaStream_t s);
 
 // k_gemm.cu
+// k_gemm_tc.cu: the same product on the tensor cores (0 ok, 1 no memory,
+// 2 CUDA failure, 3 sizes beyond its tile layout: nothing enqueued)
+int launch_gemm_tc(int dt, int ta, int tb, int64_t m, int64_t n, int64_t k, double alpha,
+                   const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
+                   int64_t ldc, cudaStream_t s);
 void launch_gemm(int dt, int ta, int tb, int64_t m, int64_t n, int64_t k, double alpha,
                  const void* A, int64_t lda, const void* B, int64_t ldb, double beta, void* C,
                  int64_t ldc, cudaStream_t s);

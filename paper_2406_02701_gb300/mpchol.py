@@ -71,6 +71,8 @@ _SIGS = {
     "mp_logdet": (C.c_int, [P, P]),
     "mp_tmat_set_wait_budget": (C.c_int, [P, C.c_int32]),
     "mp_trsm": (C.c_int, [P, C.c_int, P, C.c_int64, C.c_int32]),
+    "mp_solve": (C.c_int, [P, P, C.c_int64, C.c_int32]),
+    "mp_chol2inv": (C.c_int, [P, P, C.c_int64]),
     "mp_loglik": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
     "mp_tile_norms": (C.c_int, [P, C.c_int64, C.c_int32, P, mp_matern, P, P]),
     "mp_map_guarded": (C.c_int, [C.c_int32, P, C.c_int32, C.c_uint8, C.c_uint8, C.c_double, P]),
@@ -273,6 +275,20 @@ class TiledMatrix:
 
     def logdet(self, out):
         self.ctx.check(self.lib.mp_logdet(self.h, _ptr(out)))
+
+    def solve(self, Bt):
+        """Sigma X = B in place; Bt is (nrhs, n) float64 on the device (the
+        transpose of the column-major n x nrhs B)."""
+        self.ctx.check(self.lib.mp_solve(self.h, _ptr(Bt), Bt.shape[1], Bt.shape[0]))
+        return Bt
+
+    def chol2inv(self, out=None):
+        """(L L^T)^-1 as an (n, n) float64 device tensor (symmetric)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n, self.n), dtype=torch.float64, device=torch.device("cuda", self.ctx.device))
+        self.ctx.check(self.lib.mp_chol2inv(self.h, _ptr(out), self.n))
+        return out
 
     def trsm(self, B, trans=0):
         """B: (nrhs, ld) float64 CUDA tensor = column-major n x nrhs."""

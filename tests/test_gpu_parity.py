@@ -498,3 +498,66 @@ def test_batch_equals_single_evaluations(ctx):
     torch.cuda.synchronize()
     ok = np.concatenate([np.full(len(s["ll"]), not bad) for s, bad in zip(singles, expect_bad)])
     assert np.array_equal(ll2.cpu().numpy()[ok], ll[ok])
+
+
+@pytest.mark.parametrize("dt", [I.BF16, I.F32, I.E4M3])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N")])
+def test_gemm_tensor_cores_several_tiles_and_k_groups(ctx, dt, ta, tb):
+    """Sizes that span several output tiles with ragged edges and more than
+    one group of contraction tiles (K = 9000 > 4096): the tensor-core
+    product against the oracle's FP32-accumulated product."""
+    from paper_2406_02701_gb300 import mpchol
+    m, n, k = 1100, 700, 9000
+    rng = np.random.default_rng(dt * 7 + len(ta))
+    A0 = rng.standard_normal((m, k) if ta == "N" else (k, m))
+    B0 = rng.standard_normal((k, n))
+    C0 = rng.standard_normal((m, n))
+    A, B, Cm = (OF.round_to(x, dt) for x in (A0, B0, C0))
+    ref = OC.gemm(A, B, Cm, dt, alpha=0.75, beta=0.5, ta=ta == "T")
+
+    def dev(x):
+        raw = mpchol.encode(np.ascontiguousarray(x.T).reshape(-1), dt)
+        return torch.from_numpy(raw).to(DEV), x.shape[0]
+    dA, lda = dev(A)
+    dB, ldb = dev(B)
+    dC, ldc = dev(Cm)
+    ctx.gemm(dt, ta, tb, m, n, k, 0.75, dA, lda, dB, ldb, 0.5, dC, ldc)
+    torch.cuda.synchronize()
+    got = mpchol.decode(dC.cpu().numpy(), dt).reshape(n, m).T
+    a = A.T if ta == "T" else A
+    bound = 0.75 * 2 * k * 2.0 ** -24 * (np.abs(a) @ np.abs(B))
+    assert_close_fmt(got, ref, dt, extra=bound + (1e-6 * np.abs(Cm) if dt != I.F32 else 0), what="gemm tc")
+
+
+def test_solve_and_chol2inv_through_the_factor(ctx):
+    """mp_solve (Sigma X = B by the factor) and mp_chol2inv ((L L^T)^-1)
+    against the oracle's tiled solves and a LAPACK inverse of the GPU's own
+    factor L L^T (downloaded tile by tile)."""
+    n, b = 700, 128
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 1)
+    T = _mk(ctx, n, b, pmap)
+    T.generate(torch.from_numpy(I.points(n, 6)).to(DEV), 1.0, 0.05, 1.5, 1e-2)
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    state = OC.TiledMatrix(n=n, b=b, nt=nt, pmap=pmap)
+    for i in range(nt):
+        for j in range(i + 1):
+            vals, codes, sc = T.get_tile(i, j)
+            state.tiles[(i, j)] = OC.Tile(np.tril(codes) if i == j else codes, int(pmap[i, j]), sc)
+    L = state.dense_lower()[:n, :n]
+    Sig = L @ L.T
+    B = I.rhs(n, 5, 6)
+    X = T.solve(torch.from_numpy(np.ascontiguousarray(B.T)).to(DEV))
+    torch.cuda.synchronize()
+    zp = np.zeros((nt * b, 5))
+    zp[:n] = B
+    ref = OC.backward_solve(state, OC.forward_solve_padded(state, zp))[:n]
+    assert np.allclose(X.cpu().numpy().T, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    inv = T.chol2inv()
+    torch.cuda.synchronize()
+    G = inv.cpu().numpy()          # column-major n x n: the transpose of this array; symmetric
+    want = np.linalg.inv(Sig)
+    assert np.allclose(G, G.T, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+    assert np.allclose(G.T, want, rtol=1e-8, atol=1e-8 * np.abs(want).max())
