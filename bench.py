@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the norm-guard eps sweep")
+    p.add_argument("--no-sec5", action="store_true", help="skip the n=32768 crossprod/backsolve context")
     p.add_argument("--no-fp8", action="store_true", help="skip the n=65536 E4M3 workload")
     p.add_argument("--fp8-eps", type=float, default=1e-6, help="norm guard of the E4M3 map (2-D field)")
     p.add_argument("--fp8-eps-ar1", type=float, default=1e-5, help="norm guard of the AR(1) check")
@@ -488,6 +489,80 @@ def general_nu_generation(ctx, cfg, dsorted, pmap, stream, nus=(1.0, 0.3, 2.2)):
     return out
 
 
+def sec5_operations(ctx, dev, stream, n=32768):
+    """The paper's standalone operation benchmark at its largest size
+    (Sec. 5: crossprod and backsolve at n = 32768), for context: crossprod
+    X^T X through mp_gemm in each lower format on the tensor cores
+    (2 n^3 flops; a few entries checked against float64 dot products of
+    the rounded inputs), and the triangular solve with a mixed-precision
+    factor of an n = 32768 Matérn matrix (mp_trsm, FP64 arithmetic, n^2
+    flops per right-hand side) for 16 and 256 right-hand sides."""
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    out = {"n": n, "crossprod": {}, "backsolve": {}}
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    X64 = torch.randn((n, n), generator=g, dtype=torch.float32, device=dev)
+    rows = [3, 1000, 32000]
+    cols = [7, 20000, 32767]
+    for name, dt, tdt in [("bf16", mpchol.MP_BF16, torch.bfloat16), ("f16", mpchol.MP_F16, torch.float16),
+                          ("f32", mpchol.MP_F32, torch.float32), ("e4m3", mpchol.MP_E4M3, torch.float8_e4m3fn)]:
+        X = X64.to(tdt)
+        Cm = torch.zeros((n, n), dtype=tdt, device=dev)
+        args = (dt, "T", "N", n, n, n, 1.0, X, n, X, n, 0.0, Cm, n)
+        ctx.gemm(*args)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.gemm(*args)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        # storage is column-major: element (r, c) of C sits at C_t[c, r]
+        Xh = X.to(torch.float64)
+        err = 0.0
+        for r, c in zip(rows, cols):
+            exact = float(torch.dot(Xh[r], Xh[c]))        # column r of X . column c of X
+            got = float(Cm[c, r].to(torch.float64))
+            scale = float(torch.dot(Xh[r].abs(), Xh[c].abs()))
+            err = max(err, abs(got - exact) / scale)
+        out["crossprod"][name] = {"ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12,
+                                  "sampled_err_rel_to_sum_abs": err}
+        del X, Cm, Xh
+        torch.cuda.empty_cache()
+    del X64
+    torch.cuda.empty_cache()
+    # backsolve with a mixed-precision factor (guarded BF16 map, b = 512)
+    b = 512
+    ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 77)).to(dev))
+    norms = ctx.tile_norms(n, b, ds, 1.0, 0.05, 1.5, 1e-4).cpu().numpy()
+    pm = ctx.map_guarded(norms, 2, I.F32, I.BF16, 1e-6)
+    T = mpchol.TiledMatrix(ctx, n, b, pm)
+    T.generate(ds, 1.0, 0.05, 1.5, 1e-4)
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    out["backsolve"]["factor_info"] = int(info.item())
+    for nrhs in (16, 256):
+        Bt = torch.randn((nrhs, n), dtype=torch.float64, device=dev)
+        T.trsm(Bt, 1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T.trsm(Bt, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["backsolve"][f"nrhs={nrhs}"] = {"ms": ms, "tflops": float(n) ** 2 * nrhs / (ms * 1e-3) / 1e12}
+    T.close()
+    out["paper_context"] = {"hardware": "the paper's GPU (cuBLAS/cuSOLVER), Sec. 5",
+                            "crossprod_s": {"double": 10.22, "single": 5.02, "half": 0.811},
+                            "backsolve_s": {"double": 5.49, "single": 2.88},
+                            "chol_s": {"double": 2.81, "single": 1.05}}
+    return out
+
+
 def cusolver_context(dev, cfg, dsorted, stream):
     """Context only: the vendor FP64 Cholesky (torch.linalg.cholesky, which
     calls cuSOLVER's potrf) of the same covariance as one dense n x n FP64
@@ -877,6 +952,10 @@ def ours(args, cfg):
     if not args.no_fp8:
         fp8 = fp8_workload(ctx, dev, args.fp8_eps, args.fp8_eps_ar1)
 
+    sec5 = None
+    if not args.no_sec5:
+        sec5 = sec5_operations(ctx, dev, stream)
+
     batch = None
     if not args.no_batch:
         batch = batch_run(ctx, args, dev)
@@ -918,6 +997,7 @@ def ours(args, cfg):
         "eps_sweep": sweep,
         "fp8_workload": fp8,
         "general_nu_generation": gen_nu,
+        "sec5_operations_n32768": sec5,
         "chol_graph_tflops": F / (phases["chol_graph_ms"] * 1e-3) / 1e12,
         "serving": serve,
         "batch": batch,

@@ -35,7 +35,41 @@ struct mp_ctx {
   unsigned long long* keys = nullptr;
   int64_t keys_cap = 0;
   std::mutex mu;
+  // pinned host buffers lent to matrices for their uploads and taken back
+  // when they are destroyed (freeing page-locked memory synchronises the
+  // device, which a serving loop must not do per request)
+  std::mutex pin_mu;
+  std::vector<std::pair<char*, size_t>> pin_free;
 };
+
+namespace {
+// Lends a pinned buffer of at least `bytes` (the smallest free one that
+// fits, else a new one); nullptr if none can be had.
+char* pin_borrow(mp_ctx* ctx, size_t bytes, size_t* cap) {
+  {
+    std::lock_guard<std::mutex> lk(ctx->pin_mu);
+    size_t best = (size_t)-1;
+    for (size_t k = 0; k < ctx->pin_free.size(); ++k)
+      if (ctx->pin_free[k].second >= bytes && (best == (size_t)-1 || ctx->pin_free[k].second < ctx->pin_free[best].second))
+        best = k;
+    if (best != (size_t)-1) {
+      auto e = ctx->pin_free[best];
+      ctx->pin_free.erase(ctx->pin_free.begin() + best);
+      *cap = e.second;
+      return e.first;
+    }
+  }
+  char* p = nullptr;
+  if (cudaMallocHost((void**)&p, bytes) != cudaSuccess) return nullptr;
+  *cap = bytes;
+  return p;
+}
+void pin_return(mp_ctx* ctx, char* p, size_t cap) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(ctx->pin_mu);
+  ctx->pin_free.push_back({p, cap});
+}
+}  // namespace
 
 namespace {
 
@@ -271,6 +305,12 @@ struct mp_tmat {
   std::vector<char> ll_key;
   char* d_sitems = nullptr;
   size_t d_sitems_cap = 0;
+  // pinned staging of the solve items: a copy from pageable memory waits
+  // for the stream (here: for the factorisation just enqueued)
+  char* h_pin = nullptr;
+  size_t h_pin_cap = 0;
+  cudaEvent_t pin_ev = nullptr;
+  bool pin_used = false;
   std::vector<void*> ws_allocs;
   ~mp_tmat() {
     if (ll_exec) cudaGraphExecDestroy(ll_exec);
@@ -278,6 +318,8 @@ struct mp_tmat {
     P.raw_free(d_gen);
     P.raw_free(d_sitems);
     P.raw_free(d_ktab);
+    if (pin_ev) { if (pin_used) cudaEventSynchronize(pin_ev); cudaEventDestroy(pin_ev); }
+    pin_return(P.ctx, h_pin, h_pin_cap);
   }
 };
 
@@ -1069,6 +1111,7 @@ mp_status mp_ctx_create(int device, mp_ctx** out) {
 void mp_ctx_destroy(mp_ctx* ctx) {
   if (!ctx) return;
   if (ctx->keys) cudaFree(ctx->keys);
+  for (auto& e : ctx->pin_free) cudaFreeHost(e.first);
   delete ctx;
 }
 
@@ -1102,6 +1145,15 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
+  // pinned staging for the solve items, sized for the three solve plans and
+  // the residual items of mp_loglik (grown later if ever short), allocated
+  // here while the stream has no work of this matrix yet
+  {
+    const size_t nt = (size_t)t->P.mats[0].nt, pb = (size_t)b / 32;
+    const size_t bytes = 3 * (sizeof(SolveTask) * pb * nt * (nt + 3) / 2 + 2 * sizeof(ItemSolveDag) + 512) +
+                         sizeof(ItemResTile) * nt * (nt + 1) / 2 + sizeof(ItemResRow) * nt + 4096;
+    t->h_pin = pin_borrow(ctx, bytes, &t->h_pin_cap);
+  }
   *out = t;
   return MP_OK;
 }
@@ -1416,6 +1468,27 @@ void run_solve(const Plan& P, const char* dbase, const SolvePlan& sp, const int*
 
 }  // namespace
 
+// Copies bytes of solve items into t->d_sitems through the pinned staging
+// buffer, so that the host does not wait for the work already on the stream;
+// the buffer is rewritten only after its previous copy has run.
+static cudaError_t upload_pinned(mp_tmat* t, const char* src, size_t bytes) {
+  Plan& P = t->P;
+  cudaError_t e = cudaSuccess;
+  if (!t->pin_ev && (e = cudaEventCreateWithFlags(&t->pin_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if (t->pin_used && (e = cudaEventSynchronize(t->pin_ev)) != cudaSuccess) return e;
+  if (bytes > t->h_pin_cap) {
+    pin_return(P.ctx, t->h_pin, t->h_pin_cap);
+    t->h_pin_cap = 0;
+    t->h_pin = pin_borrow(P.ctx, bytes, &t->h_pin_cap);
+    if (!t->h_pin) return cudaErrorMemoryAllocation;
+  }
+  memcpy(t->h_pin, src, bytes);
+  if ((e = cudaMemcpyAsync(t->d_sitems, t->h_pin, bytes, cudaMemcpyHostToDevice, P.stream)) != cudaSuccess)
+    return e;
+  t->pin_used = true;
+  return cudaEventRecord(t->pin_ev, P.stream);
+}
+
 // Solve workspace of a single-matrix handle for nrhs right-hand sides.
 static mp_status ensure_ws(mp_tmat* t, int nrhs) {
   if (t->ws_nrhs >= nrhs) return MP_OK;
@@ -1597,7 +1670,7 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
       if (e != cudaSuccess) { P.h_items.swap(saved); return fail(P.ctx, MP_ERR_OOM, "solve items"); }
       t->d_sitems_cap = bytes;
     }
-    cudaError_t e = P.upload(t->d_sitems, P.h_items.data(), bytes);
+    cudaError_t e = upload_pinned(t, P.h_items.data(), bytes);
     P.h_items.swap(saved);
     if (e != cudaSuccess) return fail(P.ctx, MP_ERR_CUDA, "solve items copy");
     double* red = t->red;
