@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the norm-guard eps sweep")
     p.add_argument("--no-sec5", action="store_true", help="skip the n=32768 crossprod/backsolve context")
+    p.add_argument("--profile-case", default=None,
+                   help="run one operation for a profiler and exit: gemm_<bf16|f16|f32|e4m3>_<n> "
+                        "(crossprod through mp_gemm) or gen_nu<nu>_<n> (Matérn generation, b = 512)")
     p.add_argument("--no-fp8", action="store_true", help="skip the n=65536 E4M3 workload")
     p.add_argument("--fp8-eps", type=float, default=1e-6, help="norm guard of the E4M3 map (2-D field)")
     p.add_argument("--fp8-eps-ar1", type=float, default=1e-5, help="norm guard of the AR(1) check")
@@ -1009,8 +1012,39 @@ def ours(args, cfg):
         dist.barrier()
 
 
+def profile_case(name):
+    """One operation, twice (the second is the one to capture), for ncu."""
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    dev = torch.device("cuda", 0)
+    ctx = mpchol.Context(0)
+    kind, _, size = name.rpartition("_")
+    n = int(size)
+    if kind.startswith("gemm_"):
+        fmt = kind[len("gemm_"):]
+        dt, tdt = {"bf16": (mpchol.MP_BF16, torch.bfloat16), "f16": (mpchol.MP_F16, torch.float16),
+                   "f32": (mpchol.MP_F32, torch.float32), "e4m3": (mpchol.MP_E4M3, torch.float8_e4m3fn)}[fmt]
+        X = torch.randn((n, n), dtype=torch.float32, device=dev).to(tdt)
+        Cm = torch.zeros((n, n), dtype=tdt, device=dev)
+        for _ in range(2):
+            ctx.gemm(dt, "T", "N", n, n, n, 1.0, X, n, X, n, 0.0, Cm, n)
+    elif kind.startswith("gen_nu"):
+        nu = float(kind[len("gen_nu"):])
+        ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 11)).to(dev))
+        T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(-(-n // 512), I.F64, I.F32, I.BF16, 2))
+        for _ in range(2):
+            T.generate(ds, 1.0, 0.05, nu, 1e-4)
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     cfg = dict(I.CONFIGS[args.workload])
     if args.impl == "reference":
         reference_arm(args, cfg)
