@@ -837,6 +837,9 @@ mp_status finish_plan(Plan& P) {
     size_t bytes = (size_t)P.pool_count[d] * b * b * esize(d);
     if (mp_status st = P.alloc(&p, bytes)) return st;
     P.pool[d] = (char*)p;
+    // zero once: the blocks of W = L^{-T} below its diagonal are never
+    // written (the factorisation writes W's diagonal and upper blocks only)
+    if (d == F64 && bytes) CK(P.ctx, cudaMemsetAsync(p, 0, bytes, P.stream));
   }
   int64_t panel_slots = 0, v_slots = 0;
   count_scratch(P, &panel_slots, &v_slots);

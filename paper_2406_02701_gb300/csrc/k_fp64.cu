@@ -182,7 +182,8 @@ __device__ __forceinline__ void dag_solve(const double (*Ab)[DB + 1], const doub
 // R_rj = -sum_{k=j}^{r-1} L_rk Y_kj), stored transposed as W:
 //   E(r, k, j) r > k >= j:  W_jr -= W_jk L_rk^T   (R_rj -= L_rk Y_kj)
 //   V(r, j)    r > j:       W_jr = W_jr Dinv_r^T   (Y_rj = Dinv_r R_rj)
-// F and G also write W_kk = Dinv_k^T and zero the blocks of W left of it.
+// F and G also write W_kk = Dinv_k^T (the blocks of W left of it are zero
+// from the plan's creation on).
 // ver[r nb + c] counts the operations finished on block (r, c) of the
 // factor (its c updates, then the factorisation or solve); ver[nb^2 +
 // j nb + r] those on block (j, r) of W (its r - j updates, then the solve;
@@ -383,8 +384,9 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       }
     }
     // off the critical chain, after publishing: W_kk = Dinv_k^T (published on
-    // its own counter, read by the E(r, k, k)), the log-determinant part and
-    // the zero blocks of W left of W_kk (no task reads them)
+    // its own counter, read by the E(r, k, k)) and the log-determinant part
+    // (the blocks of W left of W_kk are zero from the plan's creation:
+    // nothing writes them)
     if (tk.op == 0 || tk.op == 3) {
       for (int e = tid; e < DB * DB; e += blockDim.x) {
         const int64_t o = (int64_t)k * DB * b + (int64_t)(e / DB) * b + k * DB + e % DB;
@@ -402,8 +404,6 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         st_release(&wv[k * nb + k], 1);
       }
       dag_logdet<DB>(S2, ldparts + it.ldslot + k);
-      double* Wk = it.w + (int64_t)k * DB * b;
-      for (int e = tid; e < DB * k * DB; e += blockDim.x) Wk[(int64_t)(e / (k * DB)) * b + e % (k * DB)] = 0.0;
     }
   }
 }

@@ -561,3 +561,38 @@ def test_solve_and_chol2inv_through_the_factor(ctx):
     want = np.linalg.inv(Sig)
     assert np.allclose(G, G.T, rtol=1e-10, atol=1e-10 * np.abs(want).max())
     assert np.allclose(G.T, want, rtol=1e-8, atol=1e-8 * np.abs(want).max())
+
+
+def test_general_nu_in_batches_norms_and_maps(ctx):
+    """Requests with nu without a closed form: a batch holds one Matérn
+    table per distinct nu and gives each request the bits of its single
+    evaluation; the tile norms (and so the guarded map) follow the oracle's
+    definition through scipy's K_nu."""
+    from paper_2406_02701_gb300 import mpchol
+    b = 128
+    specs, singles = [], []
+    for r, (n, nu) in enumerate([(600, 0.7), (900, 1.3), (500, 0.7), (700, 2.5)]):
+        nt = -(-n // b)
+        pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 1)
+        locs, _ = OM.morton_order(I.points(n, 60 + r))
+        dl = torch.from_numpy(locs).to(DEV)
+        zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, 60 + r).T)).to(DEV)
+        z = I.rhs(n, 1, 60 + r)
+        specs.append(dict(n=n, map=pmap, locs=dl, zt=zt, sigma2=1.0, range=0.04, nu=nu, nugget=1e-2))
+        s = _run(ctx, n, b, pmap, locs, z, nu, 0.04, 1.0, 1e-2, ozaki=True)
+        assert s["info"] == 0
+        S = OM.covariance(locs, nu, 0.04, 1.0, 1e-2)
+        tl, ex = OC.tiled_loglik(S, z, b, pmap), OC.exact_loglik(S, z)
+        err = np.abs(s["ll"] - ex["loglik"]) / np.abs(ex["loglik"])
+        assert np.all(np.abs(s["ll"] - tl["loglik"]) / np.abs(tl["loglik"]) <= np.maximum(10 * err, 1e-9))
+        singles.append(s["ll"])
+    B = mpchol.Batch(ctx, specs, b=b)
+    ll, st = B.run()
+    torch.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    assert np.array_equal(ll.cpu().numpy(), np.concatenate(singles))
+    n = 1100
+    locs, _ = OM.morton_order(I.points(n, 70))
+    got = ctx.tile_norms(n, b, torch.from_numpy(locs).to(DEV), 1.0, 0.05, 1.3, 1e-4).cpu().numpy()
+    ref = OC.tile_norms(OM.covariance(locs, 1.3, 0.05, 1.0, 1e-4), b)
+    assert np.allclose(got, ref, rtol=1e-11, atol=0)
