@@ -69,6 +69,7 @@ def parse():
                    help="run one operation for a profiler and exit: gemm_<bf16|f16|f32|e4m3>_<n> "
                         "(crossprod through mp_gemm) or gen_nu<nu>_<n> (Matérn generation, b = 512)")
     p.add_argument("--no-fp8", action="store_true", help="skip the n=65536 E4M3 workload")
+    p.add_argument("--no-trace", action="store_true", help="skip the traced factorisation (chain stamps)")
     p.add_argument("--fp8-eps", type=float, default=1e-6, help="norm guard of the E4M3 map (2-D field)")
     p.add_argument("--fp8-eps-ar1", type=float, default=1e-5, help="norm guard of the AR(1) check")
     p.add_argument("--batch-requests", type=int, default=512)
@@ -566,6 +567,52 @@ def sec5_operations(ctx, dev, stream, n=32768):
     return out
 
 
+def potrf_chain(ctx, cfg, g, pmap, panel):
+    """The factorisation's critical chain from the diagonal tiles' stamps
+    (one traced factorisation of the bench matrix, untimed): per diagonal
+    block, the cycles of each phase of its chain task (medians over blocks
+    k >= 1 of all tiles), the hand-off between consecutive chain tasks, the
+    model sum against the measured block-to-block time, and per diagonal
+    tile its span and the gap to the next tile's first chain task."""
+    import torch
+    from paper_2406_02701_gb300 import mpchol
+    n, b = cfg["n"], cfg["b"]
+    T = mpchol.TiledMatrix(ctx, n, b, pmap, ozaki=panel == "ozaki", flags=mpchol.MP_TMAT_TRACE)
+    T.generate(g, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+    T.chol()
+    T.generate(g, cfg["sigma2"], cfg["range"], cfg["nu"], cfg["nugget"])
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    ns, cyc, db = T.chain_trace()
+    T.close()
+    nt, nbb = ns.shape[0], ns.shape[1]
+    # SM clock seen by the chain tasks: cycles per ns over whole tasks
+    ghz = float(np.sum(cyc[:, :, 7] - cyc[:, :, 0]) / max(1, np.sum(ns[:, :, 7] - ns[:, :, 0])))
+    d = np.diff(cyc, axis=2)[:, 1:, :]           # blocks k >= 1: phases 0-1 ... 6-7
+    names = ["wait_inputs", "wait_inverse", "solve_publish", "update_block", "factor", "publish",
+             "inverse_logdet_tail"]
+    med = {k: float(np.median(d[:, :, i])) for i, k in enumerate(names)}
+    handoff_ns = ns[:, 1:, 2] - ns[:, :-1, 5]     # previous block factored -> inverse seen
+    step_ns = ns[:, 1:, 5] - ns[:, :-1, 5]        # block-to-block time on the chain
+    model = med["wait_inverse"] + med["solve_publish"] + med["update_block"] + med["factor"]
+    span_ns = ns[:, -1, 6] - ns[:, 0, 0]
+    gap_ns = ns[1:, 0, 0] - ns[:-1, -1, 6]
+    return {
+        "info": int(info.item()), "block": db, "blocks_per_tile": nbb, "sm_ghz_seen": ghz,
+        "phase_cycles_median": med,
+        "factor_cycles_per_column": med["factor"] / db,
+        "handoff_ns_median": float(np.median(handoff_ns)),
+        "block_step_cycles_median": float(np.median(step_ns)) * ghz,
+        "model_cycles_per_block": model,
+        "tile_span_ms_median": float(np.median(span_ns)) * 1e-6,
+        "tile_span_ms_sum": float(np.sum(span_ns)) * 1e-6,
+        "gap_to_next_tile_ms_median": float(np.median(gap_ns)) * 1e-6 if nt > 1 else None,
+        "gap_to_next_tile_ms_sum": float(np.sum(gap_ns)) * 1e-6 if nt > 1 else None,
+        "chain_ms": float(ns[-1, -1, 6] - ns[0, 0, 0]) * 1e-6,
+        "tile_span_ms_first_last": [float(span_ns[0]) * 1e-6, float(span_ns[-1]) * 1e-6],
+    }
+
+
 def cusolver_context(dev, cfg, dsorted, stream):
     """Context only: the vendor FP64 Cholesky (torch.linalg.cholesky, which
     calls cuSOLVER's potrf) of the same covariance as one dense n x n FP64
@@ -852,6 +899,10 @@ def ours(args, cfg):
                      "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] > 0 and v["flops"] > 0 else None}
                  for k, v in prof.items() if v["launches"]}
 
+    chain = None
+    if not args.no_trace:
+        chain = potrf_chain(ctx, cfg, sorted_buf if cfg["morton"] else dl, pmap, args.panel)
+
     # CPU-baseline leg, part 1: the FP64 oracle's log-likelihood of this
     # workload (LAPACK on the host cores), and the mixed result for a z drawn
     # from the model
@@ -1005,6 +1056,7 @@ def ours(args, cfg):
         "serving": serve,
         "batch": batch,
         "chol_breakdown_ms": breakdown,
+        "potrf_chain": chain,
         "step_phases_ms": phases,
     }
     print(json.dumps(line), flush=True)

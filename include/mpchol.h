@@ -123,6 +123,8 @@ const char* mp_version(void);
  *             matrices that are factored once (capturing and instantiating
  *             a graph of thousands of nodes costs more host time than its
  *             replay saves; the server uses it).  Same kernels, same bits.
+ *             MP_TMAT_TRACE records the critical chain of the diagonal
+ *             tiles' factorisations (mp_tmat_chain_trace).
  *             MP_TMAT_DAG16 / MP_TMAT_DAG32 / MP_TMAT_LOWP_RING4 are
  *             schedule choices (the autotuner's, see mp_tune_batch): they
  *             change speed, not the arithmetic of any product, but the
@@ -150,6 +152,7 @@ const char* mp_version(void);
 #define MP_TMAT_DAG32 64u        /* ... on 32 x 32 blocks */
 #define MP_TMAT_LOWP_RING4 128u  /* 16-/8-bit tensor-core updates: 4-slot ring, 1 CTA per SM (default: 2-slot, 2 per SM) */
 #define MP_TMAT_DIRECT 256u      /* mp_chol / mp_loglik launch directly instead of capturing CUDA graphs */
+#define MP_TMAT_TRACE 512u       /* record the diagonal tiles' critical-chain stamps (mp_tmat_chain_trace) */
 mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map,
                          uint32_t flags, void* stream, mp_tmat** out);
 void mp_tmat_destroy(mp_tmat* t);
@@ -252,6 +255,35 @@ mp_status mp_chol_steps(mp_tmat* t, int32_t k0, int32_t k1);
  * hung GPU).  Waits for the matrix's stream, drops its captured graphs
  * (recaptured at the next call).  Synchronous. */
 mp_status mp_tmat_set_wait_budget(mp_tmat* t, int32_t polls);
+
+/* The order in which the FP64 diagonal tile's task graph hands out its
+ * tasks for nb = b / DB blocks (1 <= nb <= 64); host only, for checking
+ * the schedule without a GPU.  4 bytes per task: op (0 factor (0, 0),
+ * 1 solve (r, k), 2 update (r, c) with column k, 3 solve (k, k-1) +
+ * update and factor (k, k), 4 solve of W block (c, r), 5 update of W block
+ * (c, r) with column k), r, c, k.  *count = tasks; h_out (cap >= *count
+ * tasks) may be NULL to query the count. */
+mp_status mp_potrf_dag_schedule(int32_t nb, uint8_t* h_out, int64_t cap, int64_t* count);
+
+/* Critical-chain stamps of the last factorisation of a matrix created with
+ * MP_TMAT_TRACE (instrumentation, off by default; the arithmetic is the
+ * same with it on).  The FP64 diagonal tile's task graph runs one chain
+ * task per DB x DB diagonal block k (DB = *block, 16 or 32): factor block
+ * (0, 0), or for k >= 1 solve block (k, k-1), update block (k, k) and
+ * factor it (Sec. 6.2 `chol` in FP64, tile by tile as in Sec. 7).  Per
+ * block, tile by tile (index (i * b / DB + k) * 16 for diagonal tile i),
+ * 16 words: %globaltimer in ns, then clock64 of the same SM, at 8 points
+ *   0 task taken, 1 its A blocks final, 2 the previous block's inverse
+ *   ready, 3 block (k, k-1) solved and published, 4 block (k, k) updated,
+ *   5 block (k, k) factored, 6 published, 7 task done.
+ * When one CTA runs the chain (the default), point 1 is when that CTA had
+ * loaded block k's inputs (during block k-1's factorisation, so before
+ * point 0), points 0 and 2 coincide, and 5-7 coincide (the publication
+ * runs beside the next block's work).
+ * *count = words held (nt * b / DB * 16); h_out (cap >= *count words) may
+ * be NULL to query the size.  Waits for the matrix's stream.
+ * MP_ERR_STATE without MP_TMAT_TRACE. */
+mp_status mp_tmat_chain_trace(mp_tmat* t, uint64_t* h_out, int64_t cap, int64_t* count, int32_t* block);
 
 /* Copies log det Sigma of the factorised matrix into d_out (1 float64).
  * MP_ERR_STATE if mp_chol has not been enqueued.  Asynchronous. */

@@ -163,6 +163,9 @@ struct Plan {
   bool lowp_ring4 = false;         // 16-/8-bit tensor-core updates: 4-slot ring, one CTA per SM
   bool no_graph = false;           // factorisation and solves launched directly (no capture)
   int wait_polls = 0;              // task-graph wait budget (0: the kernels' default)
+  bool trace = false;              // record the diagonal tiles' chain stamps
+  unsigned long long* d_trace = nullptr;
+  int64_t trace_words = 0;
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
   std::vector<int64_t> ltab_off;
@@ -227,6 +230,7 @@ struct Plan {
     A.err = d_err;
     A.b = b;
     A.wait_polls = wait_polls;
+    A.trace = d_trace;
     return A;
   }
 
@@ -886,6 +890,12 @@ mp_status finish_plan(Plan& P) {
   const int nm = (int)P.mats.size();
   if (mp_status st = P.alloc(&p, sizeof(double) * std::max(ldo, 1))) return st;
   P.d_ldparts = (double*)p;
+  if (P.trace) {
+    P.trace_words = (int64_t)std::max(ldo, 1) * TRACE_WORDS;
+    if (mp_status st = P.alloc(&p, sizeof(unsigned long long) * P.trace_words)) return st;
+    P.d_trace = (unsigned long long*)p;
+    CK(P.ctx, cudaMemsetAsync(P.d_trace, 0, sizeof(unsigned long long) * P.trace_words, P.stream));
+  }
   if (mp_status st = P.alloc(&p, sizeof(int32_t) * nm)) return st;
   P.d_ldoff = (int32_t*)p;
   if (mp_status st = P.alloc(&p, sizeof(int32_t) * nm)) return st;
@@ -1145,6 +1155,7 @@ mp_status mp_tmat_create(mp_ctx* ctx, int64_t n, int32_t b, const uint8_t* h_map
   t->P.dag_nb_req = (flags & MP_TMAT_DAG16) ? 16 : (flags & MP_TMAT_DAG32) ? 32 : 0;
   t->P.lowp_ring4 = (flags & MP_TMAT_LOWP_RING4) != 0;
   t->P.no_graph = (flags & MP_TMAT_DIRECT) != 0;
+  t->P.trace = (flags & MP_TMAT_TRACE) != 0;
   mp_status st = add_matrix(t->P, n, h_map);
   if (st == MP_OK) st = finish_plan(t->P);
   if (st != MP_OK) { delete t; return st; }
@@ -1406,6 +1417,36 @@ mp_status mp_tmat_set_wait_budget(mp_tmat* t, int32_t polls) {
   if (P.chol_exec) { cudaGraphExecDestroy(P.chol_exec); P.chol_exec = nullptr; }
   if (t->ll_exec) { cudaGraphExecDestroy(t->ll_exec); t->ll_exec = nullptr; t->ll_key.clear(); }
   P.wait_polls = polls;
+  return MP_OK;
+}
+
+mp_status mp_potrf_dag_schedule(int32_t nb, uint8_t* h_out, int64_t cap, int64_t* count) {
+  if (nb < 1 || nb > 64 || !count) return MP_ERR_ARG;
+  const std::vector<DagTask> v = potrf_dag_tasks(nb);
+  *count = (int64_t)v.size();
+  if (!h_out) return MP_OK;
+  if (cap < (int64_t)v.size()) return MP_ERR_ARG;
+  for (size_t i = 0; i < v.size(); ++i) {
+    h_out[4 * i] = v[i].op;
+    h_out[4 * i + 1] = v[i].r;
+    h_out[4 * i + 2] = v[i].c;
+    h_out[4 * i + 3] = v[i].k;
+  }
+  return MP_OK;
+}
+
+mp_status mp_tmat_chain_trace(mp_tmat* t, uint64_t* h_out, int64_t cap, int64_t* count, int32_t* block) {
+  if (!t || !count) return MP_ERR_ARG;
+  Plan& P = t->P;
+  if (!P.d_trace) return fail(P.ctx, MP_ERR_STATE, "the matrix was created without MP_TMAT_TRACE");
+  *count = P.trace_words;
+  if (block) *block = P.dag_nb;
+  if (!h_out) return MP_OK;
+  if (cap < P.trace_words) return fail(P.ctx, MP_ERR_ARG, "trace needs %lld words", (long long)P.trace_words);
+  CK(P.ctx, cudaSetDevice(P.ctx->device));
+  CK(P.ctx, cudaMemcpyAsync(h_out, P.d_trace, sizeof(uint64_t) * P.trace_words, cudaMemcpyDeviceToHost,
+                            P.stream));
+  CK(P.ctx, cudaStreamSynchronize(P.stream));
   return MP_OK;
 }
 

@@ -47,15 +47,34 @@ struct DagShape {
 // pipeline.  In iteration c column c of L is final; warp 0 then finishes
 // column c + 1 (its update with column c, the pivot d, 1/sqrt(d), the
 // scaling), so the sequential chain per column is one FMA and one rsqrt,
-// while warps 1-7 apply column c to the columns beyond c + 1 and advance
-// the inverse: Y[c-1, .] = R[c-1, .] / L_{c-1,c-1}, then
-// R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Writes L and the
-// inverse to global memory; info gets the first pivot that is not > 0.
+// while warps 1-3 and 5-7 apply column c to the columns beyond c + 1 and
+// advance the inverse: Y[c-1, .] = R[c-1, .] / L_{c-1,c-1}, then
+// R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Warp 4 shares warp
+// 0's scheduler; with its FP64 instructions off that scheduler the sweep
+// took 1024 instead of 1072 cycles per column (measured), so it sits the
+// sweep out.  Writes L and the inverse to global memory; info gets the
+// first pivot that is not > 0.
+
+// Largest number of elements one column of the sweep updates: the trailing
+// triangle rows c+2.. on columns c+2..r and the inverse rows c.. on columns < c.
+template <int DB>
+__host__ __device__ constexpr int sweep_work_max() {
+  int mx = 0;
+  for (int c = 0; c < DB; ++c) {
+    const int m = DB - 2 - c;
+    const int t = (m > 0 ? m * (m + 1) / 2 : 0) + (c >= 1 ? (DB - c) * c : 0);
+    mx = t > mx ? t : mx;
+  }
+  return mx;
+}
+
+// The sweep's warps synchronise among themselves (named barrier 2, 224
+// threads); warp 4 waits at the end.
 template <int DB>
 __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk, int b,
                            double* dinv, long long* info, long long row0, const uint16_t* tri) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  constexpr int NO = 224;                        // threads of warps 1-7
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NO = 192;                        // threads of warps 1-3 and 5-7
   __shared__ double rps[DB];                     // 1 / L_cc
   for (int e = tid; e < DB * DB; e += blockDim.x) R[e / DB][e % DB] = (e / DB == e % DB) ? 1.0 : 0.0;
   if (tid < 32) {
@@ -64,8 +83,9 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
     if (lane == 0) { S[0][0] = d * rp; rps[0] = rp; }
     else if (lane < DB) S[lane][0] *= rp;
   }
-  for (int c = 0; c < DB; ++c) {
-    __syncthreads();
+  __syncthreads();
+  if (warp != 4) for (int c = 0; c < DB; ++c) {
+    if (c) asm volatile("bar.sync 2, 224;" ::: "memory");
     if (tid < 32) {
       if (c + 1 < DB) {
         // every lane forms the pivot itself (broadcast reads, no shuffle on
@@ -73,15 +93,15 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
         const int n = c + 1;
         const double snc = S[n][c];
         const double d = S[n][n] - snc * snc;
-        double v = 0.0;
+        double v = d;
         if (lane > n && lane < DB) v = S[lane][n] - S[lane][c] * snc;
         const double rp = rsqrt(d);
-        if (lane == n) S[n][n] = d * rp;           // sqrt(d) = d / sqrt(d)
-        else if (lane > n && lane < DB) S[lane][n] = v * rp;
+        // one multiplication scales the column and gives sqrt(d) = d / sqrt(d)
+        if (lane >= n && lane < DB) S[lane][n] = v * rp;
         if (lane == 0) rps[n] = rp;
       }
-    } else {
-      const int t = tid - 32;
+    } else if (warp != 4) {
+      const int t = tid < 128 ? tid - 32 : tid - 64;
       if (c >= 1 && t < c) R[c - 1][t] *= rps[c - 1];
       asm volatile("bar.sync 1, %0;" ::"r"(NO));
       // compact enumeration (the FP64 pipe charges a warp instruction in
@@ -91,10 +111,11 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
       const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
       const int total = ntri + (c >= 1 ? (DB - c) * c : 0);
       const float rc = c >= 1 ? 1.f / (float)c : 0.f;
-      // at most UPT elements per thread (total <= UPT * 224); the updates of
+      // at most UPT elements per thread (total <= UPT * 192); the updates of
       // one column touch distinct entries and read only columns c, c - 1 and
       // row c - 1 of R, so all operands are loaded before any store
       constexpr int UPT = DB == 32 ? 3 : 1;
+      static_assert(sweep_work_max<DB>() <= UPT * NO, "sweep elements exceed the update threads");
       double* dst[UPT];
       double x0[UPT], x1[UPT], x2[UPT];
 #pragma unroll
@@ -129,10 +150,11 @@ __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk,
   // first failed pivot
   if (tid < DB && !(S[tid][tid] > 0.0)) atomicMin(info, row0 + tid + 1);
   __syncthreads();
+  // the inverse first: it is what the tasks waiting on this block read
+  for (int e = tid; e < DB * DB; e += blockDim.x) dinv[e] = R[e / DB][e % DB];
   for (int e = tid; e < DB * DB; e += blockDim.x) {
     const int r = e / DB, c = e % DB;
     if (c <= r) Tk[(int64_t)r * b + c] = S[r][c];
-    dinv[e] = R[r][c];
   }
 }
 
@@ -148,25 +170,54 @@ __device__ void dag_logdet(double (*S)[DB + 1], double* ldpart) {
 }
 
 // X = A Dinv^T for a DB x DB block (Dinv lower triangular): X[i][j] =
-// sum_{t <= j} A[i][t] Dinv[j][t].  Thread (ty, tx) returns row ty,
-// columns tx + DTX q.
+// sum_{t <= j} A[i][t] Dinv[j][t], in order of t (terms past j multiply
+// Dinv's exact zeros above the diagonal and leave the sum unchanged).
+// Output q of thread tid is element solve_rc(tid, q).  DB = 16: warp w
+// takes the column pair p(w) = w (w < 4) or 11 - w, 16 rows each, and stops
+// at t = 2p + 1 (a bound uniform over the warp): the FP64 pipe charges a
+// warp instruction in full however many lanes it masks, so skipping the
+// zeros by whole warps takes 72 FMA instructions instead of 128, and
+// warps s and s + 4 (one scheduler) get 18 of them each.
+// DB = 32: thread (ty, tx) takes row ty, columns tx + DTX q.
+template <int DB>
+__device__ __forceinline__ void solve_rc(int tid, int q, int& r, int& c) {
+  if constexpr (DB == 16) {
+    const int w = tid >> 5, l = tid & 31, p = w < 4 ? w : 11 - w;
+    r = l & 15;
+    c = 2 * p + (l >> 4);
+  } else {
+    constexpr int DTX = DagShape<DB>::DTX;
+    r = tid / DTX;
+    c = tid % DTX + DTX * q;
+  }
+}
+
 template <int DB>
 __device__ __forceinline__ void dag_solve(const double (*Ab)[DB + 1], const double (*D)[DB + 1],
                                           double out[DagShape<DB>::DJ]) {
   constexpr int DJ = DagShape<DB>::DJ, DTX = DagShape<DB>::DTX;
-  const int ty = threadIdx.x / DTX, tx = threadIdx.x % DTX;
-  double acc[DJ] = {};
-  // DJ independent accumulation chains; D[c][q] = 0 for q > c, so column
-  // group j stops at q = DTX j + DTX - 1 (a bound uniform over the warp)
+  if constexpr (DB == 16) {
+    const int w = threadIdx.x >> 5, p = w < 4 ? w : 11 - w;
+    int r, c;
+    solve_rc<DB>(threadIdx.x, 0, r, c);
+    double acc = 0.0;
+    for (int q = 0; q <= 2 * p + 1; ++q) acc += Ab[r][q] * D[c][q];
+    out[0] = acc;
+  } else {
+    const int ty = threadIdx.x / DTX, tx = threadIdx.x % DTX;
+    double acc[DJ] = {};
+    // DJ independent accumulation chains; D[c][q] = 0 for q > c, so column
+    // group j stops at q = DTX j + DTX - 1 (a bound uniform over the warp)
 #pragma unroll 4
-  for (int q = 0; q < DB; ++q) {
-    const double a = Ab[ty][q];
+    for (int q = 0; q < DB; ++q) {
+      const double a = Ab[ty][q];
 #pragma unroll
-    for (int j = 0; j < DJ; ++j)   // D is lower triangular with exact zeros above
-      if (q <= DTX * j + DTX - 1) acc[j] += a * D[tx + DTX * j][q];
+      for (int j = 0; j < DJ; ++j)
+        if (q <= DTX * j + DTX - 1) acc[j] += a * D[tx + DTX * j][q];
+    }
+#pragma unroll
+    for (int j = 0; j < DJ; ++j) out[j] = acc[j];
   }
-#pragma unroll
-  for (int j = 0; j < DJ; ++j) out[j] = acc[j];
 }
 
 // One persistent launch factors the FP64 diagonal tile of every item as a
@@ -221,6 +272,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     const int r = tk.r, c = tk.c, k = tk.k;
     int* ver = it.ver;
     int* wv = ver + nb * nb;
+    // chain trace (tracing on, chain task, thread 0 only)
+    unsigned long long* tr = (A.trace && (tk.op == 0 || tk.op == 3) && tid == 0)
+                                 ? A.trace + (int64_t)(it.ldslot + k) * TRACE_WORDS : nullptr;
+    chain_stamp(tr, 0);
     if (tid == 0) {
       bool ok;
       if (tk.op == 0) ok = dag_wait(&ver[0], 0, A.err, A.wait_polls);
@@ -238,6 +293,8 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
              dag_wait(&wv[c * nb + r], k - c, A.err, A.wait_polls);
       if (!ok) atomicExch(A.err, 1);
       s_ok = ok;
+      chain_stamp(tr, 1);
+      if (tk.op == 0) chain_stamp(tr, 2);
     }
     __syncthreads();
     if (!s_ok) break;
@@ -255,6 +312,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         if (tid == 0) {
           s_ok2 = dag_wait(&ver[(k - 1) * nb + k - 1], k, A.err, A.wait_polls);
           if (!s_ok2) atomicExch(A.err, 1);
+          chain_stamp(tr, 2);
         }
         __syncthreads();
         if (!s_ok2) break;
@@ -265,10 +323,13 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < DJ; ++j) {
-          S0[ty][tx + DTX * j] = out[j];
-          Tl[(int64_t)ty * b + tx + DTX * j] = out[j];
+          int rr, cc;
+          solve_rc<DB>(tid, j, rr, cc);
+          S0[rr][cc] = out[j];
+          Tl[(int64_t)rr * b + cc] = out[j];
         }
         __syncthreads();
+        chain_stamp(tr, 3);
         // published by the last thread, which has no share of the update
         // below when DB = 16 (136 entries): the fence overlaps the update
         if (tid == blockDim.x - 1) {
@@ -288,8 +349,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         }
       }
       __syncthreads();
+      if (tk.op == 0) chain_stamp(tr, 3);
+      chain_stamp(tr, 4);
       dag_factor<DB>(S2, S1, Tk, b, it.dinv + (int64_t)k * DB * DB, info + it.mat,
-                 it.row0 + (long long)k * DB, tri);
+                     it.row0 + (long long)k * DB, tri);
     } else if (tk.op == 1) {
       // L_rk = A_rk Dinv_k^T (Dinv_k lower triangular)
       double* Tr = T + (int64_t)r * DB * b + k * DB;
@@ -302,7 +365,11 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       double out[DJ];
       dag_solve<DB>(S0, S1, out);
 #pragma unroll
-      for (int j = 0; j < DJ; ++j) Tr[(int64_t)ty * b + tx + DTX * j] = out[j];
+      for (int j = 0; j < DJ; ++j) {
+        int rr, cc;
+        solve_rc<DB>(tid, j, rr, cc);
+        Tr[(int64_t)rr * b + cc] = out[j];
+      }
     } else if (tk.op == 4) {
       // W_jr = W_jr Dinv_r^T
       double* Wb = it.w + (int64_t)c * DB * b + r * DB;
@@ -316,8 +383,10 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
       dag_solve<DB>(S0, S1, out);
 #pragma unroll
       for (int j = 0; j < DJ; ++j) {
-        const int64_t o = (int64_t)c * DB * b + r * DB + (int64_t)ty * b + tx + DTX * j;
-        Wb[(int64_t)ty * b + tx + DTX * j] = out[j];
+        int rr, cc;
+        solve_rc<DB>(tid, j, rr, cc);
+        const int64_t o = (int64_t)c * DB * b + r * DB + (int64_t)rr * b + cc;
+        Wb[(int64_t)rr * b + cc] = out[j];
         if (it.whi) {
           const float h = (float)out[j];
           it.whi[o] = h;
@@ -375,6 +444,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     }
     __syncthreads();
     if (tid == 0) {
+      chain_stamp(tr, 5);
       __threadfence();
       if (tk.op == 4) st_release(&wv[c * nb + r], r - c + 1);
       else if (tk.op == 5) st_release(&wv[c * nb + r], k - c + 1);
@@ -382,6 +452,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         const int blk = (tk.op == 0 || tk.op == 3) ? k * nb + k : tk.op == 1 ? r * nb + k : r * nb + c;
         st_release(&ver[blk], k + 1);
       }
+      chain_stamp(tr, 6);
     }
     // off the critical chain, after publishing: W_kk = Dinv_k^T (published on
     // its own counter, read by the E(r, k, k)) and the log-determinant part
@@ -404,6 +475,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         st_release(&wv[k * nb + k], 1);
       }
       dag_logdet<DB>(S2, ldparts + it.ldslot + k);
+      chain_stamp(tr, 7);
     }
   }
 }
@@ -603,9 +675,12 @@ __global__ void __launch_bounds__(256) k_panel_round(Arena A, const ItemRound* _
 }  // namespace
 
 std::vector<DagTask> potrf_dag_tasks(int nb) {
-  // F(0), T(r, 0) for r >= 2; then per k: G(k+1) (the critical chain), the
-  // column-(k+1) updates, T(r, k+1) for r >= k+3, then the rest of step k's
-  // updates.  Every task's inputs come earlier in this order.
+  // F(0), T(r, 0) for r >= 2, G(1); then per step k: the column-(k+1)
+  // updates, the update of block (k+2, k+2) and at once G(k+2) (the
+  // critical chain, one step ahead: the CTA that takes it loads its blocks
+  // and waits for G(k+1) while the rest of step k is still being handed
+  // out), T(r, k+1) for r >= k+3, the rest of step k's updates, then the
+  // blocks of W.  Every task's inputs come earlier in this order.
   std::vector<DagTask> v;
   auto add = [&](int op, int r, int c, int k) {
     v.push_back(DagTask{(uint8_t)op, (uint8_t)r, (uint8_t)c, (uint8_t)k});
@@ -619,12 +694,17 @@ std::vector<DagTask> potrf_dag_tasks(int nb) {
   };
   add(0, 0, 0, 0);
   for (int r = 2; r < nb; ++r) add(1, r, 0, 0);
+  if (nb > 1) add(3, 1, 1, 1);
   for (int k = 0; k + 1 < nb; ++k) {
-    add(3, k + 1, k + 1, k + 1);
     for (int r = k + 2; r < nb; ++r) add(2, r, k + 1, k);
+    if (k + 2 < nb) {
+      add(2, k + 2, k + 2, k);
+      add(3, k + 2, k + 2, k + 2);
+    }
     for (int r = k + 3; r < nb; ++r) add(1, r, k + 1, k + 1);
     for (int c = k + 2; c < nb; ++c)
-      for (int r = c; r < nb; ++r) add(2, r, c, k);
+      for (int r = c; r < nb; ++r)
+        if (r != k + 2 || c != k + 2) add(2, r, c, k);
     wtasks(k);
   }
   for (int j = 0; j + 1 < nb; ++j) add(4, nb - 1, j, 0);

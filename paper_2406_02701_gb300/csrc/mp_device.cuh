@@ -106,6 +106,16 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 // Waits until *ver >= need; false on timeout or when another CTA gave up.
+// Chain-trace stamp `point` (%globaltimer ns and clock64) into a block's
+// TRACE_WORDS words; no-op when tr is NULL (tracing off).
+__device__ __forceinline__ void chain_stamp(unsigned long long* tr, int point) {
+  if (!tr) return;
+  unsigned long long g;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g));
+  tr[point] = g;
+  tr[8 + point] = (unsigned long long)clock64();
+}
+
 __device__ __forceinline__ bool dag_wait(const int* ver, int need, const int* err, int polls) {
   const uint32_t limit = polls > 0 ? (uint32_t)polls : DAG_WAIT_LIMIT;
   for (uint32_t i = 0; i < limit; ++i) {

@@ -38,7 +38,11 @@ struct Arena {
   int* err;                       // set to 1 when a bounded device wait ran out
   int b;
   int wait_polls;                 // polls of a task-graph wait before it gives up (0: DAG_WAIT_LIMIT)
+  // chain trace of the diagonal tiles' task graphs (NULL: off): per
+  // diagonal block (log-determinant slot order) TRACE_WORDS stamps
+  unsigned long long* trace;
 };
+constexpr int TRACE_WORDS = 16;   // 8 %globaltimer (ns) then 8 clock64 stamps per block
 
 template <typename T>
 __host__ __device__ inline T* tile_ptr(const Arena& A, int id) {

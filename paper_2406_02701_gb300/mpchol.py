@@ -24,6 +24,9 @@ MP_TMAT_DAG16 = 32
 MP_TMAT_DAG32 = 64
 MP_TMAT_LOWP_RING4 = 128
 MP_TMAT_DIRECT = 256
+MP_TMAT_TRACE = 512
+TRACE_POINTS = ("taken", "inputs_final", "inverse_ready", "solved", "updated", "factored",
+                "published", "done")
 ELEM_BYTES = {MP_F64: 8, MP_F32: 4, MP_BF16: 2, MP_F16: 2, MP_E4M3: 1}
 
 
@@ -70,6 +73,8 @@ _SIGS = {
     "mp_chol_steps": (C.c_int, [P, C.c_int32, C.c_int32]),
     "mp_logdet": (C.c_int, [P, P]),
     "mp_tmat_set_wait_budget": (C.c_int, [P, C.c_int32]),
+    "mp_tmat_chain_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "mp_potrf_dag_schedule": (C.c_int, [C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "mp_trsm": (C.c_int, [P, C.c_int, P, C.c_int64, C.c_int32]),
     "mp_solve": (C.c_int, [P, P, C.c_int64, C.c_int32]),
     "mp_chol2inv": (C.c_int, [P, P, C.c_int64]),
@@ -272,6 +277,19 @@ class TiledMatrix:
     def set_wait_budget(self, polls: int):
         """Polls a task-graph wait makes before it gives up (0: default)."""
         self.ctx.check(self.lib.mp_tmat_set_wait_budget(self.h, polls))
+
+    def chain_trace(self):
+        """Stamps of the last factorisation's critical chain (the matrix
+        was created with flags=MP_TMAT_TRACE): returns (ns, cycles, DB) with
+        ns and cycles of shape (nt, b / DB, 8), the points of TRACE_POINTS
+        for each diagonal block of each diagonal tile."""
+        cnt, blk = C.c_int64(), C.c_int32()
+        self.ctx.check(self.lib.mp_tmat_chain_trace(self.h, None, 0, C.byref(cnt), C.byref(blk)))
+        buf = np.zeros(cnt.value, dtype=np.uint64)
+        self.ctx.check(self.lib.mp_tmat_chain_trace(self.h, buf.ctypes.data_as(C.c_void_p), cnt.value,
+                                                    C.byref(cnt), C.byref(blk)))
+        w = buf.reshape(self.nt, -1, 16).astype(np.int64)
+        return w[:, :, :8], w[:, :, 8:], blk.value
 
     def logdet(self, out):
         self.ctx.check(self.lib.mp_logdet(self.h, _ptr(out)))
@@ -501,6 +519,21 @@ def matern_host(r, sigma2, range_, nu):
     if st != MP_OK:
         raise MPError(st, "mp_matern_host")
     return out
+
+
+def potrf_dag_schedule(nb):
+    """The diagonal tile's task order for nb blocks: int array (tasks, 4)
+    of op, r, c, k (host only)."""
+    lib = load()
+    cnt = C.c_int64()
+    st = lib.mp_potrf_dag_schedule(nb, None, 0, C.byref(cnt))
+    if st != MP_OK:
+        raise MPError(st, "mp_potrf_dag_schedule")
+    out = np.empty(4 * cnt.value, dtype=np.uint8)
+    st = lib.mp_potrf_dag_schedule(nb, out.ctypes.data_as(C.c_void_p), cnt.value, C.byref(cnt))
+    if st != MP_OK:
+        raise MPError(st, "mp_potrf_dag_schedule")
+    return out.reshape(-1, 4).astype(np.int64)
 
 
 def map_bound(n, b, sorted_locs, cov, band, near, far, eps):

@@ -596,3 +596,37 @@ def test_general_nu_in_batches_norms_and_maps(ctx):
     got = ctx.tile_norms(n, b, torch.from_numpy(locs).to(DEV), 1.0, 0.05, 1.3, 1e-4).cpu().numpy()
     ref = OC.tile_norms(OM.covariance(locs, 1.3, 0.05, 1.0, 1e-4), b)
     assert np.allclose(got, ref, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("flags", [0, 32, 64])
+def test_chain_trace_is_ordered_and_leaves_the_factor_alone(ctx, flags):
+    """MP_TMAT_TRACE stamps the diagonal tiles' chain tasks: the factor and
+    log-determinant carry the same bits as without it, the stamps of every
+    block are in program order, and each chain task sees the previous
+    block's inverse only after that block was factored."""
+    from paper_2406_02701_gb300 import mpchol
+    n, b = 1500, 512
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.F32, 1)
+    locs = torch.from_numpy(I.points(n, 15)).to(DEV)
+    out = []
+    for fl in (flags, flags | mpchol.MP_TMAT_TRACE):
+        T = mpchol.TiledMatrix(ctx, n, b, pmap, flags=fl)
+        T.generate(locs, 1.0, 0.05, 1.5, 1e-3)
+        info, ld = T.chol()
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        out.append((ld.item(), [T.get_tile(i, j)[1].copy() for i in range(nt) for j in range(i + 1)], T))
+    assert out[1][0] == out[0][0]
+    for a, c in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, c)
+    with pytest.raises(RuntimeError):
+        out[0][2].chain_trace()
+    ns, cyc, db = out[1][2].chain_trace()
+    assert db == {0: 16, 32: 16, 64: 32}[flags]
+    assert ns.shape == (nt, b // db, 8) and cyc.shape == ns.shape
+    assert np.all(ns[:, :, 0] > 0)
+    assert np.all(np.diff(cyc, axis=2) >= 0)
+    assert np.all(np.diff(ns, axis=2) >= 0)
+    assert np.all(ns[:, 1:, 2] >= ns[:, :-1, 5])
+    assert np.all(ns[1:, 0, 0] >= ns[:-1, -1, 5])
