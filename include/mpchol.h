@@ -265,6 +265,18 @@ mp_status mp_tmat_set_wait_budget(mp_tmat* t, int32_t polls);
  * tasks) may be NULL to query the count. */
 mp_status mp_potrf_dag_schedule(int32_t nb, uint8_t* h_out, int64_t cap, int64_t* count);
 
+/* The order in which a triangular solve's task graph hands out its tasks
+ * for one matrix of nt tile rows split into p_blocks row blocks per tile
+ * (b / 32); trans = 0 forward (L x = z), 1 backward (L^T x = z).  Host
+ * only, for checking the schedule without a GPU.  One word per task: bits
+ * 24-27 op (0 diagonal block: out_i[p] from in_i - chain_i; 1 update in
+ * place: in_i[p] -= L_ij out_j, or L_ji^T out_j backward; 2 the same
+ * product with the row j solved just before i, stored in chain_i[p]),
+ * bits 28-39 i, 40-51 j, 52-59 p (bits 0-23: the matrix, 0 here).  *count = tasks; h_out (cap >= *count)
+ * may be NULL to query the count. */
+mp_status mp_solve_dag_schedule(int32_t nt, int32_t p_blocks, int32_t trans, uint64_t* h_out, int64_t cap,
+                                int64_t* count);
+
 /* Critical-chain stamps of the last factorisation of a matrix created with
  * MP_TMAT_TRACE (instrumentation, off by default; the arithmetic is the
  * same with it on).  The FP64 diagonal tile's task graph runs one chain

@@ -169,7 +169,7 @@ struct Plan {
   int* d_dag = nullptr;            // diagonal-tile task graph: ticket, then per matrix 2 (b/dag_nb)^2 counters
   int32_t* d_ltab = nullptr;       // per matrix: nt*nt factor tile ids, then nt ids of L_ii^{-T}
   std::vector<int64_t> ltab_off;
-  int* d_scnt = nullptr;           // solve task graph: ticket, then per matrix nt (b/32 + 1) counters
+  int* d_scnt = nullptr;           // solve task graph: ticket, then per matrix nt (2 b/32 + 1) counters
   size_t scnt_bytes = 0;
   std::vector<int64_t> scnt_off;
   size_t dag_bytes = 0;
@@ -300,6 +300,7 @@ struct mp_tmat {
   // loglik workspace + graph
   int ws_nrhs = 0;
   double *zp = nullptr, *x = nullptr, *r = nullptr, *w = nullptr, *d = nullptr;
+  double* c = nullptr;              // the solves' chain products (scratch)
   double *rowabs = nullptr, *red = nullptr;
   double* rpart = nullptr;          // residual partial products: nt * nt * b * nrhs
   float* rpabs = nullptr;           // residual partial absolute sums: nt * nt * b
@@ -919,7 +920,7 @@ mp_status finish_plan(Plan& P) {
       ltab.insert(ltab.end(), M.linv_hi.begin(), M.linv_hi.end());
       ltab.insert(ltab.end(), M.linv_lo.begin(), M.linv_lo.end());
       P.scnt_off.push_back((int64_t)cnt);
-      cnt += (size_t)M.nt * (nbb + 1);
+      cnt += (size_t)M.nt * (2 * nbb + 1);
     }
     if (mp_status st = P.alloc(&p, sizeof(int32_t) * ltab.size())) return st;
     P.d_ltab = (int32_t*)p;
@@ -1435,6 +1436,17 @@ mp_status mp_potrf_dag_schedule(int32_t nb, uint8_t* h_out, int64_t cap, int64_t
   return MP_OK;
 }
 
+mp_status mp_solve_dag_schedule(int32_t nt, int32_t p_blocks, int32_t trans, uint64_t* h_out, int64_t cap,
+                                int64_t* count) {
+  if (nt < 1 || nt > 4095 || p_blocks < 1 || p_blocks > 255 || !count) return MP_ERR_ARG;
+  const std::vector<SolveTask> v = solve_dag_tasks({nt}, p_blocks, trans ? 1 : 0);
+  *count = (int64_t)v.size();
+  if (!h_out) return MP_OK;
+  if (cap < (int64_t)v.size()) return MP_ERR_ARG;
+  for (size_t i = 0; i < v.size(); ++i) h_out[i] = v[i];
+  return MP_OK;
+}
+
 mp_status mp_tmat_chain_trace(mp_tmat* t, uint64_t* h_out, int64_t cap, int64_t* count, int32_t* block) {
   if (!t || !count) return MP_ERR_ARG;
   Plan& P = t->P;
@@ -1471,11 +1483,12 @@ struct SolvePlan {
 };
 
 // Forward (trans = 0: out = L^{-1} in) or backward (trans = 1: out = L^{-T}
-// in) tiled solve of the plan's matrices, out of place; `in` is consumed.
-// Vectors are given per matrix as padded N x nrhs blocks with leading
-// dimension ld.
+// in) tiled solve of the plan's matrices, out of place; `in` is consumed,
+// `chain` is scratch.  Vectors are given per matrix as padded N x nrhs
+// blocks with leading dimension ld.
 SolvePlan build_solve(Plan& P, const std::vector<double*>& in, const std::vector<double*>& out,
-                      const std::vector<int64_t>& ld, const std::vector<int>& nrhs, int trans) {
+                      const std::vector<double*>& chain, const std::vector<int64_t>& ld,
+                      const std::vector<int>& nrhs, int trans) {
   SolvePlan sp;
   std::vector<ItemSolveDag> items;
   std::vector<int> nts;
@@ -1486,6 +1499,7 @@ SolvePlan build_solve(Plan& P, const std::vector<double*>& in, const std::vector
     it.linv = it.tiles + (int64_t)M.nt * M.nt;
     it.in = in[m];
     it.out = out[m];
+    it.chain = chain[m];
     it.cnt = P.d_scnt + P.scnt_off[m];
     it.ld = ld[m];
     it.nt = M.nt;
@@ -1552,6 +1566,7 @@ static mp_status ensure_ws(mp_tmat* t, int nrhs) {
   if ((st = A((void**)&t->r, sizeof(double) * N * nrhs))) return st;
   if ((st = A((void**)&t->w, sizeof(double) * N * nrhs))) return st;
   if ((st = A((void**)&t->d, sizeof(double) * N * nrhs))) return st;
+  if ((st = A((void**)&t->c, sizeof(double) * N * nrhs))) return st;
   if ((st = A((void**)&t->rowabs, sizeof(double) * N))) return st;
   if (P.keep_sigma) {
     const size_t nt = (size_t)P.mats[0].nt;
@@ -1629,7 +1644,7 @@ extern "C" mp_status mp_trsm(mp_tmat* t, int trans, double* d_B, int64_t ldb, in
   // solve on the padded copy, then copy the first n rows back
   std::vector<char> saved;
   saved.swap(P.h_items);
-  const SolvePlan ls = build_solve(P, {t->x}, {t->w}, {N}, {nrhs}, trans ? 1 : 0);
+  const SolvePlan ls = build_solve(P, {t->x}, {t->w}, {t->c}, {N}, {nrhs}, trans ? 1 : 0);
   size_t bytes = P.h_items.size();
   if (bytes > t->d_sitems_cap) {
     P.raw_free(t->d_sitems);
@@ -1674,9 +1689,9 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
     std::vector<char> saved;
     saved.swap(P.h_items);
     // r -> w (forward), w -> x or w -> d (backward)
-    const SolvePlan fwd_rw = build_solve(P, {t->r}, {t->w}, {N}, {nrhs}, 0);
-    const SolvePlan bwd_wx = build_solve(P, {t->w}, {t->x}, {N}, {nrhs}, 1);
-    const SolvePlan bwd_wd = build_solve(P, {t->w}, {t->d}, {N}, {nrhs}, 1);
+    const SolvePlan fwd_rw = build_solve(P, {t->r}, {t->w}, {t->c}, {N}, {nrhs}, 0);
+    const SolvePlan bwd_wx = build_solve(P, {t->w}, {t->x}, {t->c}, {N}, {nrhs}, 1);
+    const SolvePlan bwd_wd = build_solve(P, {t->w}, {t->d}, {t->c}, {N}, {nrhs}, 1);
     std::vector<ItemResTile> rtiles;
     std::vector<ItemResRow> rrows;
     for (int i = 0; i < M.nt && refine_iters > 0; ++i) {
@@ -1921,6 +1936,8 @@ extern "C" mp_status mp_batch_create_ex(mp_ctx* ctx, int32_t count, const mp_req
   double* vec = (double*)p;
   if ((st = P.alloc(&p, sizeof(double) * vec_total))) { delete B; return st; }
   double* wout = (double*)p;
+  if ((st = P.alloc(&p, sizeof(double) * vec_total))) { delete B; return st; }
+  double* chn = (double*)p;
   if ((st = P.alloc(&p, sizeof(double) * B->total_rhs))) { delete B; return st; }
   B->d_llbuf = (double*)p;
   if ((st = P.alloc(&p, sizeof(int32_t) * count))) { delete B; return st; }
@@ -1946,7 +1963,7 @@ extern "C" mp_status mp_batch_create_ex(mp_ctx* ctx, int32_t count, const mp_req
   std::vector<ItemGen> gamax, gall;
   std::vector<ItemBatchCopy> cp;
   std::vector<ItemBatchOut> outs;
-  std::vector<double*> vp, wp;
+  std::vector<double*> vp, wp, cp_;
   std::vector<int64_t> ld;
   std::vector<int> nr;
   int64_t vo = 0;
@@ -1988,13 +2005,14 @@ extern "C" mp_status mp_batch_create_ex(mp_ctx* ctx, int32_t count, const mp_req
     outs.push_back(o);
     vp.push_back(vec + vo);
     wp.push_back(wout + vo);
+    cp_.push_back(chn + vo);
     ld.push_back(N);
     nr.push_back(reqs[r].nrhs);
     vo += N * reqs[r].nrhs;
     rhs_o += reqs[r].nrhs;
   }
   size_t off_ga = P.push(gamax), off_g = P.push(gall), off_cp = P.push(cp), off_out = P.push(outs);
-  const SolvePlan fwd = build_solve(P, vp, wp, ld, nr, 0);
+  const SolvePlan fwd = build_solve(P, vp, wp, cp_, ld, nr, 0);
   if ((st = upload_items(P))) { delete B; return st; }
   st = capture_graph(ctx, P.cap, [&](cudaStream_t s) {
     const Arena A = P.arena();

@@ -28,18 +28,26 @@ __device__ __forceinline__ bool gated(const int* gate) { return gate && *gate ==
 // ------------------------------------------------------------ solve graph
 //
 // One persistent launch runs a whole tiled triangular solve as tasks over
-// 32-row blocks (P = b / 32 per tile row):
-//   D(i, p)     diagonal block: out_i[p] from in_i with the explicit
-//               inverse X = L_ii^{-T} (float64);
-//   O(i, j, p)  off-diagonal block: in_i[p] -= L_ij out_j (forward) or
-//               in_i[p] -= L_ji^T out_j (backward).
-// Counters (zero at launch) per tile row i: updates applied to each block
-// of in_i, and finished blocks of out_i.  D(i, p) waits until the blocks of
-// in_i it reads have all their updates; O(i, j, p) waits for the whole of
-// out_j and for the update before it on the same block (updates to one
-// block are applied in a fixed order, so the result is deterministic).
-// Tasks are taken by an atomic ticket in a topological order, so the graph
-// cannot deadlock whatever the number of co-resident CTAs.
+// 32-row blocks (P = b / 32 per tile row), tile rows taken in solve order
+// s_0, s_1, ... (forward 0, 1, ...; backward nt-1, nt-2, ...):
+//   D(i, p)     diagonal block: out_i[p] from in_i - chain_i with the
+//               explicit inverse X = L_ii^{-T};
+//   O(i, j, p)  off-diagonal block applied in place: in_i[p] -= L_ij out_j
+//               (forward) or L_ji^T out_j (backward), for every j but the
+//               row solved just before i;
+//   C(i, j, p)  the same product with that last row j, stored in chain_i[p]
+//               (the critical chain: it does not wait for the in-place
+//               updates, so it can be handed out right after D(j)).
+// Counters (zero at launch) per tile row i: updates applied in place to
+// each block of in_i, finished blocks of out_i, and the chain product of
+// each block.  D(i, p) waits until the blocks of in_i it reads have all
+// their in-place updates and chain products; O and C wait for the whole of
+// out_j, O also for the in-place update before it on the same block
+// (updates to one block are applied in a fixed order and the chain
+// product is subtracted last, so the result is deterministic and equals
+// in-place accumulation in solve order).  Tasks are taken by an atomic
+// ticket in a topological order, so the graph cannot deadlock whatever the
+// number of co-resident CTAs.
 //
 // Off-diagonal tiles stored in FP32 or below hold values exact in FP32, so
 // their products run on the FP32 pipe in float-float arithmetic: out_j is
@@ -73,12 +81,19 @@ __device__ __forceinline__ void ff_madd(float& hi, float& lo, float a, float h, 
 constexpr int MLP = 32;   // loads a thread issues before using them
 
 // Diagonal block: out_i[p] from in_i with X = L_ii^{-T} (float64).
+// in_i - chain_i (the chain product is the row's last update; none for the
+// first row solved)
+__device__ __forceinline__ double solve_in(const double* v, const double* ch, int64_t o) {
+  return ch ? __ldcg(v + o) - __ldcg(ch + o) : __ldcg(v + o);
+}
+
 template <int RCT>
 __device__ void solve_diag(const Arena& A, const ItemSolveDag& it, int i, int p, int trans,
-                           double* vs, double* part) {
+                           double* vs, double* part, bool first) {
   const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* X = tile_ptr<double>(A, it.linv[i]);
   const double* v = it.in + (int64_t)i * b;
+  const double* ch = first ? nullptr : it.chain + (int64_t)i * b;
   double* o = it.out + (int64_t)i * b;
   const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
@@ -86,7 +101,7 @@ __device__ void solve_diag(const Arena& A, const ItemSolveDag& it, int i, int p,
     __syncthreads();
     for (int e = tid; e < (t1 - t0) * RCT; e += blockDim.x) {
       const int t = t0 + e / RCT, c = e % RCT;
-      vs[t * RCT + c] = c < nc ? __ldcg(v + (int64_t)(c0 + c) * it.ld + t) : 0.0;
+      vs[t * RCT + c] = c < nc ? solve_in(v, ch, (int64_t)(c0 + c) * it.ld + t) : 0.0;
     }
     __syncthreads();
     double acc[RCT];
@@ -168,11 +183,12 @@ __device__ __forceinline__ void ff_madd2(float& hi, float& lo, float xh, float x
 // same data flow as solve_diag, the products on the FP32 pipe.
 template <int RCT>
 __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int p, int trans,
-                              double* vs, double* part) {
+                              double* vs, double* part, bool first) {
   const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = it.nt;
   const float* Xh = tile_ptr<float>(A, it.linv[nt + i]);
   const float* Xl = tile_ptr<float>(A, it.linv[2 * nt + i]);
   const double* v = it.in + (int64_t)i * b;
+  const double* ch = first ? nullptr : it.chain + (int64_t)i * b;
   double* o = it.out + (int64_t)i * b;
   float2* vsf = reinterpret_cast<float2*>(vs);
   const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
@@ -181,7 +197,7 @@ __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int
     __syncthreads();
     for (int e = tid; e < (t1 - t0) * RCT; e += blockDim.x) {
       const int t = t0 + e / RCT, c = e % RCT;
-      const double x = c < nc ? __ldcg(v + (int64_t)(c0 + c) * it.ld + t) : 0.0;
+      const double x = c < nc ? solve_in(v, ch, (int64_t)(c0 + c) * it.ld + t) : 0.0;
       const float h = (float)x;
       vsf[t * RCT + c] = make_float2(h, (float)(x - (double)h));
     }
@@ -257,7 +273,8 @@ __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int
 // Off-diagonal block, tiles stored in FP32 or below (DT), float-float sums.
 template <int RCT, int DT>
 __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, int b, int p,
-                             int trans, const float2* ys, double* part, double* r, int c0, int nc) {
+                             int trans, const float2* ys, double* part, double* r, int c0, int nc,
+                             bool store) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float hi[RCT], lo[RCT];
 #pragma unroll
@@ -287,7 +304,7 @@ __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, i
       for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
       if (sg == 0) {
         double* rp = r + (int64_t)(c0 + c) * it.ld + q;
-        *rp = __ldcg(rp) - sum;
+        *rp = store ? sum : __ldcg(rp) - sum;
       }
     }
   } else {
@@ -318,7 +335,7 @@ __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, i
         double sum = 0.0;
         for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
         double* rp = r + (int64_t)(c0 + c) * it.ld + q;
-        *rp = __ldcg(rp) - sum;
+        *rp = store ? sum : __ldcg(rp) - sum;
       }
     }
   }
@@ -327,7 +344,7 @@ __device__ void solve_off_ff(const char* L, float scf, const ItemSolveDag& it, i
 // Off-diagonal block of an FP64 tile, float64 sums.
 template <int RCT>
 __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, int p, int trans,
-                              const double* vs, double* part, double* r, int c0, int nc) {
+                              const double* vs, double* part, double* r, int c0, int nc, bool store) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double acc[RCT];
 #pragma unroll
@@ -352,7 +369,7 @@ __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, in
       for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
       if (sg == 0) {
         double* rp = r + (int64_t)(c0 + c) * it.ld + q;
-        *rp = __ldcg(rp) - sum;
+        *rp = store ? sum : __ldcg(rp) - sum;
       }
     }
   } else {
@@ -377,7 +394,7 @@ __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, in
         double sum = 0.0;
         for (int w = 0; w < 8; ++w) sum += part[(w * 32 + lane) * RCT + c];
         double* rp = r + (int64_t)(c0 + c) * it.ld + q;
-        *rp = __ldcg(rp) - sum;
+        *rp = store ? sum : __ldcg(rp) - sum;
       }
     }
   }
@@ -385,7 +402,7 @@ __device__ void solve_off_f64(const double* L, const ItemSolveDag& it, int b, in
 
 template <int RCT>
 __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, int p, int trans,
-                          double* vs, double* part) {
+                          double* vs, double* part, bool store) {
   const int b = A.b, tid = threadIdx.x, nt = it.nt;
   const int tile = trans ? it.tiles[j * nt + i] : it.tiles[i * nt + j];
   const TileRef ref = A.tiles[tile];
@@ -393,7 +410,7 @@ __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, 
   const float scf = (float)A.scale[tile];       // a power of two (1 except E4M3)
   const bool f64 = ref.dt == F64;
   const double* y = it.out + (int64_t)j * b;
-  double* r = it.in + (int64_t)i * b;
+  double* r = (store ? it.chain : it.in) + (int64_t)i * b;
   float2* ys = reinterpret_cast<float2*>(vs);
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
     const int nc = min(RCT, it.nrhs - c0);
@@ -410,12 +427,52 @@ __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, 
     }
     __syncthreads();
     switch (ref.dt) {
-      case F64: solve_off_f64<RCT>(reinterpret_cast<const double*>(L), it, b, p, trans, vs, part, r, c0, nc); break;
-      case F32: solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
-      case BF16: solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
-      case F16: solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
-      default: solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc); break;
+      case F64: solve_off_f64<RCT>(reinterpret_cast<const double*>(L), it, b, p, trans, vs, part, r, c0, nc, store); break;
+      case F32: solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
+      case BF16: solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
+      case F16: solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
+      default: solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
     }
+  }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Before a task waits: pull the factor data it will read (final before the
+// solve starts) from HBM into L2, one 128-byte line per request, so that
+// the reads after the wait hit L2.  A rows x (cols elements of esz bytes)
+// block with row stride b.
+__device__ __forceinline__ void prefetch_block(const char* base, int b, int esz, int r0, int rows,
+                                               int c0, int cols) {
+  const int lpr = (cols * esz + 127) / 128;          // lines per row (segments start 128-byte aligned)
+  for (int e = threadIdx.x; e < rows * lpr; e += blockDim.x) {
+    const int r = r0 + e / lpr, l = e % lpr;
+    prefetch_l2(base + ((int64_t)r * b + c0) * esz + 128 * l);
+  }
+}
+
+__device__ void solve_prefetch(const Arena& A, const ItemSolveDag& it, int op, int i, int j, int p,
+                               int trans) {
+  const int b = A.b, nt = it.nt;
+  if (op == 0) {
+    // X = L_ii^{-T}: forward rows t < 32 (p + 1), columns of block p;
+    // backward rows of block p, columns t >= 32 p
+    const int r0 = trans ? 32 * p : 0, rows = trans ? 32 : 32 * (p + 1);
+    const int c0 = trans ? 32 * p : 32 * p, cols = trans ? b - 32 * p : 32;
+    if (it.ffdiag) {
+      prefetch_block(tile_bytes(A, it.linv[nt + i]), b, 4, r0, rows, c0, cols);
+      prefetch_block(tile_bytes(A, it.linv[2 * nt + i]), b, 4, r0, rows, c0, cols);
+    } else {
+      prefetch_block(tile_bytes(A, it.linv[i]), b, 8, r0, rows, c0, cols);
+    }
+  } else {
+    // L_ij rows of block p (forward), or L_ji's columns of block p (backward)
+    const int tile = trans ? it.tiles[j * nt + i] : it.tiles[i * nt + j];
+    const int esz = esize(A.tiles[tile].dt);
+    if (trans) prefetch_block(tile_bytes(A, tile), b, esz, 0, b, 32 * p, 32);
+    else prefetch_block(tile_bytes(A, tile), b, esz, 32 * p, 32, 0, b);
   }
 }
 
@@ -440,15 +497,20 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
     const ItemSolveDag it = items[m];
     int* cnt = it.cnt;
     const int nt = it.nt;
+    solve_prefetch(A, it, op, i, j, p, trans);
+    const int CS = 2 * P + 1;                      // counters per tile row
+    const int sti = trans ? nt - 1 - i : i;        // i's place in solve order
     if (warp == 0) {
       bool ok = true;
       if (op == 0) {
-        // the blocks of in_i this block reads: p' <= p (forward), p' >= p (backward)
-        const int need = trans ? nt - 1 - i : i;
-        if (lane < P && (trans ? lane >= p : lane <= p)) ok = dag_wait(&cnt[i * (P + 1) + lane], need, A.err, A.wait_polls);
+        // the blocks of in_i this block reads: p' <= p (forward), p' >= p
+        // (backward), with their sti - 1 in-place updates and chain product
+        if (lane < P && (trans ? lane >= p : lane <= p) && sti >= 1)
+          ok = dag_wait(&cnt[i * CS + lane], sti - 1, A.err, A.wait_polls) &&
+               dag_wait(&cnt[i * CS + P + 1 + lane], 1, A.err, A.wait_polls);
       } else if (lane == 0) {
-        const int need = trans ? nt - 1 - j : j;
-        ok = dag_wait(&cnt[j * (P + 1) + P], P, A.err, A.wait_polls) && dag_wait(&cnt[i * (P + 1) + p], need, A.err, A.wait_polls);
+        ok = dag_wait(&cnt[j * CS + P], P, A.err, A.wait_polls);
+        if (op == 1) ok = ok && dag_wait(&cnt[i * CS + p], trans ? nt - 1 - j : j, A.err, A.wait_polls);
       }
       ok = __all_sync(0xffffffffu, ok);
       if (lane == 0) {
@@ -459,15 +521,16 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
     __syncthreads();
     if (!s_ok) break;
     if (op == 0) {
-      if (it.ffdiag) solve_diag_ff<RCT>(A, it, i, p, trans, vs, part);
-      else solve_diag<RCT>(A, it, i, p, trans, vs, part);
+      if (it.ffdiag) solve_diag_ff<RCT>(A, it, i, p, trans, vs, part, sti == 0);
+      else solve_diag<RCT>(A, it, i, p, trans, vs, part, sti == 0);
     }
-    else solve_off<RCT>(A, it, i, j, p, trans, vs, part);
+    else solve_off<RCT>(A, it, i, j, p, trans, vs, part, op == 2);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      if (op == 0) atomicAdd(&cnt[i * (P + 1) + P], 1);
-      else st_release(&cnt[i * (P + 1) + p], trans ? nt - j : j + 1);
+      if (op == 0) atomicAdd(&cnt[i * CS + P], 1);
+      else if (op == 1) st_release(&cnt[i * CS + p], trans ? nt - j : j + 1);
+      else st_release(&cnt[i * CS + P + 1 + p], 1);
     }
   }
 }
@@ -722,9 +785,13 @@ __global__ void k_loglik(const double* logdet, const double* quad, int64_t n, in
 }  // namespace
 
 std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int P, int trans) {
-  // per matrix: for each step the diagonal blocks, then the updates of the
-  // next tile row (the critical chain), then the other updates; matrices
-  // are interleaved round-robin, which keeps each matrix's order
+  // per matrix, rows in solve order s_0, s_1, ...: D(s_0), then per step t
+  // the chain products of s_{t+1} with out_{s_t} and at once the diagonal
+  // blocks of s_{t+1} (the critical chain, handed out together), then the
+  // in-place updates of the rows s_{t+2}.. with out_{s_t}, which run while
+  // the chain waits; the in-place updates of a row come in solve order of
+  // their columns.  Matrices are interleaved round-robin, which keeps each
+  // matrix's order.
   std::vector<std::vector<SolveTask>> per(nts.size());
   auto pack = [](int m, int op, int i, int j, int p) {
     return (SolveTask)m | ((SolveTask)op << 24) | ((SolveTask)i << 28) | ((SolveTask)j << 40) |
@@ -734,16 +801,14 @@ std::vector<SolveTask> solve_dag_tasks(const std::vector<int>& nts, int P, int t
   for (size_t m = 0; m < nts.size(); ++m) {
     const int nt = nts[m];
     auto& v = per[m];
-    for (int st = 0; st < nt; ++st) {
-      const int s = trans ? nt - 1 - st : st;
-      for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 0, s, 0, trans ? P - 1 - q : q));
-      if (!trans) {
-        for (int i = s + 1; i < nt; ++i)
-          for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 1, i, s, q));
-      } else {
-        for (int i = s - 1; i >= 0; --i)
-          for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 1, i, s, q));
-      }
+    auto row = [&](int st) { return trans ? nt - 1 - st : st; };
+    auto blk = [&](int q) { return trans ? P - 1 - q : q; };
+    for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 0, row(0), 0, blk(q)));
+    for (int st = 0; st + 1 < nt; ++st) {
+      for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 2, row(st + 1), row(st), blk(q)));
+      for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 0, row(st + 1), 0, blk(q)));
+      for (int u = st + 2; u < nt; ++u)
+        for (int q = 0; q < P; ++q) v.push_back(pack((int)m, 1, row(u), row(st), q));
     }
     total += v.size();
   }

@@ -187,15 +187,21 @@ struct ItemSolveDag {
                           // of its FP32 hi parts and nt of its lo parts (ffdiag)
   double* in;             // N x nrhs (column stride ld), consumed
   double* out;            // N x nrhs (column stride ld)
-  int* cnt;
+  double* chain;          // N x nrhs (column stride ld): each tile row's update with the
+                          // row solved just before it (kept apart, subtracted by the
+                          // diagonal step)
+  int* cnt;               // per tile row 2 P + 1 counters (P = b / 32): updates applied
+                          // in place to each block, finished diagonal blocks, chain
+                          // update of each block done
   int64_t ld;
   int32_t nt, nrhs;
   int32_t ffdiag;         // 1: diagonal steps in float-float from the hi/lo parts
   int32_t pad_;
 };
 // Task of the solve graph: matrix (bits 0-23), op (24-27: 0 diagonal block,
-// 1 off-diagonal block), target tile row i (28-39), source tile row j
-// (40-51), 32-row block p (52-59).
+// 1 off-diagonal block applied in place, 2 off-diagonal block into the
+// chain vector), target tile row i (28-39), source tile row j (40-51),
+// 32-row block p (52-59).
 typedef uint64_t SolveTask;
 
 // Refinement residual r = z - Sigma x from the float64 copy of Sigma's lower

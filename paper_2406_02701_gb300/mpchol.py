@@ -75,6 +75,7 @@ _SIGS = {
     "mp_tmat_set_wait_budget": (C.c_int, [P, C.c_int32]),
     "mp_tmat_chain_trace": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "mp_potrf_dag_schedule": (C.c_int, [C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
+    "mp_solve_dag_schedule": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]),
     "mp_trsm": (C.c_int, [P, C.c_int, P, C.c_int64, C.c_int32]),
     "mp_solve": (C.c_int, [P, P, C.c_int64, C.c_int32]),
     "mp_chol2inv": (C.c_int, [P, P, C.c_int64]),
@@ -534,6 +535,25 @@ def potrf_dag_schedule(nb):
     if st != MP_OK:
         raise MPError(st, "mp_potrf_dag_schedule")
     return out.reshape(-1, 4).astype(np.int64)
+
+
+def solve_dag_schedule(nt, p_blocks, trans):
+    """A triangular solve's task order: int array (tasks, 4) of op, i, j, p
+    (host only)."""
+    lib = load()
+    cnt = C.c_int64()
+    st = lib.mp_solve_dag_schedule(nt, p_blocks, trans, None, 0, C.byref(cnt))
+    if st != MP_OK:
+        raise MPError(st, "mp_solve_dag_schedule")
+    out = np.empty(cnt.value, dtype=np.uint64)
+    st = lib.mp_solve_dag_schedule(nt, p_blocks, trans, out.ctypes.data_as(C.c_void_p), cnt.value,
+                                   C.byref(cnt))
+    if st != MP_OK:
+        raise MPError(st, "mp_solve_dag_schedule")
+    w = out.astype(np.uint64)
+    return np.stack([(w >> np.uint64(24)) & np.uint64(0xf), (w >> np.uint64(28)) & np.uint64(0xfff),
+                     (w >> np.uint64(40)) & np.uint64(0xfff), (w >> np.uint64(52)) & np.uint64(0xff)],
+                    axis=1).astype(np.int64)
 
 
 def map_bound(n, b, sorted_locs, cov, band, near, far, eps):

@@ -102,3 +102,63 @@ def test_schedule_rejects_bad_sizes():
     for nb in (0, 65, -3):
         with pytest.raises(mpchol.MPError):
             mpchol.potrf_dag_schedule(nb)
+
+
+def _replay_solve(tasks, nt, P, trans):
+    """The solve graph's rules: block p of in_i counts the updates applied to
+    it in place (they must come in solve order of the columns j); the
+    product with the row solved just before i goes to a chain vector
+    instead (op 2) and waits only for out_j; D(i, p) waits for all
+    in-place updates and chain products of the blocks of in_i it reads
+    (p' <= p forward, p' >= p backward); an update with out_j waits for all
+    P blocks of out_j."""
+    order = {(nt - 1 - st if trans else st): st for st in range(nt)}
+    cnt = np.zeros((nt, P), dtype=np.int64)
+    chain = np.zeros((nt, P), dtype=np.int64)
+    done = np.zeros(nt, dtype=np.int64)
+    seen = set()
+    for t in map(tuple, tasks):
+        op, i, j, p = t
+        assert t not in seen, f"task {t} listed twice"
+        seen.add(t)
+        if op == 0:
+            blocks = range(p, P) if trans else range(p + 1)
+            if order[i] >= 1:
+                assert all(cnt[i, q] == order[i] - 1 and chain[i, q] == 1 for q in blocks), \
+                    f"task {t} before its row's updates"
+            done[i] += 1
+        else:
+            assert done[j] == P, f"task {t} before out_{j} is complete"
+            if op == 2:
+                assert order[j] == order[i] - 1, f"chain task {t} with a row other than the previous"
+                chain[i, p] += 1
+            else:
+                assert order[j] <= order[i] - 2, f"in-place task {t} with the previous row or later"
+                assert cnt[i, p] == order[j], f"task {t} out of column order"
+                cnt[i, p] += 1
+    assert np.all(done == P)
+    for i in range(nt):
+        assert np.all(cnt[i] == max(order[i] - 1, 0))
+        assert np.all(chain[i] == (1 if order[i] >= 1 else 0))
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+@pytest.mark.parametrize("nt,P", [(1, 4), (2, 16), (3, 4), (7, 16), (32, 16), (64, 32)])
+def test_solve_order_is_topological_and_complete(nt, P, trans):
+    from paper_2406_02701_gb300 import mpchol
+    tasks = mpchol.solve_dag_schedule(nt, P, trans)
+    assert len(tasks) == nt * P + nt * (nt - 1) // 2 * P
+    assert np.sum(tasks[:, 0] == 2) == (nt - 1) * P
+    _replay_solve(tasks, nt, P, trans)
+
+
+def test_solve_order_hands_out_the_chain_first():
+    """The chain products of row s+1 and its diagonal blocks come together,
+    ahead of the in-place updates with out_s."""
+    from paper_2406_02701_gb300 import mpchol
+    nt, P = 8, 4
+    tasks = [tuple(t) for t in mpchol.solve_dag_schedule(nt, P, 0)]
+    pos = {t: i for i, t in enumerate(tasks)}
+    for s in range(nt - 2):
+        assert pos[(0, s + 1, 0, 0)] == pos[(2, s + 1, s, P - 1)] + 1
+        assert pos[(0, s + 1, 0, P - 1)] < pos[(1, s + 2, s, 0)]
