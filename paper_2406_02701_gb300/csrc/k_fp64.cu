@@ -43,29 +43,94 @@ struct DagShape {
 };
 
 // Block (k, k) in S: Cholesky factor in place (lower part) and the block's
-// inverse Y = L^{-1} in R, in one right-looking sweep run as a two-stage
-// pipeline.  In iteration c column c of L is final; warp 0 then finishes
-// column c + 1 (its update with column c, the pivot d, 1/sqrt(d), the
-// scaling), so the sequential chain per column is one FMA and one rsqrt,
-// while warps 1-3 and 5-7 apply column c to the columns beyond c + 1 and
-// advance the inverse: Y[c-1, .] = R[c-1, .] / L_{c-1,c-1}, then
-// R[r, .] -= L_{r,c-1} Y[c-1, .] for the rows below.  Warp 4 shares warp
-// 0's scheduler; with its FP64 instructions off that scheduler the sweep
-// took 1024 instead of 1072 cycles per column (measured), so it sits the
-// sweep out.  Writes L and the inverse to global memory; info gets the
-// first pivot that is not > 0.
+// inverse Y = L^{-1} in R, in one right-looking sweep over column pairs run
+// as a two-stage pipeline.  In iteration p columns 2p and 2p + 1 of L are
+// final; warp 0 then finishes the next pair (dag_pair): it applies columns
+// 2p and 2p + 1 to columns n = 2p + 2 and n + 1 and takes both pivots from
+// one rsqrt, because the second pivot is a ratio of leading minors,
+// d_{n+1} = delta / a with a = A_nn, delta = A_nn A_{n+1,n+1} - A_{n+1,n}^2
+// (the updated entries): so the sequential chain per pair of columns is
+// two FMAs, the minor, one rsqrt and two multiplications, where a column
+// at a time took one FMA, one rsqrt and one multiplication per column.
+// Meanwhile warps 1-3 and 5-7 apply columns 2p and 2p + 1 to the columns
+// beyond 2p + 3 and advance the inverse by the pair before:
+// Y[c, .] = R[c, .] / L_cc, Y[c+1, .] = (R[c+1, .] - L_{c+1,c} Y[c, .]) /
+// L_{c+1,c+1} (c = 2p - 2), then R[r, .] -= L_rc Y[c, .] + L_{r,c+1}
+// Y[c+1, .] for the rows below.  Warp 4 shares warp 0's scheduler and sits
+// the sweep out (the FP64 pipe issues one warp instruction per 64 cycles
+// per scheduler, so any FP64 instruction there lengthens the chain).
+// Writes L and the inverse to global memory; info gets the first pivot
+// that is not > 0.
 
-// Largest number of elements one column of the sweep updates: the trailing
-// triangle rows c+2.. on columns c+2..r and the inverse rows c.. on columns < c.
+// Largest number of elements one pair of the sweep updates: the trailing
+// triangle rows 2p+4.. on columns 2p+4..r and the inverse rows 2p.. on
+// columns < 2p.
 template <int DB>
 __host__ __device__ constexpr int sweep_work_max() {
   int mx = 0;
-  for (int c = 0; c < DB; ++c) {
-    const int m = DB - 2 - c;
-    const int t = (m > 0 ? m * (m + 1) / 2 : 0) + (c >= 1 ? (DB - c) * c : 0);
+  for (int p = 0; p < DB / 2; ++p) {
+    const int m = DB - 4 - 2 * p;
+    const int t = (m > 0 ? m * (m + 1) / 2 : 0) + (p >= 1 ? (DB - 2 * p) * 2 * p : 0);
     mx = t > mx ? t : mx;
   }
   return mx;
+}
+
+// Warp 0: columns n and n + 1 (n even) of the block factor.  Their entries
+// in S carry the updates of the columns before n - 2; with PREV the final
+// columns n - 2 and n - 1 are applied here.  Lanes 0-15 take column n,
+// lanes 16-31 column n + 1, one row per lane and 16-row slot.  With v the
+// updated column n, v' the updated column n + 1, a = v_n, beta = v_{n+1},
+// delta = a v'_{n+1} - beta^2:
+//   L_in      = v_i rsqrt(a)
+//   L_{i,n+1} = (a v'_i - beta v_i) rsqrt(a) rsqrt(delta)
+// (L_{n+1,n+1} = delta rsqrt(a) rsqrt(delta) = sqrt(delta / a)); lanes 0 and
+// 1 form rsqrt(a) and rsqrt(delta) in the same instructions.  rps gets
+// 1 / L_nn = rsqrt(a) and rsqrt(a) rsqrt(delta), pa gets a: 1 / L_{n+1,n+1}
+// = a rsqrt(a) rsqrt(delta) is formed by the inverse's update, off the chain.
+// A pivot that is not > 0 leaves L_nn or L_{n+1,n+1} NaN (rsqrt of a
+// negative number, or 0 * inf), and every later pivot with it.
+template <int DB, bool PREV>
+__device__ __forceinline__ void dag_pair(double (*S)[DB + 1], int n, double* rps, double* pa) {
+  constexpr int NS = DB / 16;                  // 16-row slots per lane
+  const int lane = threadIdx.x & 31, hi = lane >> 4, col = n + hi;
+  double g0 = 0.0, g1 = 0.0;
+  if (PREV) { g0 = S[col][n - 2]; g1 = S[col][n - 1]; }
+  double v[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int i = (lane & 15) + 16 * s;
+    double x = 0.0;
+    if (16 * s + 16 > n) {                     // uniform: the slot reaches row n
+      x = S[i][col];
+      if (PREV) x = fma(-S[i][n - 1], g1, fma(-S[i][n - 2], g0, x));
+    }
+    v[s] = x;
+  }
+  const int r0 = n & 15;                       // rows n and n + 1 share a slot
+  const double vs = (NS == 1 || n < 16) ? v[0] : v[NS - 1];
+  const double a = __shfl_sync(0xffffffffu, vs, r0);
+  const double beta = __shfl_sync(0xffffffffu, vs, r0 + 1);
+  const double gam = __shfl_sync(0xffffffffu, vs, r0 + 17);
+  const double delta = fma(a, gam, -(beta * beta));
+  const double y = rsqrt((lane & 1) ? delta : a);
+  const double rp = __shfl_sync(0xffffffffu, y, 0);
+  const double rq = __shfl_sync(0xffffffffu, y, 1);
+  const double m = rp * rq;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (16 * s + 16 <= n) continue;            // uniform
+    const int i = (lane & 15) + 16 * s;
+    const double u = __shfl_xor_sync(0xffffffffu, v[s], 16);   // the other column, row i
+    const double w = fma(a, v[s], -(beta * u));
+    const double out = (hi ? w : v[s]) * (hi ? m : rp);
+    if (i >= col) S[i][col] = out;
+  }
+  if (lane == 0) {
+    rps[n] = rp;
+    rps[n + 1] = m;
+    pa[n + 1] = a;
+  }
 }
 
 // The sweep's warps synchronise among themselves (named barrier 2, 224
@@ -73,81 +138,82 @@ __host__ __device__ constexpr int sweep_work_max() {
 template <int DB>
 __device__ void dag_factor(double (*S)[DB + 1], double (*R)[DB + 1], double* Tk, int b,
                            double* dinv, long long* info, long long row0, const uint16_t* tri) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   constexpr int NO = 192;                        // threads of warps 1-3 and 5-7
-  __shared__ double rps[DB];                     // 1 / L_cc
+  constexpr int NP = DB / 2;                     // column pairs
+  __shared__ double rps[DB];                     // see dag_pair
+  __shared__ double pa[DB];
   for (int e = tid; e < DB * DB; e += blockDim.x) R[e / DB][e % DB] = (e / DB == e % DB) ? 1.0 : 0.0;
-  if (tid < 32) {
-    const double d = S[0][0];
-    const double rp = rsqrt(d);
-    if (lane == 0) { S[0][0] = d * rp; rps[0] = rp; }
-    else if (lane < DB) S[lane][0] *= rp;
-  }
+  if (tid < 32) dag_pair<DB, false>(S, 0, rps, pa);
   __syncthreads();
-  if (warp != 4) for (int c = 0; c < DB; ++c) {
-    if (c) asm volatile("bar.sync 2, 224;" ::: "memory");
+  if (warp != 4) for (int p = 0; p < NP; ++p) {
+    if (p) asm volatile("bar.sync 2, 224;" ::: "memory");
     if (tid < 32) {
-      if (c + 1 < DB) {
-        // every lane forms the pivot itself (broadcast reads, no shuffle on
-        // the chain); the pivot test is made once after the sweep
-        const int n = c + 1;
-        const double snc = S[n][c];
-        const double d = S[n][n] - snc * snc;
-        double v = d;
-        if (lane > n && lane < DB) v = S[lane][n] - S[lane][c] * snc;
-        const double rp = rsqrt(d);
-        // one multiplication scales the column and gives sqrt(d) = d / sqrt(d)
-        if (lane >= n && lane < DB) S[lane][n] = v * rp;
-        if (lane == 0) rps[n] = rp;
-      }
-    } else if (warp != 4) {
+      if (p + 1 < NP) dag_pair<DB, true>(S, 2 * p + 2, rps, pa);
+    } else {
       const int t = tid < 128 ? tid - 32 : tid - 64;
-      if (c >= 1 && t < c) R[c - 1][t] *= rps[c - 1];
+      const int c = 2 * p - 2;                   // the pair whose rows of Y finish here
+      if (p >= 1 && t < c + 2) {
+        const double y0 = R[c][t] * rps[c];
+        R[c][t] = y0;
+        R[c + 1][t] = (R[c + 1][t] - S[c + 1][c] * y0) * (pa[c + 1] * rps[c + 1]);
+      }
       asm volatile("bar.sync 1, %0;" ::"r"(NO));
       // compact enumeration (the FP64 pipe charges a warp instruction in
-      // full however many lanes it masks): trailing rows c+2.. on columns
-      // c+2..r through the triangle table, then inverse rows c.. on columns < c
-      const int m = DB - 2 - c;
+      // full however many lanes it masks): trailing rows 2p+4.. on columns
+      // 2p+4..r through the triangle table, then inverse rows 2p.. on
+      // columns < 2p
+      const int m = DB - 4 - 2 * p;
       const int ntri = m > 0 ? m * (m + 1) / 2 : 0;
-      const int total = ntri + (c >= 1 ? (DB - c) * c : 0);
-      const float rc = c >= 1 ? 1.f / (float)c : 0.f;
+      const int w2 = 2 * p;
+      const int total = ntri + (p >= 1 ? (DB - w2) * w2 : 0);
+      const float rc = p >= 1 ? 1.f / (float)w2 : 0.f;
       // at most UPT elements per thread (total <= UPT * 192); the updates of
-      // one column touch distinct entries and read only columns c, c - 1 and
-      // row c - 1 of R, so all operands are loaded before any store
+      // one pair touch distinct entries and read only columns 2p - 2 .. 2p + 1
+      // and rows 2p - 2, 2p - 1 of R, so all operands are loaded before any store
       constexpr int UPT = DB == 32 ? 3 : 1;
       static_assert(sweep_work_max<DB>() <= UPT * NO, "sweep elements exceed the update threads");
       double* dst[UPT];
-      double x0[UPT], x1[UPT], x2[UPT];
+      double x0[UPT], x1[UPT], x2[UPT], x3[UPT], x4[UPT];
 #pragma unroll
       for (int u = 0; u < UPT; ++u) {
         const int e = t + u * NO;
         dst[u] = nullptr;
         if (e < ntri) {
           const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
-          const int r = c + 2 + rr, j = c + 2 + cc;
+          const int r = w2 + 4 + rr, j = w2 + 4 + cc;
           dst[u] = &S[r][j];
-          x1[u] = S[r][c];
-          x2[u] = S[j][c];
+          x1[u] = S[r][w2];
+          x2[u] = S[j][w2];
+          x3[u] = S[r][w2 + 1];
+          x4[u] = S[j][w2 + 1];
         } else if (e < total) {
           const int q = e - ntri;
-          const int qr = (int)(((float)q + 0.5f) * rc);   // q / c, exact for q < 2^12
-          const int r = c + qr, j = q - qr * c;
+          const int qr = (int)(((float)q + 0.5f) * rc);   // q / 2p, exact for q < 2^12
+          const int r = w2 + qr, j = q - qr * w2;
           dst[u] = &R[r][j];
-          x1[u] = S[r][c - 1];
-          x2[u] = R[c - 1][j];
+          x1[u] = S[r][w2 - 2];
+          x2[u] = R[w2 - 2][j];
+          x3[u] = S[r][w2 - 1];
+          x4[u] = R[w2 - 1][j];
         }
         if (dst[u]) x0[u] = *dst[u];
       }
 #pragma unroll
       for (int u = 0; u < UPT; ++u)
-        if (dst[u]) *dst[u] = x0[u] - x1[u] * x2[u];
+        if (dst[u]) *dst[u] = x0[u] - x1[u] * x2[u] - x3[u] * x4[u];
     }
   }
   __syncthreads();
-  if (tid < DB) R[DB - 1][tid] *= rps[DB - 1];
-  // a pivot d that is not > 0 leaves L_cc = d rsqrt(d) NaN (d < 0, NaN) or
-  // 0 * inf = NaN (d = 0): the first diagonal entry that is not > 0 is the
-  // first failed pivot
+  if (tid < DB) {
+    // rows DB - 2 and DB - 1 of Y (the last pair)
+    const int c = DB - 2;
+    const double y0 = R[c][tid] * rps[c];
+    R[c][tid] = y0;
+    R[c + 1][tid] = (R[c + 1][tid] - S[c + 1][c] * y0) * (pa[c + 1] * rps[c + 1]);
+  }
+  // a pivot d that is not > 0 leaves L_cc NaN (see dag_pair): the first
+  // diagonal entry that is not > 0 is the first failed pivot
   if (tid < DB && !(S[tid][tid] > 0.0)) atomicMin(info, row0 + tid + 1);
   __syncthreads();
   // the inverse first: it is what the tasks waiting on this block read
