@@ -397,11 +397,8 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         __syncthreads();
         chain_stamp(tr, 3);
         // published by the last thread, which has no share of the update
-        // below when DB = 16 (136 entries): the fence overlaps the update
-        if (tid == blockDim.x - 1) {
-          __threadfence();
-          st_release(&ver[k * nb + k - 1], k);
-        }
+        // below when DB = 16 (136 entries): the release overlaps the update
+        if (tid == blockDim.x - 1) st_release(&ver[k * nb + k - 1], k);
         // A_kk -= X X^T on the lower triangle (DB (DB + 1) / 2 entries, table order)
         for (int e = tid; e < DB * (DB + 1) / 2; e += blockDim.x) {
           const int rr = tri[e] >> 8, cc = tri[e] & 0xff;
@@ -511,7 +508,6 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
     __syncthreads();
     if (tid == 0) {
       chain_stamp(tr, 5);
-      __threadfence();
       if (tk.op == 4) st_release(&wv[c * nb + r], r - c + 1);
       else if (tk.op == 5) st_release(&wv[c * nb + r], k - c + 1);
       else {
@@ -536,10 +532,7 @@ __global__ void __launch_bounds__(256) k_potrf_dag(Arena A, const ItemPotrf* __r
         }
       }
       __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        st_release(&wv[k * nb + k], 1);
-      }
+      if (tid == 0) st_release(&wv[k * nb + k], 1);
       dag_logdet<DB>(S2, ldparts + it.ldslot + k);
       chain_stamp(tr, 7);
     }

@@ -527,8 +527,7 @@ __global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* 
     else solve_off<RCT>(A, it, i, j, p, trans, vs, part, op == 2);
     __syncthreads();
     if (tid == 0) {
-      __threadfence();
-      if (op == 0) atomicAdd(&cnt[i * CS + P], 1);
+      if (op == 0) red_release_add(&cnt[i * CS + P], 1);
       else if (op == 1) st_release(&cnt[i * CS + p], trans ? nt - j : j + 1);
       else st_release(&cnt[i * CS + P + 1 + p], 1);
     }

@@ -102,8 +102,14 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// A release at gpu scope is cumulative: after a __syncthreads(), one
+// thread's release store (or reduction) publishes the stores that every
+// thread of the block made before the barrier, with no separate fence.
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 // Waits until *ver >= need; false on timeout or when another CTA gave up.
 // Chain-trace stamp `point` (%globaltimer ns and clock64) into a block's
