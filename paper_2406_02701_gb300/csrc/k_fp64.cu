@@ -781,9 +781,14 @@ void launch_potrf_dag(const Arena& A, const ItemPotrf* items, int count, const D
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   const int64_t total = (int64_t)ntasks * count;
-  // one CTA per SM while few tiles share the launch (a CTA on the critical
-  // chain then has its SM's FP64 pipe to itself); two when many do
-  const int per_sm = count > 4 ? 2 : 1;
+  // two CTAs per SM: a block task spends about half its time in round trips
+  // (its counter polls, the loads of its blocks, the release, the next
+  // ticket), which the other CTA's arithmetic fills.  With one CTA per SM
+  // the blocks the critical chain reads arrived 5-15k cycles after the
+  // block before it was factored (the bulk tasks are handed out too slowly),
+  // with two they arrive before it: b = 512, n = 16384: 0.42 -> 0.32 ms per
+  // diagonal tile, 25.2 -> 24.3 ms per factorisation, measured
+  const int per_sm = 2;
   const int grid =
       (int)std::min<int64_t>(total, std::max<int64_t>(16, std::min<int64_t>(per_sm * sms, total / 8)));
   if (db == 16) k_potrf_dag<16><<<grid, 256, 0, s>>>(A, items, count, tasks, ntasks, ticket, ldparts, info);
