@@ -629,6 +629,7 @@ void build_chol_schedule(Plan& P, int64_t* panel_slots, int64_t* v_slots) {
         for (int d = 0; d < MAX_SHADOW; ++d) g.shadow[d] = rd.shadow[d];
         g.hi = rd.hi;
         g.lo = rd.lo;
+        g.s = ozaki_digits(P.h_tiles[it.tile].dt);
         ozg.push_back(g);
         if (e4) rest_round.push_back(rd);
       }

@@ -20,11 +20,15 @@
 //   X = sigma_r tau_c sum_{l < S} 2^(-6(l+2)) sum_{p+q=l} (D_p E_q^T)
 // which, with the digits' own remainders, leaves an error of at most
 // K (1 + (S + 3) / 3) 2^(-6S) sigma_r tau_c (about 8.5e-12 sigma_r tau_c
-// for K = 512).  The levels are added from the smallest to the largest in
-// float-float (pairs of FP32 numbers: about S^2 2^-48 relative error),
-// scaled by the power of two sigma_r tau_c, and written in float64.  Both
-// bounds sit far below the FP32/BF16 rounding the panel result then
-// receives.
+// for K = 512 and S = 8).  The levels are added from the smallest to the
+// largest in float-float (pairs of FP32 numbers: about S^2 2^-48 relative
+// error), scaled by the power of two sigma_r tau_c, and written in float64.
+// The splits hold S = 8 digits; a unit uses the first s of them (dropping a
+// digit only moves more of the operand into the dropped levels, so the bound
+// holds with s in place of S), s = ozaki_digits of the panel tile's format:
+// the smallest s whose bound at K = 1024 sits 2^11 below half a unit in the
+// last place of that format (FP32 8, BF16 and FP16 6, E4M3 5), so a 16-bit
+// tile takes 8 MMAs per K slice instead of 12 and an E4M3 tile 6.
 //
 // Data movement of the product (one work unit = 128 rows x 64 columns of
 // X; persistent CTAs walk the units): per K chunk of 64, the S digit chunks
@@ -254,12 +258,13 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(Arena A, const ItemOzW* _
 
 constexpr int OZ_ACH = 128 * 128;          // A digit chunk: 128 rows x 128 bytes
 
-// Order in which a K chunk's A digits are consumed: digit p pairs with the
-// S - p digits of W, so large and small amounts of MMA work alternate
-// (0, S-1, 1, S-2, ...) and the ring never waits on several short chunks in
-// a row.  Digit 0 comes first: it opens every level's accumulator.
-__device__ __forceinline__ int oz_digit_order(int pi) {
-  return (pi & 1) ? OZ_S_MAX_ORDER - 1 - (pi >> 1) : (pi >> 1);
+// Order in which a K chunk's A digits are consumed when a unit uses s
+// digits: digit p pairs with the s - p digits of W, so large and small
+// amounts of MMA work alternate (0, s-1, 1, s-2, ...) and the ring never
+// waits on several short chunks in a row.  Digit 0 comes first: it opens
+// every level's accumulator.
+__device__ __forceinline__ int oz_digit_order(int pi, int s) {
+  return (pi & 1) ? s - 1 - (pi >> 1) : (pi >> 1);
 }
 constexpr int OZ_ASTG = 3;                 // A ring slots
 constexpr int OZ_BSTG = 2;                 // W ring slots (S chunks each)
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(192, 1)
   static_assert(S * BN <= 512 && (S * BN) % 32 == 0, "levels exceed tensor memory");
   constexpr int BCH = BN * 128;            // W digit chunk: BN rows x 128 bytes
   constexpr uint32_t TCOLS = S * BN;       // tensor-memory columns (a power of two)
-  static_assert(S == OZ_S_MAX_ORDER, "digit order table is for S digits");
+  static_assert(S <= OZ_S_MAX_ORDER, "at most 8 digits per operand");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* bring = smem;                                   // OZ_BSTG x S x BCH
@@ -331,20 +336,21 @@ __global__ void __launch_bounds__(192, 1)
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const ItemOz& it = items[u / (nnb * nmb)];
         const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * BN;
+        const int su = it.s;                // digits this unit uses (<= S)
         int32_t aidx[S], widx[S];
 #pragma unroll
         for (int p = 0; p < S; ++p) { aidx[p] = A.tiles[it.a[p]].idx; widx[p] = A.tiles[it.w[p]].idx; }
         for (int kt = 0; kt < KT && ok; ++kt) {
           const int sb = nb % OZ_BSTG;
           if (nb >= OZ_BSTG && !(ok = mb_wait(&bempty[sb], ((nb / OZ_BSTG) - 1) & 1, A.err))) break;
-          mb_expect(&bfull[sb], S * BCH);
+          mb_expect(&bfull[sb], su * BCH);
 #pragma unroll
           for (int q = 0; q < S; ++q)
-            tma2d(bring + (sb * S + q) * BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
+            if (q < su) tma2d(bring + (sb * S + q) * BCH, &mapB, kt * 64, widx[q] * b + n0, &bfull[sb]);
           ++nb;
 #pragma unroll 1
-          for (int pi = 0; pi < S; ++pi) {
-            const int p = oz_digit_order(pi);
+          for (int pi = 0; pi < su; ++pi) {
+            const int p = oz_digit_order(pi, su);
             const int sa = na % OZ_ASTG;
             if (na >= OZ_ASTG && !(ok = mb_wait(&aempty[sa], ((na / OZ_ASTG) - 1) & 1, A.err))) break;
             mb_expect(&afull[sa], OZ_ACH);
@@ -369,13 +375,14 @@ __global__ void __launch_bounds__(192, 1)
         // the epilogue has read the previous unit's levels
         if (t >= 1 && !(ok = mb_wait(tfree, (t - 1) & 1, A.err))) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int su = items[u / (nnb * nmb)].s;
         for (int kt = 0; kt < KT && ok; ++kt) {
           const int sb = nb % OZ_BSTG;
           if (!(ok = mb_wait(&bfull[sb], (nb / OZ_BSTG) & 1, A.err))) break;
           const uint32_t b0 = su32(bring + sb * S * BCH);
 #pragma unroll 1
-          for (int pi = 0; pi < S; ++pi) {
-            const int p = oz_digit_order(pi);
+          for (int pi = 0; pi < su; ++pi) {
+            const int p = oz_digit_order(pi, su);
             const int sa = na % OZ_ASTG;
             if (!(ok = mb_wait(&afull[sa], (na / OZ_ASTG) & 1, A.err))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -389,8 +396,8 @@ __global__ void __launch_bounds__(192, 1)
             for (int kk = 0; kk < 4; ++kk) {
               const uint32_t acc = !(kt == 0 && p == 0 && kk == 0);   // level p+q first touched at p = 0
 #pragma unroll 1
-              for (int q0 = 0; q0 < S - p; q0 += 256 / BN) {
-                const int nq = min(256 / BN, S - p - q0);
+              for (int q0 = 0; q0 < su - p; q0 += 256 / BN) {
+                const int nq = min(256 / BN, su - p - q0);
                 mma_bf16(tmem + (uint32_t)(p + q0) * BN, sdesc(a0 + kk * 32),
                          sdesc(b0 + q0 * BCH + kk * 32), acc, oz_idesc(nq * BN));
               }
@@ -420,12 +427,12 @@ __global__ void __launch_bounds__(192, 1)
       const int m0 = ((u / nnb) % nmb) * 128, n0 = (u % nnb) * BN;
       if (!mb_wait(accf, t & 1, A.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // levels from the smallest (l = S-1) to the largest, in float-float
+      // levels from the smallest (l = s-1) to the largest, in float-float
       float hi[BN], lo[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
 #pragma unroll 1
-      for (int l = S - 1; l >= 0; --l) {
+      for (int l = it.s - 1; l >= 0; --l) {
         const float scl = ldexpf(1.f, -6 * (l + 2));
 #pragma unroll
         for (int h = 0; h < BN / 32; ++h) {

@@ -145,10 +145,20 @@ struct ItemOz {             // X = A W for one panel tile
   int32_t tile;             // (fuse) the panel tile
   int32_t shadow[MAX_SHADOW];
   int32_t hi, lo;
+  int32_t s;                // digits per operand used (ozaki_digits of the tile's format)
   const float* sigma;
   const float* tau;
   double* x;                // b x b float64 result (when not fused)
 };
+
+// Digits per operand of the integer-digit panel product for a panel tile
+// stored in format dt: the smallest S whose truncation bound
+// b (1 + (S + 3) / 3) 2^(-6S) sigma_r tau_c, at b = 1024, sits 2^11 below
+// half a unit in the last place of the format (FP32 8, BF16 and FP16 6,
+// E4M3 5).
+inline int ozaki_digits(int dt) {
+  return dt == F32 ? 8 : (dt == BF16 || dt == F16) ? 6 : dt == E4M3 ? 5 : 8;
+}
 
 // Rounds an E4M3 target from its FP32 scratch with the new scale.
 struct ItemFp8 {

@@ -67,6 +67,22 @@ def _pow2_above(x):
     return np.where(x > 0, np.ldexp(1.0, np.where(m == 0.5, e - 1, e)), 1.0)
 
 
+def _ozaki_digits(fmt):
+    """Digits per operand the integer-digit panel product uses for a tile of
+    format fmt: the smallest S whose truncation bound
+    1024 (1 + (S + 3) / 3) 2^(-6S) is at most 2^-11 of half a unit in the
+    last place (2^-p, p significand bits)."""
+    p = {I.F32: 24, I.BF16: 8, I.F16: 11, I.E4M3: 4}[fmt]
+    s = 1
+    while 1024 * (1 + (s + 3) / 3) * 2.0 ** (-6 * s) > 2.0 ** (-11 - p):
+        s += 1
+    return s
+
+
+def test_ozaki_digit_rule():
+    assert [_ozaki_digits(f) for f in (I.F32, I.BF16, I.F16, I.E4M3)] == [8, 6, 6, 5]
+
+
 def _ozaki_bound(a, lkk, x, digits=8):
     """Error bound of X = A W, W = L^{-T}, from 6-bit digit splits: digit
     remainders and dropped levels K (1 + (S + 3) / 3) 2^(-6S) sigma_r tau_c,
@@ -243,7 +259,8 @@ def _single_steps(ctx, n, b, far, mode, a):
                 extra = 1e-13 * np.abs(rt.values()).max()
                 frac = 2e-3
                 if ozaki:
-                    ob = _ozaki_bound(before[(i, k)].values(), state.tiles[(k, k)].codes, rt.values())
+                    ob = _ozaki_bound(before[(i, k)].values(), state.tiles[(k, k)].codes, rt.values(),
+                                      _ozaki_digits(fmt))
                     extra = extra + ob
                     # a rounding flips where the exact value lies within the
                     # error of a rounding boundary: at most 2 bound / ulp
