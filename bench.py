@@ -204,7 +204,7 @@ def measured_peaks():
 # dram__bytes_write.sum from one ncu capture of the kernel as it is now on
 # this workload (kernel -> bytes); absent where no capture of the current
 # kernel exists.
-TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_BYTES_PER_LAUNCH = {"k_potrf_dag": 1212672 + 7680}   # b = 512 diagonal tile
 
 
 # digits per operand of the integer-digit panel product by the panel tile's
@@ -1103,6 +1103,16 @@ def profile_case(name):
         T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(-(-n // 512), I.F64, I.F32, I.BF16, 2))
         for _ in range(2):
             T.generate(ds, 1.0, 0.05, nu, 1e-4)
+    elif kind == "chol":
+        # the factorisation of an n-point field, b = 512, FP64 diagonal and
+        # FP32 elsewhere (the diagonal tile's task graph is the same launch
+        # whatever n)
+        ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 11)).to(dev))
+        nt = -(-n // 512)
+        T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(nt, I.F64, I.F32, I.F32, 1))
+        for _ in range(2):
+            T.generate(ds, 1.0, 0.05, 1.5, 1e-4)
+            T.chol()
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
