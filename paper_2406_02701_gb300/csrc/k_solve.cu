@@ -179,6 +179,189 @@ __device__ __forceinline__ void ff_madd2(float& hi, float& lo, float xh, float x
   lo += err + e + cross;
 }
 
+// Four consecutive values (exact in FP32) of a tile stored in format DT,
+// from element i, a multiple of 4: one 16-, 8- or 4-byte load.
+template <int DT>
+__device__ __forceinline__ float4 tval4(const char* base, int64_t i) {
+  if (DT == F32) return __ldcg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(base) + i));
+  if (DT == BF16 || DT == F16) {
+    const uint2 u = __ldcg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(base) + i));
+    const uint32_t w[4] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16};
+    float f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      f[j] = DT == BF16 ? __uint_as_float(w[j] << 16) : __half2float(__ushort_as_half((unsigned short)w[j]));
+    return make_float4(f[0], f[1], f[2], f[3]);
+  }
+  const uint32_t u = __ldcg(reinterpret_cast<const unsigned int*>(reinterpret_cast<const uint8_t*>(base) + i));
+  float f[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_fp8_e4m3 v;
+    v.__x = (__nv_fp8_storage_t)((u >> (8 * j)) & 0xffu);
+    f[j] = (float)v;
+  }
+  return make_float4(f[0], f[1], f[2], f[3]);
+}
+
+__device__ __forceinline__ float f4(const float4& v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// The 32 columns of block p: thread (row group rg = tid / 8, column quad
+// cq = tid % 8) has the float-float sums of columns 32 p + 4 cq + j over its
+// rows; sums over the four row groups of a warp, then over the warps in
+// order, give column 32 p + lane to warp 0 (returned there, 0 elsewhere).
+__device__ __forceinline__ double ff_column_sums(const float* hi, const float* lo, double* part) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double s = (double)hi[j] + (double)lo[j];
+    s += __shfl_xor_sync(0xffffffffu, s, 8);
+    s += __shfl_xor_sync(0xffffffffu, s, 16);
+    if (lane < 8) part[warp * 32 + 4 * lane + j] = s;
+  }
+  __syncthreads();
+  double sum = 0.0;
+  if (warp == 0)
+    for (int w = 0; w < 8; ++w) sum += part[w * 32 + lane];
+  return sum;
+}
+
+// One right-hand side, off-diagonal block of a tile stored in FP32 or below,
+// with 16-byte loads: a thread keeps all of its share of the 32 x b block
+// (or b x 32 for the backward solve) in flight at once.  Items with one
+// right-hand side take this code in every launch (ys_stride: the staging's
+// right-hand sides per row), so a request's bits do not depend on the
+// other requests of its batch.
+constexpr int VB = 16;     // vector loads a thread issues before using them
+template <int DT>
+__device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans, const float2* ys,
+                              int ys_stride, double* part, double* r, bool store) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nk = b / 32;
+  if (!trans) {
+    // in_i[q] -= sum_t L_ij[q][t] y[t]: thread (row q = 32 p + tid / 8,
+    // sg = tid % 8), t = 4 sg + 32 k + j
+    const int q = p * 32 + (tid >> 3), sg = tid & 7;
+    const int64_t row = (int64_t)q * b + 4 * sg;
+    float hi = 0.f, lo = 0.f;
+    for (int k0 = 0; k0 < nk; k0 += VB) {
+      float4 a[VB];
+#pragma unroll
+      for (int u = 0; u < VB; ++u)
+        a[u] = k0 + u < nk ? tval4<DT>(L, row + 32 * (k0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < VB; ++u) {
+        if (k0 + u >= nk) break;                   // uniform
+        const int t = 4 * sg + 32 * (k0 + u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 h = ys[(t + j) * ys_stride];
+          ff_madd(hi, lo, f4(a[u], j) * scf, h.x, h.y);
+        }
+      }
+    }
+    double sum = (double)hi + (double)lo;
+    for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+    if (sg == 0) {
+      double* rp = r + q;
+      *rp = store ? sum : __ldcg(rp) - sum;
+    }
+  } else {
+    // in_i[q] -= sum_t L_ji[t][q] y[t], q = 32 p + 4 cq + j: thread (row
+    // group rg = tid / 8, cq = tid % 8) takes rows t = rg + 32 k
+    const int rg = tid >> 3, cq = tid & 7;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < nk; k0 += VB) {
+      float4 a[VB];
+#pragma unroll
+      for (int u = 0; u < VB; ++u)
+        a[u] = k0 + u < nk ? tval4<DT>(L, (int64_t)(rg + 32 * (k0 + u)) * b + p * 32 + 4 * cq)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < VB; ++u) {
+        if (k0 + u >= nk) break;
+        const float2 h = ys[(rg + 32 * (k0 + u)) * ys_stride];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_madd(hi[j], lo[j], f4(a[u], j) * scf, h.x, h.y);
+      }
+    }
+    const double sum = ff_column_sums(hi, lo, part);
+    if (warp == 0) {
+      double* rp = r + p * 32 + lane;
+      *rp = store ? sum : __ldcg(rp) - sum;
+    }
+  }
+}
+
+// One right-hand side, diagonal block p in float-float from W's FP32 hi/lo
+// parts, with 16-byte loads (vsf holds in_i - chain_i split as float pairs).
+// X = L_ii^{-T} is upper triangular: the products outside it are masked
+// (only the triangle is guaranteed to be written).
+constexpr int VBD = 8;     // vector loads of each of hi and lo in flight
+__device__ void solve_diag_ff1(const float* Xh, const float* Xl, int b, int p, int trans,
+                               const float2* vsf, int v_stride, double* part, double* o) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!trans) {
+    // out[r] = sum_{t <= r} X[t][r] v[t], r = 32 p + 4 cq + j: thread (row
+    // group rg = tid / 8, cq = tid % 8) takes rows t = rg + 32 k, k <= p
+    const int rg = tid >> 3, cq = tid & 7, r0 = p * 32 + 4 * cq;
+    const int nk = p + 1;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < nk; k0 += VBD) {
+      float4 xh[VBD], xl[VBD];
+#pragma unroll
+      for (int u = 0; u < VBD; ++u) {
+        const int64_t o4 = (int64_t)(rg + 32 * (k0 + u)) * b + r0;
+        const bool ok = k0 + u < nk;
+        xh[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xh + o4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xl[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xl + o4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < VBD; ++u) {
+        if (k0 + u >= nk) break;                   // uniform
+        const int t = rg + 32 * (k0 + u);
+        const float2 w = vsf[t * v_stride];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (t <= r0 + j) ff_madd2(hi[j], lo[j], f4(xh[u], j), f4(xl[u], j), w.x, w.y);
+      }
+    }
+    const double sum = ff_column_sums(hi, lo, part);
+    if (warp == 0) o[p * 32 + lane] = sum;
+  } else {
+    // out[r] = sum_{t >= r} X[r][t] v[t], r = 32 p + tid / 8: thread (r,
+    // sg = tid % 8) takes t = 32 p + 4 sg + 32 k + j
+    const int r = p * 32 + (tid >> 3), sg = tid & 7;
+    const int nk = (b - p * 32) / 32;
+    const int64_t row = (int64_t)r * b + p * 32 + 4 * sg;
+    float hi = 0.f, lo = 0.f;
+    for (int k0 = 0; k0 < nk; k0 += VBD) {
+      float4 xh[VBD], xl[VBD];
+#pragma unroll
+      for (int u = 0; u < VBD; ++u) {
+        const bool ok = k0 + u < nk;
+        xh[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xh + row + 32 * (k0 + u))) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xl[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xl + row + 32 * (k0 + u))) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < VBD; ++u) {
+        if (k0 + u >= nk) break;
+        const int t = p * 32 + 4 * sg + 32 * (k0 + u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 w = vsf[(t + j) * v_stride];
+          if (t + j >= r) ff_madd2(hi, lo, f4(xh[u], j), f4(xl[u], j), w.x, w.y);
+        }
+      }
+    }
+    double sum = (double)hi + (double)lo;
+    for (int o2 = 4; o2 > 0; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+    if (sg == 0) o[r] = sum;
+  }
+}
+
 // Diagonal block in float-float from W's FP32 hi/lo parts (mixed factors):
 // same data flow as solve_diag, the products on the FP32 pipe.
 template <int RCT>
@@ -202,6 +385,10 @@ __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int
       vsf[t * RCT + c] = make_float2(h, (float)(x - (double)h));
     }
     __syncthreads();
+    if (it.nrhs == 1) {   // one right-hand side: the same code whatever RCT
+      solve_diag_ff1(Xh, Xl, b, p, trans, vsf, RCT, part, o);
+      continue;
+    }
     float hi[RCT], lo[RCT];
 #pragma unroll
     for (int c = 0; c < RCT; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
@@ -428,10 +615,22 @@ __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, 
     __syncthreads();
     switch (ref.dt) {
       case F64: solve_off_f64<RCT>(reinterpret_cast<const double*>(L), it, b, p, trans, vs, part, r, c0, nc, store); break;
-      case F32: solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
-      case BF16: solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
-      case F16: solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
-      default: solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store); break;
+      case F32:
+        if (it.nrhs == 1) solve_off_ff1<F32>(L, scf, b, p, trans, ys, RCT, part, r, store);
+        else solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        break;
+      case BF16:
+        if (it.nrhs == 1) solve_off_ff1<BF16>(L, scf, b, p, trans, ys, RCT, part, r, store);
+        else solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        break;
+      case F16:
+        if (it.nrhs == 1) solve_off_ff1<F16>(L, scf, b, p, trans, ys, RCT, part, r, store);
+        else solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        break;
+      default:
+        if (it.nrhs == 1) solve_off_ff1<E4M3>(L, scf, b, p, trans, ys, RCT, part, r, store);
+        else solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        break;
     }
   }
 }
@@ -477,9 +676,9 @@ __device__ void solve_prefetch(const Arena& A, const ItemSolveDag& it, int op, i
 }
 
 template <int RCT>
-__global__ void __launch_bounds__(256) k_solve_dag(Arena A, const ItemSolveDag* __restrict__ items,
-                                                   const SolveTask* __restrict__ tasks, int ntasks,
-                                                   int* ticket, int trans, const int* gate) {
+__global__ void __launch_bounds__(256, RCT == 1 ? 2 : 1)
+    k_solve_dag(Arena A, const ItemSolveDag* __restrict__ items, const SolveTask* __restrict__ tasks,
+                int ntasks, int* ticket, int trans, const int* gate) {
   if (gated(gate)) return;
   extern __shared__ double sm[];
   double* vs = sm;                               // b x RCT (doubles or float pairs)
