@@ -230,16 +230,27 @@ __device__ __forceinline__ double ff_column_sums(const float* hi, const float* l
 
 // One right-hand side, off-diagonal block of a tile stored in FP32 or below,
 // with 16-byte loads: a thread keeps all of its share of the 32 x b block
-// (or b x 32 for the backward solve) in flight at once.  Items with one
-// right-hand side take this code in every launch (ys_stride: the staging's
-// right-hand sides per row), so a request's bits do not depend on the
-// other requests of its batch.
+// (or b x 32 for the backward solve) in flight at once, issued before the
+// vector it multiplies is staged.  Items with one right-hand side take this
+// code in every launch, so a request's bits do not depend on the other
+// requests of its batch.
 constexpr int VB = 16;     // vector loads a thread issues before using them
 template <int DT>
-__device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans, const float2* ys,
-                              int ys_stride, double* part, double* r, bool store) {
+__device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans, const double* y,
+                              float2* ys, double* part, double* r, bool store) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nk = b / 32;
+  // y (the solved block the task waits for) is staged as float pairs while
+  // the block's first loads are in flight
+  auto stage = [&]() {
+    for (int t = tid; t < b; t += blockDim.x) {
+      const double v = __ldcg(y + t);
+      const float h = (float)v;
+      ys[t] = make_float2(h, (float)(v - (double)h));
+    }
+    __syncthreads();
+  };
+  const int ys_stride = 1;
   if (!trans) {
     // in_i[q] -= sum_t L_ij[q][t] y[t]: thread (row q = 32 p + tid / 8,
     // sg = tid % 8), t = 4 sg + 32 k + j
@@ -251,6 +262,7 @@ __device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans,
 #pragma unroll
       for (int u = 0; u < VB; ++u)
         a[u] = k0 + u < nk ? tval4<DT>(L, row + 32 * (k0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k0 == 0) stage();
 #pragma unroll
       for (int u = 0; u < VB; ++u) {
         if (k0 + u >= nk) break;                   // uniform
@@ -279,6 +291,7 @@ __device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans,
       for (int u = 0; u < VB; ++u)
         a[u] = k0 + u < nk ? tval4<DT>(L, (int64_t)(rg + 32 * (k0 + u)) * b + p * 32 + 4 * cq)
                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k0 == 0) stage();
 #pragma unroll
       for (int u = 0; u < VB; ++u) {
         if (k0 + u >= nk) break;
@@ -296,13 +309,26 @@ __device__ void solve_off_ff1(const char* L, float scf, int b, int p, int trans,
 }
 
 // One right-hand side, diagonal block p in float-float from W's FP32 hi/lo
-// parts, with 16-byte loads (vsf holds in_i - chain_i split as float pairs).
+// parts, with 16-byte loads issued before in_i - chain_i is staged.
 // X = L_ii^{-T} is upper triangular: the products outside it are masked
 // (only the triangle is guaranteed to be written).
 constexpr int VBD = 8;     // vector loads of each of hi and lo in flight
 __device__ void solve_diag_ff1(const float* Xh, const float* Xl, int b, int p, int trans,
-                               const float2* vsf, int v_stride, double* part, double* o) {
+                               const double* v, const double* ch, float2* vsf, double* part,
+                               double* o) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // in_i - chain_i over the rows the block reads, staged as float pairs
+  // while the first loads of X are in flight
+  const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
+  auto stage = [&]() {
+    for (int t = t0 + tid; t < t1; t += blockDim.x) {
+      const double x = solve_in(v, ch, t);
+      const float h = (float)x;
+      vsf[t] = make_float2(h, (float)(x - (double)h));
+    }
+    __syncthreads();
+  };
+  const int v_stride = 1;
   if (!trans) {
     // out[r] = sum_{t <= r} X[t][r] v[t], r = 32 p + 4 cq + j: thread (row
     // group rg = tid / 8, cq = tid % 8) takes rows t = rg + 32 k, k <= p
@@ -318,6 +344,7 @@ __device__ void solve_diag_ff1(const float* Xh, const float* Xl, int b, int p, i
         xh[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xh + o4)) : make_float4(0.f, 0.f, 0.f, 0.f);
         xl[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xl + o4)) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      if (k0 == 0) stage();
 #pragma unroll
       for (int u = 0; u < VBD; ++u) {
         if (k0 + u >= nk) break;                   // uniform
@@ -345,6 +372,7 @@ __device__ void solve_diag_ff1(const float* Xh, const float* Xl, int b, int p, i
         xh[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xh + row + 32 * (k0 + u))) : make_float4(0.f, 0.f, 0.f, 0.f);
         xl[u] = ok ? __ldcg(reinterpret_cast<const float4*>(Xl + row + 32 * (k0 + u))) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      if (k0 == 0) stage();
 #pragma unroll
       for (int u = 0; u < VBD; ++u) {
         if (k0 + u >= nk) break;
@@ -374,6 +402,10 @@ __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int
   const double* ch = first ? nullptr : it.chain + (int64_t)i * b;
   double* o = it.out + (int64_t)i * b;
   float2* vsf = reinterpret_cast<float2*>(vs);
+  if (it.nrhs == 1) {   // one right-hand side: the same code whatever RCT
+    solve_diag_ff1(Xh, Xl, b, p, trans, v, ch, vsf, part, o);
+    return;
+  }
   const int t0 = trans ? p * 32 : 0, t1 = trans ? b : (p + 1) * 32;
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
     const int nc = min(RCT, it.nrhs - c0);
@@ -385,10 +417,6 @@ __device__ void solve_diag_ff(const Arena& A, const ItemSolveDag& it, int i, int
       vsf[t * RCT + c] = make_float2(h, (float)(x - (double)h));
     }
     __syncthreads();
-    if (it.nrhs == 1) {   // one right-hand side: the same code whatever RCT
-      solve_diag_ff1(Xh, Xl, b, p, trans, vsf, RCT, part, o);
-      continue;
-    }
     float hi[RCT], lo[RCT];
 #pragma unroll
     for (int c = 0; c < RCT; ++c) { hi[c] = 0.f; lo[c] = 0.f; }
@@ -599,6 +627,15 @@ __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, 
   const double* y = it.out + (int64_t)j * b;
   double* r = (store ? it.chain : it.in) + (int64_t)i * b;
   float2* ys = reinterpret_cast<float2*>(vs);
+  if (it.nrhs == 1 && !f64) {
+    switch (ref.dt) {
+      case F32: solve_off_ff1<F32>(L, scf, b, p, trans, y, ys, part, r, store); break;
+      case BF16: solve_off_ff1<BF16>(L, scf, b, p, trans, y, ys, part, r, store); break;
+      case F16: solve_off_ff1<F16>(L, scf, b, p, trans, y, ys, part, r, store); break;
+      default: solve_off_ff1<E4M3>(L, scf, b, p, trans, y, ys, part, r, store); break;
+    }
+    return;
+  }
   for (int c0 = 0; c0 < it.nrhs; c0 += RCT) {
     const int nc = min(RCT, it.nrhs - c0);
     __syncthreads();
@@ -616,20 +653,16 @@ __device__ void solve_off(const Arena& A, const ItemSolveDag& it, int i, int j, 
     switch (ref.dt) {
       case F64: solve_off_f64<RCT>(reinterpret_cast<const double*>(L), it, b, p, trans, vs, part, r, c0, nc, store); break;
       case F32:
-        if (it.nrhs == 1) solve_off_ff1<F32>(L, scf, b, p, trans, ys, RCT, part, r, store);
-        else solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        solve_off_ff<RCT, F32>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
         break;
       case BF16:
-        if (it.nrhs == 1) solve_off_ff1<BF16>(L, scf, b, p, trans, ys, RCT, part, r, store);
-        else solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        solve_off_ff<RCT, BF16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
         break;
       case F16:
-        if (it.nrhs == 1) solve_off_ff1<F16>(L, scf, b, p, trans, ys, RCT, part, r, store);
-        else solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        solve_off_ff<RCT, F16>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
         break;
       default:
-        if (it.nrhs == 1) solve_off_ff1<E4M3>(L, scf, b, p, trans, ys, RCT, part, r, store);
-        else solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
+        solve_off_ff<RCT, E4M3>(L, scf, it, b, p, trans, ys, part, r, c0, nc, store);
         break;
     }
   }
