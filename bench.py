@@ -1113,6 +1113,18 @@ def profile_case(name):
         for _ in range(2):
             T.generate(ds, 1.0, 0.05, 1.5, 1e-4)
             T.chol()
+    elif kind == "loglik":
+        # the same factorisation, then the log-likelihood of one right-hand
+        # side with FP64 refinement (forward and backward solve graphs,
+        # residuals)
+        ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 11)).to(dev))
+        nt = -(-n // 512)
+        T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(nt, I.F64, I.F32, I.F32, 1), keep_sigma=True)
+        T.generate(ds, 1.0, 0.05, 1.5, 1e-4)
+        T.chol()
+        zt = torch.from_numpy(np.ascontiguousarray(I.rhs(n, 1, 12).T)).to(dev)
+        for _ in range(2):
+            T.loglik(zt, refine_iters=10)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
