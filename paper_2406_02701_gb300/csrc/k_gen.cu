@@ -34,6 +34,13 @@ namespace {
 constexpr int GEN_TAB = 131;
 __constant__ double c_gen_tab[GEN_TAB];
 
+// The same for float-float evaluation (set by init_gen_tables): [0, 64)
+// 2^{j/64} rounded to float, [64, 128) the remainders rounded to float,
+// [128] ln2/64 rounded to float, [129] the remainder, [130] 64/ln2, [131]
+// 1/3 rounded to float, [132] the remainder.
+constexpr int GEN_FTAB = 133;
+__constant__ float c_gen_ftab[GEN_FTAB];
+
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
   uint32_t k = 0;
   for (int bit = 0; bit < 16; ++bit) k |= ((v >> bit) & 1u) << (2 * bit);
@@ -183,6 +190,109 @@ __device__ __forceinline__ double entry(const ItemGen& it, double inv_range, con
   return v;
 }
 
+// ---------------------------------------------------------- float-float
+//
+// Tiles stored in FP32 or a 16-bit format, in a matrix that keeps no
+// float64 copy of Sigma, only need the entry rounded into their format: it
+// is evaluated in float-float arithmetic (pairs h + l of floats, about 2^-44
+// relative) on the FP32 pipe, which GB300 runs at 64 times its FP64 rate.
+// Error-free transformations: two_sum (Knuth), two_prod (one FMA).
+struct ffl { float h, l; };
+
+__device__ __forceinline__ ffl ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ffl ff_fast(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ffl ff_two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ffl ff_add(ffl a, ffl b) {
+  const ffl s = ff_two_sum(a.h, b.h);
+  return ff_fast(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ ffl ff_mul(ffl a, ffl b) {
+  const ffl p = ff_two_prod(a.h, b.h);
+  return ff_fast(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ ffl ff_sqrt(ffl a) {   // a >= 0
+  if (!(a.h > 0.f)) return {0.f, 0.f};
+  const float y = __fsqrt_rn(a.h);
+  const ffl y2 = ff_two_prod(y, y);
+  const float d = ((a.h - y2.h) - y2.l) + a.l;
+  return ff_fast(y, d * __fdividef(0.5f, y));
+}
+
+// x = h + l with h the first 24 significant bits of x (truncated) and l the
+// remaining 29 converted to float (so h + l = x to 2^-48 relative), from
+// the bit pattern alone (no FP64 instruction).  ok is false outside
+// [2^-60, 2^60] in magnitude (x = 0 is fine).
+__device__ __forceinline__ ffl ff_split(double x, bool& ok) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 && (u << 1) == 0) return {0.f, 0.f};
+  if (e < 1023 - 60 || e > 1023 + 60) { ok = false; return {0.f, 0.f}; }
+  const unsigned sg = (unsigned)(u >> 63) << 31;
+  const float h = __uint_as_float(sg | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+  // low 29 bits times 2^(e - 1075), a normal float for e >= 1023 - 60
+  const float sc = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+  const float lo = (float)(unsigned)(u & 0x1fffffffu) * sc;
+  return {h, sg ? -lo : lo};
+}
+
+// e^{-x} for 0 <= x <= 80 in float-float, Tang's table-driven method as in
+// exp_neg: -x = (k / 64) ln2 + t with k = rint(-64 x / ln2), t from an exact
+// product k (ln2/64)_h (two_prod) and the float remainder of ln2/64 (|t| <=
+// ln2/64 with k from a float product); e^t = 1 + q with q = t + t^2/2 in
+// float-float and t^3/6 + t^4/24 + t^5/120 in float (below 2.2e-7, the
+// truncation below 3e-15); times 2^{j/64} as a float pair and 2^m
+// (k = 64 m + j).
+__device__ __forceinline__ ffl exp_neg_ff(ffl x, const float* ft) {
+  const float kf = rintf(-x.h * ft[130]);                 // k (<= 0)
+  const ffl p = ff_two_prod(kf, ft[128]);                 // k (ln2/64)_h exactly
+  ffl t = ff_two_sum(-x.h, -p.h);                         // -x - k ln2/64 = t
+  t = ff_two_sum(t.h, t.l + ((-x.l - p.l) - kf * ft[129]));
+  const ffl t2 = ff_two_prod(t.h, t.h);
+  const ffl half_t2 = {0.5f * t2.h, 0.5f * fmaf(2.f * t.h, t.l, t2.l)};
+  const float th = t.h;
+  const float c = th * th * th * fmaf(th, fmaf(th, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f);
+  ffl q = ff_add(t, half_t2);
+  q = ff_two_sum(q.h, q.l + c);
+  const int k = (int)kf;
+  const int m = k >> 6, j = k & 63;                       // k = 64 m + j, 0 <= j < 64
+  const ffl T = {ft[j], ft[64 + j]};
+  const ffl r = ff_add(T, ff_mul(T, q));                  // 2^{j/64} (1 + q)
+  const float sc = __uint_as_float((unsigned)(m + 127) << 23);   // 2^m, m >= -116
+  return {r.h * sc, r.l * sc};
+}
+
+// Matérn entry in float-float (nu in {1/2, 3/2, 5/2} by `kind` 0, 1, 2;
+// off-diagonal tiles): the same formula as `entry` -- x = r (1/range) with
+// r = sqrt(dx^2 + dy^2) -- from the float pairs (x_h, x_l, y_h, y_l) of the
+// two locations.  big: x > 80 (the caller takes the float64 entry).
+__device__ __forceinline__ ffl entry_ff(int kind, ffl inv_range, ffl s2, const float* ft, float4 pi,
+                                        float4 pj, bool& big) {
+  const ffl dx = ff_add({pi.x, pi.y}, {-pj.x, -pj.y});
+  const ffl dy = ff_add({pi.z, pi.w}, {-pj.z, -pj.w});
+  const ffl sq = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+  const ffl x = ff_mul(ff_sqrt(sq), inv_range);
+  big = !(x.h <= 80.f);
+  if (big) return {0.f, 0.f};
+  const ffl e = exp_neg_ff(x, ft);
+  ffl poly = s2;
+  if (kind == 1) {
+    poly = ff_mul(s2, ff_add(x, {1.f, 0.f}));
+  } else if (kind == 2) {
+    const ffl x2_3 = ff_mul(ff_mul(x, x), {ft[131], ft[132]});
+    poly = ff_mul(s2, ff_add(ff_add(x, {1.f, 0.f}), x2_3));
+  }
+  return ff_mul(poly, e);
+}
+
 constexpr int GEN_ROWS = 16;
 
 template <bool AMAX>
@@ -213,6 +323,46 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
   double mx = 0.0;
   double inv_s = 1.0;
   if (!AMAX && dt == E4M3) inv_s = 1.0 / e4m3_scale(amax_value(&A.amax[it.tile]));
+  // float-float evaluation: an off-diagonal tile stored in FP32 or a 16-bit
+  // format, closed-form nu, no float64 copy of Sigma, locations within
+  // [2^-60, 2^60] in magnitude (or zero); the CTA decides as a whole
+  bool ff = !AMAX && it.ti != it.tj && !it.sigma64 && !it.ktab && (dt == F32 || dt == BF16 || dt == F16);
+  if (ff) {
+    __shared__ float ftab[GEN_FTAB];
+    for (int e = threadIdx.x; e < GEN_FTAB; e += blockDim.x) ftab[e] = c_gen_ftab[e];
+    float4* cf = reinterpret_cast<float4*>(sloc + 2 * b + 2 * GEN_ROWS);   // b columns, then GEN_ROWS rows
+    bool ok = true;
+    const ffl inv = ff_split(inv_range, ok), s2 = ff_split(it.sigma2, ok);
+    for (int q = threadIdx.x; q < b + GEN_ROWS; q += blockDim.x) {
+      const double* pt = q < b ? cx + 2 * q : rx + 2 * (q - b);
+      const ffl px = ff_split(pt[0], ok), py = ff_split(pt[1], ok);
+      cf[q] = make_float4(px.h, px.l, py.h, py.l);
+    }
+    ff = __syncthreads_and(ok);
+    if (ff) {
+      const int kind = it.nu == 0.5 ? 0 : it.nu == 1.5 ? 1 : 2;
+      for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
+        const int r = e / b, c = e - r * b;
+        const int64_t gi = gi0 + r, gj = gj0 + c;
+        const int64_t off = (int64_t)(r0 + r) * b + c;
+        float f;
+        if (gi >= it.n || gj >= it.n) {
+          f = 0.f;                                 // identity padding (off the diagonal)
+        } else {
+          bool big;
+          const ffl v = entry_ff(kind, inv, s2, ftab, cf[b + r], cf[c], big);
+          if (big)                                 // x > 80: the float64 entry
+            f = (float)entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi, gj);
+          else
+            f = __fadd_rn(v.h, v.l);
+        }
+        if (dt == F32) reinterpret_cast<float*>(dst)[off] = f;
+        else store_round_f32(dst, dt, off, f);
+      }
+      if (blockIdx.y == 0 && threadIdx.x == 0) A.scale[it.tile] = 1.0;
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
     double v = entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r,
@@ -405,6 +555,18 @@ int init_gen_tables() {
   h[128] = head;
   h[129] = (double)(l - (long double)head);
   h[130] = (double)(64.0L / std::log(2.0L));
+  float f[GEN_FTAB];
+  for (int j = 0; j < 64; ++j) {
+    const long double v = std::exp2((long double)j / 64.0L);
+    f[j] = (float)v;
+    f[64 + j] = (float)(v - (long double)f[j]);
+  }
+  f[128] = (float)l;
+  f[129] = (float)(l - (long double)f[128]);
+  f[130] = (float)(64.0L / std::log(2.0L));
+  f[131] = (float)(1.0L / 3.0L);
+  f[132] = (float)(1.0L / 3.0L - (long double)f[131]);
+  if (cudaMemcpyToSymbol(c_gen_ftab, f, sizeof(f)) != cudaSuccess) return 1;
   return cudaMemcpyToSymbol(c_gen_tab, h, sizeof(h)) == cudaSuccess ? 0 : 1;
 }
 
@@ -448,7 +610,8 @@ void launch_gen_amax(const Arena& A, const ItemGen* items, int count, cudaStream
 void launch_generate(const Arena& A, const ItemGen* items, int count, cudaStream_t s) {
   if (count <= 0) return;
   dim3 grid(count, A.b / GEN_ROWS);
-  size_t smem = sizeof(double) * (2 * A.b + 2 * GEN_ROWS);
+  // the locations as doubles, then as float pairs (float-float tiles)
+  size_t smem = sizeof(double) * (2 * A.b + 2 * GEN_ROWS) + sizeof(float4) * (A.b + GEN_ROWS);
   k_generate<false><<<grid, 256, smem, s>>>(A, items);
 }
 

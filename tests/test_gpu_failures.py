@@ -56,8 +56,10 @@ def test_wait_that_runs_out_reports_timeout_and_context_recovers(ctx):
     info2, ld2, ll2 = evaluate()
     assert info2 == 0
     assert ld2 == ld0 and np.array_equal(ll2, ll0)
-    # the context serves other matrices as before
-    T2 = mpchol.TiledMatrix(ctx, n, b, pmap)
+    # the context serves other matrices as before (one of the same kind:
+    # without a float64 copy of Sigma the FP32/BF16 tiles are generated in
+    # float-float, which can round a value one unit apart)
+    T2 = mpchol.TiledMatrix(ctx, n, b, pmap, keep_sigma=True)
     T2.generate(dl, 1.0, 0.05, 0.5, 1e-4)
     info3, ld3 = T2.chol()
     torch.cuda.synchronize()

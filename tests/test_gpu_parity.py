@@ -171,6 +171,36 @@ def test_generation_matches_oracle_every_format(ctx, nu):
                 assert_close_fmt(got, want, fmt, frac=1e-3, what=f"tile {i},{j}")
 
 
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("a", [0.013, 0.05, 0.3])
+def test_float_float_generation(ctx, nu, a):
+    """Without a float64 copy of Sigma, tiles stored in FP32, BF16 or FP16
+    are evaluated in float-float on the FP32 pipe: every value within one
+    unit of the oracle's rounding, at most 1e-4 of them one unit apart; and
+    the same against the float64 evaluation the matrix with the copy uses.
+    Near-duplicate points and long distances (x up to 80) included."""
+    n, b = 900, 128
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 2)
+    pmap[nt - 1, 0] = I.F16
+    locs = I.points(n, 6)
+    locs[5] = locs[200] + 1e-9                   # near-duplicate pairs in FP32 tiles
+    locs[130] = locs[300] + np.array([3e-7, -2e-7])   # (1, 0) and (2, 1)
+    dl = torch.from_numpy(locs).to(DEV)
+    T = _mk(ctx, n, b, pmap)
+    T.generate(dl, 1.3, a, nu, 1e-4)
+    Ts = _mk(ctx, n, b, pmap, keep_sigma=True)
+    Ts.generate(dl, 1.3, a, nu, 1e-4)
+    torch.cuda.synchronize()
+    ref = OC.tiled_from_dense(OM.covariance(locs, nu, a, 1.3, 1e-4), b, pmap)
+    for i in range(nt):
+        for j in range(i):
+            fmt = int(pmap[i, j])
+            got = T.get_tile(i, j)[0]
+            assert_close_fmt(got, ref.tiles[(i, j)].values(), fmt, frac=1e-4, what=f"tile {i},{j}")
+            assert_close_fmt(got, Ts.get_tile(i, j)[0], fmt, frac=1e-4, what=f"paths {i},{j}")
+
+
 def test_tile_norms_and_guarded_map(ctx):
     n, b = 1500, 128
     nt = -(-n // b)
