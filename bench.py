@@ -223,14 +223,50 @@ def ozaki_executed_ratio(pmap):
     return float(np.mean(r)) if r else 72.0
 
 
-def kernel_rooflines(prof, chol_ms, peak64, b, oz_ratio=72.0):
+def tf32_sustained_tflops(seconds=1.0, n=8192):
+    """TF32 tensor-core rate measured in this run: cuBLAS FP32 GEMMs with
+    TF32 allowed, n^3, back to back for about `seconds` (the sustained rate
+    under the power cap, the denominator for a kernel timed inside a long
+    step); 2 n^3 flops per GEMM, CUDA events.  None if it cannot run."""
+    import torch
+    try:
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        a = torch.randn((n, n), device="cuda", dtype=torch.float32)
+        c = torch.empty_like(a)
+        for _ in range(3):
+            torch.matmul(a, a, out=c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps, t0 = 0, time.time()
+        e0.record()
+        while time.time() - t0 < seconds:
+            for _ in range(10):
+                torch.matmul(a, a, out=c)
+            reps += 10
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        torch.backends.cuda.matmul.allow_tf32 = old
+        ms = e0.elapsed_time(e1)
+        del a, c
+        return 2.0 * n ** 3 * reps / (ms * 1e-3) / 1e12
+    except Exception:
+        return None
+
+
+def kernel_rooflines(prof, chol_ms, peak64, b, oz_ratio=72.0, tf32=None):
     """Roofline of the hot kernels of one factorisation; the dominant one
     (largest share of the instrumented run) first."""
     peaks, which = measured_peaks()
     bf16 = peaks["bf16_tflops_sustained"]
-    # FP32-kind products are three TF32 MMAs; TF32 runs at the nominal
-    # TF32/BF16 dense ratio 1.1/2.25 of the BF16 rate
-    tf32x3 = bf16 * (1.1 / 2.25) / 3.0
+    # FP32-kind products are three TF32 MMAs: a third of the TF32 rate
+    # measured in this run, else the nominal TF32/BF16 dense ratio 1.1/2.25
+    # of the measured BF16 rate
+    if tf32:
+        tf32x3, tf32_src = tf32 / 3.0, "cuBLAS TF32 GEMM 8192^3 measured in this run (1 s loop) / 3"
+    else:
+        tf32x3, tf32_src = bf16 * (1.1 / 2.25) / 3.0, f"bf16_tflops_sustained {which} x 1.1/2.25 / 3"
     kinds = {
         "potrf_tile": ("k_potrf_dag", "alu", peak64,
                        "FP64 DFMA loop probe in this run (mp_probe_fp64_peak); achieved counts the "
@@ -238,8 +274,7 @@ def kernel_rooflines(prof, chol_ms, peak64, b, oz_ratio=72.0):
                        "the inverse W = L^-T it also forms)"),
         "panel_trsm_first": ("k_panel_trsm (chain)", "alu", peak64, "FP64 DFMA loop probe in this run"),
         "panel_trsm": ("k_panel_trsm (bulk)", "alu", peak64, "FP64 DFMA loop probe in this run"),
-        "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 products)", "tensor", tf32x3,
-                             f"bf16_tflops_sustained {which} x 1.1/2.25 / 3"),
+        "update_tc_3xtf32": ("k_update_tc_p (FP32 kind, 3 TF32 products)", "tensor", tf32x3, tf32_src),
         "update_tc_lowp": ("k_update_tc_p (BF16/FP16/E4M3 kinds)", "tensor", bf16,
                            f"bf16_tflops_sustained {which}"),
         "panel_ozaki_gemm": ("k_oz_gemm", "tensor", bf16,
@@ -911,7 +946,8 @@ def ours(args, cfg):
     # kernel breakdown (one instrumented factorisation, CUDA events on the stream)
     prof = T.profile()
     chol_ms = sum(v["ms"] for v in prof.values())
-    roofline = kernel_rooflines(prof, chol_ms, ctx.fp64_peak(), b, ozaki_executed_ratio(pmap))
+    roofline = kernel_rooflines(prof, chol_ms, ctx.fp64_peak(), b, ozaki_executed_ratio(pmap),
+                                tf32_sustained_tflops())
     breakdown = {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
                      "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["ms"] > 0 and v["flops"] > 0 else None}
                  for k, v in prof.items() if v["launches"]}
