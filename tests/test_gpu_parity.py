@@ -467,6 +467,29 @@ def test_not_spd_reports_first_bad_row(ctx, n, b, bad):
     assert oinfo == bad + 1
 
 
+@pytest.mark.parametrize("n,b,r", [(512, 128, 300), (512, 128, 301), (512, 128, 287),
+                                   (768, 384, 420), (768, 384, 421), (768, 384, 399)])
+def test_not_spd_coupled_pair_reports_first_bad_row(ctx, n, b, r):
+    """The diagonal block factor takes two columns per step, the second
+    pivot from the pair's leading 2 x 2 minor.  A coupled block [[1, 1.5],
+    [1.5, 1]] at rows (r, r+1) of an identity breaks down at row r+1: as
+    the second column of a pair (r even), as the first column of the next
+    pair after its update (r odd), and across a 32- or 16-block boundary
+    (r = 287 = 9 * 32 - 1, r = 399 = 384 + 16 - 1)."""
+    T = _mk(ctx, n, b, None)
+    A = np.eye(n)
+    A[r, r + 1] = A[r + 1, r] = 1.5
+    A[r + 60, r + 60] = -1.0      # a later failure must not mask the first
+    for i in range(n // b):
+        for j in range(i + 1):
+            T.set_tile(i, j, A[i * b:(i + 1) * b, j * b:(j + 1) * b])
+    info, _ = T.chol()
+    torch.cuda.synchronize()
+    _, oinfo = OC.potrf_textbook(A)
+    assert oinfo == r + 2
+    assert int(info.item()) == r + 2
+
+
 @pytest.mark.parametrize("dt", [I.F64, I.F32, I.BF16, I.F16, I.E4M3])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
 def test_gemm_per_precision(ctx, dt, ta, tb):
