@@ -1133,10 +1133,13 @@ def profile_case(name):
         Cm = torch.zeros((n, n), dtype=tdt, device=dev)
         for _ in range(2):
             ctx.gemm(dt, "T", "N", n, n, n, 1.0, X, n, X, n, 0.0, Cm, n)
-    elif kind.startswith("gen_nu"):
-        nu = float(kind[len("gen_nu"):])
+    elif kind.startswith("gen_nu") or kind.startswith("gen64_nu"):
+        # gen64: with the float64 copy of Sigma the log-likelihood refines
+        # against, as in the bench's step (every entry float64-accurate)
+        nu = float(kind[kind.index("nu") + 2:])
         ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 11)).to(dev))
-        T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(-(-n // 512), I.F64, I.F32, I.BF16, 2))
+        T = mpchol.TiledMatrix(ctx, n, 512, I.band_map(-(-n // 512), I.F64, I.F32, I.BF16, 2),
+                               keep_sigma=kind.startswith("gen64"))
         for _ in range(2):
             T.generate(ds, 1.0, 0.05, nu, 1e-4)
     elif kind == "chol":

@@ -8,14 +8,17 @@
 // Generation (the Matérn model of Sec. 6.2; half-integer nu by the closed
 // forms, any other nu in (0, 16] from a Chebyshev table of x^nu K_nu(x)
 // built on the host, see matern_nu_table): every entry of a lower tile is
-// computed in float64 from the two locations and rounded once into the
-// tile's format.  exp(-x) follows Tang's
-// table-driven method (fewer FP64 operations than the general exp; the
-// kernel is bound by the FP64 pipe).  E4M3 tiles first get
-// the tile's amax from a separate pass (`gen_amax`), then the power-of-two
-// scale.  Rows/columns beyond n are identity padding.  The coordinate
-// differences are written with explicit _rn intrinsics; the squared
-// distance, the polynomial and exp use fused multiply-adds on purpose.
+// computed to float64 accuracy from the two locations and rounded once into
+// the tile's format.  The coordinate differences and the squared distance
+// are float64 (explicit _rn intrinsics, one fused multiply-add); for the
+// closed forms the square root, e^{-x} and the polynomial then run in
+// 64-bit fixed point on the integer pipe (mp_fixed.cuh), since GB300's FP64
+// pipe is 1/64 of its FP32 rate; other nu, and the rare entries outside the
+// fixed-point path's range, take float64 with Tang's table-driven e^{-x}.
+// Off-diagonal FP32/16-bit tiles of a matrix without a float64 copy of Sigma
+// are evaluated in float-float instead (below).  E4M3 tiles first get the
+// tile's amax from a separate pass (`gen_amax`), then the power-of-two
+// scale.  Rows/columns beyond n are identity padding.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -23,6 +26,7 @@
 #include <vector>
 
 #include "mp_device.cuh"
+#include "mp_fixed.cuh"
 
 namespace mp {
 
@@ -40,6 +44,11 @@ __constant__ double c_gen_tab[GEN_TAB];
 // 1/3 rounded to float, [132] the remainder.
 constexpr int GEN_FTAB = 133;
 __constant__ float c_gen_ftab[GEN_FTAB];
+
+// 2^{-j/1024} 2^63 rounded, j in [0, 1024), for the fixed-point e^{-x}
+// (set by init_gen_tables; copied into shared memory by each CTA)
+constexpr int GEN_T2 = 1024;
+__device__ uint64_t g_gen_t2[GEN_T2];
 
 __device__ __forceinline__ uint32_t spread16(uint32_t v) {
   uint32_t k = 0;
@@ -162,9 +171,9 @@ __device__ __forceinline__ double knu_table(const double* __restrict__ tab, int 
 // within 1 ulp: r within 1.5 ulp); x is r times the rounded reciprocal of the range (GB300's FP64
 // pipe makes a division cost about ten FP64 operations): |dx| <= 3 ulp(x),
 // which exp(-x) carries as a relative error of at most 3 x 2^-53.
-__device__ __forceinline__ double entry(const ItemGen& it, double inv_range, const double* tab,
-                                        double xi, double yi, double xj, double yj, int64_t gi,
-                                        int64_t gj) {
+__device__ __forceinline__ double entry_f64(const ItemGen& it, double inv_range, const double* tab,
+                                            double xi, double yi, double xj, double yj, int64_t gi,
+                                            int64_t gj) {
   if (gi >= it.n || gj >= it.n) return gi == gj ? 1.0 : 0.0;
   double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
   const double s2 = fma(dx, dx, __dmul_rn(dy, dy));
@@ -188,6 +197,145 @@ __device__ __forceinline__ double entry(const ItemGen& it, double inv_range, con
   }
   if (gi == gj) v = __dadd_rn(v, it.nugget);
   return v;
+}
+
+constexpr int GEN_ROWS = 16;   // rows of a tile per CTA
+
+// Per-CTA constants of one item's entries.
+struct GenCtx {
+  const double* tab;     // Tang's tables (float64 evaluation)
+  const uint64_t* t2;    // 2^{-j/1024} (fixed-point evaluation)
+  double inv_range;
+  double sig2_nug;       // sigma^2 + nugget (the diagonal)
+  fx ir, sig2;           // 1/range (from a double-double, truncated to 64 bits), sigma^2
+  int kind;              // 0, 1, 2 for nu = 1/2, 3/2, 5/2 in fixed point; -1: float64 only
+};
+
+__device__ __forceinline__ GenCtx gen_ctx(const ItemGen& it, const double* tab, const uint64_t* t2) {
+  GenCtx g;
+  g.tab = tab;
+  g.t2 = t2;
+  g.inv_range = 1.0 / it.range;
+  g.sig2_nug = __dadd_rn(it.sigma2, it.nugget);
+  g.kind = -1;
+  g.ir = g.sig2 = fx{1ull << 63, 0};
+  const double ir = g.inv_range;
+  // closed-form nu, sigma^2 and 1/range well inside the normal range (each
+  // entry's exponent is checked again before it is rounded)
+  if (!it.ktab && (it.nu == 0.5 || it.nu == 1.5 || it.nu == 2.5) && it.sigma2 >= 0x1p-900 &&
+      it.sigma2 <= 0x1p900 && ir >= 0x1p-900 && ir <= 0x1p900) {
+    g.kind = it.nu == 0.5 ? 0 : it.nu == 1.5 ? 1 : 2;
+    g.sig2 = fx_of(it.sigma2);
+    // 1/range = ir + lo with lo = ir (1 - range ir), the residual exact
+    const double lo = fma(-it.range, ir, 1.0) * ir;
+    const fx f = fx_of(ir);
+    uint64_t m = f.m + (uint64_t)(int64_t)rint(ldexp(lo, 63 - f.e));
+    int e = f.e;
+    if (m < (1ull << 63)) {   // ir a power of two just above 1/range
+      m <<= 1;
+      e -= 1;
+    }
+    g.ir = fx{m, e};
+  }
+  return g;
+}
+
+// The Matérn entry: in fixed point (mp_fixed.cuh) for the closed forms,
+// from the float64 squared distance; the float64 evaluation for other nu,
+// subnormal or huge distances, x > 700 and results outside the normal range.
+// Within 0.56 ulp of the exact value for x up to 100 (against long double
+// over 10^7 random pairs, with the float seeds perturbed by 2^-21).
+__device__ __forceinline__ double entry(const ItemGen& it, const GenCtx& g, double xi, double yi,
+                                        double xj, double yj, int64_t gi, int64_t gj) {
+  if (gi >= it.n || gj >= it.n) return gi == gj ? 1.0 : 0.0;
+  if (g.kind >= 0) {
+    const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
+    const double s2 = fma(dx, dx, __dmul_rn(dy, dy));
+    const uint64_t sb = mpx_bits(s2);
+    if (sb == 0) return gi == gj ? g.sig2_nug : it.sigma2;
+    const uint32_t be = (uint32_t)(sb >> 52);
+    if (be != 0 && be < 0x7ff) {
+      const fx s = fx_of(s2);
+      float fm;
+      const int odd = fx_sqrt_prep(s, fm);
+      const float r0 = fm * rsqrtf(fm);
+      float y;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r0));
+      const fx x = fx_mul(fx_sqrt_finish(s, odd, r0, y), g.ir);
+      if (x.e < 9 || (x.e == 9 && x.m <= (700ull << 54))) {
+        fx p = g.sig2;
+        if (g.kind == 1) {
+          p = fx_mul(p, fx_one_plus(x));
+        } else if (g.kind == 2) {
+          const fx third{12297829382473034411ull, -2};   // 1/3
+          p = fx_mul(p, fx_add(fx_one_plus(x), fx_mul(fx_mul(x, x), third)));
+        }
+        // (s^2 > 0: two points apart, never the diagonal's nugget)
+        const fx v = fx_mul(p, fx_exp_neg(x, g.t2));
+        if (v.e >= -1022 && v.e <= 1022) return fx_to_double(v);
+      }
+    }
+  }
+  return entry_f64(it, g.inv_range, g.tab, xi, yi, xj, yj, gi, gj);
+}
+
+// Values outside FP32's normal range (zero, tiny or huge): the conversion
+// instructions, out of line so that they stay a branch.
+__device__ __noinline__ void store_cvt(char* base, int dt, int64_t i, double v) {
+  if (dt == F32) reinterpret_cast<float*>(base)[i] = __double2float_rn(v);
+  else reinterpret_cast<__nv_bfloat16*>(base)[i] = __double2bfloat16(v);
+}
+
+// v rounded to nearest into format DT (E4M3: v times the tile's 1/scale),
+// stored at element i.  FP32 and BF16 round the double's bits with integer
+// operations (one rounding to nearest even, as cvt.rn does) when v lies in
+// their normal range, since the conversion instructions from float64 take
+// the FP64 pipe.
+template <int DT>
+__device__ __forceinline__ void store_fmt(char* base, int64_t i, double v, double inv_s) {
+  if (DT == F64) {
+    reinterpret_cast<double*>(base)[i] = v;
+  } else if (DT == F32 || DT == BF16) {
+    const uint64_t bv = mpx_bits(v);
+    const uint64_t mag = bv & 0x7FFFFFFFFFFFFFFFull;
+    const uint32_t ed = (uint32_t)(mag >> 52);
+    const int drop = DT == F32 ? 29 : 45;         // fraction bits dropped
+    if (ed >= 897 && ed <= 1150) {                // 2^-126 <= |v| < 2^128
+      const uint64_t r = (mag + ((1ull << (drop - 1)) - 1) + ((mag >> drop) & 1)) >> drop;
+      const uint32_t sgn = (uint32_t)(bv >> 63);
+      if (DT == F32)
+        reinterpret_cast<uint32_t*>(base)[i] = (uint32_t)(r - (896ull << 23)) | (sgn << 31);
+      else
+        reinterpret_cast<uint16_t*>(base)[i] = (uint16_t)((uint32_t)(r - (896ull << 7)) | (sgn << 15));
+    } else {
+      store_cvt(base, DT, i, v);
+    }
+  } else if (DT == F16) {
+    reinterpret_cast<__half*>(base)[i] = __double2half(v);
+  } else {
+    reinterpret_cast<__nv_fp8_storage_t*>(base)[i] =
+        __nv_cvt_double_to_fp8(v * inv_s, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// GEN_ROWS rows of one tile: entries, their rounding into the tile's format
+// and the float64 copy
+template <int DT>
+__device__ __forceinline__ void gen_rows(const ItemGen& it, const GenCtx& g, char* dst, double inv_s,
+                                         const double* rx, const double* cx, int b, int r0,
+                                         int64_t gi0, int64_t gj0) {
+  int r = (int)threadIdx.x / b, c = (int)threadIdx.x - r * b;
+  while (r < GEN_ROWS) {
+    const double v = entry(it, g, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
+    const int64_t off = (int64_t)(r0 + r) * b + c;
+    store_fmt<DT>(dst, off, v, inv_s);
+    if (it.sigma64) it.sigma64[off] = v;
+    c += blockDim.x;
+    while (c >= b) {
+      c -= b;
+      ++r;
+    }
+  }
 }
 
 // ---------------------------------------------------------- float-float
@@ -293,13 +441,14 @@ __device__ __forceinline__ ffl entry_ff(int kind, ffl inv_range, ffl s2, const f
   return ff_mul(poly, e);
 }
 
-constexpr int GEN_ROWS = 16;
 
 template <bool AMAX>
 __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __restrict__ items) {
   extern __shared__ double sloc[];           // b column points (x, y) + GEN_ROWS row points
   __shared__ double tab[GEN_TAB];
+  __shared__ uint64_t t2[GEN_T2];
   for (int e = threadIdx.x; e < GEN_TAB; e += blockDim.x) tab[e] = c_gen_tab[e];
+  for (int e = threadIdx.x; e < GEN_T2; e += blockDim.x) t2[e] = g_gen_t2[e];
   const ItemGen it = items[blockIdx.x];
   const int b = A.b;
   const int r0 = blockIdx.y * GEN_ROWS;
@@ -319,7 +468,8 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
   __syncthreads();
   const int dt = A.tiles[it.tile].dt;
   char* dst = tile_bytes(A, it.tile);
-  const double inv_range = 1.0 / it.range;
+  const GenCtx g = gen_ctx(it, tab, t2);
+  const double inv_range = g.inv_range;
   double mx = 0.0;
   double inv_s = 1.0;
   if (!AMAX && dt == E4M3) inv_s = 1.0 / e4m3_scale(amax_value(&A.amax[it.tile]));
@@ -352,7 +502,7 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
           bool big;
           const ffl v = entry_ff(kind, inv, s2, ftab, cf[b + r], cf[c], big);
           if (big)                                 // x > 80: the float64 entry
-            f = (float)entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi, gj);
+            f = (float)entry(it, g, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi, gj);
           else
             f = __fadd_rn(v.h, v.l);
         }
@@ -363,16 +513,18 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
       return;
     }
   }
-  for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
-    int r = e / b, c = e - r * b;
-    double v = entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r,
-                     gj0 + c);
-    int64_t off = (int64_t)(r0 + r) * b + c;
-    if (AMAX) {
-      mx = fmax(mx, fabs(v));
-    } else {
-      store_round(dst, dt, off, dt == E4M3 ? v * inv_s : v);
-      if (it.sigma64) it.sigma64[off] = v;
+  if (AMAX) {
+    for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
+      const int r = e / b, c = e - r * b;
+      mx = fmax(mx, fabs(entry(it, g, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c)));
+    }
+  } else {
+    switch (dt) {
+      case F64: gen_rows<F64>(it, g, dst, inv_s, rx, cx, b, r0, gi0, gj0); break;
+      case F32: gen_rows<F32>(it, g, dst, inv_s, rx, cx, b, r0, gi0, gj0); break;
+      case BF16: gen_rows<BF16>(it, g, dst, inv_s, rx, cx, b, r0, gi0, gj0); break;
+      case F16: gen_rows<F16>(it, g, dst, inv_s, rx, cx, b, r0, gi0, gj0); break;
+      default: gen_rows<E4M3>(it, g, dst, inv_s, rx, cx, b, r0, gi0, gj0);
     }
   }
   if (AMAX) {
@@ -395,7 +547,9 @@ __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __rest
                                                     double* __restrict__ partial) {
   extern __shared__ double sloc[];
   __shared__ double tab[GEN_TAB];
+  __shared__ uint64_t t2[GEN_T2];
   for (int e = threadIdx.x; e < GEN_TAB; e += blockDim.x) tab[e] = c_gen_tab[e];
+  for (int e = threadIdx.x; e < GEN_T2; e += blockDim.x) t2[e] = g_gen_t2[e];
   const ItemGen it = items[blockIdx.x];
   const int r0 = blockIdx.y * GEN_ROWS;
   const int64_t gi0 = (int64_t)it.ti * b + r0, gj0 = (int64_t)it.tj * b;
@@ -412,12 +566,11 @@ __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __rest
     rx[2 * r + 1] = g < it.n ? it.locs[2 * g + 1] : 0.0;
   }
   __syncthreads();
-  const double inv_range = 1.0 / it.range;
+  const GenCtx g = gen_ctx(it, tab, t2);
   double ss = 0.0;
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
-    double v = entry(it, inv_range, tab, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r,
-                     gj0 + c);
+    double v = entry(it, g, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
     ss += v * v;
   }
   __shared__ double red[8];
@@ -567,6 +720,12 @@ int init_gen_tables() {
   f[131] = (float)(1.0L / 3.0L);
   f[132] = (float)(1.0L / 3.0L - (long double)f[131]);
   if (cudaMemcpyToSymbol(c_gen_ftab, f, sizeof(f)) != cudaSuccess) return 1;
+  // 2^{-j/1024} 2^63 to nearest: long double holds it within half a unit
+  // of 2^-63 (64 significant bits or more)
+  uint64_t t[GEN_T2];
+  for (int j = 0; j < GEN_T2; ++j)
+    t[j] = (uint64_t)std::floor(std::ldexp(std::exp2(-(long double)j / GEN_T2), 63) + 0.5L);
+  if (cudaMemcpyToSymbol(g_gen_t2, t, sizeof(t)) != cudaSuccess) return 1;
   return cudaMemcpyToSymbol(c_gen_tab, h, sizeof(h)) == cudaSuccess ? 0 : 1;
 }
 

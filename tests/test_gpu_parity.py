@@ -171,6 +171,66 @@ def test_generation_matches_oracle_every_format(ctx, nu):
                 assert_close_fmt(got, want, fmt, frac=1e-3, what=f"tile {i},{j}")
 
 
+def _exact_entry(p, q, s2d, nu, a, sigma2):
+    """sigma^2 P(x) e^{-x}, x = sqrt(s2d) / a, in 40-digit decimal arithmetic
+    from the float64 squared distance s2d (the closed forms of Sec. 6.2)."""
+    import decimal
+    with decimal.localcontext() as dc:
+        dc.prec = 40
+        x = decimal.Decimal(s2d).sqrt() / decimal.Decimal(a)
+        poly = {0.5: decimal.Decimal(1), 1.5: 1 + x, 2.5: 1 + x + x * x / 3}[nu]
+        return decimal.Decimal(sigma2) * poly * (-x).exp()
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("a", [0.013, 0.3])
+def test_float64_entries_within_0p6_ulp(ctx, nu, a):
+    """Float64 tile entries of the closed forms (evaluated in 64-bit fixed
+    point from the float64 squared distance s^2 = fma(dx, dx, dy dy)) lie
+    within 0.55 + x/128 units in the last place of the exact value of
+    sigma^2 P(x) e^{-x} at that s^2 -- the final rounding, a few units of
+    2^-63 from the products, and x's own error (at most 8 units of 2^-63
+    relative) carried x-fold by e^{-x}: 3000 sampled entries, s^2 rebuilt
+    exactly with rationals (the fma's one rounding), the rest in 40 digits.
+    Near-duplicate points and x up to about 240 included."""
+    from fractions import Fraction
+    n, b = 1000, 128
+    nt = -(-n // b)
+    pmap = np.full((nt, nt), I.F64, dtype=np.int32)
+    locs = I.points(n, 21)
+    locs[5] = locs[200] + 1e-9
+    locs[130] = locs[300] + np.array([3e-7, -2e-7])
+    sigma2, nugget = 1.3, 1e-4
+    T = _mk(ctx, n, b, pmap, keep_sigma=True)
+    T.generate(torch.from_numpy(locs).to(DEV), sigma2, a, nu, nugget)
+    torch.cuda.synchronize()
+    tiles = {}
+    rng = np.random.default_rng(5)
+    pairs = [(5, 200), (200, 5), (300, 130), (7, 7)]
+    while len(pairs) < 3000:
+        i, j = rng.integers(0, n, 2)
+        pairs.append((max(i, j), min(i, j)))
+    worst = 0.0
+    for i, j in pairs:
+        i, j = max(i, j), min(i, j)
+        key = (i // b, j // b)
+        if key not in tiles:
+            tiles[key] = T.get_tile(*key)[0]
+        got = tiles[key][i % b, j % b]
+        if i == j:
+            want = Fraction(sigma2) + Fraction(nugget)
+            assert got == float(want)
+            continue
+        dx, dy = locs[i, 0] - locs[j, 0], locs[i, 1] - locs[j, 1]
+        s2 = float(Fraction(dx) * Fraction(dx) + Fraction(dy * dy))   # fma: one rounding
+        ref = _exact_entry(i, j, s2, nu, a, sigma2)
+        e = math.frexp(float(ref))[1]
+        err = abs(Fraction(got) - Fraction(ref)) / Fraction(2) ** (e - 53)
+        x = math.sqrt(s2) / a
+        worst = max(worst, float(err) - x / 128)
+    assert worst <= 0.55, worst
+
+
 @pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
 @pytest.mark.parametrize("a", [0.013, 0.05, 0.3])
 def test_float_float_generation(ctx, nu, a):
