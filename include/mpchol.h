@@ -95,8 +95,9 @@ const char* mp_version(void);
  *   h_map   : NT*NT bytes, row-major, entry [i*NT + j] is the mp_dtype of
  *             tile (i, j); only the lower triangle i >= j is read; the
  *             diagonal must be MP_F64.  NULL means all MP_F64.
- *   flags   : MP_TMAT_KEEP_SIGMA keeps a float64 copy of the generated
- *             lower tiles for the FP64 refinement residual (needs
+ *   flags   : MP_TMAT_KEEP_SIGMA keeps a copy of the generated lower
+ *             tiles for the FP64 refinement residual, in 62-bit fixed
+ *             point under one power of two (see mp_loglik; needs
  *             8 * NT(NT+1)/2 * b^2 more bytes).  MP_TMAT_SIMT_UPDATES runs
  *             the lower-precision trailing updates on CUDA cores (FP32
  *             FMA) instead of the tcgen05 tensor cores (BF16/FP16/E4M3
@@ -213,11 +214,13 @@ mp_status mp_morton_order_noalloc(int64_t n, const double* d_locs_in, double* d_
 
 /* Fills every lower tile with the Matérn covariance of the locations
  * d_locs (n x 2 row-major float64; borrowed until the generation kernels
- * have run on the matrix's stream).  With MP_TMAT_KEEP_SIGMA the float64
- * values are also kept for the refinement residual.  Each entry is computed in float64 and
- * rounded once to its tile's format (RNE; E4M3 with satfinite and a
- * per-tile scale from the tile's amax).  Resets the factorisation state.
- * Asynchronous. */
+ * have run on the matrix's stream).  With MP_TMAT_KEEP_SIGMA the values
+ * are also kept, in fixed point, for the refinement residual.  Each entry
+ * is computed to float64 accuracy (the closed forms in 64-bit fixed point,
+ * within 0.55 + x/128 ulp of the exact value at the float64 squared
+ * distance) and rounded once to its tile's format (RNE; E4M3 with
+ * satfinite and a per-tile scale from the tile's amax).  Resets the
+ * factorisation state.  Asynchronous. */
 mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p);
 
 /* --------------------------------------------------------- factorisation */
@@ -329,8 +332,14 @@ mp_status mp_chol2inv(mp_tmat* t, double* d_out, int64_t ldo);
  * refine_iters = 0: quad = ||L^{-1} z||^2.
  * refine_iters > 0: FP64 iterative refinement of Sigma x = z (the paper's
  *   "double precision for refinement", Sec. 1): x0 = L^-T L^-1 z, then up to
- *   refine_iters times r = z - Sigma x with Sigma in float64 (the copy kept
- *   by MP_TMAT_KEEP_SIGMA; MP_ERR_STATE without it); a column stops when
+ *   refine_iters times r = z - Sigma x from the copy of Sigma kept by
+ *   MP_TMAT_KEEP_SIGMA (MP_ERR_STATE without it, or when a tile was set by
+ *   mp_tile_set after the last mp_generate_matern).  The copy holds each
+ *   entry as a 62-bit integer below 2^E, 2^E the power of two above
+ *   max(sigma^2 + nugget, 1) (within 2^(E-63) of the float64 entry); x is
+ *   scaled to 54-bit integers per b-long segment, so the products and each
+ *   tile's sums are exact, rounded to float64 once per tile and summed in
+ *   float64 over the tiles of a row; a column stops when
  *   ||r||_inf <= n 2^-53 (||Sigma||_inf ||x||_inf + ||z||_inf), otherwise
  *   x += L^-T L^-1 r; quad = z^T x.
  * Outputs (device, may be NULL except d_ll): d_ll[nrhs] loglik,

@@ -297,6 +297,10 @@ struct mp_tmat {
   size_t d_ktab_cap = 0;
   double ktab_nu = 0.0;
   int ktab_e0 = 0;
+  // exponent of the fixed-point copy of Sigma (device, set by the
+  // generation); whether the copy holds the matrix (no mp_tile_set since)
+  int32_t* d_sig_e = nullptr;
+  bool sig_valid = false;
   // loglik workspace + graph
   int ws_nrhs = 0;
   double *zp = nullptr, *x = nullptr, *r = nullptr, *w = nullptr, *d = nullptr;
@@ -323,6 +327,7 @@ struct mp_tmat {
     P.raw_free(d_gen);
     P.raw_free(d_sitems);
     P.raw_free(d_ktab);
+    P.raw_free(d_sig_e);
     if (pin_ev) { if (pin_used) cudaEventSynchronize(pin_ev); cudaEventDestroy(pin_ev); }
     pin_return(P.ctx, h_pin, h_pin_cap);
   }
@@ -1208,6 +1213,7 @@ static mp_status tile_xfer(mp_tmat* t, int32_t i, int32_t j, void* h, double* sc
     CK(P.ctx, cudaMemcpyAsync(P.d_scale + id, &s, sizeof(double), cudaMemcpyHostToDevice, P.stream));
     CK(P.ctx, cudaStreamSynchronize(P.stream));
     t->generated = true;
+    t->sig_valid = false;   // the refinement's copy of Sigma no longer matches
     P.factored = false;
   }
   return MP_OK;
@@ -1250,6 +1256,10 @@ static mp_status build_gen_items(mp_tmat* t) {
   Plan& P = t->P;
   const MatDesc& M = P.mats[0];
   std::vector<ItemGen> amax, all;
+  // the exponent of the fixed-point copy of Sigma: every entry (at most
+  // sigma^2 + nugget, and the identity padding) below 2^sig_e
+  int sig_e = 0;
+  std::frexp(std::max(t->cov.sigma2 + t->cov.nugget, 1.0), &sig_e);
   for (int i = 0; i < M.nt; ++i)
     for (int j = 0; j <= i; ++j) {
       ItemGen g{};
@@ -1263,14 +1273,16 @@ static mp_status build_gen_items(mp_tmat* t) {
       g.range = t->cov.range;
       g.nu = t->cov.nu;
       g.nugget = t->cov.nugget;
-      g.sigma64 = nullptr;
+      g.sigfix = nullptr;
       if (!matern_nu_closed(t->cov.nu)) {
         g.ktab = t->d_ktab;
         g.ke0 = t->ktab_e0;
       }
       if (P.keep_sigma) {
         const TileRef r = P.h_tiles[M.sig[i * M.nt + j]];
-        g.sigma64 = (double*)(P.pool[F64] + (size_t)r.idx * P.b * P.b * 8);
+        g.sigfix = (uint64_t*)(P.pool[F64] + (size_t)r.idx * P.b * P.b * 8);
+        g.sig_e = sig_e;
+        g.sig_e_out = t->d_sig_e;
       }
       if (P.h_tiles[g.tile].dt == E4M3) amax.push_back(g);
       all.push_back(g);
@@ -1343,6 +1355,10 @@ mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p) {
     t->ktab_nu = p.nu;
     t->gen_key.clear();          // the items carry the table's pointer and octave
   }
+  if (P.keep_sigma && !t->d_sig_e) {
+    CK(P.ctx, P.raw_alloc((void**)&t->d_sig_e, sizeof(int32_t)));
+    t->gen_key.clear();
+  }
   std::vector<char> key(sizeof(void*) + sizeof(mp_matern));
   memcpy(key.data(), &d_locs, sizeof(void*));
   memcpy(key.data() + sizeof(void*), &p, sizeof(mp_matern));
@@ -1358,6 +1374,7 @@ mp_status mp_generate_matern(mp_tmat* t, const double* d_locs, mp_matern p) {
   launch_gen_amax(A, (const ItemGen*)(t->d_gen + t->gen_off_amax), t->gen_n_amax, s);
   launch_generate(A, (const ItemGen*)(t->d_gen + t->gen_off_all), t->gen_n_all, s);
   t->generated = true;
+  t->sig_valid = P.keep_sigma;
   P.factored = false;
   return check_launch(P.ctx);
 }
@@ -1677,6 +1694,8 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
   if (refine_iters < 0 || refine_iters > 100) return fail(P.ctx, MP_ERR_ARG, "refine_iters in [0, 100]");
   if (refine_iters > 0 && !P.keep_sigma)
     return fail(P.ctx, MP_ERR_STATE, "refinement needs MP_TMAT_KEEP_SIGMA");
+  if (refine_iters > 0 && !t->sig_valid)
+    return fail(P.ctx, MP_ERR_STATE, "refinement needs Sigma from mp_generate_matern (tiles set since)");
   CK(P.ctx, cudaSetDevice(P.ctx->device));
   if (mp_status st = ensure_ws(t, nrhs)) return st;
   std::vector<char> key(sizeof(void*) * 4 + sizeof(int64_t) + 2 * sizeof(int32_t));
@@ -1702,6 +1721,7 @@ extern "C" mp_status mp_loglik(mp_tmat* t, const double* d_z, int64_t ldz, int32
         it.ti = i;
         it.tj = j;
         it.nt = M.nt;
+        it.sig_e = t->d_sig_e;
         it.x = t->x;
         it.part = t->rpart;
         it.pabs = t->rpabs;

@@ -318,8 +318,23 @@ __device__ __forceinline__ void store_fmt(char* base, int64_t i, double v, doubl
   }
 }
 
+// round(v 2^(62 - E)) for 0 <= v < 2^E: the refinement's fixed-point copy of
+// Sigma (entries far below 2^E keep their absolute accuracy, 2^(E - 63),
+// which is what a residual sum of them needs)
+__device__ __forceinline__ uint64_t sigma_fix(double v, int E) {
+  const uint64_t bv = mpx_bits(v);
+  const int be = (int)(bv >> 52);
+  if (be == 0) return 0ull;                      // zero or subnormal: below the resolution
+  const uint64_t mant = (bv & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = be - 1075 + 62 - E;             // v = mant 2^(be - 1075)
+  if (sh >= 0) return mant << sh;                // sh <= 9
+  const int d = -sh;
+  if (d > 54) return 0ull;
+  return (mant + (1ull << (d - 1)) - 1 + ((mant >> d) & 1)) >> d;   // to nearest even
+}
+
 // GEN_ROWS rows of one tile: entries, their rounding into the tile's format
-// and the float64 copy
+// and the fixed-point copy of Sigma
 template <int DT>
 __device__ __forceinline__ void gen_rows(const ItemGen& it, const GenCtx& g, char* dst, double inv_s,
                                          const double* rx, const double* cx, int b, int r0,
@@ -329,7 +344,7 @@ __device__ __forceinline__ void gen_rows(const ItemGen& it, const GenCtx& g, cha
     const double v = entry(it, g, rx[2 * r], rx[2 * r + 1], cx[2 * c], cx[2 * c + 1], gi0 + r, gj0 + c);
     const int64_t off = (int64_t)(r0 + r) * b + c;
     store_fmt<DT>(dst, off, v, inv_s);
-    if (it.sigma64) it.sigma64[off] = v;
+    if (it.sigfix) it.sigfix[off] = sigma_fix(v, it.sig_e);
     c += blockDim.x;
     while (c >= b) {
       c -= b;
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
   // float-float evaluation: an off-diagonal tile stored in FP32 or a 16-bit
   // format, closed-form nu, no float64 copy of Sigma, locations within
   // [2^-60, 2^60] in magnitude (or zero); the CTA decides as a whole
-  bool ff = !AMAX && it.ti != it.tj && !it.sigma64 && !it.ktab && (dt == F32 || dt == BF16 || dt == F16);
+  bool ff = !AMAX && it.ti != it.tj && !it.sigfix && !it.ktab && (dt == F32 || dt == BF16 || dt == F16);
   if (ff) {
     __shared__ float ftab[GEN_FTAB];
     for (int e = threadIdx.x; e < GEN_FTAB; e += blockDim.x) ftab[e] = c_gen_ftab[e];
@@ -538,6 +553,7 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
     }
   } else if (blockIdx.y == 0 && threadIdx.x == 0) {
     A.scale[it.tile] = dt == E4M3 ? e4m3_scale(amax_value(&A.amax[it.tile])) : 1.0;
+    if (it.sigfix && it.ti == 0 && it.tj == 0) *it.sig_e_out = it.sig_e;
   }
 }
 

@@ -766,141 +766,225 @@ __global__ void __launch_bounds__(256, RCT == 1 ? 2 : 1)
   }
 }
 
-// Residual pass 1: one CTA per lower tile of Sigma (float64).  The tile's
-// columns are split into G = max(1, b / 512) groups of at most 512; the
-// eight warps are spread over the groups and take rows round-robin.  For a
-// row, a lane loads its 16 (or fewer) entries (the next row's loads are
-// issued before the current row's arithmetic), adds their products with
-// x_j into the row's dot product (reduced across the warp) and their
-// products with x_i[row] into per-column accumulators (the transposed
-// product).  Column accumulators are combined across the warps of a group
-// in warp order; row dots across groups in group order.  Absolute sums
-// (first iteration only) use FP32: they only scale the stopping tolerance.
-constexpr int RES_NCOL = 16;
+// Residual pass 1: one CTA per lower tile of the fixed-point copy of Sigma:
+// entries M = Sigma 2^(62 - E) (unsigned, below 2^62), E set by the
+// matrix's generation (every entry, the identity padding included, is
+// below 2^E).  The CTA scales the two segments of x it reads to integers
+// X = x 2^(54 - e), 2^e above the segment's largest magnitude (per
+// right-hand side), so each product M X is exact in 128 bits and so is
+// every sum of them: a tile's row and column partials are rounded to
+// float64 once.  The integer pipe carries the multiply-adds (GB300's FP64
+// pipe runs at 1/64 of its FP32 rate).
+//
+// Columns are split into the fewest groups of at most 32 NCOL (NCOL = 16
+// for one right-hand side per pass, 8 for two); the warps of a group take
+// rows round-robin.
+// For a row, a lane loads its NCOL entries (the next row's loads issued
+// before the current row's arithmetic), adds their products with X_j into
+// the row's sum (reduced across the warp) and their products with
+// X_i[row] into per-column sums (the transposed product).  Group and warp
+// sums meet in shared memory through 64-bit atomic adds with the carry
+// passed on explicitly: exact integers, so the order does not matter and
+// the result is deterministic.  Absolute sums (first iteration only) add
+// M >> 42: they only scale the stopping tolerance.
+struct s128 {
+  uint64_t lo;
+  int64_t hi;   // value hi 2^64 + lo
+};
+
+__device__ __forceinline__ void mac128(s128& a, uint64_t m, int64_t x) {
+  const uint64_t plo = m * (uint64_t)x;
+  const int64_t phi = __mul64hi((long long)m, (long long)x);   // m < 2^62
+  const uint64_t lo = a.lo + plo;
+  a.hi += phi + (int64_t)(lo < plo);
+  a.lo = lo;
+}
+
+__device__ __forceinline__ s128 warp_sum128(s128 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t ol = __shfl_xor_sync(0xffffffffu, (unsigned long long)a.lo, o);
+    const int64_t oh = __shfl_xor_sync(0xffffffffu, (long long)a.hi, o);
+    const uint64_t lo = a.lo + ol;
+    a.hi += oh + (int64_t)(lo < ol);
+    a.lo = lo;
+  }
+  return a;
+}
+
+__device__ __forceinline__ void atomic_add128(unsigned long long* lo, unsigned long long* hi, s128 v) {
+  const unsigned long long old = atomicAdd(lo, (unsigned long long)v.lo);
+  atomicAdd(hi, (unsigned long long)v.hi + (unsigned long long)(old + v.lo < old));
+}
+
+__device__ __forceinline__ double s128_double(unsigned long long lo, unsigned long long hi) {
+  return fma((double)(long long)hi, 0x1p64, (double)lo);
+}
+
 template <int RC>
 __global__ void __launch_bounds__(256) k_residual_tile(Arena A, const ItemResTile* __restrict__ items,
                                                        int want_abs, const int* gate) {
   if (gated(gate)) return;
-  extern __shared__ double rsm[];
+  constexpr int NCOL = RC == 1 ? 16 : 8;
+  extern __shared__ unsigned long long rsm[];
+  __shared__ double s_mx[2 * RC][8];
+  __shared__ int s_e[2 * RC];
   const ItemResTile it = items[blockIdx.x];
   const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = b > 512 ? b / 512 : 1;              // column groups
-  const int W = 8 / G;                              // warps per group
+  // column groups: the fewest (1, 2 or 4) with at most 32 NCOL columns each
+  // (b a multiple of 128 up to 1024: b / G is a multiple of 32)
+  int G = 1;
+  while (b > G * 32 * NCOL) G <<= 1;
+  const int W = 8 / G;                                  // warps per group
   const int g = warp / W, wl = warp % W;
-  const int gw = b / G;                             // columns per group
-  const int ncol = gw / 32;                         // columns per lane (<= 16)
+  const int gw = b / G;                                 // columns per group
+  const int ncol = gw / 32;                             // columns per lane (<= NCOL)
   const int cbase = g * gw;
   const bool diag = it.ti == it.tj;
-  double* xj = rsm;                                 // [b][RC]
-  double* xi = xj + (size_t)b * RC;                 // [b][RC]
-  double* yrow = xi + (size_t)b * RC;               // [G][b][RC]
-  double* csum = yrow + (size_t)G * b * RC;         // [b][RC]
-  float* arow = reinterpret_cast<float*>(csum + (size_t)b * RC);   // [G][b]
-  float* acol = arow + (size_t)G * b;                               // [b]
-  const double* S = tile_ptr<double>(A, it.tile);
+  const int E = *it.sig_e;
+  long long* Xj = reinterpret_cast<long long*>(rsm);   // [b][RC]
+  long long* Xi = Xj + (size_t)b * RC;                  // [b][RC]
+  unsigned long long* yl = rsm + (size_t)2 * b * RC;    // row sums [b][RC], low / high words
+  unsigned long long* yh = yl + (size_t)b * RC;
+  unsigned long long* cl = yh + (size_t)b * RC;         // column sums [b][RC]
+  unsigned long long* ch = cl + (size_t)b * RC;
+  unsigned* arow = reinterpret_cast<unsigned*>(ch + (size_t)b * RC);   // [b]
+  unsigned* acol = arow + b;                                            // [b]
+  const uint64_t* S = tile_ptr<uint64_t>(A, it.tile);
   const double* xjg = it.x + (int64_t)it.tj * b;
   const double* xig = it.x + (int64_t)it.ti * b;
   for (int c0 = 0; c0 < it.nrhs; c0 += RC) {
     const int nc = min(RC, it.nrhs - c0);
     const bool abs_now = want_abs && c0 == 0;
     __syncthreads();
+    // the segments' largest magnitudes (a NaN or infinity makes the
+    // partials NaN, as float64 arithmetic would)
+    double mx[2 * RC];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 2 * RC; ++q) mx[q] = 0.0;
+    for (int t = tid; t < b; t += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < RC; ++c) {
+        if (c >= nc) break;
+        const double vj = xjg[(int64_t)(c0 + c) * it.ld + t], vi = xig[(int64_t)(c0 + c) * it.ld + t];
+        bad |= !isfinite(vj) || !isfinite(vi);
+        mx[c] = fmax(mx[c], fabs(vj));
+        mx[RC + c] = fmax(mx[RC + c], fabs(vi));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * RC; ++q) {
+      mx[q] = warp_max(mx[q]);
+      if (lane == 0) s_mx[q][warp] = mx[q];
+    }
+    bad = __syncthreads_or(bad);
+    if (tid < 2 * RC) {
+      double m = 0.0;
+      for (int w = 0; w < 8; ++w) m = fmax(m, s_mx[tid][w]);
+      s_e[tid] = m > 0.0 ? ilogb(m) + 1 : 0;   // |x| < 2^e on the segment
+    }
+    __syncthreads();
+    if (bad) {
+      double* pr = it.part + ((size_t)(it.ti * it.nt + it.tj) * it.nrhs) * b;
+      double* pc = it.part + ((size_t)(it.tj * it.nt + it.ti) * it.nrhs) * b;
+      for (int e = tid; e < b * nc; e += blockDim.x) {
+        pr[(size_t)c0 * b + e] = __longlong_as_double(0x7ff8000000000000ll);
+        if (!diag) pc[(size_t)c0 * b + e] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      continue;
+    }
     for (int e = tid; e < b * RC; e += blockDim.x) {
       const int t = e / RC, c = e % RC;
-      xj[e] = c < nc ? xjg[(int64_t)(c0 + c) * it.ld + t] : 0.0;
-      xi[e] = c < nc ? xig[(int64_t)(c0 + c) * it.ld + t] : 0.0;
-      csum[e] = 0.0;
+      Xj[e] = c < nc ? __double2ll_rn(ldexp(xjg[(int64_t)(c0 + c) * it.ld + t], 54 - s_e[c])) : 0;
+      Xi[e] = c < nc ? __double2ll_rn(ldexp(xig[(int64_t)(c0 + c) * it.ld + t], 54 - s_e[RC + c])) : 0;
+      yl[e] = yh[e] = cl[e] = ch[e] = 0ull;
     }
     if (abs_now)
-      for (int e = tid; e < b; e += blockDim.x) acol[e] = 0.f;
+      for (int e = tid; e < b; e += blockDim.x) arow[e] = acol[e] = 0u;
     __syncthreads();
-    double cacc[RES_NCOL][RC];
-    float cabs[RES_NCOL];
+    s128 cacc[NCOL][RC];
+    unsigned cabs[NCOL];
 #pragma unroll
-    for (int m = 0; m < RES_NCOL; ++m) {
-      cabs[m] = 0.f;
+    for (int m = 0; m < NCOL; ++m) {
+      cabs[m] = 0u;
 #pragma unroll
-      for (int c = 0; c < RC; ++c) cacc[m][c] = 0.0;
+      for (int c = 0; c < RC; ++c) cacc[m][c] = s128{0ull, 0ll};
     }
-    double cur[RES_NCOL], nxt[RES_NCOL];
+    uint64_t cur[NCOL], nxt[NCOL];
     int r = wl;
 #pragma unroll
-    for (int m = 0; m < RES_NCOL; ++m)
-      cur[m] = (m < ncol && r < b) ? S[(int64_t)r * b + cbase + lane + 32 * m] : 0.0;
+    for (int m = 0; m < NCOL; ++m)
+      cur[m] = (m < ncol && r < b) ? S[(int64_t)r * b + cbase + lane + 32 * m] : 0ull;
     for (; r < b; r += W) {
       const int rn = r + W;
 #pragma unroll
-      for (int m = 0; m < RES_NCOL; ++m)
-        nxt[m] = (m < ncol && rn < b) ? S[(int64_t)rn * b + cbase + lane + 32 * m] : 0.0;
+      for (int m = 0; m < NCOL; ++m)
+        nxt[m] = (m < ncol && rn < b) ? S[(int64_t)rn * b + cbase + lane + 32 * m] : 0ull;
       // a diagonal tile holds its lower half: row r uses columns <= r, and
       // the transposed product takes the columns < r
-      double dot[RC];
+      s128 dot[RC];
 #pragma unroll
-      for (int c = 0; c < RC; ++c) dot[c] = 0.0;
-      float ra = 0.f;
+      for (int c = 0; c < RC; ++c) dot[c] = s128{0ull, 0ll};
+      unsigned ra = 0u;
 #pragma unroll
-      for (int m = 0; m < RES_NCOL; ++m) {
+      for (int m = 0; m < NCOL; ++m) {
         const int col = cbase + lane + 32 * m;
-        const double sv = (m < ncol && (!diag || col <= r)) ? cur[m] : 0.0;
-        const double tv = (!diag || col < r) ? sv : 0.0;
+        const uint64_t sv = (m < ncol && (!diag || col <= r)) ? cur[m] : 0ull;
+        const uint64_t tv = (!diag || col < r) ? sv : 0ull;
 #pragma unroll
         for (int c = 0; c < RC; ++c) {
-          dot[c] += sv * xj[(m < ncol ? col : 0) * RC + c];
-          cacc[m][c] += tv * xi[r * RC + c];
+          mac128(dot[c], sv, Xj[(m < ncol ? col : 0) * RC + c]);
+          mac128(cacc[m][c], tv, Xi[r * RC + c]);
         }
         if (abs_now) {
-          ra += fabsf((float)sv);
-          cabs[m] += fabsf((float)tv);
+          ra += (unsigned)(sv >> 42);
+          cabs[m] += (unsigned)(tv >> 42);
         }
       }
 #pragma unroll
-      for (int c = 0; c < RC; ++c) dot[c] = warp_sum(dot[c]);
+      for (int c = 0; c < RC; ++c) dot[c] = warp_sum128(dot[c]);
       if (abs_now)
         for (int o = 16; o > 0; o >>= 1) ra += __shfl_xor_sync(0xffffffffu, ra, o);
       if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < RC; ++c) yrow[((size_t)g * b + r) * RC + c] = dot[c];
-        if (abs_now) arow[(size_t)g * b + r] = ra;
+        for (int c = 0; c < RC; ++c) atomic_add128(&yl[r * RC + c], &yh[r * RC + c], dot[c]);
+        if (abs_now) atomicAdd(&arow[r], ra);
       }
 #pragma unroll
-      for (int m = 0; m < RES_NCOL; ++m) cur[m] = nxt[m];
+      for (int m = 0; m < NCOL; ++m) cur[m] = nxt[m];
     }
-    // column sums: the warps of a group add in warp order
-    for (int w = 0; w < W; ++w) {
-      if (wl == w) {
 #pragma unroll
-        for (int m = 0; m < RES_NCOL; ++m) {
-          if (m >= ncol) break;
-          const int col = cbase + lane + 32 * m;
+    for (int m = 0; m < NCOL; ++m) {
+      if (m >= ncol) break;
+      const int col = cbase + lane + 32 * m;
 #pragma unroll
-          for (int c = 0; c < RC; ++c) csum[col * RC + c] += cacc[m][c];
-          if (abs_now) acol[col] += cabs[m];
-        }
-      }
-      __syncthreads();
+      for (int c = 0; c < RC; ++c) atomic_add128(&cl[col * RC + c], &ch[col * RC + c], cacc[m][c]);
+      if (abs_now) atomicAdd(&acol[col], cabs[m]);
     }
-    // write the partials
+    __syncthreads();
+    // the partials: float64, each rounded once from its exact sum
     double* pr = it.part + ((size_t)(it.ti * it.nt + it.tj) * it.nrhs) * b;
     double* pc = it.part + ((size_t)(it.tj * it.nt + it.ti) * it.nrhs) * b;
     for (int e = tid; e < b * nc; e += blockDim.x) {
-      const int c = e / b, t = e % b;
-      double v = 0.0;
-      for (int q = 0; q < G; ++q) v += yrow[((size_t)q * b + t) * RC + c];
-      if (diag) pr[(size_t)(c0 + c) * b + t] = v + csum[t * RC + c];
-      else {
-        pr[(size_t)(c0 + c) * b + t] = v;
-        pc[(size_t)(c0 + c) * b + t] = csum[t * RC + c];
+      const int c = e / b, t = e % b, k = t * RC + c;
+      if (diag) {   // x_i = x_j: one scale; the two sums added exactly first
+        const unsigned long long lo = yl[k] + cl[k];
+        const unsigned long long hi = yh[k] + ch[k] + (lo < yl[k]);
+        pr[(size_t)(c0 + c) * b + t] = ldexp(s128_double(lo, hi), E - 62 + s_e[c] - 54);
+      } else {
+        pr[(size_t)(c0 + c) * b + t] = ldexp(s128_double(yl[k], yh[k]), E - 62 + s_e[c] - 54);
+        pc[(size_t)(c0 + c) * b + t] = ldexp(s128_double(cl[k], ch[k]), E - 62 + s_e[RC + c] - 54);
       }
     }
     if (abs_now) {
       float* ar = it.pabs + (size_t)(it.ti * it.nt + it.tj) * b;
       float* ac = it.pabs + (size_t)(it.tj * it.nt + it.ti) * b;
       for (int t = tid; t < b; t += blockDim.x) {
-        float v = 0.f;
-        for (int q = 0; q < G; ++q) v += arow[(size_t)q * b + t];
-        if (diag) ar[t] = v + acol[t];
+        if (diag) ar[t] = ldexpf((float)(arow[t] + acol[t]), E - 62 + 42);
         else {
-          ar[t] = v;
-          ac[t] = acol[t];
+          ar[t] = ldexpf((float)arow[t], E - 62 + 42);
+          ac[t] = ldexpf((float)acol[t], E - 62 + 42);
         }
       }
     }
@@ -1072,17 +1156,18 @@ void launch_solve_dag(const Arena& A, const ItemSolveDag* items, const SolveTask
 void launch_residual(const Arena& A, const ItemResTile* tiles, int ntiles, const ItemResRow* rows,
                      int nrows, int nrhs, int want_rowabs, const int* gate, cudaStream_t s) {
   if (ntiles <= 0) return;
-  const int b = A.b, G = b > 512 ? b / 512 : 1;
-  const int rc = nrhs == 1 ? 1 : 4;
-  const size_t smem = sizeof(double) * (size_t)b * rc * (3 + G) + sizeof(float) * (size_t)b * (G + 1);
+  const int b = A.b;
+  const int rc = nrhs == 1 ? 1 : 2;
+  // X_j, X_i, row and column sums (two words each), absolute sums
+  const size_t smem = sizeof(unsigned long long) * (size_t)b * rc * 6 + sizeof(unsigned) * (size_t)b * 2;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_residual_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_residual_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_residual_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   if (rc == 1) k_residual_tile<1><<<ntiles, 256, smem, s>>>(A, tiles, want_rowabs, gate);
-  else k_residual_tile<4><<<ntiles, 256, smem, s>>>(A, tiles, want_rowabs, gate);
+  else k_residual_tile<2><<<ntiles, 256, smem, s>>>(A, tiles, want_rowabs, gate);
   k_residual_rows<<<dim3(nrows, (b + 255) / 256), 256, 0, s>>>(b, rows, want_rowabs, gate);
 }
 

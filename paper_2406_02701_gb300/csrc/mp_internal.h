@@ -175,12 +175,16 @@ struct ItemGen {
   const double* locs; // n x 2
   int64_t n;
   double sigma2, range, nu, nugget;
-  double* sigma64;    // optional float64 copy (b x b row-major) or null
+  // optional copy of Sigma for the refinement residual, b x b row-major, in
+  // fixed point: round(Sigma 2^(62 - sig_e)) (every entry below 2^sig_e);
+  // null: no copy.  The CTA of tile (0, 0) stores sig_e at *sig_e_out.
+  uint64_t* sigfix;
   // nu without a closed form: the Matérn table of matern_nu_table (device
   // copy) and its first octave; null for nu in {1/2, 3/2, 5/2}
   const double* ktab;
   int32_t ke0;
-  int32_t kpad_;
+  int32_t sig_e;
+  int32_t* sig_e_out;
 };
 
 // Solve items.  Diagonal: tile = L_ii^{-T} (FP64), xj = X-product of xi
@@ -223,13 +227,14 @@ typedef uint64_t SolveTask;
 // holds b x nrhs doubles at ((i nt + j) nrhs + c) b; pabs the same for the
 // absolute row sums (float, one column; NULL: not wanted).
 struct ItemResTile {
-  int32_t tile;       // Sigma tile (FP64)
+  int32_t tile;       // tile of the fixed-point copy of Sigma
   int32_t ti, tj, nt;
   const double* x;    // N x nrhs (column stride ld)
   double* part;
   float* pabs;
   int64_t ld;
   int32_t nrhs, pad_;
+  const int32_t* sig_e;   // the copy's exponent (written by the generation)
 };
 struct ItemResRow {
   int32_t ti, nt;

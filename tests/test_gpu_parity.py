@@ -478,6 +478,28 @@ def test_mixed_loglik_matches_oracle_b384(ctx, far, refine, ozaki):
         assert np.all(err_gpu < 1e-4)
 
 
+@pytest.mark.parametrize("b,nrhs", [(640, 1), (768, 3), (896, 2)])
+def test_refined_loglik_tile_sizes_beyond_512(ctx, b, nrhs):
+    """The refinement residual's column groups at tile sizes that are not a
+    power of two above 512 (one right-hand side per pass: two groups of
+    320 / 384 / 448 columns; two per pass: four groups; nrhs = 3 leaves a
+    last pass of one): the refined quadratic forms equal the oracle's
+    exact ones, and the iteration counts the oracle's tiled refinement."""
+    n = 2000
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.BF16, 1)
+    locs, _ = OM.morton_order(I.points(n, 41))
+    z = I.rhs(n, nrhs, 41)
+    S = OM.covariance(locs, 0.5, 0.03, 1.0, 1e-4)
+    ex = OC.exact_loglik(S, z)
+    tl = OC.tiled_loglik(S, z, b, pmap, refine_iters=10)
+    r = _run(ctx, n, b, pmap, locs, z, 0.5, 0.03, 1.0, 1e-4, refine=10, ozaki=True)
+    assert r["info"] == 0
+    assert np.all(tl["iters"] < 10)
+    assert np.all(np.abs(r["iters"] - tl["iters"]) <= 1)
+    assert np.allclose(r["quad"], ex["quad"], rtol=1e-10)
+
+
 def test_trsm_forward_backward(ctx):
     """mp_trsm against the oracle's tiled solves applied to the GPU's own
     factor (downloaded tile by tile), so only the solve is compared."""
