@@ -776,9 +776,9 @@ __global__ void __launch_bounds__(256, RCT == 1 ? 2 : 1)
 // float64 once.  The integer pipe carries the multiply-adds (GB300's FP64
 // pipe runs at 1/64 of its FP32 rate).
 //
-// Columns are split into the fewest groups of at most 32 NCOL (NCOL = 16
-// for one right-hand side per pass, 8 for two); the warps of a group take
-// rows round-robin.
+// Columns are split into the fewest groups of at most 32 NCOL (NCOL = 8 for
+// one right-hand side per pass, 4 for two: two CTAs fit an SM); the warps
+// of a group take rows round-robin.
 // For a row, a lane loads its NCOL entries (the next row's loads issued
 // before the current row's arithmetic), adds their products with X_j into
 // the row's sum (reduced across the warp) and their products with
@@ -792,12 +792,12 @@ struct s128 {
   int64_t hi;   // value hi 2^64 + lo
 };
 
+// a += m x (m < 2^62, read as signed): the low product with carry out,
+// the high product with carry in
 __device__ __forceinline__ void mac128(s128& a, uint64_t m, int64_t x) {
-  const uint64_t plo = m * (uint64_t)x;
-  const int64_t phi = __mul64hi((long long)m, (long long)x);   // m < 2^62
-  const uint64_t lo = a.lo + plo;
-  a.hi += phi + (int64_t)(lo < plo);
-  a.lo = lo;
+  asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.s64 %1, %2, %3, %1;"
+      : "+l"(a.lo), "+l"(a.hi)
+      : "l"(m), "l"(x));
 }
 
 __device__ __forceinline__ s128 warp_sum128(s128 a) {
@@ -822,25 +822,25 @@ __device__ __forceinline__ double s128_double(unsigned long long lo, unsigned lo
 }
 
 template <int RC>
-__global__ void __launch_bounds__(256) k_residual_tile(Arena A, const ItemResTile* __restrict__ items,
+__global__ void __launch_bounds__(256, 2) k_residual_tile(Arena A, const ItemResTile* __restrict__ items,
                                                        int want_abs, const int* gate) {
   if (gated(gate)) return;
-  constexpr int NCOL = RC == 1 ? 16 : 8;
+  constexpr int NCOL = RC == 1 ? 8 : 4;
   extern __shared__ unsigned long long rsm[];
   __shared__ double s_mx[2 * RC][8];
   __shared__ int s_e[2 * RC];
   const ItemResTile it = items[blockIdx.x];
   const int b = A.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // column groups: the fewest (1, 2 or 4) with at most 32 NCOL columns each
-  // (b a multiple of 128 up to 1024: b / G is a multiple of 32)
+  // column groups: the fewest (1, 2, 4 or 8) with at most 32 NCOL columns
+  // each; lane l holds the group's columns l + 32 m below gw
   int G = 1;
   while (b > G * 32 * NCOL) G <<= 1;
   const int W = 8 / G;                                  // warps per group
   const int g = warp / W, wl = warp % W;
   const int gw = b / G;                                 // columns per group
-  const int ncol = gw / 32;                             // columns per lane (<= NCOL)
   const int cbase = g * gw;
   const bool diag = it.ti == it.tj;
+  const bool full = !diag && gw == 32 * NCOL;
   const int E = *it.sig_e;
   long long* Xj = reinterpret_cast<long long*>(rsm);   // [b][RC]
   long long* Xi = Xj + (size_t)b * RC;                  // [b][RC]
@@ -915,31 +915,44 @@ __global__ void __launch_bounds__(256) k_residual_tile(Arena A, const ItemResTil
     int r = wl;
 #pragma unroll
     for (int m = 0; m < NCOL; ++m)
-      cur[m] = (m < ncol && r < b) ? S[(int64_t)r * b + cbase + lane + 32 * m] : 0ull;
+      cur[m] = (lane + 32 * m < gw && r < b) ? S[(int64_t)r * b + cbase + lane + 32 * m] : 0ull;
     for (; r < b; r += W) {
       const int rn = r + W;
 #pragma unroll
       for (int m = 0; m < NCOL; ++m)
-        nxt[m] = (m < ncol && rn < b) ? S[(int64_t)rn * b + cbase + lane + 32 * m] : 0ull;
+        nxt[m] = (lane + 32 * m < gw && rn < b) ? S[(int64_t)rn * b + cbase + lane + 32 * m] : 0ull;
       // a diagonal tile holds its lower half: row r uses columns <= r, and
       // the transposed product takes the columns < r
       s128 dot[RC];
 #pragma unroll
       for (int c = 0; c < RC; ++c) dot[c] = s128{0ull, 0ll};
       unsigned ra = 0u;
+      if (full && !abs_now) {   // an off-diagonal tile, every lane's NCOL columns in it
 #pragma unroll
-      for (int m = 0; m < NCOL; ++m) {
-        const int col = cbase + lane + 32 * m;
-        const uint64_t sv = (m < ncol && (!diag || col <= r)) ? cur[m] : 0ull;
-        const uint64_t tv = (!diag || col < r) ? sv : 0ull;
+        for (int m = 0; m < NCOL; ++m) {
+          const int col = cbase + lane + 32 * m;
 #pragma unroll
-        for (int c = 0; c < RC; ++c) {
-          mac128(dot[c], sv, Xj[(m < ncol ? col : 0) * RC + c]);
-          mac128(cacc[m][c], tv, Xi[r * RC + c]);
+          for (int c = 0; c < RC; ++c) {
+            mac128(dot[c], cur[m], Xj[col * RC + c]);
+            mac128(cacc[m][c], cur[m], Xi[r * RC + c]);
+          }
         }
-        if (abs_now) {
-          ra += (unsigned)(sv >> 42);
-          cabs[m] += (unsigned)(tv >> 42);
+      } else {
+#pragma unroll
+        for (int m = 0; m < NCOL; ++m) {
+          const int col = cbase + lane + 32 * m;
+          const bool in = lane + 32 * m < gw;
+          const uint64_t sv = (in && (!diag || col <= r)) ? cur[m] : 0ull;
+          const uint64_t tv = (!diag || col < r) ? sv : 0ull;
+#pragma unroll
+          for (int c = 0; c < RC; ++c) {
+            mac128(dot[c], sv, Xj[(in ? col : 0) * RC + c]);
+            mac128(cacc[m][c], tv, Xi[r * RC + c]);
+          }
+          if (abs_now) {
+            ra += (unsigned)(sv >> 42);
+            cabs[m] += (unsigned)(tv >> 42);
+          }
         }
       }
 #pragma unroll
@@ -956,7 +969,7 @@ __global__ void __launch_bounds__(256) k_residual_tile(Arena A, const ItemResTil
     }
 #pragma unroll
     for (int m = 0; m < NCOL; ++m) {
-      if (m >= ncol) break;
+      if (lane + 32 * m >= gw) break;
       const int col = cbase + lane + 32 * m;
 #pragma unroll
       for (int c = 0; c < RC; ++c) atomic_add128(&cl[col * RC + c], &ch[col * RC + c], cacc[m][c]);
