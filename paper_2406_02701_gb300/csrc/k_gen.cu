@@ -458,7 +458,7 @@ __device__ __forceinline__ ffl entry_ff(int kind, ffl inv_range, ffl s2, const f
 
 
 template <bool AMAX>
-__global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __restrict__ items) {
+__global__ void __launch_bounds__(256, 5) k_generate(Arena A, const ItemGen* __restrict__ items) {
   extern __shared__ double sloc[];           // b column points (x, y) + GEN_ROWS row points
   __shared__ double tab[GEN_TAB];
   __shared__ uint64_t t2[GEN_T2];
@@ -480,14 +480,21 @@ __global__ void __launch_bounds__(256) k_generate(Arena A, const ItemGen* __rest
     rx[2 * r] = g < it.n ? it.locs[2 * g] : 0.0;
     rx[2 * r + 1] = g < it.n ? it.locs[2 * g + 1] : 0.0;
   }
-  __syncthreads();
   const int dt = A.tiles[it.tile].dt;
+  // the item's constants, once per CTA (a division and a few float64
+  // operations per thread would add a third to the FP64 work of the entries)
+  __shared__ GenCtx s_g;
+  __shared__ double s_inv_s;
+  if (threadIdx.x == 0) {
+    s_g = gen_ctx(it, tab, t2);
+    s_inv_s = !AMAX && dt == E4M3 ? 1.0 / e4m3_scale(amax_value(&A.amax[it.tile])) : 1.0;
+  }
+  __syncthreads();
   char* dst = tile_bytes(A, it.tile);
-  const GenCtx g = gen_ctx(it, tab, t2);
+  const GenCtx& g = s_g;
   const double inv_range = g.inv_range;
   double mx = 0.0;
-  double inv_s = 1.0;
-  if (!AMAX && dt == E4M3) inv_s = 1.0 / e4m3_scale(amax_value(&A.amax[it.tile]));
+  const double inv_s = s_inv_s;
   // float-float evaluation: an off-diagonal tile stored in FP32 or a 16-bit
   // format, closed-form nu, no float64 copy of Sigma, locations within
   // [2^-60, 2^60] in magnitude (or zero); the CTA decides as a whole
@@ -581,8 +588,10 @@ __global__ void __launch_bounds__(256) k_tile_sumsq(int b, const ItemGen* __rest
     rx[2 * r] = g < it.n ? it.locs[2 * g] : 0.0;
     rx[2 * r + 1] = g < it.n ? it.locs[2 * g + 1] : 0.0;
   }
+  __shared__ GenCtx s_g;
+  if (threadIdx.x == 0) s_g = gen_ctx(it, tab, t2);
   __syncthreads();
-  const GenCtx g = gen_ctx(it, tab, t2);
+  const GenCtx& g = s_g;
   double ss = 0.0;
   for (int e = threadIdx.x; e < GEN_ROWS * b; e += blockDim.x) {
     int r = e / b, c = e - r * b;
