@@ -336,7 +336,7 @@ mp_status mp_chol2inv(mp_tmat* t, double* d_out, int64_t ldo);
  *   MP_TMAT_KEEP_SIGMA (MP_ERR_STATE without it, or when a tile was set by
  *   mp_tile_set after the last mp_generate_matern).  The copy holds each
  *   entry as a 62-bit integer below 2^E, 2^E the power of two above
- *   max(sigma^2 + nugget, 1) (within 2^(E-63) of the float64 entry); x is
+ *   sigma^2 + nugget (within 2^(E-63) of the float64 entry); x is
  *   scaled to 54-bit integers per b-long segment, so the products and each
  *   tile's sums are exact, rounded to float64 once per tile and summed in
  *   float64 over the tiles of a row; a column stops when

@@ -1257,9 +1257,9 @@ static mp_status build_gen_items(mp_tmat* t) {
   const MatDesc& M = P.mats[0];
   std::vector<ItemGen> amax, all;
   // the exponent of the fixed-point copy of Sigma: every entry (at most
-  // sigma^2 + nugget, and the identity padding) below 2^sig_e
+  // sigma^2 + nugget) below 2^sig_e
   int sig_e = 0;
-  std::frexp(std::max(t->cov.sigma2 + t->cov.nugget, 1.0), &sig_e);
+  std::frexp(t->cov.sigma2 + t->cov.nugget, &sig_e);
   for (int i = 0; i < M.nt; ++i)
     for (int j = 0; j <= i; ++j) {
       ItemGen g{};

@@ -318,21 +318,6 @@ __device__ __forceinline__ void store_fmt(char* base, int64_t i, double v, doubl
   }
 }
 
-// round(v 2^(62 - E)) for 0 <= v < 2^E: the refinement's fixed-point copy of
-// Sigma (entries far below 2^E keep their absolute accuracy, 2^(E - 63),
-// which is what a residual sum of them needs)
-__device__ __forceinline__ uint64_t sigma_fix(double v, int E) {
-  const uint64_t bv = mpx_bits(v);
-  const int be = (int)(bv >> 52);
-  if (be == 0) return 0ull;                      // zero or subnormal: below the resolution
-  const uint64_t mant = (bv & ((1ull << 52) - 1)) | (1ull << 52);
-  const int sh = be - 1075 + 62 - E;             // v = mant 2^(be - 1075)
-  if (sh >= 0) return mant << sh;                // sh <= 9
-  const int d = -sh;
-  if (d > 54) return 0ull;
-  return (mant + (1ull << (d - 1)) - 1 + ((mant >> d) & 1)) >> d;   // to nearest even
-}
-
 // GEN_ROWS rows of one tile: entries, their rounding into the tile's format
 // and the fixed-point copy of Sigma
 template <int DT>

@@ -206,4 +206,23 @@ MPX_FN fx fx_exp_neg(fx x, const uint64_t* t2) {
   return fx{E << z, -(int)(k >> 10) - z};
 }
 
+// The refinement's fixed-point copy of Sigma: round(v 2^(62 - E)) to
+// nearest even for 0 <= v < 2^E (exact for v >= 2^(E - 9); entries far
+// below 2^E keep their absolute accuracy, 2^(E - 63), which is what a
+// residual sum of them needs); values at or above 2^E (the identity
+// padding, when sigma^2 + nugget < 1) clamp to 2^62 - 1: the residual only
+// ever multiplies them by zero.
+MPX_FN uint64_t sigma_fix(double v, int E) {
+  const uint64_t bv = mpx_bits(v);
+  const int be = (int)(bv >> 52);
+  if (be == 0) return 0ull;                      // zero or subnormal: below 2^-1022
+  const uint64_t mant = (bv & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = be - 1075 + 62 - E;             // v = mant 2^(be - 1075)
+  if (sh >= 10) return (1ull << 62) - 1;         // v >= 2^E
+  if (sh >= 0) return mant << sh;
+  const int d = -sh;
+  if (d > 54) return 0ull;
+  return (mant + (1ull << (d - 1)) - 1 + ((mant >> d) & 1)) >> d;
+}
+
 }  // namespace mp

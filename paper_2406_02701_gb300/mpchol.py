@@ -241,8 +241,13 @@ class TiledMatrix:
         self.h = h
 
     def close(self):
+        # a handle outlives its context only at interpreter shutdown (objects
+        # held in reference cycles are finalised in any order): its memory
+        # went with the context's process state, and destroying it would
+        # reach through the freed context
         if getattr(self, "h", None):
-            self.lib.mp_tmat_destroy(self.h)
+            if getattr(getattr(self, "ctx", None), "h", None):
+                self.lib.mp_tmat_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -431,8 +436,13 @@ class Batch:
         return ll, status
 
     def close(self):
+        # a handle outlives its context only at interpreter shutdown (objects
+        # held in reference cycles are finalised in any order): its memory
+        # went with the context's process state, and destroying it would
+        # reach through the freed context
         if getattr(self, "h", None):
-            self.lib.mp_batch_destroy(self.h)
+            if getattr(getattr(self, "ctx", None), "h", None):
+                self.lib.mp_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -498,8 +508,13 @@ class Server:
         return dict(queued=q.value, running=r.value, kept=k.value, bytes=b.value)
 
     def close(self):
+        # a handle outlives its context only at interpreter shutdown (objects
+        # held in reference cycles are finalised in any order): its memory
+        # went with the context's process state, and destroying it would
+        # reach through the freed context
         if getattr(self, "h", None):
-            self.lib.mp_server_destroy(self.h)
+            if getattr(getattr(self, "ctx", None), "h", None):
+                self.lib.mp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

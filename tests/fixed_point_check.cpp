@@ -10,6 +10,9 @@
 //                less x/128 (x's own error, a few units of 2^-63 relative,
 //                is carried x-fold by e^{-x}); ranges 0.05 and 0.005 (x up
 //                to about 280 on the unit square)
+//   sigma_fix_bad  codes of the refinement's fixed-point copy that differ
+//                  from round-half-even of v 2^(62 - E) (0 for v in [0, 2^E),
+//                  2^62 - 1 at or above)
 // Usage: fixed_point_check <samples>
 #define MPX_FN static inline
 #include <cmath>
@@ -87,7 +90,21 @@ int main(int argc, char** argv) {
       ent = fmax(ent, (double)(fabsl(((long double)v - ref) / ldexpl(1.0L, e - 53)) - xl / 128));
     }
   }
-  printf("{\"sqrt_units\": %.4f, \"exp_units\": %.4f, \"exp700_units\": %.4f, \"entry_ulp\": %.4f}\n", sq, ex,
-         ex7, ent);
+  long bad = 0;
+  for (long t = 0; t < N; ++t) {
+    const int E = (int)(rng() % 2001) - 1000;
+    const int k = (int)(rng() % 80);             // v about 2^(E - k)
+    double v = ldexp(urand(), E - k);
+    if (t % 97 == 0) v = ldexp(1.0, E - 1 - (int)(rng() % 3));
+    if (t % 101 == 0) v = ldexp(1.0 + urand(), E + (int)(rng() % 3));   // at or above 2^E
+    if (t % 103 == 0) v = 0.0;
+    if (!(v < 0x1p1023) || (v != 0 && v < 0x1p-1022)) continue;   // normal doubles and zero
+    uint64_t want;
+    if (v >= ldexp(1.0, E)) want = (1ull << 62) - 1;
+    else want = (uint64_t)nearbyintl(ldexpl((long double)v, 62 - E));
+    if (mp::sigma_fix(v, E) != want) ++bad;
+  }
+  printf("{\"sqrt_units\": %.4f, \"exp_units\": %.4f, \"exp700_units\": %.4f, \"entry_ulp\": %.4f, "
+         "\"sigma_fix_bad\": %ld}\n", sq, ex, ex7, ent, bad);
   return 0;
 }

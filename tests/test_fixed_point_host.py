@@ -5,7 +5,9 @@ the ones the kernel's accuracy rests on: sqrt within a few units of 2^-63,
 e^{-x} within 2^-58 for x <= 100 and 2^-55 up to x = 700, and the whole
 entry sigma^2 P(x) e^{-x} within 0.55 + x/128 ulp of its exact value at the
 same float64 squared distance (one final rounding, a few units of 2^-63 from
-the products, and x's own error of at most 8 units of 2^-63 carried x-fold).
+the products, and x's own error of at most 8 units of 2^-63 carried x-fold);
+and the refinement's fixed-point copy of Sigma holds round-half-even of
+v 2^(62 - E) bit for bit.
 """
 import json
 import os
@@ -33,3 +35,4 @@ def test_fixed_point_entry_accuracy(tmp_path):
     assert out["exp_units"] <= 32, out
     assert out["exp700_units"] <= 256, out
     assert out["entry_ulp"] <= 0.55, out
+    assert out["sigma_fix_bad"] == 0, out

@@ -500,6 +500,28 @@ def test_refined_loglik_tile_sizes_beyond_512(ctx, b, nrhs):
     assert np.allclose(r["quad"], ex["quad"], rtol=1e-10)
 
 
+@pytest.mark.parametrize("c", [2.0 ** -40, 2.0 ** 30])
+def test_refinement_scale_equivariance(ctx, c):
+    """Sigma and c Sigma (sigma^2 and the nugget scaled by a power of two,
+    exact in every tile format) with right-hand sides z and sqrt(c) z: the
+    refined quadratic forms agree and take the same number of corrections,
+    the log-determinant moves by n log c.  The refinement's fixed-point copy of Sigma takes its exponent
+    from sigma^2 + nugget, so its codes -- and the residual's accuracy -- do
+    not depend on c."""
+    n, b, nrhs = 1500, 256, 2
+    nt = -(-n // b)
+    pmap = I.band_map(nt, I.F64, I.F32, I.F32, 1)
+    locs, _ = OM.morton_order(I.points(n, 43))
+    z = I.rhs(n, nrhs, 43)
+    r1 = _run(ctx, n, b, pmap, locs, z, 1.5, 0.05, 1.3, 1e-4, refine=10, ozaki=True)
+    r2 = _run(ctx, n, b, pmap, locs, z * math.sqrt(c), 1.5, 0.05, 1.3 * c, 1e-4 * c, refine=10, ozaki=True)
+    assert r1["info"] == 0 and r2["info"] == 0
+    assert np.all(r1["iters"] < 10)
+    assert np.array_equal(r1["iters"], r2["iters"])
+    assert np.allclose(r2["quad"], r1["quad"], rtol=1e-12)       # (sqrt(c) z)^T (c Sigma)^{-1} (sqrt(c) z)
+    assert math.isclose(r2["logdet"], r1["logdet"] + n * math.log(c), rel_tol=1e-12)
+
+
 def test_trsm_forward_backward(ctx):
     """mp_trsm against the oracle's tiled solves applied to the GPU's own
     factor (downloaded tile by tile), so only the solve is compared."""
