@@ -2119,7 +2119,7 @@ extern "C" mp_status mp_tile_norms(mp_ctx* ctx, int64_t n, int32_t b, const doub
       g.ktab = d_ktab; g.ke0 = ke0;
       items.push_back(g);
     }
-  const int parts = b / 16;
+  const int parts = tile_norm_parts(b);
   ItemGen* d_items = nullptr;
   double* partial = nullptr;
   cudaError_t e = cudaMalloc(&d_items, sizeof(ItemGen) * items.size());

@@ -739,6 +739,8 @@ int init_gen_tables() {
   return cudaMemcpyToSymbol(c_gen_tab, h, sizeof(h)) == cudaSuccess ? 0 : 1;
 }
 
+int tile_norm_parts(int b) { return b / GEN_ROWS; }
+
 void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,
                        double* norms, cudaStream_t s) {
   if (count <= 0) return;

@@ -275,6 +275,9 @@ int matern_nu_table(double nu, std::vector<double>& coef, int* e0);
 double matern_nu_host(const double* coef, int e0, double x);
 // Frobenius norm of every generated lower tile into norms[ti * nt + tj]
 // (partial: count * b/16 doubles of scratch).
+// partial sums per tile that launch_tile_norms writes (its `partial` holds
+// count times this many doubles)
+int tile_norm_parts(int b);
 void launch_tile_norms(int b, const ItemGen* items, int count, int nt, double* partial,
                        double* norms, cudaStream_t s);
 
