@@ -1134,7 +1134,7 @@ def profile_case(name):
         for _ in range(2):
             ctx.gemm(dt, "T", "N", n, n, n, 1.0, X, n, X, n, 0.0, Cm, n)
     elif kind.startswith("gen_nu") or kind.startswith("gen64_nu"):
-        # gen64: with the float64 copy of Sigma the log-likelihood refines
+        # gen64: with the copy of Sigma the log-likelihood refines
         # against, as in the bench's step (every entry float64-accurate)
         nu = float(kind[kind.index("nu") + 2:])
         ds, _ = ctx.morton_order(torch.from_numpy(I.points(n, 11)).to(dev))
