@@ -231,6 +231,57 @@ def test_float64_entries_within_0p6_ulp(ctx, nu, a):
     assert worst <= 0.55, worst
 
 
+@pytest.mark.parametrize("nu,a,keep", [(0.5, 1e-3, True)])
+def test_generation_far_tail_every_format(ctx, nu, a, keep):
+    """A range so short that x = r / a runs to about 1400 on the unit square:
+    entries leave the fixed-point path for float64 (x > 700, or a result
+    below the normal range), FP32 / BF16 / FP16 values fall below their
+    normal range into subnormals and zeros, E4M3 tiles take their scale from
+    amaxes down to zero -- every format against the oracle's rounding."""
+    n, b = 700, 128
+    nt = -(-n // b)
+    pmap = _mixed_map(nt)
+    locs = I.points(n, 15)
+    T = _mk(ctx, n, b, pmap, keep_sigma=keep)
+    T.generate(torch.from_numpy(locs).to(DEV), 1.3, a, nu, 1e-4)
+    torch.cuda.synchronize()
+    ref = OC.tiled_from_dense(OM.covariance(locs, nu, a, 1.3, 1e-4), b, pmap)
+    for i in range(nt):
+        for j in range(i + 1):
+            got, codes, s = T.get_tile(i, j)
+            rt = ref.tiles[(i, j)]
+            fmt = int(pmap[i, j])
+            want = rt.values()
+            if i == j:
+                got, want = np.tril(got), np.tril(want)
+            if fmt == I.E4M3:
+                assert s == rt.scale, (i, j, s, rt.scale)
+                assert_close_fmt(codes, rt.codes, fmt, frac=1e-3, what=f"tile {i},{j}")
+            elif fmt == I.F64:
+                ri = np.arange(i * b, min((i + 1) * b, n))
+                rj = np.arange(j * b, min((j + 1) * b, n))
+                d = np.hypot(locs[ri, 0][:, None] - locs[rj, 0][None, :],
+                             locs[ri, 1][:, None] - locs[rj, 1][None, :])
+                x = np.zeros((b, b))
+                x[:len(ri), :len(rj)] = d / a
+                # relative (4 + 4x) ulps as in the moderate-range test; beyond
+                # x = 708 e^{-x} is subnormal before it is multiplied by
+                # sigma^2 P(x) (in the oracle, and in the kernel's float64
+                # evaluation past x = 700), so each carries up to
+                # sigma^2 P(x) 2^-1074 of absolute error
+                poly = {0.5: 1.0 + 0 * x, 1.5: 1.0 + x, 2.5: 1.0 + x + x * x / 3.0}[nu]
+                tol = (4 + 4 * x) * 2.0 ** -52 * np.abs(want) + 2.0 ** -1070 + 4 * 1.3 * poly * 2.0 ** -1074
+                if i == j:
+                    tol = np.tril(tol)
+                assert np.all(np.abs(got - want) <= tol), (i, j, np.max(np.abs(got - want) - tol))
+            else:
+                assert_close_fmt(got, want, fmt, frac=1e-3, what=f"tile {i},{j}")
+    # the range is short enough that tiles hold values beyond the fixed-point
+    # path and below FP32's normal range
+    dmax = np.max(OM.distances(locs, locs))
+    assert dmax / a > 700
+
+
 @pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
 @pytest.mark.parametrize("a", [0.013, 0.05, 0.3])
 def test_float_float_generation(ctx, nu, a):
