@@ -42,3 +42,34 @@ def test_context_without_device_is_an_error_not_a_crash():
     h = ctypes.c_void_p()
     st = lib.mp_ctx_create(0, ctypes.byref(h))
     assert st == mpchol.MP_ERR_ARG
+
+
+def test_handles_skip_destroy_once_their_context_is_closed():
+    """A matrix, batch or server handle whose context is already closed (at
+    interpreter shutdown, objects in reference cycles are finalised in any
+    order) is dropped without calling its destroy function, which would
+    reach through the freed context; with the context open it is destroyed
+    once."""
+    from paper_2406_02701_gb300 import mpchol
+
+    class Lib:
+        def __init__(self):
+            self.calls = []
+
+        def __getattr__(self, name):
+            return lambda *a: self.calls.append(name)
+
+    class Ctx:
+        h = object()
+
+    for cls, fn in ((mpchol.TiledMatrix, "mp_tmat_destroy"), (mpchol.Batch, "mp_batch_destroy"),
+                    (mpchol.Server, "mp_server_destroy")):
+        for open_ctx in (True, False):
+            obj = cls.__new__(cls)
+            obj.lib, obj.ctx, obj.h = Lib(), Ctx(), object()
+            if not open_ctx:
+                obj.ctx.h = None
+            obj.close()
+            obj.close()
+            assert obj.h is None
+            assert obj.lib.calls == ([fn] if open_ctx else []), (cls.__name__, open_ctx)
